@@ -1,0 +1,453 @@
+"""CPU FP64 oracle for the coupled head / heat finite element step.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and
+its Python binding) may import or call this module; only ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg of
+``bench.py`` use it.  It shares no code with the CUDA path: it consumes the
+same seeded inputs (``scenarios``) and nothing else.
+
+What it computes, written out the plain way (global sparse matrices assembled
+cell by cell from shape functions evaluated directly at every Gauss point, no
+sum factorisation, no blocking, then a sparse direct solve):
+
+* Head (Eq. 1 in hydraulic-head form, discretised as in Eq. 3 with backward
+  Euler): (S_s M + dt K_K) h^{n+1} = S_s M h^n + dt F_h, where
+  M_ij = int N_i N_j and K_K,ij = sum_c K_c int_c grad N_i . grad N_j.
+  With p = rho_w g (h - z) the gravity term of Eq. 1 / Eq. 3 vanishes.
+* Heat (Eq. 2 in energy form, discretised as in Eq. 4):
+  (M_cT + dt L_lambda + dt C(q) + dt D_w) T^{n+1} = M_cT T^n + dt F_T, with
+  C_ij = sum_qp w c_w N_i (q . grad N_j) and q = -K_c grad h^{n+1} evaluated at
+  the same Gauss points (Darcy's law, Section 2, q = -k (grad p + rho_w g)).
+  D_w is the lumped line term of an injection well, c_w (Q/L) int N_i dz.
+* Quadrature: (p+1)-point Gauss-Legendre per direction for order p.
+* Dirichlet nodes: rows replaced by the identity and the prescribed values
+  moved to the right-hand side (columns eliminated, so the head operator stays
+  symmetric).  Free rows see no Dirichlet columns.
+
+Parity pins (tests/test_oracle_pins.py) tie this code to closed forms: the 1D
+Q1/Q2 mass and stiffness matrices, exact symbolic integrals on one cell,
+discrete eigenmode decay, exactness for linear heads, energy balance, the
+erfc and Ogata-Banks 1D solutions and manufactured-solution convergence
+orders.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+HEAD, TEMP = 0, 1
+NONE, DIRICHLET, FLUX = 0, 1, 2
+
+
+# ---------------------------------------------------------------------------
+# 1D ingredients
+# ---------------------------------------------------------------------------
+def gauss01(n: int):
+    """n-point Gauss-Legendre rule mapped to [0, 1]."""
+    xi, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (xi + 1.0), 0.5 * w
+
+
+def lagrange_nodes(p: int) -> np.ndarray:
+    return np.linspace(0.0, 1.0, p + 1)
+
+
+def lagrange_value(p: int, a: int, xi: float) -> float:
+    """phi_a(xi) for equispaced Lagrange nodes on [0, 1], product formula."""
+    nodes = lagrange_nodes(p)
+    v = 1.0
+    for m in range(p + 1):
+        if m != a:
+            v *= (xi - nodes[m]) / (nodes[a] - nodes[m])
+    return v
+
+
+def lagrange_deriv(p: int, a: int, xi: float) -> float:
+    """phi_a'(xi) by differentiating the product formula term by term."""
+    nodes = lagrange_nodes(p)
+    s = 0.0
+    for m in range(p + 1):
+        if m == a:
+            continue
+        term = 1.0 / (nodes[a] - nodes[m])
+        for k in range(p + 1):
+            if k != a and k != m:
+                term *= (xi - nodes[k]) / (nodes[a] - nodes[k])
+        s += term
+    return s
+
+
+# ---------------------------------------------------------------------------
+# Mesh
+# ---------------------------------------------------------------------------
+class Mesh:
+    """Structured box of nx*ny*nz Lagrange hexahedra of order p."""
+
+    def __init__(self, nx, ny, nz, p, origin, extent):
+        self.nx, self.ny, self.nz, self.p = nx, ny, nz, p
+        self.origin = tuple(float(v) for v in origin)
+        self.extent = tuple(float(v) for v in extent)
+        self.H = (self.extent[0] / nx, self.extent[1] / ny, self.extent[2] / nz)
+        self.N = (p * nx + 1, p * ny + 1, p * nz + 1)
+        self.n_nodes = self.N[0] * self.N[1] * self.N[2]
+        self.n_cells = nx * ny * nz
+        n1 = p + 1
+        self.nl = n1 ** 3
+        cz, cy, cx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        cx, cy, cz = cx.reshape(-1), cy.reshape(-1), cz.reshape(-1)
+        conn = np.empty((self.n_cells, self.nl), dtype=np.int64)
+        for c in range(n1):
+            for b in range(n1):
+                for a in range(n1):
+                    l = a + n1 * (b + n1 * c)
+                    conn[:, l] = self.node_index(p * cx + a, p * cy + b, p * cz + c)
+        self.conn = conn
+
+    def node_index(self, i, j, k):
+        return i + self.N[0] * (j + self.N[1] * k)
+
+    def node_ijk(self):
+        idx = np.arange(self.n_nodes)
+        i = idx % self.N[0]
+        j = (idx // self.N[0]) % self.N[1]
+        k = idx // (self.N[0] * self.N[1])
+        return i, j, k
+
+    def node_xyz(self):
+        i, j, k = self.node_ijk()
+        hx, hy, hz = (self.H[d] / self.p for d in range(3))
+        return (self.origin[0] + i * hx, self.origin[1] + j * hy, self.origin[2] + k * hz)
+
+    def face_nodes(self, face: int) -> np.ndarray:
+        i, j, k = self.node_ijk()
+        axis, side = face // 2, face % 2
+        coord = (i, j, k)[axis]
+        last = self.N[axis] - 1
+        return np.nonzero(coord == (last if side else 0))[0]
+
+
+# ---------------------------------------------------------------------------
+# Reference element, evaluated directly at the Gauss points
+# ---------------------------------------------------------------------------
+def reference_element(p: int, H, nq: Optional[int] = None):
+    """Shape values N[q, l], physical gradients G[q, l, d] and weights W[q]
+    (including the cell volume) at the nq^3 tensor Gauss points of a cell of
+    size H = (Hx, Hy, Hz).  Local node l = a + n*(b + n*c)."""
+    n = p + 1
+    nq = n if nq is None else nq
+    xi, w = gauss01(nq)
+    nl = n ** 3
+    N = np.zeros((nq ** 3, nl))
+    G = np.zeros((nq ** 3, nl, 3))
+    W = np.zeros(nq ** 3)
+    vol = H[0] * H[1] * H[2]
+    for qz in range(nq):
+        for qy in range(nq):
+            for qx in range(nq):
+                q = qx + nq * (qy + nq * qz)
+                W[q] = w[qx] * w[qy] * w[qz] * vol
+                for c in range(n):
+                    for b in range(n):
+                        for a in range(n):
+                            l = a + n * (b + n * c)
+                            vx, vy, vz = (lagrange_value(p, a, xi[qx]), lagrange_value(p, b, xi[qy]),
+                                          lagrange_value(p, c, xi[qz]))
+                            dx, dy, dz = (lagrange_deriv(p, a, xi[qx]), lagrange_deriv(p, b, xi[qy]),
+                                          lagrange_deriv(p, c, xi[qz]))
+                            N[q, l] = vx * vy * vz
+                            G[q, l, 0] = dx * vy * vz / H[0]
+                            G[q, l, 1] = vx * dy * vz / H[1]
+                            G[q, l, 2] = vx * vy * dz / H[2]
+    return N, G, W
+
+
+def element_mass(N, W):
+    return np.einsum("q,ql,qm->lm", W, N, N)
+
+
+def element_stiffness(G, W):
+    return np.einsum("q,qld,qmd->lm", W, G, G)
+
+
+def assemble(mesh: Mesh, coef: np.ndarray, Ke: np.ndarray) -> sp.csr_matrix:
+    """Global matrix sum_c coef[c] * Ke (Ke either [nl, nl] or [cells, nl, nl])."""
+    nl = mesh.nl
+    rows = np.repeat(mesh.conn[:, :, None], nl, axis=2)
+    cols = np.repeat(mesh.conn[:, None, :], nl, axis=1)
+    if Ke.ndim == 2:
+        data = coef[:, None, None] * Ke[None, :, :]
+    else:
+        data = coef[:, None, None] * Ke
+    A = sp.coo_matrix((data.reshape(-1), (rows.reshape(-1), cols.reshape(-1))),
+                      shape=(mesh.n_nodes, mesh.n_nodes))
+    return A.tocsr()
+
+
+def darcy_at_qp(mesh: Mesh, K: np.ndarray, G: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """q = -K_c grad h at every Gauss point of every cell: [cells, q, 3]."""
+    he = h[mesh.conn]                                   # [c, l]
+    gh = np.einsum("cl,qld->cqd", he, G)
+    return -K[:, None, None] * gh
+
+
+def advection_elements(N, G, W, qf: np.ndarray, cw: float) -> np.ndarray:
+    """C_e[c, l, m] = sum_q W_q c_w N_l(q) (q_c(q) . grad N_m(q))."""
+    qg = np.einsum("cqd,qmd->cqm", qf, G)               # q . grad N_m
+    return cw * np.einsum("q,ql,cqm->clm", W, N, qg)
+
+
+# ---------------------------------------------------------------------------
+# Loads
+# ---------------------------------------------------------------------------
+def _column_weights(mesh: Mesh, x: float, y: float):
+    """Cell column containing (x, y) and the x / y shape factors there."""
+    p = mesh.p
+    out = []
+    for d, v in ((0, x), (1, y)):
+        s = (v - mesh.origin[d]) / mesh.H[d]
+        n = (mesh.nx, mesh.ny)[d]
+        c = int(min(max(math.floor(s), 0), n - 1))
+        xi = s - c
+        out.append((c, [lagrange_value(p, a, xi) for a in range(p + 1)]))
+    return out
+
+
+def line_weights(mesh: Mesh, x: float, y: float, z_top: float, z_bot: float) -> Dict[int, float]:
+    """w_i = int_{z_bot}^{z_top} N_i(x, y, z) dz for a vertical segment."""
+    p = mesh.p
+    (cx, fx), (cy, fy) = _column_weights(mesh, x, y)
+    z0, Hz = mesh.origin[2], mesh.H[2]
+    lo, hi = max(min(z_bot, z_top), z0), min(max(z_bot, z_top), z0 + mesh.extent[2])
+    w: Dict[int, float] = {}
+    if hi <= lo:
+        return w
+    xg, wg = gauss01(3)
+    for cz in range(mesh.nz):
+        a0, a1 = z0 + cz * Hz, z0 + (cz + 1) * Hz
+        s0, s1 = max(a0, lo), min(a1, hi)
+        if s1 <= s0:
+            continue
+        # exact integral of phi_c over [s0, s1] in cell-local coordinates
+        for c in range(p + 1):
+            Iz = 0.0
+            for g in range(3):
+                zz = s0 + (s1 - s0) * xg[g]
+                Iz += wg[g] * (s1 - s0) * lagrange_value(p, c, (zz - a0) / Hz)
+            for b in range(p + 1):
+                for a in range(p + 1):
+                    node = mesh.node_index(p * cx + a, p * cy + b, p * cz + c)
+                    w[node] = w.get(node, 0.0) + fx[a] * fy[b] * Iz
+    return w
+
+
+def face_load(mesh: Mesh, face: int, value: float) -> np.ndarray:
+    """F_i = value * int_face N_i dS for a uniform normal flux into the domain."""
+    p = mesh.p
+    F = np.zeros(mesh.n_nodes)
+    axis = face // 2
+    t1, t2 = [d for d in range(3) if d != axis]
+    xg, wg = gauss01(p + 1)
+    i1 = [sum(wg[g] * lagrange_value(p, a, xg[g]) for g in range(p + 1)) for a in range(p + 1)]
+    n1, n2 = (mesh.nx, mesh.ny, mesh.nz)[t1], (mesh.nx, mesh.ny, mesh.nz)[t2]
+    fixed = 0 if face % 2 == 0 else mesh.N[axis] - 1
+    for c2 in range(n2):
+        for c1 in range(n1):
+            for b in range(p + 1):
+                for a in range(p + 1):
+                    ijk = [0, 0, 0]
+                    ijk[axis] = fixed
+                    ijk[t1] = p * c1 + a
+                    ijk[t2] = p * c2 + b
+                    F[mesh.node_index(*ijk)] += value * i1[a] * mesh.H[t1] * i1[b] * mesh.H[t2]
+    return F
+
+
+def pile_amplitude(pile, t: float) -> float:
+    """q_l(t) = mean + amp sin(2 pi t / period + phase), W/m."""
+    return pile[4] + pile[5] * math.sin(2.0 * math.pi * t / pile[6] + pile[7])
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet handling and solves
+# ---------------------------------------------------------------------------
+def dirichlet_data(mesh: Mesh, bc: Dict[int, Tuple[int, float]]):
+    """Mask and values of Dirichlet nodes; later faces override earlier ones
+    on shared edges."""
+    mask = np.zeros(mesh.n_nodes, dtype=bool)
+    g = np.zeros(mesh.n_nodes)
+    for face in range(6):
+        if face in bc and bc[face][0] == DIRICHLET:
+            nodes = mesh.face_nodes(face)
+            mask[nodes] = True
+            g[nodes] = bc[face][1]
+    return mask, g
+
+
+def constrain(A: sp.csr_matrix, mask: np.ndarray) -> sp.csr_matrix:
+    """A0 = P A P + (I - P), P = projector on free nodes."""
+    free = (~mask).astype(np.float64)
+    P = sp.diags(free)
+    return (P @ A @ P + sp.diags(mask.astype(np.float64))).tocsr()
+
+
+def lifted_rhs(A: sp.csr_matrix, rhs: np.ndarray, mask: np.ndarray, g: np.ndarray) -> np.ndarray:
+    gD = np.where(mask, g, 0.0)
+    b = rhs - A @ gD
+    return np.where(mask, g, b)
+
+
+def solve(A0: sp.csr_matrix, b: np.ndarray, method: str = "direct", tol: float = 1e-14,
+          x0: Optional[np.ndarray] = None, maxiter: int = 100000):
+    if not np.any(b):
+        return np.zeros_like(b)
+    if method == "direct":
+        return spla.spsolve(A0.tocsc(), b)
+    M = sp.diags(1.0 / A0.diagonal())
+    if method == "cg":
+        x, info = spla.cg(A0, b, x0=x0, rtol=tol, atol=0.0, M=M, maxiter=maxiter)
+    else:
+        x, info = spla.bicgstab(A0, b, x0=x0, rtol=tol, atol=0.0, M=M, maxiter=maxiter)
+    if info != 0:
+        raise RuntimeError(f"oracle iterative solve did not converge (info={info})")
+    return x
+
+
+# ---------------------------------------------------------------------------
+# The simulator
+# ---------------------------------------------------------------------------
+class OracleSim:
+    """Plain FP64 reference of one coupled step (head, then heat)."""
+
+    def __init__(self, sc, solver: str = "direct", tol: float = 1e-14):
+        self.sc = sc
+        self.mesh = Mesh(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent)
+        m = self.mesh
+        self.N, self.G, self.W = reference_element(sc.order, m.H)
+        self.Me = element_mass(self.N, self.W)
+        self.Ke = element_stiffness(self.G, self.W)
+        nc = m.n_cells
+        self.K = np.asarray(sc.K, dtype=np.float64)
+        self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, sc.lam))
+        self.cT_c = np.asarray(sc.cT_cells if sc.cT_cells is not None else np.full(nc, sc.cT))
+        self.cw, self.Ss = sc.cw, sc.Ss
+        self.M = assemble(m, np.ones(nc), self.Me)
+        self.KK = assemble(m, self.K, self.Ke)
+        self.McT = assemble(m, self.cT_c, self.Me)
+        self.Llam = assemble(m, self.lam_c, self.Ke)
+        self.dmask = {}
+        self.gval = {}
+        for f in (HEAD, TEMP):
+            self.dmask[f], self.gval[f] = dirichlet_data(m, sc.bc.get(f, {}))
+        # static loads: Neumann faces
+        self.F_static = {HEAD: np.zeros(m.n_nodes), TEMP: np.zeros(m.n_nodes)}
+        for f in (HEAD, TEMP):
+            for face, (typ, val) in sc.bc.get(f, {}).items():
+                if typ == FLUX:
+                    self.F_static[f] += face_load(m, face, val)
+        # wells: head source and lumped heat injection term
+        self.d_well = np.zeros(m.n_nodes)
+        self.Tin_well = np.zeros(m.n_nodes)       # sum d*T_in
+        for wl in np.asarray(sc.wells).reshape(-1, 6):
+            L = abs(wl[2] - wl[3])
+            if L <= 0:
+                continue
+            wts = line_weights(m, wl[0], wl[1], wl[2], wl[3])
+            for node, wv in wts.items():
+                self.F_static[HEAD][node] += wl[4] / L * wv
+                if wl[4] > 0:
+                    self.d_well[node] += self.cw * wl[4] / L * wv
+                    self.Tin_well[node] += self.cw * wl[4] / L * wv * wl[5]
+        self.pile_w = [line_weights(m, pl[0], pl[1], pl[2], pl[3])
+                       for pl in np.asarray(sc.piles).reshape(-1, 8)]
+        self.extra = {HEAD: np.zeros(m.n_nodes), TEMP: np.zeros(m.n_nodes)}
+        self.h = np.array(sc.h0, dtype=np.float64)
+        self.T = np.array(sc.T0, dtype=np.float64)
+        self.t = 0.0
+        self.solver = solver
+        self.tol = tol
+
+    # -- operators (constrained, as the solver sees them) -------------------
+    def head_matrix(self, dt):
+        return self.Ss * self.M + dt * self.KK
+
+    def heat_matrix(self, dt, h):
+        qf = darcy_at_qp(self.mesh, self.K, self.G, h)
+        Ce = advection_elements(self.N, self.G, self.W, qf, self.cw)
+        C = assemble(self.mesh, np.ones(self.mesh.n_cells), Ce)
+        return self.McT + dt * self.Llam + dt * C + dt * sp.diags(self.d_well)
+
+    def apply_head(self, x, dt):
+        return constrain(self.head_matrix(dt), self.dmask[HEAD]) @ x
+
+    def apply_heat(self, x, h, dt):
+        return constrain(self.heat_matrix(dt, h), self.dmask[TEMP]) @ x
+
+    def diag_head(self, dt):
+        return constrain(self.head_matrix(dt), self.dmask[HEAD]).diagonal()
+
+    def diag_heat(self, h, dt):
+        return constrain(self.heat_matrix(dt, h), self.dmask[TEMP]).diagonal()
+
+    # -- loads ----------------------------------------------------------------
+    def head_load(self, t):
+        return self.F_static[HEAD] + self.extra[HEAD]
+
+    def heat_load(self, t):
+        F = self.F_static[TEMP] + self.extra[TEMP] + self.Tin_well
+        for pl, wts in zip(np.asarray(self.sc.piles).reshape(-1, 8), self.pile_w):
+            a = pile_amplitude(pl, t)
+            for node, wv in wts.items():
+                F[node] += a * wv
+        return F
+
+    def head_rhs(self, dt, t1):
+        A = self.head_matrix(dt)
+        rhs = self.Ss * (self.M @ self.h) + dt * self.head_load(t1)
+        return lifted_rhs(A, rhs, self.dmask[HEAD], self.gval[HEAD])
+
+    def heat_rhs(self, dt, t1, h1):
+        A = self.heat_matrix(dt, h1)
+        rhs = self.McT @ self.T + dt * self.heat_load(t1)
+        return lifted_rhs(A, rhs, self.dmask[TEMP], self.gval[TEMP])
+
+    # -- one backward Euler step: head first, then heat with q(h^{n+1}) -------
+    def step(self, dt):
+        t1 = self.t + dt
+        Ah = self.head_matrix(dt)
+        bh = lifted_rhs(Ah, self.Ss * (self.M @ self.h) + dt * self.head_load(t1),
+                        self.dmask[HEAD], self.gval[HEAD])
+        h1 = solve(constrain(Ah, self.dmask[HEAD]), bh, self.solver if self.solver == "direct" else "cg",
+                   self.tol, x0=self.h)
+        AT = self.heat_matrix(dt, h1)
+        bT = lifted_rhs(AT, self.McT @ self.T + dt * self.heat_load(t1),
+                        self.dmask[TEMP], self.gval[TEMP])
+        T1 = solve(constrain(AT, self.dmask[TEMP]), bT,
+                   self.solver if self.solver == "direct" else "bicgstab", self.tol, x0=self.T)
+        self.h, self.T, self.t = h1, T1, t1
+        return h1, T1
+
+    # -- outputs ----------------------------------------------------------------
+    def cell_flux(self, h=None):
+        """Darcy flux q = -K_c grad h at each cell centre: [3, cells]."""
+        h = self.h if h is None else h
+        m = self.mesh
+        p = m.p
+        n = p + 1
+        he = h[m.conn]
+        g = np.zeros((m.n_cells, 3))
+        for c in range(n):
+            for b in range(n):
+                for a in range(n):
+                    l = a + n * (b + n * c)
+                    vx, vy, vz = (lagrange_value(p, a, 0.5), lagrange_value(p, b, 0.5),
+                                  lagrange_value(p, c, 0.5))
+                    dx, dy, dz = (lagrange_deriv(p, a, 0.5), lagrange_deriv(p, b, 0.5),
+                                  lagrange_deriv(p, c, 0.5))
+                    g[:, 0] += he[:, l] * dx * vy * vz / m.H[0]
+                    g[:, 1] += he[:, l] * vx * dy * vz / m.H[1]
+                    g[:, 2] += he[:, l] * vx * vy * dz / m.H[2]
+        return (-self.K[:, None] * g).T.copy()

@@ -1,0 +1,286 @@
+"""Seeded synthetic input generators for the hydrothermal solver.
+
+This module only *draws inputs*: mesh sizes, per-cell hydraulic conductivity
+fields, material constants, boundary-condition choices, pile / well tables and
+initial fields.  It holds none of the finite element arithmetic (no shape
+functions, no quadrature, no operators, no loads), so both the CUDA path and
+the CPU oracle can consume the same inputs without sharing any method code.
+
+Physical parameters follow the paper: the mixture rules of Section 2 (below
+Eq. 2) give the bulk thermal conductivity and heat capacity, the specific
+storage S_s = rho_w g / B_poro follows from Eq. 1 rewritten for hydraulic head,
+and Table 1 / Table 3 supply the material values.  The synthetic workloads
+(sizes, layering, random fields, pile and well layouts) stand in for the
+paper's ATES benchmark (Section 2) and Treasure Island energy-pile case
+(Section 3), whose site data exist only in figures.
+
+Conventions
+-----------
+* Structured box [x0, x0+Lx] x [y0, y0+Ly] x [z0, z0+Lz], z up, nx*ny*nz
+  hexahedral cells of order p (1 = trilinear Q1, 2 = triquadratic Q2).
+* Cell index  c = cx + nx*(cy + ny*cz); node index n = i + Nx*(j + Ny*k),
+  Nx = p*nx + 1 (x fastest).
+* Faces: 0 x-min, 1 x-max, 2 y-min, 3 y-max, 4 z-min (bottom), 5 z-max (top).
+* Piles (line heat sources): rows [x, y, z_top, z_bot, mean, amp, period, phase]
+  giving q_l(t) = mean + amp*sin(2*pi*t/period + phase) in W/m.
+* Wells: rows [x, y, z_top, z_bot, Q, T_in]; Q in m^3/s (+ injection) spread
+  uniformly along the screen; injected water enters at temperature T_in.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+DAY = 86400.0
+RHO_W = 1000.0
+G_ACC = 9.81
+
+HEAD, TEMP = 0, 1
+NONE, DIRICHLET, FLUX = 0, 1, 2
+
+
+@dataclasses.dataclass
+class Scenario:
+    """One hydrothermal problem: mesh, coefficients, boundary data, loads."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    order: int
+    origin: Tuple[float, float, float]
+    extent: Tuple[float, float, float]
+    K: np.ndarray                      # [cells] hydraulic conductivity, m/s
+    lam: float                         # bulk thermal conductivity, W/(m K)
+    cT: float                          # bulk volumetric heat capacity, J/(m^3 K)
+    cw: float                          # water volumetric heat capacity, J/(m^3 K)
+    Ss: float                          # specific storage, 1/m
+    bc: Dict[int, Dict[int, Tuple[int, float]]]   # field -> face -> (type, value)
+    piles: np.ndarray                  # [n, 8]
+    wells: np.ndarray                  # [n, 6]
+    h0: np.ndarray                     # [nodes] initial head, m
+    T0: np.ndarray                     # [nodes] initial temperature
+    dt: float                          # time step, s
+    n_steps: int
+    lam_cells: Optional[np.ndarray] = None   # optional per-cell lambda
+    cT_cells: Optional[np.ndarray] = None    # optional per-cell c_T
+
+    @property
+    def n_cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def node_dims(self) -> Tuple[int, int, int]:
+        p = self.order
+        return (p * self.nx + 1, p * self.ny + 1, p * self.nz + 1)
+
+    @property
+    def n_nodes(self) -> int:
+        a, b, c = self.node_dims
+        return a * b * c
+
+    def node_coords(self):
+        """Node coordinate axes (1D arrays along x, y, z)."""
+        Nx, Ny, Nz = self.node_dims
+        x0, y0, z0 = self.origin
+        Lx, Ly, Lz = self.extent
+        return (x0 + Lx * np.arange(Nx) / (Nx - 1),
+                y0 + Ly * np.arange(Ny) / (Ny - 1),
+                z0 + Lz * np.arange(Nz) / (Nz - 1))
+
+    def cell_centres(self):
+        x0, y0, z0 = self.origin
+        Lx, Ly, Lz = self.extent
+        return (x0 + Lx * (np.arange(self.nx) + 0.5) / self.nx,
+                y0 + Ly * (np.arange(self.ny) + 0.5) / self.ny,
+                z0 + Lz * (np.arange(self.nz) + 0.5) / self.nz)
+
+
+def mixture(phi: float, lam_s: float, lam_w: float, c_s: float, c_w: float):
+    """Bulk conductivity and heat capacity by the volume-fraction mixture rules
+    stated beneath Eq. 2 (Section 2)."""
+    return (1.0 - phi) * lam_s + phi * lam_w, (1.0 - phi) * c_s + phi * c_w
+
+
+def specific_storage(B_poro: float, rho_w: float = RHO_W, g: float = G_ACC) -> float:
+    """S_s = rho_w g / B_poro: Eq. 1 divided through by rho_w g with p = rho_w g (h - z)."""
+    return rho_w * g / B_poro
+
+
+# Sand / water thermal values shared by the synthetic workloads.
+SAND = dict(phi=0.3, lam_s=2.5, lam_w=0.6, c_s=2.0e6, c_w=4.18e6)
+B_PORO_TABLE1 = 1.0e5   # Table 1
+
+
+def _sand():
+    lam, cT = mixture(SAND["phi"], SAND["lam_s"], SAND["lam_w"], SAND["c_s"], SAND["c_w"])
+    return lam, cT, SAND["c_w"], specific_storage(B_PORO_TABLE1)
+
+
+def _linear_x(sc_dims, origin, extent, order, a, b, nx, ny, nz):
+    """Nodal field a + b*x (used for initial heads)."""
+    p = order
+    Nx, Ny, Nz = p * nx + 1, p * ny + 1, p * nz + 1
+    x = origin[0] + extent[0] * np.arange(Nx) / (Nx - 1)
+    f = np.broadcast_to((a + b * x)[None, None, :], (Nz, Ny, Nx))
+    return np.ascontiguousarray(f).reshape(-1).astype(np.float64)
+
+
+def gaussian_field_fft(shape, spacing, corr_len, sigma, rng):
+    """Stationary zero-mean Gaussian field on a periodic grid, covariance
+    sigma^2 exp(-r^2 / (2 l^2)), by spectral (FFT) filtering of white noise.
+
+    shape = (nz, ny, nx) cell counts, spacing = (hz, hy, hx).
+    """
+    nz, ny, nx = shape
+    hz, hy, hx = spacing
+    noise = rng.standard_normal(shape)
+    kz = 2 * np.pi * np.fft.fftfreq(nz, d=hz)
+    ky = 2 * np.pi * np.fft.fftfreq(ny, d=hy)
+    kx = 2 * np.pi * np.fft.rfftfreq(nx, d=hx)
+    k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    amp = np.exp(-0.25 * k2 * corr_len ** 2)          # sqrt of Gaussian spectrum
+    f = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=shape)
+    std = f.std()
+    return sigma * f / (std if std > 0 else 1.0)
+
+
+def _bc(head: Dict[int, Tuple[int, float]], temp: Dict[int, Tuple[int, float]]):
+    return {HEAD: dict(head), TEMP: dict(temp)}
+
+
+def config1(nx: int = 16, ny: Optional[int] = None, nz: Optional[int] = None,
+            order: int = 1, n_steps: int = 10) -> Scenario:
+    """Plain workload: 20 m cube, homogeneous sand K = 1e-4 m/s, head gradient
+    0.01 along x, T0 = 15, 10 W/m line source on the central vertical axis,
+    backward Euler with dt = 1 day."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    lam, cT, cw, Ss = _sand()
+    L = 20.0
+    K = np.full(nx * ny * nz, 1.0e-4)
+    h0 = _linear_x(None, (0, 0, 0), (L, L, L), order, 0.2, -0.01, nx, ny, nz)
+    Nn = h0.size
+    T0 = np.full(Nn, 15.0)
+    piles = np.array([[L / 2, L / 2, L, 0.0, 10.0, 0.0, 365 * DAY, 0.0]])
+    bc = _bc({0: (DIRICHLET, 0.2), 1: (DIRICHLET, 0.2 - 0.01 * L)},
+             {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
+              3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
+    return Scenario("plain_q1_cube", nx, ny, nz, order, (0.0, 0.0, 0.0), (L, L, L),
+                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 6)), h0, T0,
+                    1.0 * DAY, n_steps)
+
+
+def config2(nx: int = 128, ny: int = 128, nz: int = 32, seed: int = 2,
+            n_steps: int = 180, order: int = 2) -> Scenario:
+    """ATES-like layered aquifer: 200 m x 200 m x 50 m, Q2 cells, three
+    horizontal layers (10/12/10 of 32 cell layers, scaled with nz) with iid
+    lognormal K per cell (geometric means 1e-6 / 1e-4 / 1e-6 m/s, sigma_lnK =
+    0.5), an injection well (+5 L/s at T0 + 10) and an extraction well
+    (-5 L/s) 60 m apart, both screened over the aquifer layer; dt = 0.5 day."""
+    rng = np.random.default_rng(seed)
+    lam, cT, cw, Ss = _sand()
+    Lx, Ly, Lz = 200.0, 200.0, 50.0
+    nb = int(round(nz * 10 / 32))
+    nt = int(round(nz * 10 / 32))
+    nm = nz - nb - nt
+    layer_mean = np.concatenate([np.full(nb, 1e-6), np.full(nm, 1e-4), np.full(nt, 1e-6)])
+    lnK = np.log(layer_mean)[:, None, None] + 0.5 * rng.standard_normal((nz, ny, nx))
+    K = np.exp(lnK).reshape(-1)
+    Hz = Lz / nz
+    z_lo, z_hi = nb * Hz, (nb + nm) * Hz
+    T_amb = 15.0
+    # wells snapped to the nearest node column
+    p = order
+    hx, hy = Lx / (p * nx), Ly / (p * ny)
+    def snap(v, h):
+        return round(v / h) * h
+    wells = np.array([
+        [snap(70.0, hx), snap(100.0, hy), z_hi, z_lo, +5.0e-3, T_amb + 10.0],
+        [snap(130.0, hx), snap(100.0, hy), z_hi, z_lo, -5.0e-3, T_amb + 10.0],
+    ])
+    Nn = (p * nx + 1) * (p * ny + 1) * (p * nz + 1)
+    h0 = np.zeros(Nn)
+    T0 = np.full(Nn, T_amb)
+    bc = _bc({0: (DIRICHLET, 0.0), 1: (DIRICHLET, 0.0), 2: (DIRICHLET, 0.0), 3: (DIRICHLET, 0.0)},
+             {0: (DIRICHLET, T_amb), 1: (DIRICHLET, T_amb), 2: (DIRICHLET, T_amb),
+              3: (DIRICHLET, T_amb), 5: (DIRICHLET, T_amb)})
+    return Scenario("ates_layered_q2", nx, ny, nz, order, (0.0, 0.0, 0.0), (Lx, Ly, Lz),
+                    K, lam, cT, cw, Ss, bc, np.zeros((0, 8)), wells, h0, T0,
+                    0.5 * DAY, n_steps)
+
+
+def config3(nx: int = 256, ny: int = 256, nz: int = 64, seed: int = 3,
+            n_steps: int = 365, n_piles: Tuple[int, int] = (40, 25),
+            extent=(2000.0, 2000.0, 100.0), order: int = 1) -> Scenario:
+    """Energy-pile field: 2 km x 2 km x 100 m, Q1 cells, Gaussian random lnK
+    (mean ln 1e-5, sigma 1, correlation length 50 m), piles on a 50 m grid
+    with +-10 m jitter, 30 m long from the top, q_l = 40 sin(2 pi t / 1 yr +
+    phase) W/m with random phases; head gradient 5.1e-4 along x (5 Pa/m,
+    Section 3.3); dt = 1 day."""
+    rng = np.random.default_rng(seed)
+    lam, cT, cw, Ss = _sand()
+    Lx, Ly, Lz = extent
+    lnK = math.log(1e-5) + gaussian_field_fft((nz, ny, nx), (Lz / nz, Ly / ny, Lx / nx),
+                                              50.0, 1.0, rng)
+    K = np.exp(lnK).reshape(-1)
+    gx, gy = n_piles
+    cx0 = Lx / 2 - 50.0 * (gx - 1) / 2
+    cy0 = Ly / 2 - 50.0 * (gy - 1) / 2
+    px = cx0 + 50.0 * np.arange(gx)
+    py = cy0 + 50.0 * np.arange(gy)
+    PX, PY = np.meshgrid(px, py, indexing="ij")
+    n = PX.size
+    jit = rng.uniform(-10.0, 10.0, size=(n, 2))
+    X = np.clip(PX.reshape(-1) + jit[:, 0], 0.0, Lx)
+    Y = np.clip(PY.reshape(-1) + jit[:, 1], 0.0, Ly)
+    phase = rng.uniform(0.0, 2 * np.pi, size=n)
+    piles = np.stack([X, Y, np.full(n, Lz), np.full(n, max(Lz - 30.0, 0.0)),
+                      np.zeros(n), np.full(n, 40.0), np.full(n, 365 * DAY), phase], axis=1)
+    grad = 5.0 / (RHO_W * G_ACC)
+    h0 = _linear_x(None, (0, 0, 0), extent, order, grad * Lx, -grad, nx, ny, nz)
+    T0 = np.full(h0.size, 15.0)
+    bc = _bc({0: (DIRICHLET, grad * Lx), 1: (DIRICHLET, 0.0)},
+             {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
+              3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
+    return Scenario("pile_field_q1", nx, ny, nz, order, (0.0, 0.0, 0.0), extent,
+                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 6)), h0, T0,
+                    1.0 * DAY, n_steps)
+
+
+def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
+                 n_piles: int = 3, n_wells: int = 2, sigma_lnK: float = 1.0,
+                 faces_head=(0, 1), faces_temp=(0, 1, 2, 3, 5),
+                 extent=(40.0, 30.0, 20.0), dt: float = 0.5 * DAY,
+                 per_cell_thermal: bool = False) -> Scenario:
+    """Small random problem for parity tests: iid lognormal K, random piles
+    and wells at arbitrary (off-node) positions, random initial fields."""
+    rng = np.random.default_rng(seed)
+    lam, cT, cw, Ss = _sand()
+    Lx, Ly, Lz = extent
+    nc = nx * ny * nz
+    K = np.exp(math.log(3e-5) + sigma_lnK * rng.standard_normal(nc))
+    p = order
+    Nn = (p * nx + 1) * (p * ny + 1) * (p * nz + 1)
+    h0 = rng.uniform(-0.5, 0.5, Nn)
+    T0 = 15.0 + rng.uniform(-1.0, 1.0, Nn)
+    piles = np.stack([rng.uniform(0, Lx, n_piles), rng.uniform(0, Ly, n_piles),
+                      rng.uniform(0.6 * Lz, Lz, n_piles), rng.uniform(0.0, 0.4 * Lz, n_piles),
+                      rng.uniform(-20, 20, n_piles), rng.uniform(0, 40, n_piles),
+                      np.full(n_piles, 30 * DAY), rng.uniform(0, 2 * np.pi, n_piles)], axis=1) \
+        if n_piles else np.zeros((0, 8))
+    wells = np.stack([rng.uniform(0, Lx, n_wells), rng.uniform(0, Ly, n_wells),
+                      rng.uniform(0.5 * Lz, Lz, n_wells), rng.uniform(0.0, 0.5 * Lz, n_wells),
+                      np.where(np.arange(n_wells) % 2 == 0, 2e-3, -2e-3),
+                      np.full(n_wells, 25.0)], axis=1) if n_wells else np.zeros((0, 6))
+    bc = {HEAD: {f: (DIRICHLET, float(rng.uniform(-0.3, 0.3))) for f in faces_head},
+          TEMP: {f: (DIRICHLET, float(rng.uniform(14, 16))) for f in faces_temp}}
+    sc = Scenario(f"random_q{order}_{nx}x{ny}x{nz}_s{seed}", nx, ny, nz, order,
+                  (0.0, 0.0, 0.0), extent, K, lam, cT, cw, Ss, bc, piles, wells,
+                  h0, T0, dt, 3)
+    if per_cell_thermal:
+        sc.lam_cells = lam * np.exp(0.3 * rng.standard_normal(nc))
+        sc.cT_cells = cT * np.exp(0.2 * rng.standard_normal(nc))
+    return sc

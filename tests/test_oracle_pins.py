@@ -1,0 +1,372 @@
+"""Pins of the CPU oracle against mathematics it does not contain.
+
+Each test checks the oracle (``oracle.fem``) against something fixed outside
+it: textbook 1D element matrices, exact symbolic integrals, discrete
+eigen-solutions, exact reproduction of linear heads, conservation, and the
+erfc / Ogata-Banks analytic solutions.  A dropped term, a wrong sign, a wrong
+index order or a transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import closed_forms as cf
+from oracle import fem
+import scenarios as S
+
+
+def _kron3(Ax, Ay, Az):
+    # local node l = a + n*(b + n*c): x fastest -> kron(z, kron(y, x))
+    return np.kron(Az, np.kron(Ay, Ax))
+
+
+def _m1(p, H):
+    if p == 1:
+        return H / 6.0 * np.array([[2, 1], [1, 2]], dtype=float)
+    return H / 30.0 * np.array([[4, 2, -1], [2, 16, 2], [-1, 2, 4]], dtype=float)
+
+
+def _k1(p, H):
+    if p == 1:
+        return 1.0 / H * np.array([[1, -1], [-1, 1]], dtype=float)
+    return 1.0 / (3.0 * H) * np.array([[7, -8, 1], [-8, 16, -8], [1, -8, 7]], dtype=float)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_element_matrices_are_tensor_products_of_textbook_1d(p):
+    """Reference mass / stiffness equal the tensor products of the standard
+    1D Lagrange element matrices (Q1: H/6[2 1;1 2], 1/H[1 -1;-1 1];
+    Q2: H/30[4 2 -1;2 16 2;-1 2 4], 1/(3H)[7 -8 1;-8 16 -8;1 -8 7])."""
+    H = (1.3, 0.7, 2.1)
+    N, G, W = fem.reference_element(p, H)
+    Me = fem.element_mass(N, W)
+    Ke = fem.element_stiffness(G, W)
+    Mx, My, Mz = (_m1(p, h) for h in H)
+    Kx, Ky, Kz = (_k1(p, h) for h in H)
+    np.testing.assert_allclose(Me, _kron3(Mx, My, Mz), rtol=1e-13, atol=1e-15)
+    Kref = _kron3(Kx, My, Mz) + _kron3(Mx, Ky, Mz) + _kron3(Mx, My, Kz)
+    np.testing.assert_allclose(Ke, Kref, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_advection_element_matches_symbolic_integral(p):
+    """C_lm = c_w int N_l (q . grad N_m), q = -K grad h, integrated exactly by
+    sympy on one cell.  For Q1 (any h) and Q2 with a trilinear h the Gauss
+    rule of the oracle is exact, so the two must agree to rounding."""
+    sympy = pytest.importorskip("sympy")
+    x, y, z = sympy.symbols("x y z")
+    H = (1.5, 0.8, 1.1)
+    n = p + 1
+    nodes = [sympy.Rational(i, p) for i in range(n)]
+
+    def lag(a, s):
+        e = sympy.Integer(1)
+        for m in range(n):
+            if m != a:
+                e *= (s - nodes[m]) / (nodes[a] - nodes[m])
+        return e
+
+    rng = np.random.default_rng(7)
+    # h trilinear in physical coordinates
+    hc = [sympy.Rational(int(v), 64) for v in rng.integers(-64, 64, 8)]
+    H = tuple(sympy.Rational(v).limit_denominator(100) for v in H)
+    X, Y, Z = x * H[0], y * H[1], z * H[2]
+    h_expr = (hc[0] + hc[1] * X + hc[2] * Y + hc[3] * Z + hc[4] * X * Y + hc[5] * Y * Z
+              + hc[6] * X * Z + hc[7] * X * Y * Z)
+    Kc, cw = sympy.Rational(23, 100000), 4180000
+    gh = [sympy.diff(h_expr, v) / H[i] for i, v in enumerate((x, y, z))]
+    q = [-Kc * g for g in gh]
+    shapes = []
+    for c in range(n):
+        for b in range(n):
+            for a in range(n):
+                shapes.append(lag(a, x) * lag(b, y) * lag(c, z))
+    Hf = tuple(float(v) for v in H)
+    N, G, W = fem.reference_element(p, Hf)
+    mesh = fem.Mesh(1, 1, 1, p, (0, 0, 0), Hf)
+    # nodal h: evaluate h at the element nodes
+    xs = [float(v) for v in nodes]
+    hn = np.zeros(n ** 3)
+    for c in range(n):
+        for b in range(n):
+            for a in range(n):
+                hn[a + n * (b + n * c)] = float(h_expr.subs({x: xs[a], y: xs[b], z: xs[c]}))
+    qf = fem.darcy_at_qp(mesh, np.array([float(Kc)]), G, hn)
+    Ce = fem.advection_elements(N, G, W, qf, float(cw))[0]
+    vol = H[0] * H[1] * H[2]
+    stride_l, stride_m = (3, 2) if p == 1 else (7, 9)
+    for l in range(0, n ** 3, stride_l):
+        for m in range(1, n ** 3, stride_m):
+            dN = [sympy.diff(shapes[m], v) / H[i] for i, v in enumerate((x, y, z))]
+            integrand = cw * shapes[l] * sum(qq * d for qq, d in zip(q, dN)) * vol
+            exact = float(sympy.integrate(integrand, (x, 0, 1), (y, 0, 1), (z, 0, 1)))
+            assert abs(Ce[l, m] - exact) <= 1e-10 * max(1.0, abs(exact)), (l, m, Ce[l, m], exact)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_row_sums_symmetry_and_definiteness(p):
+    sc = S.random_small(3, 3, 2, 2, p, n_piles=0, n_wells=0)
+    o = fem.OracleSim(sc)
+    one = np.ones(o.mesh.n_nodes)
+    # constants lie in the kernel of stiffness and advection
+    assert np.max(np.abs(o.KK @ one)) < 1e-12 * np.max(np.abs(o.KK.data))
+    qf = fem.darcy_at_qp(o.mesh, o.K, o.G, o.h)
+    C = fem.assemble(o.mesh, np.ones(o.mesh.n_cells),
+                     fem.advection_elements(o.N, o.G, o.W, qf, o.cw))
+    assert np.max(np.abs(C @ one)) < 1e-10 * np.max(np.abs(C.data))
+    # mass integrates the constant exactly: sum of entries = volume
+    vol = np.prod(sc.extent)
+    assert abs(o.M.sum() - vol) < 1e-11 * vol
+    # head operator symmetric positive definite (constrained form too)
+    A = fem.constrain(o.head_matrix(S.DAY), o.dmask[S.HEAD]).toarray()
+    np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-12 * np.abs(A).max())
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("layered", [False, True])
+def test_linear_head_is_reproduced_exactly(p, layered):
+    """Q1/Q2 contain linear functions: with K uniform, or varying only in z,
+    and a head gradient along x fixed on the x faces, the discrete head stays
+    exactly linear and q_x = -K(z) dh/dx (Darcy's law, Section 2)."""
+    sc = S.config1(nx=4, ny=3, nz=5, order=p, n_steps=2)
+    sc.piles = np.zeros((0, 8))
+    if layered:
+        kz = np.exp(np.linspace(-12, -8, sc.nz))
+        sc.K = np.repeat(kz, sc.nx * sc.ny)
+    o = fem.OracleSim(sc)
+    x, _, _ = o.mesh.node_xyz()
+    exact = 0.2 - 0.01 * x
+    o.h[:] = exact + 0.0   # start on the linear solution
+    for _ in range(2):
+        o.step(sc.dt)
+        np.testing.assert_allclose(o.h, exact, rtol=0, atol=1e-12)
+    q = o.cell_flux()
+    np.testing.assert_allclose(q[0], 0.01 * sc.K, rtol=1e-10)
+    np.testing.assert_allclose(q[1:], 0.0, atol=1e-15)
+
+
+def _all_dirichlet(value):
+    return {f: (S.DIRICHLET, value) for f in range(6)}
+
+
+@pytest.mark.parametrize("field", ["heat", "head"])
+def test_discrete_sine_mode_decays_by_closed_form_factor(field):
+    """Q1, homogeneous Dirichlet on all faces, no flow: the sine mode is a
+    discrete eigenvector, T^n = T^0 / (1 + dt a sum_d mu_d)^n exactly, with
+    a = lambda / c_T (heat) or K / S_s (head)."""
+    sc = S.config1(nx=6, ny=5, nz=4, order=1)
+    sc.extent = (12.0, 7.0, 5.0)
+    sc.piles = np.zeros((0, 8))
+    o_mesh = fem.Mesh(sc.nx, sc.ny, sc.nz, 1, sc.origin, sc.extent)
+    i, j, k = o_mesh.node_ijk()
+    mode = (np.sin(np.pi * i / sc.nx) * np.sin(np.pi * j / sc.ny) * np.sin(np.pi * k / sc.nz))
+    if field == "heat":
+        sc.bc = {S.HEAD: {}, S.TEMP: _all_dirichlet(0.0)}
+        sc.h0 = np.zeros_like(mode)
+        sc.T0 = mode.copy()
+        diff = sc.lam / sc.cT
+    else:
+        sc.bc = {S.HEAD: _all_dirichlet(0.0), S.TEMP: {}}
+        sc.h0 = mode.copy()
+        sc.T0 = np.zeros_like(mode)
+        diff = sc.K[0] / sc.Ss
+    o = fem.OracleSim(sc)
+    dt = 0.3 * S.DAY if field == "heat" else 20.0
+    fac = cf.q1_mode_factor(dt, diff, o.mesh.H, sc.extent)
+    for n in range(1, 4):
+        o.step(dt)
+        got = o.T if field == "heat" else o.h
+        np.testing.assert_allclose(got, mode * fac ** n, rtol=0, atol=1e-12)
+
+
+def test_energy_balance_with_pile_flux_face_and_injection_well():
+    """Closed box, no flow, consistent loads: the stored heat sum_i
+    [M_cT (T^{n+1} - T^n)]_i equals dt * (q_l(t) * pile length + flux * face
+    area + injected c_w Q_in (T_in - T))."""
+    for p in (1, 2):
+        sc = S.random_small(5, 4, 3, 3, p, n_piles=2, n_wells=0)
+        sc.bc = {S.HEAD: {}, S.TEMP: {4: (S.FLUX, 0.89)}}
+        sc.h0 = np.full_like(sc.h0, 0.1)
+        o = fem.OracleSim(sc)
+        T0 = o.T.copy()
+        dt = sc.dt
+        o.step(dt)
+        stored = (o.McT @ (o.T - T0)).sum()
+        t1 = dt
+        expect = sum(fem.pile_amplitude(pl, t1) * abs(pl[2] - pl[3]) for pl in sc.piles)
+        expect += 0.89 * sc.extent[0] * sc.extent[1]
+        assert abs(stored - dt * expect) <= 1e-11 * abs(dt * expect)
+
+
+def test_energy_balance_with_injection_well_implicit_term():
+    sc = S.random_small(6, 4, 4, 3, 1, n_piles=0, n_wells=1)
+    sc.bc = {S.HEAD: {}, S.TEMP: {}}
+    o = fem.OracleSim(sc)
+    T0 = o.T.copy()
+    o.step(sc.dt)
+    stored = (o.McT @ (o.T - T0)).sum()
+    # advective term sum_i (C T)_i is not zero in general with a source of
+    # water; the identity is sum_i [C T]_i = sum_cells int c_w q . grad T
+    qf = fem.darcy_at_qp(o.mesh, o.K, o.G, o.h)
+    C = fem.assemble(o.mesh, np.ones(o.mesh.n_cells), fem.advection_elements(o.N, o.G, o.W, qf, o.cw))
+    wl = sc.wells[0]
+    L = wl[2] - wl[3]
+    injected = sc.cw * wl[4] / L * sum(w * (wl[5] - o.T[nd]) for nd, w in
+                                       fem.line_weights(o.mesh, wl[0], wl[1], wl[2], wl[3]).items())
+    adv = (C @ o.T).sum()
+    assert abs(stored - sc.dt * (injected - adv)) <= 1e-10 * abs(sc.dt * injected)
+
+
+def _slab(p, nx, L, dt, steps, bc_temp, bc_head=None, h0=None, K=1e-4):
+    sc = S.config1(nx=nx, ny=1, nz=1, order=p, n_steps=steps)
+    sc.extent = (L, 1.0, 1.0)
+    sc.piles = np.zeros((0, 8))
+    sc.K = np.full(sc.n_cells, K)
+    sc.bc = {S.HEAD: bc_head or {}, S.TEMP: bc_temp}
+    Nn = sc.n_nodes
+    sc.h0 = np.zeros(Nn) if h0 is None else h0
+    sc.T0 = np.zeros(Nn)
+    sc.dt = dt
+    return sc
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_erfc_conduction_converges(p):
+    """Step change T = 1 at x = 0 into a cold slab: error against
+    erfc(x / (2 sqrt(a t))) shrinks as H and dt are refined."""
+    errs = []
+    for nx, nsteps in ((40 // p, 10), (80 // p, 40)):
+        t_end = 5 * S.DAY
+        sc = _slab(p, nx, 6.0, t_end / nsteps, nsteps, {0: (S.DIRICHLET, 1.0)})
+        o = fem.OracleSim(sc)
+        for _ in range(nsteps):
+            o.step(sc.dt)
+        x, _, _ = o.mesh.node_xyz()
+        ex = cf.erfc_1d(x, t_end, sc.lam / sc.cT, 1.0)
+        errs.append(np.max(np.abs(o.T - ex)))
+    assert errs[0] < 0.02
+    assert errs[1] < errs[0] / 2.5, errs
+
+
+def test_ogata_banks_advection_diffusion_converges():
+    """Uniform Darcy flux from a linear head: heat front against the Ogata-
+    Banks solution with v = c_w q / c_T, D = lambda / c_T."""
+    errs = []
+    for nx, nsteps in ((40, 20), (80, 80)):
+        L = 4.0
+        grad = 0.05
+        p = 1
+        Nn = (nx + 1) * 2 * 2
+        sc = _slab(p, nx, L, 1.0, nsteps, {0: (S.DIRICHLET, 1.0)},
+                   bc_head={0: (S.DIRICHLET, grad * L), 1: (S.DIRICHLET, 0.0)})
+        o_mesh = fem.Mesh(nx, 1, 1, 1, (0, 0, 0), (L, 1, 1))
+        x, _, _ = o_mesh.node_xyz()
+        sc.h0 = grad * (L - x)
+        K = 1e-4
+        q = K * grad
+        v = sc.cw * q / sc.cT
+        D = sc.lam / sc.cT
+        t_end = 0.4 * L / v
+        sc.dt = t_end / nsteps
+        o = fem.OracleSim(sc)
+        for _ in range(nsteps):
+            o.step(sc.dt)
+        ex = cf.ogata_banks(x, t_end, v, D, 1.0)
+        errs.append(np.max(np.abs(o.T - ex)))
+    assert errs[0] < 0.08, errs
+    assert errs[1] < errs[0] / 2.5, errs
+
+
+def _mms_error(p, n, with_advection):
+    """One backward Euler step of a manufactured problem whose exact solution
+    u = sin(x) cos(0.7 y) exp(0.3 z) satisfies c u - dt div(k grad u) + dt
+    c_w q . grad u = f exactly; returns the L2 error of the discrete solution."""
+    L = (1.0, 1.2, 0.9)
+    sc = S.config1(nx=n, ny=n, nz=n, order=p)
+    sc.extent = L
+    sc.piles = np.zeros((0, 8))
+    Kh = 2e-5
+    sc.K = np.full(sc.n_cells, Kh)
+    grad = 0.1
+    m = fem.Mesh(n, n, n, p, (0, 0, 0), L)
+    X, Y, Z = m.node_xyz()
+
+    def u(x, y, z):
+        return np.sin(x) * np.cos(0.7 * y) * np.exp(0.3 * z)
+
+    lap = (-1.0 - 0.49 + 0.09)
+    dt = 1000.0
+    qx = Kh * grad if with_advection else 0.0
+    lam, cT, cw = sc.lam, sc.cT, sc.cw
+
+    def f(x, y, z):
+        uu = u(x, y, z)
+        ux = np.cos(x) * np.cos(0.7 * y) * np.exp(0.3 * z)
+        return -dt * lam * lap * uu + dt * cw * qx * ux
+
+    sc.bc = {S.HEAD: {0: (S.DIRICHLET, grad * L[0]), 1: (S.DIRICHLET, 0.0)} if with_advection else {},
+             S.TEMP: _all_dirichlet(0.0)}
+    sc.h0 = grad * (L[0] - X) if with_advection else np.zeros_like(X)
+    sc.T0 = np.zeros_like(X)
+    o = fem.OracleSim(sc)
+    # Dirichlet data = exact solution on the boundary
+    mask = o.dmask[S.TEMP]
+    o.gval[S.TEMP] = np.where(mask, u(X, Y, Z), 0.0)
+    # load: (f, N_i) / dt + mass term of the exact solution, 5-point Gauss
+    Nq, Gq, Wq = fem.reference_element(p, m.H, nq=5)
+    xq, _ = fem.gauss01(5)
+    F = np.zeros(m.n_nodes)
+    errsq = 0.0
+    n1 = p + 1
+    for c in range(m.n_cells):
+        cx, cy, cz = c % n, (c // n) % n, c // (n * n)
+        for qz in range(5):
+            for qy in range(5):
+                for qx_ in range(5):
+                    qi = qx_ + 5 * (qy + 5 * qz)
+                    px = (cx + xq[qx_]) * m.H[0]
+                    py = (cy + xq[qy]) * m.H[1]
+                    pz = (cz + xq[qz]) * m.H[2]
+                    F[m.conn[c]] += Wq[qi] * Nq[qi] * (f(px, py, pz) + cT * u(px, py, pz)) / dt
+    o.extra[S.TEMP] = F
+    o.T[:] = 0.0
+    # remove the mass term of T^n (= 0) -- the load already carries c_T u
+    o.step(dt)
+    for c in range(m.n_cells):
+        cx, cy, cz = c % n, (c // n) % n, c // (n * n)
+        uh = Nq @ o.T[m.conn[c]]
+        for qi in range(125):
+            qx_, qy, qz = qi % 5, (qi // 5) % 5, qi // 25
+            px = (cx + xq[qx_]) * m.H[0]
+            py = (cy + xq[qy]) * m.H[1]
+            pz = (cz + xq[qz]) * m.H[2]
+            errsq += Wq[qi] * (uh[qi] - u(px, py, pz)) ** 2
+    return math.sqrt(errsq)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("adv", [False, True])
+def test_manufactured_solution_convergence_order(p, adv):
+    e1 = _mms_error(p, 3, adv)
+    e2 = _mms_error(p, 6, adv)
+    order = math.log(e1 / e2) / math.log(2.0)
+    assert order > p + 1 - 0.35, (e1, e2, order)
+
+
+def test_mirror_symmetry_between_identical_piles():
+    """Two identical piles placed symmetrically in still water give a
+    temperature field symmetric about the midline (Section 3.5)."""
+    sc = S.config1(nx=8, ny=4, nz=4, order=1)
+    sc.extent = (16.0, 8.0, 8.0)
+    sc.piles = np.array([[5.0, 4.0, 8.0, 2.0, 10.0, 0.0, 1e9, 0.0],
+                         [11.0, 4.0, 8.0, 2.0, 10.0, 0.0, 1e9, 0.0]])
+    sc.bc = {S.HEAD: {}, S.TEMP: {0: (S.DIRICHLET, 15.0), 1: (S.DIRICHLET, 15.0), 5: (S.DIRICHLET, 15.0)}}
+    sc.h0 = np.zeros(sc.n_nodes)
+    o = fem.OracleSim(sc)
+    for _ in range(3):
+        o.step(sc.dt)
+    T = o.T.reshape(sc.node_dims[::-1])
+    np.testing.assert_allclose(T, T[:, :, ::-1], rtol=0, atol=1e-12)
