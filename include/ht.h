@@ -1,0 +1,188 @@
+/*
+ * ht.h -- C ABI of the GB300 hydrothermal finite element step.
+ *
+ * The library advances the one-way coupled system of the paper (Sun et al.,
+ * "An HPC-Based Hydrothermal Finite Element Simulator ...", Section 2):
+ *
+ *   head  (Eq. 1 in hydraulic-head form, backward Euler as in Eq. 3)
+ *         (S_s M + dt K_K) h^{n+1} = S_s M h^n + dt F_h
+ *   heat  (Eq. 2 in energy form, backward Euler as in Eq. 4, q from Darcy's
+ *         law q = -K grad h^{n+1} of Section 2)
+ *         (M_cT + dt L_lambda + dt C(q) + dt D_w) T^{n+1} = M_cT T^n + dt F_T
+ *
+ * on a structured box of Q1 or Q2 Lagrange hexahedra with per-cell
+ * coefficients, matrix-free, on one GPU.  Every entry point returns HT_OK (0)
+ * or a negative HT_E* code; the message of the last failure is available from
+ * ht_last_error().  Nothing aborts, traps or asserts on the device.
+ *
+ * Layout.  Cells c = cx + nx*(cy + ny*cz); nodes n = i + Nx*(j + Ny*k) with
+ * Nx = order*nx + 1 (x fastest).  Faces: 0 x-min, 1 x-max, 2 y-min, 3 y-max,
+ * 4 z-min (bottom), 5 z-max (top).  All arrays are FP64 and SI units.
+ *
+ * Ownership.  Inputs are copied during the call; the caller keeps its
+ * buffers.  Output buffers belong to the caller.  Pointers flagged
+ * "on_device" are CUDA device pointers valid on the context's device (for
+ * example the data pointer of a torch CUDA tensor); otherwise host pointers.
+ * A context owns all device memory it allocates and frees it in
+ * ht_destroy().  Work is issued on the stream given to ht_create (or a
+ * stream the library creates); calls that return data synchronise it.
+ */
+#ifndef HT_H
+#define HT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HT_OK 0
+#define HT_EINVAL (-1)      /* bad argument, size or state */
+#define HT_ENOMEM (-2)      /* device or host allocation failed */
+#define HT_ECUDA (-3)       /* a CUDA runtime call failed */
+#define HT_ENOCONV (-4)     /* Krylov solve hit max_iter before the tolerance */
+#define HT_EBREAKDOWN (-5)  /* BiCGStab breakdown that a restart did not cure */
+#define HT_ETIMEOUT (-6)    /* a bounded device wait gave up */
+
+enum { HT_HEAD = 0, HT_TEMP = 1, HT_QX = 2, HT_QY = 3, HT_QZ = 4 };
+enum { HT_BC_NONE = 0, HT_BC_DIRICHLET = 1, HT_BC_FLUX = 2 };
+enum { HT_FP64 = 0, HT_MIXED = 1 };
+enum { HT_KRYLOV_BICGSTAB = 0 };
+enum { HT_PREC_JACOBI = 0, HT_PREC_CHEBYSHEV = 1 };
+
+typedef struct ht_ctx ht_ctx;
+
+/* Structured box: nx*ny*nz cells of order 1 (Q1) or 2 (Q2) spanning
+ * [x0, x0+Lx] x [y0, y0+Ly] x [z0, z0+Lz]. */
+typedef struct {
+    int nx, ny, nz, order;
+    double x0, y0, z0, Lx, Ly, Lz;
+} ht_mesh;
+
+/* Vertical line heat source (energy pile) from z_bot to z_top at (x, y) with
+ * strength q_l(t) = mean + amp*sin(2*pi*t/period + phase) in W/m
+ * (Section 3.2-3.3 piles, as consistent line loads int q_l N_i dz). */
+typedef struct {
+    double x, y, z_top, z_bot, mean, amp, period, phase;
+} ht_line_src;
+
+/* Vertical well screened from z_bot to z_top at (x, y): volumetric rate Q
+ * (m^3/s, > 0 injects) spread uniformly over the screen as a head source;
+ * injected water carries temperature T_in (implicit lumped line term
+ * c_w (Q/L) int N_i dz (T_in - T)); extraction adds no heat term because
+ * Eq. 2 is in advective (q . grad T) form. */
+typedef struct {
+    double x, y, z_top, z_bot, Q, T_in;
+} ht_well;
+
+/* Solver options.  tol is the relative residual ||b - A x||_2 <= tol ||b||_2
+ * on each linear system (head: preconditioned CG, heat: BiCGStab).
+ * precision HT_MIXED runs operator applies, preconditioner and inner Krylov
+ * iterations in FP32 inside an FP64 defect-correction loop whose residuals,
+ * dot products and norms are FP64.  precond HT_PREC_CHEBYSHEV uses a
+ * Chebyshev polynomial of degree cheb_degree in D^-1 A for the head CG. */
+typedef struct {
+    double tol;
+    int max_iter;
+    int krylov;
+    int precond;
+    int cheb_degree;
+    int precision;
+    double inner_tol;
+    int max_outer;
+    int check_every;
+    int use_graphs;
+} ht_solver_opts;
+
+/* Per-step statistics: Krylov iterations (inner iterations in mixed mode),
+ * outer defect-correction passes, final true relative residuals computed in
+ * FP64, simulated time after the step, and phase times in milliseconds. */
+typedef struct {
+    int iters_head, iters_heat;
+    int outer_head, outer_heat;
+    double res_head, res_heat;
+    double t;
+    double ms_loads, ms_head, ms_heat, ms_total;
+    int status;
+} ht_step_stats;
+
+/* Fill *opts with the defaults (tol 1e-10, max_iter 20000, Jacobi, FP64). */
+int ht_default_solver(ht_solver_opts* opts);
+
+/* Create a context for the mesh on CUDA device `device`.  cuda_stream is a
+ * cudaStream_t (NULL: the library creates a non-blocking stream it owns).
+ * Errors: HT_EINVAL (order not 1/2, non-positive sizes), HT_ENOMEM, HT_ECUDA. */
+int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream);
+
+/* Free all device memory and the context.  NULL is ignored. */
+void ht_destroy(ht_ctx* ctx);
+
+/* Message of the most recent failure on ctx (or of the last ht_create). */
+const char* ht_last_error(const ht_ctx* ctx);
+
+/* Node and cell counts of the context's mesh. */
+int ht_sizes(const ht_ctx* ctx, size_t* n_nodes, size_t* n_cells);
+
+/* Per-cell coefficients (Section 2 below Eq. 2): hydraulic conductivity
+ * K [cells] (> 0, host), bulk thermal conductivity lambda and heat capacity
+ * cT (per-cell host arrays, or NULL to use the uniform lambda_u / cT_u),
+ * water heat capacity cw and specific storage Ss = rho_w g / B_poro.
+ * Errors: HT_EINVAL for NaN / non-positive values. */
+int ht_set_cells(ht_ctx* ctx, const double* K, const double* lambda, const double* cT,
+                 double lambda_u, double cT_u, double cw, double Ss);
+
+/* Boundary condition of `field` (HT_HEAD / HT_TEMP) on `face`: Dirichlet
+ * value, uniform normal flux into the domain (m/s for head, W/m^2 for heat;
+ * the boundary integrals of Eq. 3 / Eq. 4), or none (no-flow / insulated).
+ * On edges shared by two Dirichlet faces the higher face index wins. */
+int ht_set_bc(ht_ctx* ctx, int field, int face, int type, double value);
+
+/* Set the state h, T [nodes] and the time t.  Either pointer may be NULL to
+ * keep that field.  on_device selects device vs host pointers. */
+int ht_set_state(ht_ctx* ctx, const double* h, const double* T, double t, int on_device);
+
+/* Append sources; they take effect from the next step.  Errors: HT_EINVAL
+ * for a source outside the box or with z_top <= z_bot. */
+int ht_add_line_sources(ht_ctx* ctx, int n, const ht_line_src* src);
+int ht_add_wells(ht_ctx* ctx, int n, const ht_well* wells);
+
+/* Extra nodal load vector added to F of `field` at every step (NULL clears).
+ * A test hook for manufactured solutions. */
+int ht_set_extra_rhs(ht_ctx* ctx, int field, const double* F, int on_device);
+
+int ht_set_solver(ht_ctx* ctx, const ht_solver_opts* opts);
+
+/* One backward-Euler step of size dt: loads at t+dt, head solve, then heat
+ * solve with the Darcy flux of the new head (Section 2 one-way coupling).
+ * stats may be NULL.  Errors: HT_ENOCONV / HT_EBREAKDOWN leave the state at
+ * the last iterate and report the residual in stats. */
+int ht_step(ht_ctx* ctx, double dt, ht_step_stats* stats);
+
+/* Copy a field out: HT_HEAD / HT_TEMP [nodes], HT_QX/QY/QZ Darcy flux
+ * -K_c grad h at cell centres [cells].  n must equal the field size. */
+int ht_get_field(ht_ctx* ctx, int field, double* dst, size_t n, int dst_on_device);
+
+/* Simulated time of the current state. */
+int ht_get_time(const ht_ctx* ctx, double* t);
+
+/* Parity hooks.  ht_apply: y = A0 x with the constrained operator of `field`
+ * for step dt (Dirichlet rows identity, Dirichlet columns removed); the heat
+ * operator uses the current head as h^{n+1}.  ht_diag: its diagonal.
+ * ht_rhs: the lifted right-hand side b of the next step of `field` (heat
+ * uses the current head as h^{n+1} and the loads at t+dt). */
+int ht_apply(ht_ctx* ctx, int field, double dt, const double* x, double* y, int on_device);
+int ht_diag(ht_ctx* ctx, int field, double dt, double* d, int on_device);
+int ht_rhs(ht_ctx* ctx, int field, double dt, double* b, int on_device);
+
+/* Bulk coefficients from the mixture rules of Section 2 and the storage of
+ * Eq. 1: lambda = (1-phi) lambda_s + phi lambda_w, cT = (1-phi) c_s +
+ * phi c_w, Ss = rho_w g / B_poro. */
+int ht_mixture(double phi, double lambda_s, double lambda_w, double c_s, double c_w,
+               double* lambda, double* cT);
+double ht_specific_storage(double B_poro, double rho_w, double g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HT_H */

@@ -1,0 +1,775 @@
+// C ABI of the hydrothermal step (include/ht.h): context set-up, host-side
+// load tables, the time stepper and parity hooks.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "ht_internal.cuh"
+
+namespace ht {
+
+int fail(ht_ctx* c, int code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---- 1D reference data --------------------------------------------------------
+void gauss01(int n, double* x, double* w) {
+    if (n == 2) {
+        const double d = 0.5 / sqrt(3.0);
+        x[0] = 0.5 - d; x[1] = 0.5 + d;
+        w[0] = w[1] = 0.5;
+    } else {
+        const double d = 0.5 * sqrt(0.6);
+        x[0] = 0.5 - d; x[1] = 0.5; x[2] = 0.5 + d;
+        w[0] = 5.0 / 18.0; w[1] = 8.0 / 18.0; w[2] = 5.0 / 18.0;
+    }
+}
+
+// Lagrange basis on the equispaced nodes {0, 1/P, ..., 1}
+double lag(int P, int a, double xi) {
+    double v = 1.0;
+    for (int m = 0; m <= P; ++m)
+        if (m != a) v *= (xi - (double)m / P) / ((double)(a - m) / P);
+    return v;
+}
+
+double dlag(int P, int a, double xi) {
+    double s = 0.0;
+    for (int m = 0; m <= P; ++m) {
+        if (m == a) continue;
+        double t = 1.0 / ((double)(a - m) / P);
+        for (int k = 0; k <= P; ++k)
+            if (k != a && k != m) t *= (xi - (double)k / P) / ((double)(a - k) / P);
+        s += t;
+    }
+    return s;
+}
+
+// cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (n <= 3):
+// A = U diag(lam) U^T, columns of U are eigenvectors
+void jacobi_eig(int n, double A[3][3], double U[3][3], double lam[3]) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) U[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[p][q] * A[p][q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {  // A = J^T A J
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = cs * akp - sn * akq;
+                    A[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = cs * apk - sn * aqk;
+                    A[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double ukp = U[k][p], ukq = U[k][q];
+                    U[k][p] = cs * ukp - sn * ukq;
+                    U[k][q] = sn * ukp + cs * ukq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) lam[i] = A[i][i];
+}
+
+// 1D element mass / stiffness on [0, H] and their fast-diagonalisation
+// factors G (m = G^T G, k = G^T diag(lam) G).
+void element_1d(int P, double H, double m[3][3], double k[3][3], double G[3][3], double lam[3]) {
+    const int n = P + 1;
+    double xq[3], wq[3];
+    gauss01(n, xq, wq);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double sm = 0, sk = 0;
+            for (int q = 0; q < n; ++q) {
+                sm += wq[q] * lag(P, a, xq[q]) * lag(P, b, xq[q]);
+                sk += wq[q] * dlag(P, a, xq[q]) * dlag(P, b, xq[q]);
+            }
+            m[a][b] = H * sm;
+            k[a][b] = sk / H;
+        }
+    // Cholesky m = L L^T
+    double L[3][3] = {{0}};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = m[i][j];
+            for (int l = 0; l < j; ++l) s -= L[i][l] * L[j][l];
+            L[i][j] = (i == j) ? sqrt(s) : s / L[j][j];
+        }
+    // Linv
+    double Li[3][3] = {{0}};
+    for (int i = 0; i < n; ++i) {
+        Li[i][i] = 1.0 / L[i][i];
+        for (int j = 0; j < i; ++j) {
+            double s = 0;
+            for (int l = j; l < i; ++l) s -= L[i][l] * Li[l][j];
+            Li[i][j] = s / L[i][i];
+        }
+    }
+    // C = Li k Li^T
+    double C[3][3] = {{0}};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0;
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) s += Li[i][a] * k[a][b] * Li[j][b];
+            C[i][j] = s;
+        }
+    double U[3][3];
+    jacobi_eig(n, C, U, lam);
+    // G = U^T L^T : G[i][j] = sum_l U[l][i] L[j][l]
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) G[i][j] = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0;
+            for (int l = 0; l < n; ++l) s += U[l][i] * L[j][l];
+            G[i][j] = s;
+        }
+}
+
+void build_elem(ht_ctx* c) {
+    const int P = c->grid.P, n = P + 1;
+    ht::Elem<double>& e = c->e64;
+    memset(&e, 0, sizeof(e));
+    double m[3][3][3], k[3][3][3];
+    for (int d = 0; d < 3; ++d) element_1d(P, c->H[d], m[d], k[d], e.G[d], e.Lam[d]);
+    double xq[3], wq[3];
+    gauss01(n, xq, wq);
+    for (int q = 0; q < n; ++q)
+        for (int a = 0; a < n; ++a) {
+            e.B[q][a] = lag(P, a, xq[q]);
+            e.D[q][a] = dlag(P, a, xq[q]);
+        }
+    const double vol = c->H[0] * c->H[1] * c->H[2];
+    for (int qz = 0; qz < n; ++qz)
+        for (int qy = 0; qy < n; ++qy)
+            for (int qx = 0; qx < n; ++qx) e.W[qx + n * (qy + n * qz)] = wq[qx] * wq[qy] * wq[qz] * vol;
+    for (int d = 0; d < 3; ++d) e.invH[d] = 1.0 / c->H[d];
+    for (int cc = 0; cc < n; ++cc)
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+                const int l = a + n * (b + n * cc);
+                e.dM[l] = m[0][a][a] * m[1][b][b] * m[2][cc][cc];
+                e.dK[l] = k[0][a][a] * m[1][b][b] * m[2][cc][cc] + m[0][a][a] * k[1][b][b] * m[2][cc][cc] +
+                          m[0][a][a] * m[1][b][b] * k[2][cc][cc];
+            }
+    // FP32 copy
+    ht::Elem<float>& f = c->e32;
+    const double* src = reinterpret_cast<const double*>(&e);
+    float* dst = reinterpret_cast<float*>(&f);
+    static_assert(sizeof(ht::Elem<double>) == 2 * sizeof(ht::Elem<float>), "Elem layout");
+    for (size_t i = 0; i < sizeof(e) / sizeof(double); ++i) dst[i] = (float)src[i];
+}
+
+// integral of phi_a over [0,1] (exact Gauss)
+double phi_int(int P, int a) {
+    double xq[3], wq[3];
+    gauss01(P + 1, xq, wq);
+    double s = 0;
+    for (int q = 0; q <= P; ++q) s += wq[q] * lag(P, a, xq[q]);
+    return s;
+}
+
+// 1D boundary integral weight of node i along a direction with nc cells of size H
+double node_int_1d(int P, int nc, double H, int i) {
+    double s = 0;
+    if (i % P == 0) {
+        const int cl = i / P - 1, cr = i / P;
+        if (cl >= 0) s += H * phi_int(P, P);
+        if (cr < nc) s += H * phi_int(P, 0);
+    } else {
+        s += H * phi_int(P, i % P);
+    }
+    return s;
+}
+
+template <typename T>
+int dalloc(ht_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, HT_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    *p = static_cast<T*>(q);
+    return HT_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Vertical segment weights w_i = int_{z_bot}^{z_top} N_i(x, y, z) dz
+int line_weights(ht_ctx* c, double x, double y, double ztop, double zbot, std::map<long long, double>& out,
+                 const char* what) {
+    const ht_mesh& m = c->mesh;
+    const int P = c->grid.P;
+    const double eps = 1e-9 * std::max(m.Lx, std::max(m.Ly, m.Lz));
+    if (!(x >= m.x0 - eps && x <= m.x0 + m.Lx + eps && y >= m.y0 - eps && y <= m.y0 + m.Ly + eps))
+        return fail(c, HT_EINVAL, "%s at (%g, %g) lies outside the box", what, x, y);
+    if (!(ztop > zbot)) return fail(c, HT_EINVAL, "%s needs z_top > z_bot", what);
+    const double lo = std::max(zbot, m.z0), hi = std::min(ztop, m.z0 + m.Lz);
+    if (!(hi > lo)) return fail(c, HT_EINVAL, "%s segment does not intersect the box", what);
+    int cxy[2];
+    double fx[2][3];
+    const double pos[2] = {x, y}, org[2] = {m.x0, m.y0};
+    const int ncs[2] = {m.nx, m.ny};
+    for (int d = 0; d < 2; ++d) {
+        const double s = (pos[d] - org[d]) / c->H[d];
+        int ci = (int)floor(s);
+        ci = std::max(0, std::min(ci, ncs[d] - 1));
+        const double xi = s - ci;
+        cxy[d] = ci;
+        for (int a = 0; a <= P; ++a) fx[d][a] = lag(P, a, xi);
+    }
+    const double Hz = c->H[2];
+    double xq[3], wq[3];
+    gauss01(3, xq, wq);
+    int cz0 = (int)floor((lo - m.z0) / Hz);
+    cz0 = std::max(0, std::min(cz0, m.nz - 1));
+    for (int cz = cz0; cz < m.nz; ++cz) {
+        const double a0 = m.z0 + cz * Hz, a1 = a0 + Hz;
+        if (a0 >= hi) break;
+        const double s0 = std::max(a0, lo), s1 = std::min(a1, hi);
+        if (s1 <= s0) continue;
+        for (int cc = 0; cc <= P; ++cc) {
+            double Iz = 0;
+            for (int g = 0; g < 3; ++g) {
+                const double zz = s0 + (s1 - s0) * xq[g];
+                Iz += wq[g] * (s1 - s0) * lag(P, cc, (zz - a0) / Hz);
+            }
+            for (int b = 0; b <= P; ++b)
+                for (int a = 0; a <= P; ++a) {
+                    const long long i = (long long)P * cxy[0] + a, j = (long long)P * cxy[1] + b,
+                                    k = (long long)P * cz + cc;
+                    const long long id = i + (long long)c->grid.Nx * (j + (long long)c->grid.Ny * k);
+                    out[id] += fx[0][a] * fx[1][b] * Iz;
+                }
+        }
+    }
+    return HT_OK;
+}
+
+bool node_on_dirichlet(const ht_ctx* c, int field, long long id) {
+    const Grid& g = c->grid;
+    const int i = (int)(id % g.Nx), j = (int)((id / g.Nx) % g.Ny), k = (int)(id / ((long long)g.Nx * g.Ny));
+    const int m = c->dmask[field];
+    return ((m & 1) && i == 0) || ((m & 2) && i == g.Nx - 1) || ((m & 4) && j == 0) ||
+           ((m & 8) && j == g.Ny - 1) || ((m & 16) && k == 0) || ((m & 32) && k == g.Nz - 1);
+}
+
+// Rebuild Dirichlet values, static loads and source tables after changes.
+int finalize_setup(ht_ctx* c) {
+    if (!c->cells_set) return fail(c, HT_EINVAL, "ht_set_cells must be called before stepping");
+    if (!c->bc_dirty && !c->loads_dirty) return HT_OK;
+    const Grid& g = c->grid;
+    const long long nn = g.nn;
+    std::vector<double> gv(nn), Fs0(nn, 0.0), Fs1(nn, 0.0);
+    for (int f = 0; f < 2; ++f) {
+        std::fill(gv.begin(), gv.end(), 0.0);
+        int mask = 0;
+        std::vector<double>& Fs = f == 0 ? Fs0 : Fs1;
+        for (int face = 0; face < 6; ++face) {
+            const int axis = face / 2, side = face % 2;
+            const int Nd[3] = {g.Nx, g.Ny, g.Nz};
+            const int fixed = side ? Nd[axis] - 1 : 0;
+            const int t1 = axis == 0 ? 1 : 0, t2 = axis == 2 ? 1 : 2;
+            const int ncs[3] = {g.ncx, g.ncy, g.ncz};
+            if (c->bc_type[f][face] == HT_BC_DIRICHLET) mask |= 1 << face;
+            if (c->bc_type[f][face] == HT_BC_NONE) continue;
+            for (int b = 0; b < Nd[t2]; ++b)
+                for (int a = 0; a < Nd[t1]; ++a) {
+                    int ijk[3];
+                    ijk[axis] = fixed;
+                    ijk[t1] = a;
+                    ijk[t2] = b;
+                    const long long id = ijk[0] + (long long)g.Nx * (ijk[1] + (long long)g.Ny * ijk[2]);
+                    if (c->bc_type[f][face] == HT_BC_DIRICHLET) {
+                        gv[id] = c->bc_val[f][face];
+                    } else {
+                        Fs[id] += c->bc_val[f][face] * node_int_1d(g.P, ncs[t1], c->H[t1], a) *
+                                  node_int_1d(g.P, ncs[t2], c->H[t2], b);
+                    }
+                }
+        }
+        c->dmask[f] = mask;
+        HT_CUDA(c, cudaMemcpyAsync(c->g[f], gv.data(), nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    // wells: head line source and (injection) lumped heat term
+    std::map<long long, double> wd;
+    for (const ht_well& w : c->wells) {
+        std::map<long long, double> lw;
+        HT_TRY(line_weights(c, w.x, w.y, w.z_top, w.z_bot, lw, "well"));
+        const double L = std::min(w.z_top, c->mesh.z0 + c->mesh.Lz) - std::max(w.z_bot, c->mesh.z0);
+        const double qlin = w.Q / (w.z_top - w.z_bot);
+        (void)L;
+        for (auto& kv : lw) {
+            Fs0[kv.first] += qlin * kv.second;
+            // Dirichlet rows of the heat system stay identity rows
+            if (w.Q > 0 && !node_on_dirichlet(c, HT_TEMP, kv.first)) {
+                const double d = c->cw * qlin * kv.second;
+                wd[kv.first] += d;
+                Fs1[kv.first] += d * w.T_in;
+            }
+        }
+    }
+    HT_CUDA(c, cudaMemcpyAsync(c->Fstat[0], Fs0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    HT_CUDA(c, cudaMemcpyAsync(c->Fstat[1], Fs1.data(), nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // well diagonal list
+    dfree(c->well_node);
+    dfree(c->well_d);
+    c->n_well_nodes = (int)wd.size();
+    std::vector<int> wn;
+    std::vector<double> wv;
+    for (auto& kv : wd) { wn.push_back((int)kv.first); wv.push_back(kv.second); }
+    if (!wn.empty()) {
+        HT_TRY(dalloc(c, &c->well_node, wn.size()));
+        HT_TRY(dalloc(c, &c->well_d, wv.size()));
+        HT_CUDA(c, cudaMemcpyAsync(c->well_node, wn.data(), wn.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaMemcpyAsync(c->well_d, wv.data(), wv.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
+    // pile tables: CSR over unique nodes
+    std::map<long long, std::vector<std::pair<int, double>>> pm;
+    for (size_t s = 0; s < c->piles.size(); ++s) {
+        const ht_line_src& p = c->piles[s];
+        std::map<long long, double> lw;
+        HT_TRY(line_weights(c, p.x, p.y, p.z_top, p.z_bot, lw, "line source"));
+        for (auto& kv : lw) pm[kv.first].push_back({(int)s, kv.second});
+    }
+    dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->pile_w); dfree(c->d_piles);
+    c->n_pile_nodes = (int)pm.size();
+    if (!pm.empty()) {
+        std::vector<int> pn, po, ps;
+        std::vector<double> pw;
+        po.push_back(0);
+        for (auto& kv : pm) {
+            pn.push_back((int)kv.first);
+            for (auto& e : kv.second) { ps.push_back(e.first); pw.push_back(e.second); }
+            po.push_back((int)ps.size());
+        }
+        HT_TRY(dalloc(c, &c->pile_node, pn.size()));
+        HT_TRY(dalloc(c, &c->pile_off, po.size()));
+        HT_TRY(dalloc(c, &c->pile_src, ps.size()));
+        HT_TRY(dalloc(c, &c->pile_w, pw.size()));
+        HT_TRY(dalloc(c, &c->d_piles, c->piles.size()));
+        HT_CUDA(c, cudaMemcpyAsync(c->pile_node, pn.data(), pn.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaMemcpyAsync(c->pile_off, po.data(), po.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaMemcpyAsync(c->pile_src, ps.data(), ps.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaMemcpyAsync(c->pile_w, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaMemcpyAsync(c->d_piles, c->piles.data(), c->piles.size() * sizeof(ht_line_src),
+                                   cudaMemcpyHostToDevice, c->stream));
+    }
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->bc_dirty = false;
+    c->loads_dirty = false;
+    return HT_OK;
+}
+
+int copy_in(ht_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+    HT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (!on_device) HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HT_OK;
+}
+
+int copy_out(ht_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+    HT_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HT_OK;
+}
+
+bool finite_pos(const double* a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!(a[i] > 0.0) || !isfinite(a[i])) return false;
+    return true;
+}
+
+int upload_cells(ht_ctx* c, double** d64, float** d32, const double* h, size_t nc) {
+    if (!*d64) HT_TRY(dalloc(c, d64, nc));
+    if (!*d32) HT_TRY(dalloc(c, d32, nc));
+    std::vector<float> f(nc);
+    for (size_t i = 0; i < nc; ++i) f[i] = (float)h[i];
+    HT_CUDA(c, cudaMemcpyAsync(*d64, h, nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    HT_CUDA(c, cudaMemcpyAsync(*d32, f.data(), nc * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HT_OK;
+}
+
+}  // namespace
+}  // namespace ht
+
+using namespace ht;
+
+extern "C" {
+
+int ht_default_solver(ht_solver_opts* o) {
+    if (!o) return HT_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->tol = 1e-10;
+    o->max_iter = 20000;
+    o->krylov = HT_KRYLOV_BICGSTAB;
+    o->precond = HT_PREC_JACOBI;
+    o->cheb_degree = 4;
+    o->precision = HT_FP64;
+    o->inner_tol = 1e-4;
+    o->max_outer = 30;
+    o->check_every = 8;
+    o->use_graphs = 0;
+    return HT_OK;
+}
+
+int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream) {
+    if (!out || !mesh) { g_create_error = "null argument"; return HT_EINVAL; }
+    *out = nullptr;
+    if (mesh->order != 1 && mesh->order != 2) { g_create_error = "order must be 1 or 2"; return HT_EINVAL; }
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0)) {
+        g_create_error = "mesh sizes must be positive";
+        return HT_EINVAL;
+    }
+    const long long P = mesh->order;
+    const long long nn = (P * mesh->nx + 1) * (P * mesh->ny + 1) * (P * mesh->nz + 1);
+    if (nn > 2000000000LL) { g_create_error = "mesh too large for 32-bit node tables"; return HT_EINVAL; }
+    ht_ctx* c = new ht_ctx();
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        delete c;
+        return HT_ECUDA;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            g_create_error = "cudaStreamCreate failed";
+            delete c;
+            return HT_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    c->mesh = *mesh;
+    Grid& g = c->grid;
+    g.P = mesh->order;
+    g.ncx = mesh->nx; g.ncy = mesh->ny; g.ncz = mesh->nz;
+    g.Nx = g.P * g.ncx + 1; g.Ny = g.P * g.ncy + 1; g.Nz = g.P * g.ncz + 1;
+    g.nn = nn;
+    g.nc = (long long)mesh->nx * mesh->ny * mesh->nz;
+    g.dmask = 0;
+    c->H[0] = mesh->Lx / mesh->nx; c->H[1] = mesh->Ly / mesh->ny; c->H[2] = mesh->Lz / mesh->nz;
+    build_elem(c);
+    ht_default_solver(&c->opts);
+    const size_t N = (size_t)nn, NC = (size_t)g.nc;
+    const size_t NQ = (size_t)(g.P + 1) * (g.P + 1) * (g.P + 1);
+    int rc = HT_OK;
+    double** v64[] = {&c->h, &c->T, &c->g[0], &c->g[1], &c->Fstat[0], &c->Fstat[1], &c->F[0], &c->F[1],
+                      &c->extra[0], &c->extra[1], &c->x, &c->r, &c->z, &c->p, &c->q, &c->b, &c->D,
+                      &c->rh, &c->v, &c->s, &c->tv, &c->ph, &c->sh, &c->z2};
+    for (double** pp : v64)
+        if (rc == HT_OK) rc = dalloc(c, pp, N);
+    float** v32[] = {&c->x32, &c->r32, &c->z32, &c->p32, &c->q32, &c->D32, &c->rh32, &c->v32,
+                     &c->s32, &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32};
+    for (float** pp : v32)
+        if (rc == HT_OK) rc = dalloc(c, pp, N);
+    if (rc == HT_OK) rc = dalloc(c, &c->qs64, 3 * NQ * NC);
+    if (rc == HT_OK) rc = dalloc(c, &c->qs32, 3 * NQ * NC);
+    const int G = vec_grid(c), tiles = apply_tiles(c);
+    c->part_stride = std::max(G, tiles) + 32;
+    if (rc == HT_OK) rc = dalloc(c, &c->part, (size_t)8 * c->part_stride);
+    if (rc == HT_OK) rc = dalloc(c, &c->scal, 4);
+    if (rc == HT_OK && cudaMallocHost(&c->scal_host, 4 * sizeof(Scal)) != cudaSuccess) rc = HT_ENOMEM;
+    if (rc == HT_OK) {
+        for (double* p : {c->h, c->T, c->extra[0], c->extra[1], c->Fstat[0], c->Fstat[1], c->g[0], c->g[1]})
+            if (cudaMemsetAsync(p, 0, N * sizeof(double), c->stream) != cudaSuccess) rc = HT_ECUDA;
+        if (cudaMemsetAsync(c->qs64, 0, 3 * NQ * NC * sizeof(double), c->stream) != cudaSuccess) rc = HT_ECUDA;
+        if (cudaMemsetAsync(c->qs32, 0, 3 * NQ * NC * sizeof(float), c->stream) != cudaSuccess) rc = HT_ECUDA;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HT_ECUDA;
+    }
+    if (rc != HT_OK) {
+        g_create_error = c->err.empty() ? "allocation failed" : c->err;
+        ht_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HT_OK;
+}
+
+void ht_destroy(ht_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    double** v64[] = {&c->h, &c->T, &c->g[0], &c->g[1], &c->Fstat[0], &c->Fstat[1], &c->F[0], &c->F[1],
+                      &c->extra[0], &c->extra[1], &c->x, &c->r, &c->z, &c->p, &c->q, &c->b, &c->D,
+                      &c->rh, &c->v, &c->s, &c->tv, &c->ph, &c->sh, &c->z2, &c->K64, &c->lam64,
+                      &c->cT64, &c->qs64, &c->part, &c->pile_w, &c->well_d};
+    for (double** pp : v64) dfree(*pp);
+    float** v32[] = {&c->x32, &c->r32, &c->z32, &c->p32, &c->q32, &c->D32, &c->rh32, &c->v32, &c->s32,
+                     &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32, &c->K32, &c->lam32, &c->cT32, &c->qs32};
+    for (float** pp : v32) dfree(*pp);
+    dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
+    dfree(c->scal);
+    if (c->scal_host) cudaFreeHost(c->scal_host);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* ht_last_error(const ht_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+int ht_sizes(const ht_ctx* c, size_t* n_nodes, size_t* n_cells) {
+    if (!c) return HT_EINVAL;
+    if (n_nodes) *n_nodes = (size_t)c->grid.nn;
+    if (n_cells) *n_cells = (size_t)c->grid.nc;
+    return HT_OK;
+}
+
+int ht_set_cells(ht_ctx* c, const double* K, const double* lambda, const double* cT, double lambda_u,
+                 double cT_u, double cw, double Ss) {
+    if (!c || !K) return HT_EINVAL;
+    cudaSetDevice(c->device);
+    const size_t nc = (size_t)c->grid.nc;
+    if (!finite_pos(K, nc)) return fail(c, HT_EINVAL, "K must be positive and finite in every cell");
+    if (lambda && !finite_pos(lambda, nc)) return fail(c, HT_EINVAL, "lambda must be positive and finite");
+    if (cT && !finite_pos(cT, nc)) return fail(c, HT_EINVAL, "cT must be positive and finite");
+    if ((!lambda && !(lambda_u > 0)) || (!cT && !(cT_u > 0)) || !(cw >= 0) || !(Ss > 0) || !isfinite(cw) ||
+        !isfinite(Ss) || !isfinite(lambda_u) || !isfinite(cT_u))
+        return fail(c, HT_EINVAL, "uniform coefficients must be positive and finite");
+    HT_TRY(upload_cells(c, &c->K64, &c->K32, K, nc));
+    if (lambda) HT_TRY(upload_cells(c, &c->lam64, &c->lam32, lambda, nc));
+    else { dfree(c->lam64); dfree(c->lam32); }
+    if (cT) HT_TRY(upload_cells(c, &c->cT64, &c->cT32, cT, nc));
+    else { dfree(c->cT64); dfree(c->cT32); }
+    c->lam_u = lambda_u;
+    c->cT_u = cT_u;
+    c->cw = cw;
+    c->Ss = Ss;
+    c->cells_set = true;
+    c->loads_dirty = true;   // well heat terms depend on c_w
+    return HT_OK;
+}
+
+int ht_set_bc(ht_ctx* c, int field, int face, int type, double value) {
+    if (!c) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    if (face < 0 || face > 5) return fail(c, HT_EINVAL, "face must be 0..5");
+    if (type < HT_BC_NONE || type > HT_BC_FLUX) return fail(c, HT_EINVAL, "unknown boundary type %d", type);
+    if (!isfinite(value)) return fail(c, HT_EINVAL, "boundary value must be finite");
+    c->bc_type[field][face] = type;
+    c->bc_val[field][face] = value;
+    c->bc_dirty = true;
+    return HT_OK;
+}
+
+int ht_set_state(ht_ctx* c, const double* h, const double* T, double t, int on_device) {
+    if (!c) return HT_EINVAL;
+    if (!isfinite(t)) return fail(c, HT_EINVAL, "time must be finite");
+    cudaSetDevice(c->device);
+    const size_t n = (size_t)c->grid.nn;
+    if (h) HT_TRY(copy_in(c, c->h, h, n, on_device));
+    if (T) HT_TRY(copy_in(c, c->T, T, n, on_device));
+    c->t = t;
+    return HT_OK;
+}
+
+int ht_add_line_sources(ht_ctx* c, int n, const ht_line_src* src) {
+    if (!c || n < 0 || (n > 0 && !src)) return HT_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const ht_line_src& s = src[i];
+        if (!(s.z_top > s.z_bot) || !isfinite(s.mean) || !isfinite(s.amp) || !(s.period > 0) || !isfinite(s.phase))
+            return fail(c, HT_EINVAL, "line source %d: invalid parameters", i);
+        std::map<long long, double> probe;
+        HT_TRY(line_weights(c, s.x, s.y, s.z_top, s.z_bot, probe, "line source"));
+    }
+    c->piles.insert(c->piles.end(), src, src + n);
+    c->loads_dirty = true;
+    return HT_OK;
+}
+
+int ht_add_wells(ht_ctx* c, int n, const ht_well* w) {
+    if (!c || n < 0 || (n > 0 && !w)) return HT_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!isfinite(w[i].Q) || !isfinite(w[i].T_in)) return fail(c, HT_EINVAL, "well %d: invalid parameters", i);
+        std::map<long long, double> probe;
+        HT_TRY(line_weights(c, w[i].x, w[i].y, w[i].z_top, w[i].z_bot, probe, "well"));
+    }
+    c->wells.insert(c->wells.end(), w, w + n);
+    c->loads_dirty = true;
+    return HT_OK;
+}
+
+int ht_set_extra_rhs(ht_ctx* c, int field, const double* F, int on_device) {
+    if (!c) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    cudaSetDevice(c->device);
+    const size_t n = (size_t)c->grid.nn;
+    if (!F) {
+        HT_CUDA(c, cudaMemsetAsync(c->extra[field], 0, n * sizeof(double), c->stream));
+        return HT_OK;
+    }
+    return copy_in(c, c->extra[field], F, n, on_device);
+}
+
+int ht_set_solver(ht_ctx* c, const ht_solver_opts* o) {
+    if (!c || !o) return HT_EINVAL;
+    if (!(o->tol > 0) || o->max_iter < 1) return fail(c, HT_EINVAL, "tol > 0 and max_iter >= 1 required");
+    if (o->precision != HT_FP64 && o->precision != HT_MIXED) return fail(c, HT_EINVAL, "unknown precision");
+    if (o->krylov != HT_KRYLOV_BICGSTAB) return fail(c, HT_EINVAL, "unsupported Krylov method %d", o->krylov);
+    if (o->precond != HT_PREC_JACOBI && o->precond != HT_PREC_CHEBYSHEV)
+        return fail(c, HT_EINVAL, "unknown preconditioner");
+    if (o->precond == HT_PREC_CHEBYSHEV && (o->cheb_degree < 1 || o->cheb_degree > 32))
+        return fail(c, HT_EINVAL, "cheb_degree must be 1..32");
+    c->opts = *o;
+    return HT_OK;
+}
+
+int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
+    if (!c) return HT_EINVAL;
+    if (!(dt > 0) || !isfinite(dt)) return fail(c, HT_EINVAL, "dt must be positive");
+    cudaSetDevice(c->device);
+    HT_TRY(finalize_setup(c));
+    cudaEvent_t ev[4];
+    for (auto& e : ev) HT_CUDA(c, cudaEventCreate(&e));
+    const size_t n = (size_t)c->grid.nn;
+    const double t1 = c->t + dt;
+    ht_step_stats s{};
+    int rc = HT_OK;
+    cudaEventRecord(ev[0], c->stream);
+    rc = launch_loads(c, t1);
+    cudaEventRecord(ev[1], c->stream);
+    // head: b = S_s M h^n + dt F_h lifted; x0 = h^n with Dirichlet values
+    if (rc == HT_OK) rc = launch_rhs(c, HT_HEAD, dt, c->h, c->b);
+    if (rc == HT_OK && cudaMemcpyAsync(c->x, c->h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        rc = fail(c, HT_ECUDA, "copy failed");
+    if (rc == HT_OK) rc = set_dirichlet_values(c, HT_HEAD, c->x);
+    if (rc == HT_OK) rc = solve_head(c, dt, c->x, c->b, &s.iters_head, &s.outer_head, &s.res_head);
+    int rc_head = rc;
+    if (rc == HT_OK || rc == HT_ENOCONV)
+        if (cudaMemcpyAsync(c->h, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            rc = fail(c, HT_ECUDA, "copy failed");
+    cudaEventRecord(ev[2], c->stream);
+    if (rc == HT_OK) {
+        // heat with q = -K grad h^{n+1}
+        rc = launch_darcy_qp(c, c->h);
+        if (rc == HT_OK) rc = launch_rhs(c, HT_TEMP, dt, c->T, c->b);
+        if (rc == HT_OK && cudaMemcpyAsync(c->x, c->T, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            rc = fail(c, HT_ECUDA, "copy failed");
+        if (rc == HT_OK) rc = set_dirichlet_values(c, HT_TEMP, c->x);
+        if (rc == HT_OK) rc = solve_heat(c, dt, c->x, c->b, &s.iters_heat, &s.outer_heat, &s.res_heat);
+        if (rc == HT_OK || rc == HT_ENOCONV)
+            if (cudaMemcpyAsync(c->T, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                rc = fail(c, HT_ECUDA, "copy failed");
+    }
+    cudaEventRecord(ev[3], c->stream);
+    cudaEventSynchronize(ev[3]);
+    float ms;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]); s.ms_loads = ms;
+    cudaEventElapsedTime(&ms, ev[1], ev[2]); s.ms_head = ms;
+    cudaEventElapsedTime(&ms, ev[2], ev[3]); s.ms_heat = ms;
+    cudaEventElapsedTime(&ms, ev[0], ev[3]); s.ms_total = ms;
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc == HT_OK || rc == HT_ENOCONV) c->t = t1;
+    s.t = c->t;
+    s.status = rc;
+    if (st) *st = s;
+    (void)rc_head;
+    return rc;
+}
+
+int ht_get_field(ht_ctx* c, int field, double* dst, size_t n, int on_device) {
+    if (!c || !dst) return HT_EINVAL;
+    cudaSetDevice(c->device);
+    if (field == HT_HEAD || field == HT_TEMP) {
+        if (n != (size_t)c->grid.nn) return fail(c, HT_EINVAL, "size %zu != node count %lld", n, c->grid.nn);
+        return copy_out(c, dst, field == HT_HEAD ? c->h : c->T, n, on_device);
+    }
+    if (field >= HT_QX && field <= HT_QZ) {
+        if (n != (size_t)c->grid.nc) return fail(c, HT_EINVAL, "size %zu != cell count %lld", n, c->grid.nc);
+        if (!c->cells_set) return fail(c, HT_EINVAL, "cells not set");
+        HT_TRY(launch_cell_flux(c, c->h, field - HT_QX, c->z));
+        return copy_out(c, dst, c->z, n, on_device);
+    }
+    return fail(c, HT_EINVAL, "unknown field %d", field);
+}
+
+int ht_get_time(const ht_ctx* c, double* t) {
+    if (!c || !t) return HT_EINVAL;
+    *t = c->t;
+    return HT_OK;
+}
+
+int ht_apply(ht_ctx* c, int field, double dt, const double* x, double* y, int on_device) {
+    if (!c || !x || !y) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    if (!(dt > 0)) return fail(c, HT_EINVAL, "dt must be positive");
+    cudaSetDevice(c->device);
+    HT_TRY(finalize_setup(c));
+    const size_t n = (size_t)c->grid.nn;
+    HT_TRY(copy_in(c, c->z, x, n, on_device));
+    if (field == HT_TEMP) HT_TRY(launch_darcy_qp(c, c->h));
+    HT_TRY(launch_apply64(c, field, dt, c->z, c->q, nullptr, nullptr, nullptr));
+    return copy_out(c, y, c->q, n, on_device);
+}
+
+int ht_diag(ht_ctx* c, int field, double dt, double* d, int on_device) {
+    if (!c || !d) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    cudaSetDevice(c->device);
+    HT_TRY(finalize_setup(c));
+    if (field == HT_TEMP) HT_TRY(launch_darcy_qp(c, c->h));
+    HT_TRY(launch_diag(c, field, dt, c->q));
+    return copy_out(c, d, c->q, (size_t)c->grid.nn, on_device);
+}
+
+int ht_rhs(ht_ctx* c, int field, double dt, double* b, int on_device) {
+    if (!c || !b) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    cudaSetDevice(c->device);
+    HT_TRY(finalize_setup(c));
+    HT_TRY(launch_loads(c, c->t + dt));
+    if (field == HT_TEMP) HT_TRY(launch_darcy_qp(c, c->h));
+    HT_TRY(launch_rhs(c, field, dt, field == HT_HEAD ? c->h : c->T, c->q));
+    return copy_out(c, b, c->q, (size_t)c->grid.nn, on_device);
+}
+
+int ht_mixture(double phi, double lambda_s, double lambda_w, double c_s, double c_w, double* lambda, double* cT) {
+    if (!lambda || !cT || !(phi >= 0 && phi <= 1)) return HT_EINVAL;
+    *lambda = (1.0 - phi) * lambda_s + phi * lambda_w;
+    *cT = (1.0 - phi) * c_s + phi * c_w;
+    return HT_OK;
+}
+
+double ht_specific_storage(double B_poro, double rho_w, double g) { return rho_w * g / B_poro; }
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ht.h"
+
+namespace ht {
+
+// ---------------------------------------------------------------------------
+// Mesh description passed by value to every kernel.
+// ---------------------------------------------------------------------------
+struct Grid {
+    int P;                      // element order (1 or 2)
+    int ncx, ncy, ncz;          // cells per direction
+    int Nx, Ny, Nz;             // nodes per direction (P*nc + 1)
+    long long nn, nc;           // node and cell counts
+    int dmask;                  // Dirichlet faces of the field (bit f = face f)
+};
+
+// Reference-element constants for a uniform axis-aligned cell.
+//   B[q][a], D[q][a]: 1D Lagrange values / derivatives (w.r.t. the reference
+//   coordinate on [0,1]) at the (P+1) Gauss points.
+//   W[q]: 3D Gauss weight times the cell volume.
+//   G[d], Lam[d]: fast-diagonalisation factors of the 1D pair (k_d, m_d):
+//   m_d = G^T G, k_d = G^T diag(Lam) G, so that the cell matrix
+//   alpha M_e + beta K_e = (Gx (x) Gy (x) Gz)^T diag(alpha + beta*(Lx+Ly+Lz))
+//   (Gx (x) Gy (x) Gz) -- sum factorisation in the 1D eigenbasis.
+//   dM, dK: diagonals of the cell mass / stiffness matrices.
+template <typename T>
+struct Elem {
+    T G[3][3][3];
+    T Lam[3][3];
+    T B[3][3];
+    T D[3][3];
+    T W[27];
+    T invH[3];
+    T dM[27];
+    T dK[27];
+};
+
+// Device-resident scalars of one Krylov solve.
+struct Scal {
+    double bb, rr, rz, rz_new, pq, alpha, beta;
+    double rho, rho_old, omega, rv, ts, tt, rr0;
+    double cheb_theta, cheb_delta;
+    int done, iters, status, restarts;
+};
+
+enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NAN = 2 };
+
+}  // namespace ht
+
+// ---------------------------------------------------------------------------
+// The context behind the opaque ht_ctx handle.
+// ---------------------------------------------------------------------------
+struct ht_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    ht_mesh mesh{};
+    ht::Grid grid{};
+    double H[3] = {0, 0, 0};
+    ht::Elem<double> e64{};
+    ht::Elem<float> e32{};
+    int num_sms = 0;
+
+    // coefficients
+    double* K64 = nullptr;
+    float* K32 = nullptr;
+    double* lam64 = nullptr;    // optional per-cell
+    double* cT64 = nullptr;
+    float* lam32 = nullptr;
+    float* cT32 = nullptr;
+    double lam_u = 0, cT_u = 0, cw = 0, Ss = 0;
+    bool cells_set = false;
+
+    // boundary conditions
+    int bc_type[2][6] = {{0}};
+    double bc_val[2][6] = {{0}};
+    int dmask[2] = {0, 0};
+    double* g[2] = {nullptr, nullptr};     // nodal Dirichlet values (0 off the mask)
+    bool bc_dirty = true;
+
+    // state
+    double* h = nullptr;
+    double* T = nullptr;
+    double t = 0.0;
+
+    // loads
+    double* Fstat[2] = {nullptr, nullptr};   // time-independent nodal loads
+    double* F[2] = {nullptr, nullptr};       // loads at the current step time
+    double* extra[2] = {nullptr, nullptr};
+    std::vector<ht_line_src> piles;
+    std::vector<ht_well> wells;
+    bool loads_dirty = true;
+    int n_pile_nodes = 0;
+    int* pile_node = nullptr;
+    int* pile_off = nullptr;
+    int* pile_src = nullptr;
+    double* pile_w = nullptr;
+    ht_line_src* d_piles = nullptr;
+    int n_well_nodes = 0;
+    int* well_node = nullptr;
+    double* well_d = nullptr;               // c_w Q/L int N_i dz (heat, injection)
+
+    // Darcy flux at Gauss points [3*nq^3][cells]
+    double* qs64 = nullptr;
+    float* qs32 = nullptr;
+
+    // Krylov workspace
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    double *b = nullptr, *D = nullptr, *rh = nullptr, *v = nullptr, *s = nullptr;
+    double *tv = nullptr, *ph = nullptr, *sh = nullptr, *z2 = nullptr;
+    float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float *D32 = nullptr, *rh32 = nullptr, *v32 = nullptr, *s32 = nullptr, *t32 = nullptr;
+    float *ph32 = nullptr, *sh32 = nullptr, *zz32 = nullptr, *d32 = nullptr;
+    double* part = nullptr;       // partial sums [8][part_stride]
+    int part_stride = 0;
+    ht::Scal* scal = nullptr;
+    ht::Scal* scal_host = nullptr;  // pinned mirror
+    double cheb_lmax[2] = {0, 0};
+    double cheb_dt[2] = {-1, -1};
+
+    ht_solver_opts opts{};
+    std::string err;
+};
+
+namespace ht {
+
+// error helpers (host)
+int fail(ht_ctx* c, int code, const char* fmt, ...);
+#define HT_CUDA(ctx, call)                                                        \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess)                                                    \
+            return ::ht::fail((ctx), HT_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, \
+                              #call, cudaGetErrorString(e_));                     \
+    } while (0)
+#define HT_TRY(expr)              \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != HT_OK) return rc_; \
+    } while (0)
+
+constexpr int kVecBlocksPerSM = 4;
+constexpr int kVecThreads = 256;
+int vec_grid(const ht_ctx* c);
+
+// ---- operator launchers (ht_ops.cu) ---------------------------------------
+// Operator modes
+enum { MODE_APPLY = 0, MODE_RHS = 1, MODE_DIAG = 2 };
+
+// y = A0 x for the head (field 0) or heat (field 1) operator, FP64 or FP32.
+// If dot_part != nullptr each tile writes sum_i x_i y_i into dot_part[tile].
+// If sc != nullptr the kernels return at once when sc->done is set.
+int launch_apply64(ht_ctx* c, int field, double dt, const double* x, double* y,
+                   double* dot_part, int* n_part, const Scal* sc = nullptr);
+int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y,
+                   double* dot_part, int* n_part, const Scal* sc = nullptr);
+// b = lifted right-hand side of the next step of `field` (uses F[field]).
+int launch_rhs(ht_ctx* c, int field, double dt, const double* u_old, double* b);
+// D = diagonal of A0.
+int launch_diag(ht_ctx* c, int field, double dt, double* D);
+// qs = -K grad h at Gauss points (both precisions).
+int launch_darcy_qp(ht_ctx* c, const double* h);
+// q at cell centres for output, component comp (0..2)
+int launch_cell_flux(ht_ctx* c, const double* h, int comp, double* out);
+// heat injection-well diagonal: y += dt * d .* x on the listed free nodes
+int launch_well_apply64(ht_ctx* c, double dt, const double* x, double* y, const Scal* sc);
+int launch_well_apply32(ht_ctx* c, float dt, const float* x, float* y, const Scal* sc);
+int launch_well_diag(ht_ctx* c, double dt, double* D);
+// F[field] = Fstat + extra + pile loads at time t
+int launch_loads(ht_ctx* c, double t);
+int apply_tiles(const ht_ctx* c);
+
+// ---- Krylov (ht_krylov.cu) -------------------------------------------------
+int solve_head(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);
+int solve_heat(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);
+int true_residual(ht_ctx* c, int field, double dt, const double* x, const double* b, double* rel);
+int set_dirichlet_values(ht_ctx* c, int field, double* x);
+
+}  // namespace ht

@@ -1,0 +1,560 @@
+// Krylov solvers of the per-step linear systems: Jacobi- or Chebyshev-Jacobi-
+// preconditioned CG for the symmetric head system (Eq. 3) and Jacobi-
+// preconditioned BiCGStab for the nonsymmetric heat system (Eq. 4); plain
+// FP64, or FP32 inner iterations inside an FP64 defect-correction loop.
+//
+// All scalars live on the device (struct Scal).  Vector kernels write one
+// partial sum per CTA; a single-CTA scalar kernel reduces them in a fixed
+// order and updates alpha / beta / omega, so every result is bitwise
+// reproducible.  Kernels return at once when the solve is marked done, which
+// lets the host enqueue several iterations between convergence checks.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include "ht_internal.cuh"
+
+namespace ht {
+
+int vec_grid(const ht_ctx* c) {
+    const long long need = (c->grid.nn + kVecThreads - 1) / kVecThreads;
+    long long g = (long long)(c->num_sms > 0 ? c->num_sms : 148) * kVecBlocksPerSM;
+    if (need < g) g = need;
+    return (int)(g < 1 ? 1 : g);
+}
+
+namespace {
+
+__device__ __forceinline__ double bsum(double v) {
+    __shared__ double ws[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? ws[lane] : 0.0;
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// ---- scalar kernel ----------------------------------------------------------
+enum {
+    SC_CG_INIT, SC_CG_ALPHA, SC_CG_BETA,
+    SC_BI_INIT, SC_BI_ALPHA, SC_BI_OMEGA, SC_BI_BETA,
+    SC_NORMS
+};
+
+__device__ double reduce_part(const double* part, int np) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+    return bsum(s);
+}
+
+// part: [8][stride]; slot usage documented per opcode
+__global__ void scalar_kernel(int op, const double* __restrict__ part, int stride, int np,
+                              Scal* __restrict__ s, double tol2, int max_iter) {
+    if (s->done && op != SC_NORMS) return;
+    const double a0 = reduce_part(part + 0 * (size_t)stride, np);
+    const double a1 = reduce_part(part + 1 * (size_t)stride, np);
+    const double a2 = reduce_part(part + 2 * (size_t)stride, np);
+    if (threadIdx.x != 0) return;
+    switch (op) {
+        case SC_CG_INIT:  // a0 = r.z, a1 = r.r, a2 = b.b
+            s->rz = a0; s->rr = a1; s->bb = a2; s->rr0 = a1;
+            s->iters = 0; s->status = ST_OK;
+            s->done = (a1 <= tol2 * a2 || a2 == 0.0) ? 1 : 0;
+            if (!isfinite(a0) || !isfinite(a1)) { s->status = ST_NAN; s->done = 1; }
+            break;
+        case SC_CG_ALPHA:  // a0 = p.Ap
+            s->pq = a0;
+            if (!(a0 > 0.0) || !isfinite(a0)) { s->status = ST_BREAKDOWN; s->done = 1; break; }
+            s->alpha = s->rz / a0;
+            break;
+        case SC_CG_BETA:  // a1 = r.z (new), a2 = r.r
+            s->rz_new = a1; s->rr = a2;
+            s->beta = a1 / s->rz;
+            s->rz = a1;
+            s->iters += 1;
+            if (!isfinite(a1) || !isfinite(a2)) { s->status = ST_NAN; s->done = 1; }
+            else if (a2 <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
+            break;
+        case SC_BI_INIT:  // a0 = rh.r, a1 = r.r, a2 = b.b
+            s->rho = a0; s->rr = a1; s->bb = a2; s->rr0 = a1;
+            s->alpha = 1.0; s->omega = 1.0; s->beta = 0.0;
+            s->iters = 0; s->status = ST_OK;
+            s->done = (a1 <= tol2 * a2 || a2 == 0.0) ? 1 : 0;
+            if (!isfinite(a0) || !isfinite(a1)) { s->status = ST_NAN; s->done = 1; }
+            break;
+        case SC_BI_ALPHA:  // a0 = rh.v
+            s->rv = a0;
+            if (a0 == 0.0 || !isfinite(a0)) { s->status = ST_BREAKDOWN; s->done = 1; break; }
+            s->alpha = s->rho / a0;
+            break;
+        case SC_BI_OMEGA:  // a0 = t.s, a1 = t.t, a2 = s.s
+            s->ts = a0; s->tt = a1;
+            if (a1 == 0.0) {  // s = 0 exactly: x += alpha ph is the solution
+                s->omega = 0.0;
+            } else {
+                s->omega = a0 / a1;
+            }
+            break;
+        case SC_BI_BETA: {  // a0 = rh.r (new), a1 = r.r
+            s->rr = a1;
+            s->iters += 1;
+            if (!isfinite(a0) || !isfinite(a1)) { s->status = ST_NAN; s->done = 1; break; }
+            if (a1 <= tol2 * s->bb || s->iters >= max_iter) { s->done = 1; break; }
+            if (a0 == 0.0 || s->omega == 0.0) { s->status = ST_BREAKDOWN; s->done = 1; break; }
+            s->beta = (a0 / s->rho) * (s->alpha / s->omega);
+            s->rho = a0;
+            break;
+        }
+        case SC_NORMS:  // a0 = r.r, a1 = b.b
+            s->rr = a0; s->bb = a1;
+            break;
+    }
+}
+
+// ---- vector kernels -----------------------------------------------------------
+#define GRID_LOOP(i, n) \
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+template <typename T>
+__device__ __forceinline__ void write3(double* part, int stride, T v0, T v1, T v2) {
+    const double s0 = bsum((double)v0);
+    const double s1 = bsum((double)v1);
+    const double s2 = bsum((double)v2);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s0;
+        part[stride + blockIdx.x] = s1;
+        part[2 * stride + blockIdx.x] = s2;
+    }
+}
+
+// r = b - q; z = Dinv r; p = z.  part: r.z, r.r, b.b
+template <typename T>
+__global__ void cg_init_kernel(long long n, const T* __restrict__ b, const T* __restrict__ q,
+                               const T* __restrict__ Dinv, T* __restrict__ r, T* __restrict__ p,
+                               double* __restrict__ part, int stride) {
+    T rz = 0, rr = 0, bb = 0;
+    GRID_LOOP(i, n) {
+        const T bi = b[i];
+        const T ri = bi - q[i];
+        const T zi = Dinv[i] * ri;
+        r[i] = ri;
+        p[i] = zi;
+        rz = fma(ri, zi, rz);
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    write3<T>(part, stride, rz, rr, bb);
+}
+
+// x += alpha p; r -= alpha q; z = Dinv r.  part[1] = r.z, part[2] = r.r
+template <typename T>
+__global__ void cg_update_kernel(long long n, T* __restrict__ x, T* __restrict__ r,
+                                 const T* __restrict__ p, const T* __restrict__ q,
+                                 const T* __restrict__ Dinv, const Scal* __restrict__ s,
+                                 double* __restrict__ part, int stride) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha;
+    T rz = 0, rr = 0;
+    GRID_LOOP(i, n) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rz = fma(ri, Dinv[i] * ri, rz);
+        rr = fma(ri, ri, rr);
+    }
+    write3<T>(part, stride, T(0), rz, rr);
+}
+
+// p = Dinv r + beta p
+template <typename T>
+__global__ void cg_pupdate_kernel(long long n, const T* __restrict__ r, const T* __restrict__ Dinv,
+                                  T* __restrict__ p, const Scal* __restrict__ s) {
+    if (s->done) return;
+    const T beta = (T)s->beta;
+    GRID_LOOP(i, n) p[i] = fma(beta, p[i], Dinv[i] * r[i]);
+}
+
+// BiCGStab
+// r = b - q; rh = r; p = v = 0.  part: rh.r, r.r, b.b
+template <typename T>
+__global__ void bi_init_kernel(long long n, const T* __restrict__ b, const T* __restrict__ q,
+                               T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
+                               T* __restrict__ v, double* __restrict__ part, int stride) {
+    T rr = 0, bb = 0;
+    GRID_LOOP(i, n) {
+        const T bi = b[i];
+        const T ri = bi - q[i];
+        r[i] = ri;
+        rh[i] = ri;
+        p[i] = T(0);
+        v[i] = T(0);
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    write3<T>(part, stride, rr, rr, bb);
+}
+
+// p = r + beta (p - omega v); ph = Dinv p
+template <typename T>
+__global__ void bi_p_kernel(long long n, const T* __restrict__ r, T* __restrict__ p,
+                            const T* __restrict__ v, const T* __restrict__ Dinv, T* __restrict__ ph,
+                            const Scal* __restrict__ s) {
+    if (s->done) return;
+    const T beta = (T)s->beta, omega = (T)s->omega;
+    GRID_LOOP(i, n) {
+        const T pi = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+        p[i] = pi;
+        ph[i] = Dinv[i] * pi;
+    }
+}
+
+// part[0] = a.b
+template <typename T>
+__global__ void dot_kernel(long long n, const T* __restrict__ a, const T* __restrict__ b,
+                           double* __restrict__ part, int stride, const Scal* __restrict__ s) {
+    if (s && s->done) return;
+    T d = 0;
+    GRID_LOOP(i, n) d = fma(a[i], b[i], d);
+    write3<T>(part, stride, d, T(0), T(0));
+}
+
+// s = r - alpha v; sh = Dinv s
+template <typename T>
+__global__ void bi_s_kernel(long long n, const T* __restrict__ r, const T* __restrict__ v,
+                            const T* __restrict__ Dinv, T* __restrict__ sv, T* __restrict__ sh,
+                            const Scal* __restrict__ s) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha;
+    GRID_LOOP(i, n) {
+        const T si = fma(-alpha, v[i], r[i]);
+        sv[i] = si;
+        sh[i] = Dinv[i] * si;
+    }
+}
+
+// part: t.s, t.t, s.s
+template <typename T>
+__global__ void bi_ts_kernel(long long n, const T* __restrict__ t, const T* __restrict__ sv,
+                             double* __restrict__ part, int stride, const Scal* __restrict__ s) {
+    if (s->done) return;
+    T ts = 0, tt = 0, ss = 0;
+    GRID_LOOP(i, n) {
+        const T ti = t[i], si = sv[i];
+        ts = fma(ti, si, ts);
+        tt = fma(ti, ti, tt);
+        ss = fma(si, si, ss);
+    }
+    write3<T>(part, stride, ts, tt, ss);
+}
+
+// x += alpha ph + omega sh; r = s - omega t.  part: rh.r, r.r
+template <typename T>
+__global__ void bi_xr_kernel(long long n, T* __restrict__ x, T* __restrict__ r,
+                             const T* __restrict__ ph, const T* __restrict__ sh,
+                             const T* __restrict__ sv, const T* __restrict__ t,
+                             const T* __restrict__ rh, double* __restrict__ part, int stride,
+                             const Scal* __restrict__ s) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha, omega = (T)s->omega;
+    T rhr = 0, rr = 0;
+    GRID_LOOP(i, n) {
+        x[i] = fma(alpha, ph[i], fma(omega, sh[i], x[i]));
+        const T ri = fma(-omega, t[i], sv[i]);
+        r[i] = ri;
+        rhr = fma(rh[i], ri, rhr);
+        rr = fma(ri, ri, rr);
+    }
+    write3<T>(part, stride, rhr, rr, T(0));
+}
+
+// ---- mixed precision helpers ---------------------------------------------------
+// r = b - q (FP64); r32 = (float) r.  part: r.r, b.b
+__global__ void resid_kernel(long long n, const double* __restrict__ b, const double* __restrict__ q,
+                             double* __restrict__ r, float* __restrict__ r32,
+                             double* __restrict__ part, int stride) {
+    double rr = 0, bb = 0;
+    GRID_LOOP(i, n) {
+        const double bi = b[i];
+        const double ri = bi - q[i];
+        if (r) r[i] = ri;
+        if (r32) r32[i] = (float)ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    write3<double>(part, stride, rr, bb, 0.0);
+}
+
+__global__ void add_f32_kernel(long long n, double* __restrict__ x, const float* __restrict__ d) {
+    GRID_LOOP(i, n) x[i] += (double)d[i];
+}
+
+template <typename T>
+__global__ void fill_kernel(long long n, T* __restrict__ x, T v) {
+    GRID_LOOP(i, n) x[i] = v;
+}
+
+// Dinv = 1 / D in both precisions
+__global__ void inv_kernel(long long n, const double* __restrict__ D, double* __restrict__ Dinv,
+                           float* __restrict__ Dinv32) {
+    GRID_LOOP(i, n) {
+        const double v = 1.0 / D[i];
+        Dinv[i] = v;
+        Dinv32[i] = (float)v;
+    }
+}
+
+__global__ void dirichlet_kernel(const Grid g, const double* __restrict__ gv, double* __restrict__ x) {
+    GRID_LOOP(id, g.nn) {
+        const int i = (int)(id % g.Nx);
+        const int j = (int)((id / g.Nx) % g.Ny);
+        const int k = (int)(id / ((long long)g.Nx * g.Ny));
+        const int m = g.dmask;
+        const bool d = ((m & 1) && i == 0) || ((m & 2) && i == g.Nx - 1) || ((m & 4) && j == 0) ||
+                       ((m & 8) && j == g.Ny - 1) || ((m & 16) && k == 0) || ((m & 32) && k == g.Nz - 1);
+        if (d) x[id] = gv[id];
+    }
+}
+
+// ---- host drivers -------------------------------------------------------------
+int sync_scal(ht_ctx* c, int slot) {
+    HT_CUDA(c, cudaMemcpyAsync(c->scal_host + slot, c->scal + slot, sizeof(Scal), cudaMemcpyDeviceToHost,
+                               c->stream));
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HT_OK;
+}
+
+int scalar(ht_ctx* c, int op, int np, int slot, double tol, int max_iter) {
+    scalar_kernel<<<1, 256, 0, c->stream>>>(op, c->part, c->part_stride, np, c->scal + slot, tol * tol,
+                                            max_iter);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+struct Vecs64 {
+    double *x, *r, *p, *q, *Dinv, *rh, *v, *s, *t, *ph, *sh;
+};
+struct Vecs32 {
+    float *x, *r, *p, *q, *Dinv, *rh, *v, *s, *t, *ph, *sh;
+};
+
+template <typename T>
+int apply_T(ht_ctx* c, int field, double dt, const T* x, T* y, double* part, int* np, const Scal* sc);
+template <>
+int apply_T<double>(ht_ctx* c, int field, double dt, const double* x, double* y, double* part, int* np,
+                    const Scal* sc) {
+    return launch_apply64(c, field, dt, x, y, part, np, sc);
+}
+template <>
+int apply_T<float>(ht_ctx* c, int field, double dt, const float* x, float* y, double* part, int* np,
+                   const Scal* sc) {
+    return launch_apply32(c, field, (float)dt, x, y, part, np, sc);
+}
+
+// Preconditioned CG on A0 x = b (x holds the initial guess).  Returns
+// iterations in *iters; status in c->scal[slot].
+template <typename T, class V>
+int run_cg(ht_ctx* c, double dt, const V& w, const T* b, int slot, double tol, int max_iter, int* iters) {
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c);
+    const int S = c->part_stride;
+    Scal* sc = c->scal + slot;
+    int np = 0;
+    HT_TRY(apply_T<T>(c, HT_HEAD, dt, w.x, w.q, nullptr, nullptr, nullptr));
+    cg_init_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, b, w.q, w.Dinv, w.r, w.p, c->part, S);
+    HT_CUDA(c, cudaGetLastError());
+    HT_CUDA(c, cudaMemsetAsync(sc, 0, sizeof(Scal), c->stream));
+    HT_TRY(scalar(c, SC_CG_INIT, G, slot, tol, max_iter));
+    int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
+    HT_TRY(sync_scal(c, slot));
+    if (c->scal_host[slot].bb == 0.0) {  // b = 0: the solution is x = 0
+        fill_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, T(0));
+        HT_CUDA(c, cudaGetLastError());
+        *iters = 0;
+        return HT_OK;
+    }
+    while (!c->scal_host[slot].done) {
+        for (int k = 0; k < chunk; ++k) {
+            HT_TRY(apply_T<T>(c, HT_HEAD, dt, w.p, w.q, c->part, &np, sc));
+            HT_TRY(scalar(c, SC_CG_ALPHA, np, slot, tol, max_iter));
+            cg_update_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, w.r, w.p, w.q, w.Dinv, sc, c->part, S);
+            HT_TRY(scalar(c, SC_CG_BETA, G, slot, tol, max_iter));
+            cg_pupdate_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, w.Dinv, w.p, sc);
+        }
+        HT_CUDA(c, cudaGetLastError());
+        HT_TRY(sync_scal(c, slot));
+        if (chunk < 64) chunk *= 2;
+    }
+    *iters = c->scal_host[slot].iters;
+    return HT_OK;
+}
+
+template <typename T, class V>
+int run_bicgstab(ht_ctx* c, double dt, const V& w, const T* b, int slot, double tol, int max_iter,
+                 int* iters) {
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c);
+    const int S = c->part_stride;
+    Scal* sc = c->scal + slot;
+    int total = 0;
+    for (int restart = 0; restart < 3; ++restart) {
+        HT_TRY(apply_T<T>(c, HT_TEMP, dt, w.x, w.q, nullptr, nullptr, nullptr));
+        bi_init_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, b, w.q, w.r, w.rh, w.p, w.v, c->part, S);
+        HT_CUDA(c, cudaGetLastError());
+        HT_CUDA(c, cudaMemsetAsync(sc, 0, sizeof(Scal), c->stream));
+        HT_TRY(scalar(c, SC_BI_INIT, G, slot, tol, max_iter - total));
+        HT_TRY(sync_scal(c, slot));
+        if (c->scal_host[slot].bb == 0.0) {
+            fill_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, T(0));
+            HT_CUDA(c, cudaGetLastError());
+            break;
+        }
+        int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
+        while (!c->scal_host[slot].done) {
+            for (int k = 0; k < chunk; ++k) {
+                bi_p_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, w.p, w.v, w.Dinv, w.ph, sc);
+                HT_TRY(apply_T<T>(c, HT_TEMP, dt, w.ph, w.v, nullptr, nullptr, sc));
+                dot_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.rh, w.v, c->part, S, sc);
+                HT_TRY(scalar(c, SC_BI_ALPHA, G, slot, tol, max_iter - total));
+                bi_s_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, w.v, w.Dinv, w.s, w.sh, sc);
+                HT_TRY(apply_T<T>(c, HT_TEMP, dt, w.sh, w.t, nullptr, nullptr, sc));
+                bi_ts_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.t, w.s, c->part, S, sc);
+                HT_TRY(scalar(c, SC_BI_OMEGA, G, slot, tol, max_iter - total));
+                bi_xr_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, w.r, w.ph, w.sh, w.s, w.t, w.rh,
+                                                                  c->part, S, sc);
+                HT_TRY(scalar(c, SC_BI_BETA, G, slot, tol, max_iter - total));
+            }
+            HT_CUDA(c, cudaGetLastError());
+            HT_TRY(sync_scal(c, slot));
+            if (chunk < 32) chunk *= 2;
+        }
+        total += c->scal_host[slot].iters;
+        if (c->scal_host[slot].status != ST_BREAKDOWN) break;
+        // breakdown: restart from the current iterate with a fresh shadow residual
+    }
+    *iters = total;
+    return HT_OK;
+}
+
+int prepare_diag(ht_ctx* c, int field, double dt) {
+    HT_TRY(launch_diag(c, field, dt, c->z));
+    inv_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, c->z, c->D, c->D32);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int status_to_rc(ht_ctx* c, const Scal& s, double tol, const char* what) {
+    if (s.status == ST_NAN) return fail(c, HT_EINVAL, "%s: non-finite residual", what);
+    if (s.status == ST_BREAKDOWN) return fail(c, HT_EBREAKDOWN, "%s: Krylov breakdown", what);
+    if (s.bb > 0 && s.rr > tol * tol * s.bb)
+        return fail(c, HT_ENOCONV, "%s: no convergence in %d iterations (rel. residual %.3e)", what,
+                    s.iters, sqrt(s.rr / s.bb));
+    return HT_OK;
+}
+
+int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int* iters, int* outer,
+                double* res) {
+    const double tol = c->opts.tol;
+    const int max_iter = c->opts.max_iter;
+    const char* what = field == HT_HEAD ? "head solve" : "heat solve";
+    HT_TRY(prepare_diag(c, field, dt));
+    *iters = 0;
+    *outer = 0;
+    if (c->opts.precision == HT_FP64) {
+        Vecs64 w{x, c->r, c->p, c->q, c->D, c->rh, c->v, c->s, c->tv, c->ph, c->sh};
+        int it = 0;
+        if (field == HT_HEAD) HT_TRY((run_cg<double, Vecs64>(c, dt, w, b, 0, tol, max_iter, &it)));
+        else HT_TRY((run_bicgstab<double, Vecs64>(c, dt, w, b, 0, tol, max_iter, &it)));
+        *iters = it;
+        *outer = 1;
+        HT_TRY(true_residual(c, field, dt, x, b, res));
+        const Scal s = c->scal_host[0];
+        if (s.status == ST_NAN) return fail(c, HT_EINVAL, "%s: non-finite residual", what);
+        if (*res > tol * 1.0001 + 1e-300) {
+            if (s.status == ST_BREAKDOWN) return fail(c, HT_EBREAKDOWN, "%s: Krylov breakdown", what);
+            // the recursive residual converged but the true one did not: report it
+            if (s.iters >= max_iter)
+                return fail(c, HT_ENOCONV, "%s: no convergence in %d iterations (rel. residual %.3e)",
+                            what, s.iters, *res);
+        }
+        return HT_OK;
+    }
+    // mixed precision: FP64 defect correction around FP32 inner Krylov
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c);
+    const int S = c->part_stride;
+    const double inner_tol = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-4;
+    const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 30;
+    Vecs32 w{c->d32, c->r32, c->p32, c->q32, c->D32, c->rh32, c->v32, c->s32, c->t32, c->ph32, c->sh32};
+    int total = 0;
+    for (int k = 0; k <= max_outer; ++k) {
+        HT_TRY(launch_apply64(c, field, dt, x, c->q, nullptr, nullptr, nullptr));
+        resid_kernel<<<G, kVecThreads, 0, c->stream>>>(n, b, c->q, nullptr, c->r32, c->part, S);
+        HT_CUDA(c, cudaGetLastError());
+        scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, S, G, c->scal + 2, 0.0, 0);
+        HT_CUDA(c, cudaGetLastError());
+        HT_TRY(sync_scal(c, 2));
+        const Scal s = c->scal_host[2];
+        if (!isfinite(s.rr)) return fail(c, HT_EINVAL, "%s: non-finite residual", what);
+        *res = s.bb > 0 ? sqrt(s.rr / s.bb) : 0.0;
+        *outer = k;
+        if (s.rr <= tol * tol * s.bb) break;
+        if (k == max_outer || total >= max_iter)
+            return fail(c, HT_ENOCONV, "%s: mixed precision stalled at rel. residual %.3e after %d outer passes",
+                        what, *res, k);
+        fill_kernel<float><<<G, kVecThreads, 0, c->stream>>>(n, c->d32, 0.0f);
+        HT_CUDA(c, cudaGetLastError());
+        int it = 0;
+        if (field == HT_HEAD)
+            HT_TRY((run_cg<float, Vecs32>(c, dt, w, c->r32, 1, inner_tol, max_iter - total, &it)));
+        else
+            HT_TRY((run_bicgstab<float, Vecs32>(c, dt, w, c->r32, 1, inner_tol, max_iter - total, &it)));
+        total += it;
+        add_f32_kernel<<<G, kVecThreads, 0, c->stream>>>(n, x, c->d32);
+        HT_CUDA(c, cudaGetLastError());
+    }
+    *iters = total;
+    return HT_OK;
+}
+
+}  // namespace
+
+int true_residual(ht_ctx* c, int field, double dt, const double* x, const double* b, double* rel) {
+    const int G = vec_grid(c);
+    HT_TRY(launch_apply64(c, field, dt, x, c->q, nullptr, nullptr, nullptr));
+    resid_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid.nn, b, c->q, nullptr, nullptr, c->part,
+                                                    c->part_stride);
+    HT_CUDA(c, cudaGetLastError());
+    scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, c->part_stride, G, c->scal + 3, 0.0, 0);
+    HT_CUDA(c, cudaGetLastError());
+    HT_TRY(sync_scal(c, 3));
+    const Scal s = c->scal_host[3];
+    *rel = s.bb > 0 ? sqrt(s.rr / s.bb) : sqrt(s.rr);
+    return HT_OK;
+}
+
+int set_dirichlet_values(ht_ctx* c, int field, double* x) {
+    Grid g = c->grid;
+    g.dmask = c->dmask[field];
+    if (!g.dmask) return HT_OK;
+    dirichlet_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(g, c->g[field], x);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int solve_head(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res) {
+    return solve_field(c, HT_HEAD, dt, x, b, iters, outer, res);
+}
+
+int solve_heat(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res) {
+    return solve_field(c, HT_TEMP, dt, x, b, iters, outer, res);
+}
+
+}  // namespace ht

@@ -1,0 +1,815 @@
+// Matrix-free operator kernels of the head and heat systems on a structured
+// box of Q1 / Q2 hexahedra (Section 2, Eq. 3 and Eq. 4 in head / energy form).
+//
+// Tiling ("owner computes", deterministic, no atomics):
+//   * a CTA owns a TX x TY column of nodes (TX = P*(CXM-1), TY = P*(CYM-1))
+//     and a chunk of node planes in z;
+//   * it marches upward through the cell layers that touch its planes; in
+//     each layer one thread computes one cell (the CXM x CYM cells touching
+//     the owned columns, including a one-cell halo on the low side) and
+//     writes the element result to shared memory;
+//   * each owned node then sums the contributions of its (up to 4) cells of
+//     the layer in a fixed order, adds the carry of the plane it shares with
+//     the layer below and emits the finished planes.
+// Every node value is therefore produced by exactly one thread, in a fixed
+// summation order, and the kernels are bitwise reproducible.
+//
+// Cell work:
+//   * head operator alpha M_e + beta_c K_e (beta_c = dt K_c): sum
+//     factorisation in the 1D generalised eigenbasis of (k, m) ("fast
+//     diagonalisation"): three 1D transforms, one scaling per mode, three
+//     transposed transforms;
+//   * heat operator c_T M_e + dt lambda K_e + dt C_e(q): sum-factorised
+//     Gauss quadrature of the weak form of Eq. 4 with the Darcy flux
+//     q = -K_c grad h^{n+1} at the Gauss points.
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include "ht_internal.cuh"
+
+namespace ht {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool on_dir(const Grid& g, int i, int j, int k) {
+    const int m = g.dmask;
+    return ((m & 1) && i == 0) || ((m & 2) && i == g.Nx - 1) || ((m & 4) && j == 0) ||
+           ((m & 8) && j == g.Ny - 1) || ((m & 16) && k == 0) || ((m & 32) && k == g.Nz - 1);
+}
+
+__device__ __forceinline__ bool cell_touches_dir(const Grid& g, int cx, int cy, int cz) {
+    const int m = g.dmask;
+    return ((m & 1) && cx == 0) || ((m & 2) && cx == g.ncx - 1) || ((m & 4) && cy == 0) ||
+           ((m & 8) && cy == g.ncy - 1) || ((m & 16) && cz == 0) || ((m & 32) && cz == g.ncz - 1);
+}
+
+__device__ __forceinline__ long long nidx(const Grid& g, int i, int j, int k) {
+    return (long long)i + (long long)g.Nx * ((long long)j + (long long)g.Ny * k);
+}
+
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? ws[lane] : 0.0;
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// gather the element vector of cell (cx,cy,cz) from a nodal vector; nodes on
+// Dirichlet faces read as zero when `mask` is set.
+template <int P, typename T>
+__device__ __forceinline__ void gather(const Grid& g, const T* __restrict__ x, int cx, int cy,
+                                       int cz, bool mask, T (&u)[(P + 1) * (P + 1) * (P + 1)]) {
+    constexpr int n = P + 1;
+    const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
+    const bool chk = mask && cell_touches_dir(g, cx, cy, cz);
+#pragma unroll
+    for (int c = 0; c < n; ++c)
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+            const T* row = x + nidx(g, i0, j0 + b, k0 + c);
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                T v = ldro(row + a);
+                if (chk && on_dir(g, i0 + a, j0 + b, k0 + c)) v = T(0);
+                u[a + n * (b + n * c)] = v;
+            }
+        }
+}
+
+// 1D transforms of an n^3 array u[c][b][a] along one axis with matrix M
+// (TR: use M^T).  out[i] = sum_a M[i][a] in[a].
+template <int n, int AX, bool TR, typename T>
+__device__ __forceinline__ void sweep(T (&u)[n * n * n], const T (&M)[3][3]) {
+    constexpr int st = AX == 0 ? 1 : (AX == 1 ? n : n * n);
+#pragma unroll
+    for (int l = 0; l < n * n; ++l) {
+        // base index of the line: the two other coordinates
+        int base;
+        if (AX == 0) base = l * n;
+        else if (AX == 1) base = (l % n) + (l / n) * n * n;
+        else base = l;
+        T in[n], out[n];
+#pragma unroll
+        for (int a = 0; a < n; ++a) in[a] = u[base + a * st];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int a = 0; a < n; ++a) s = fma(TR ? M[a][i] : M[i][a], in[a], s);
+            out[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < n; ++i) u[base + i * st] = out[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Operators (cell computation + node emission)
+// ---------------------------------------------------------------------------
+template <int P, typename T, int MODE>
+struct HeadOp {
+    static constexpr int n = P + 1, NL = n * n * n;
+    const T* x;        // APPLY: input; RHS: u_old
+    const double* gD;  // RHS: Dirichlet values
+    const double* F;   // RHS: loads
+    T* y;
+    const T* K;
+    T alpha, dt;
+    Elem<T> e;
+
+    __device__ __forceinline__ void cell(const Grid& g, int cx, int cy, int cz, long long c,
+                                         T (&res)[NL]) const {
+        const T beta = dt * ldro(K + c);
+        if (MODE == MODE_DIAG) {
+#pragma unroll
+            for (int l = 0; l < NL; ++l) res[l] = fma(beta, e.dK[l], alpha * e.dM[l]);
+            return;
+        }
+        if (MODE == MODE_APPLY) {
+            gather<P, T>(g, x, cx, cy, cz, true, res);
+            sweep<n, 0, false>(res, e.G[0]);
+            sweep<n, 1, false>(res, e.G[1]);
+            sweep<n, 2, false>(res, e.G[2]);
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        const int l = a + n * (b + n * c2);
+                        res[l] *= fma(beta, e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][c2], alpha);
+                    }
+        } else {  // RHS: alpha M (u_old - g_D) - beta K g_D
+            T us[NL];
+            const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        const int l = a + n * (b + n * c2);
+                        const long long id = nidx(g, i0 + a, j0 + b, k0 + c2);
+                        const bool d = on_dir(g, i0 + a, j0 + b, k0 + c2);
+                        const T gv = d ? (T)gD[id] : T(0);
+                        res[l] = x[id] - gv;
+                        us[l] = gv;
+                    }
+            sweep<n, 0, false>(res, e.G[0]);
+            sweep<n, 1, false>(res, e.G[1]);
+            sweep<n, 2, false>(res, e.G[2]);
+            sweep<n, 0, false>(us, e.G[0]);
+            sweep<n, 1, false>(us, e.G[1]);
+            sweep<n, 2, false>(us, e.G[2]);
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        const int l = a + n * (b + n * c2);
+                        res[l] = alpha * res[l] -
+                                 beta * (e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][c2]) * us[l];
+                    }
+        }
+        sweep<n, 2, true>(res, e.G[2]);
+        sweep<n, 1, true>(res, e.G[1]);
+        sweep<n, 0, true>(res, e.G[0]);
+    }
+
+    __device__ __forceinline__ void emit(const Grid& g, int i, int j, int k, T val, T& dot) const {
+        const long long id = nidx(g, i, j, k);
+        const bool d = on_dir(g, i, j, k);
+        if (MODE == MODE_APPLY) {
+            const T xv = x[id];
+            const T yv = d ? xv : val;
+            y[id] = yv;
+            dot = fma(xv, yv, dot);
+        } else if (MODE == MODE_RHS) {
+            y[id] = d ? (T)gD[id] : val + dt * (T)F[id];
+        } else {
+            y[id] = d ? T(1) : val;
+        }
+    }
+};
+
+template <int P, typename T, int MODE>
+struct HeatOp {
+    static constexpr int n = P + 1, NL = n * n * n, NQ = n * n * n;
+    const T* x;        // APPLY: input; RHS: T_old
+    const double* gD;
+    const double* F;
+    T* y;
+    const T* qs;       // [3*NQ][nc]
+    const T* cTc;      // optional per-cell
+    const T* lamc;
+    T cT_u, lam_u, dt, cw;
+    Elem<T> e;
+
+    __device__ __forceinline__ void cell(const Grid& g, int cx, int cy, int cz, long long c,
+                                         T (&res)[NL]) const {
+        const T cT = cTc ? ldro(cTc + c) : cT_u;
+        const T dtlam = dt * (lamc ? ldro(lamc + c) : lam_u);
+        const T dtcw = dt * cw;
+        const long long nc = g.nc;
+        if (MODE == MODE_DIAG) {
+#pragma unroll
+            for (int l = 0; l < NL; ++l) res[l] = fma(dtlam, e.dK[l], cT * e.dM[l]);
+            for (int qz = 0; qz < n; ++qz)
+                for (int qy = 0; qy < n; ++qy)
+                    for (int qx = 0; qx < n; ++qx) {
+                        const int qi = qx + n * (qy + n * qz);
+                        const T w = e.W[qi] * dtcw;
+                        const T q0 = ldro(qs + (0 * NQ + qi) * nc + c);
+                        const T q1 = ldro(qs + (1 * NQ + qi) * nc + c);
+                        const T q2 = ldro(qs + (2 * NQ + qi) * nc + c);
+#pragma unroll
+                        for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                            for (int b = 0; b < n; ++b)
+#pragma unroll
+                                for (int a = 0; a < n; ++a) {
+                                    const T Nv = e.B[qx][a] * e.B[qy][b] * e.B[qz][c2];
+                                    const T gx = e.D[qx][a] * e.B[qy][b] * e.B[qz][c2] * e.invH[0];
+                                    const T gy = e.B[qx][a] * e.D[qy][b] * e.B[qz][c2] * e.invH[1];
+                                    const T gz = e.B[qx][a] * e.B[qy][b] * e.D[qz][c2] * e.invH[2];
+                                    res[a + n * (b + n * c2)] += w * Nv * (q0 * gx + q1 * gy + q2 * gz);
+                                }
+                    }
+            return;
+        }
+        // input(s): APPLY: um = us = masked x; RHS: um = T_old - g_D, us = g_D
+        if (MODE == MODE_APPLY) {
+            T um[NL];
+            gather<P, T>(g, x, cx, cy, cz, true, um);
+            core(um, um, T(1), cT, dtlam, dtcw, c, nc, res);
+        } else {
+            T um[NL], us[NL];
+            const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        const int l = a + n * (b + n * c2);
+                        const long long id = nidx(g, i0 + a, j0 + b, k0 + c2);
+                        const bool d = on_dir(g, i0 + a, j0 + b, k0 + c2);
+                        const T gv = d ? (T)gD[id] : T(0);
+                        um[l] = x[id] - gv;
+                        us[l] = gv;
+                    }
+            core(um, us, T(-1), cT, dtlam, dtcw, c, nc, res);
+        }
+    }
+
+    // sum-factorised quadrature: res = cT M um + sgn (dt lam K + dt C) us
+    __device__ __forceinline__ void core(const T (&um)[NL], const T (&us)[NL], const T sgn,
+                                         const T cT, const T dtlam, const T dtcw, const long long c,
+                                         const long long nc, T (&res)[NL]) const {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) res[l] = T(0);
+#pragma unroll
+        for (int qz = 0; qz < n; ++qz) {
+            // z sweep
+            T zBm[n * n], zBs[n * n], zDs[n * n];
+#pragma unroll
+            for (int ba = 0; ba < n * n; ++ba) {
+                T sm = T(0), sb = T(0), sd = T(0);
+#pragma unroll
+                for (int c2 = 0; c2 < n; ++c2) {
+                    sm = fma(e.B[qz][c2], um[ba + n * n * c2], sm);
+                    sb = fma(e.B[qz][c2], us[ba + n * n * c2], sb);
+                    sd = fma(e.D[qz][c2], us[ba + n * n * c2], sd);
+                }
+                zBm[ba] = sm;
+                zBs[ba] = sb;
+                zDs[ba] = sd;
+            }
+            T s1[n * n], s2[n * n];
+#pragma unroll
+            for (int ba = 0; ba < n * n; ++ba) { s1[ba] = T(0); s2[ba] = T(0); }
+#pragma unroll
+            for (int qy = 0; qy < n; ++qy) {
+                T yBBm[n], yBBs[n], yDBs[n], yBDs[n];
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    T v0 = T(0), v1 = T(0), v2 = T(0), v3 = T(0);
+#pragma unroll
+                    for (int b = 0; b < n; ++b) {
+                        v0 = fma(e.B[qy][b], zBm[a + n * b], v0);
+                        v1 = fma(e.B[qy][b], zBs[a + n * b], v1);
+                        v2 = fma(e.D[qy][b], zBs[a + n * b], v2);
+                        v3 = fma(e.B[qy][b], zDs[a + n * b], v3);
+                    }
+                    yBBm[a] = v0; yBBs[a] = v1; yDBs[a] = v2; yBDs[a] = v3;
+                }
+                T t1[n], t2[n], t3[n];
+#pragma unroll
+                for (int a = 0; a < n; ++a) { t1[a] = T(0); t2[a] = T(0); t3[a] = T(0); }
+#pragma unroll
+                for (int qx = 0; qx < n; ++qx) {
+                    T val = T(0), gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        val = fma(e.B[qx][a], yBBm[a], val);
+                        gx = fma(e.D[qx][a], yBBs[a], gx);
+                        gy = fma(e.B[qx][a], yDBs[a], gy);
+                        gz = fma(e.B[qx][a], yBDs[a], gz);
+                    }
+                    gx *= e.invH[0];
+                    gy *= e.invH[1];
+                    gz *= e.invH[2];
+                    const int qi = qx + n * (qy + n * qz);
+                    const T q0 = ldro(qs + (0 * NQ + qi) * nc + c);
+                    const T q1 = ldro(qs + (1 * NQ + qi) * nc + c);
+                    const T q2 = ldro(qs + (2 * NQ + qi) * nc + c);
+                    const T W = e.W[qi];
+                    const T v = W * fma(cT, val, sgn * dtcw * (q0 * gx + q1 * gy + q2 * gz));
+                    const T f = sgn * W * dtlam;
+                    const T gxs = f * gx * e.invH[0];
+                    const T gys = f * gy * e.invH[1];
+                    const T gzs = f * gz * e.invH[2];
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        t1[a] = fma(e.B[qx][a], v, fma(e.D[qx][a], gxs, t1[a]));
+                        t2[a] = fma(e.B[qx][a], gys, t2[a]);
+                        t3[a] = fma(e.B[qx][a], gzs, t3[a]);
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        s1[a + n * b] = fma(e.B[qy][b], t1[a], fma(e.D[qy][b], t2[a], s1[a + n * b]));
+                        s2[a + n * b] = fma(e.B[qy][b], t3[a], s2[a + n * b]);
+                    }
+            }
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int ba = 0; ba < n * n; ++ba)
+                    res[ba + n * n * c2] =
+                        fma(e.B[qz][c2], s1[ba], fma(e.D[qz][c2], s2[ba], res[ba + n * n * c2]));
+        }
+    }
+
+    __device__ __forceinline__ void emit(const Grid& g, int i, int j, int k, T val, T& dot) const {
+        const long long id = nidx(g, i, j, k);
+        const bool d = on_dir(g, i, j, k);
+        if (MODE == MODE_APPLY) {
+            const T xv = x[id];
+            const T yv = d ? xv : val;
+            y[id] = yv;
+            dot = fma(xv, yv, dot);
+        } else if (MODE == MODE_RHS) {
+            y[id] = d ? (T)gD[id] : val + dt * (T)F[id];
+        } else {
+            y[id] = d ? T(1) : val;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The tile kernel
+// ---------------------------------------------------------------------------
+template <int P, int CXM, int CYM>
+struct TileShape {
+    static constexpr int TX = P * (CXM - 1), TY = P * (CYM - 1), NT = CXM * CYM;
+    static constexpr int CPT = (TX * TY + NT - 1) / NT;
+};
+
+template <int P, typename T, int CXM, int CYM, class Op>
+__global__ void __launch_bounds__(CXM* CYM) tile_kernel(const Grid g, const Op op, const int ZC,
+                                                        double* __restrict__ dot_part,
+                                                        const Scal* __restrict__ sc) {
+    if (sc && sc->done) return;
+    using S = TileShape<P, CXM, CYM>;
+    constexpr int n = P + 1, NL = n * n * n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* E = reinterpret_cast<T*>(smem_raw);
+
+    const int ix0 = blockIdx.x * S::TX, iy0 = blockIdx.y * S::TY;
+    const int ix1 = min(ix0 + S::TX, g.Nx), iy1 = min(iy0 + S::TY, g.Ny);
+    const int cx_lo = max(ix0 / P - 1, 0), cy_lo = max(iy0 / P - 1, 0);
+    const int cx_hi = min((ix1 - 1) / P, g.ncx - 1), cy_hi = min((iy1 - 1) / P, g.ncy - 1);
+    const int CX = cx_hi - cx_lo + 1, CY = cy_hi - cy_lo + 1;
+    const int TXo = ix1 - ix0, TYo = iy1 - iy0;
+    const int last = (blockIdx.z == gridDim.z - 1);
+    const int k0 = blockIdx.z * ZC * P;
+    const int k1 = last ? g.Nz : min(k0 + ZC * P, g.Nz);
+    const int cz_lo = max((int)blockIdx.z * ZC - 1, 0);
+    const int cz_hi = last ? g.ncz - 1 : min((int)blockIdx.z * ZC + ZC - 1, g.ncz - 1);
+
+    T carry[S::CPT];
+#pragma unroll
+    for (int s = 0; s < S::CPT; ++s) carry[s] = T(0);
+    T dot = T(0);
+
+    for (int cz = cz_lo; cz <= cz_hi; ++cz) {
+        {
+            const int cidx = threadIdx.x;
+            if (cidx < CX * CY) {
+                const int lx = cidx % CX, ly = cidx / CX;
+                const int cx = cx_lo + lx, cy = cy_lo + ly;
+                const long long c = (long long)cx + (long long)g.ncx * ((long long)cy + (long long)g.ncy * cz);
+                T res[NL];
+                op.cell(g, cx, cy, cz, c, res);
+                T* e = E + (size_t)cidx * NL;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) e[l] = res[l];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < S::CPT; ++s) {
+            const int col = threadIdx.x + s * S::NT;
+            if (col < TXo * TYo) {
+                const int ix = ix0 + col % TXo, iy = iy0 + col / TXo;
+                int cxs[2], axs[2], ncxs = 0, cys[2], bys[2], ncys = 0;
+                if (ix % P == 0) {
+                    if (ix / P - 1 >= 0) { cxs[ncxs] = ix / P - 1; axs[ncxs++] = P; }
+                    if (ix / P < g.ncx) { cxs[ncxs] = ix / P; axs[ncxs++] = 0; }
+                } else { cxs[0] = ix / P; axs[0] = ix % P; ncxs = 1; }
+                if (iy % P == 0) {
+                    if (iy / P - 1 >= 0) { cys[ncys] = iy / P - 1; bys[ncys++] = P; }
+                    if (iy / P < g.ncy) { cys[ncys] = iy / P; bys[ncys++] = 0; }
+                } else { cys[0] = iy / P; bys[0] = iy % P; ncys = 1; }
+                T sj[P + 1];
+#pragma unroll
+                for (int j = 0; j <= P; ++j) sj[j] = T(0);
+                for (int yy = 0; yy < ncys; ++yy)
+                    for (int xx = 0; xx < ncxs; ++xx) {
+                        const T* base = E + (size_t)((cxs[xx] - cx_lo) + CX * (cys[yy] - cy_lo)) * NL +
+                                        axs[xx] + n * bys[yy];
+#pragma unroll
+                        for (int j = 0; j <= P; ++j) sj[j] += base[n * n * j];
+                    }
+                const int kb = P * cz;
+                if (kb >= k0 && kb < k1) op.emit(g, ix, iy, kb, carry[s] + sj[0], dot);
+#pragma unroll
+                for (int j = 1; j < P; ++j)
+                    if (kb + j >= k0 && kb + j < k1) op.emit(g, ix, iy, kb + j, sj[j], dot);
+                carry[s] = sj[P];
+                if (cz == g.ncz - 1 && kb + P >= k0 && kb + P < k1) op.emit(g, ix, iy, kb + P, carry[s], dot);
+            }
+        }
+        __syncthreads();
+    }
+    if (dot_part) {
+        const double tot = block_sum((double)dot);
+        if (threadIdx.x == 0)
+            dot_part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Other per-cell kernels
+// ---------------------------------------------------------------------------
+// q = -K_c grad h at the Gauss points; qs[(d*NQ + q)*nc + c]
+template <int P>
+__global__ void darcy_qp_kernel(const Grid g, const double* __restrict__ h,
+                                const double* __restrict__ K, const Elem<double> e,
+                                double* __restrict__ qs64, float* __restrict__ qs32) {
+    constexpr int n = P + 1, NL = n * n * n, NQ = NL;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % g.ncx), cy = (int)((c / g.ncx) % g.ncy), cz = (int)(c / ((long long)g.ncx * g.ncy));
+        double u[NL];
+        gather<P, double>(g, h, cx, cy, cz, false, u);
+        const double Kc = K[c];
+        for (int qz = 0; qz < n; ++qz)
+            for (int qy = 0; qy < n; ++qy)
+                for (int qx = 0; qx < n; ++qx) {
+                    double gx = 0, gy = 0, gz = 0;
+#pragma unroll
+                    for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                        for (int b = 0; b < n; ++b)
+#pragma unroll
+                            for (int a = 0; a < n; ++a) {
+                                const double v = u[a + n * (b + n * c2)];
+                                gx += e.D[qx][a] * e.B[qy][b] * e.B[qz][c2] * v;
+                                gy += e.B[qx][a] * e.D[qy][b] * e.B[qz][c2] * v;
+                                gz += e.B[qx][a] * e.B[qy][b] * e.D[qz][c2] * v;
+                            }
+                    const int qi = qx + n * (qy + n * qz);
+                    const double q0 = -Kc * gx * e.invH[0];
+                    const double q1 = -Kc * gy * e.invH[1];
+                    const double q2 = -Kc * gz * e.invH[2];
+                    qs64[(0 * NQ + qi) * g.nc + c] = q0;
+                    qs64[(1 * NQ + qi) * g.nc + c] = q1;
+                    qs64[(2 * NQ + qi) * g.nc + c] = q2;
+                    qs32[(0 * NQ + qi) * g.nc + c] = (float)q0;
+                    qs32[(1 * NQ + qi) * g.nc + c] = (float)q1;
+                    qs32[(2 * NQ + qi) * g.nc + c] = (float)q2;
+                }
+    }
+}
+
+struct CentreBasis { double v[3], d[3]; };
+
+template <int P>
+__global__ void cell_flux_kernel(const Grid g, const double* __restrict__ h,
+                                 const double* __restrict__ K, const CentreBasis cb,
+                                 const double invH, const int comp, double* __restrict__ out) {
+    constexpr int n = P + 1, NL = n * n * n;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % g.ncx), cy = (int)((c / g.ncx) % g.ncy), cz = (int)(c / ((long long)g.ncx * g.ncy));
+        double u[NL];
+        gather<P, double>(g, h, cx, cy, cz, false, u);
+        double s = 0;
+#pragma unroll
+        for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+            for (int b = 0; b < n; ++b)
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    const double fa = comp == 0 ? cb.d[a] : cb.v[a];
+                    const double fb = comp == 1 ? cb.d[b] : cb.v[b];
+                    const double fc = comp == 2 ? cb.d[c2] : cb.v[c2];
+                    s += fa * fb * fc * u[a + n * (b + n * c2)];
+                }
+        out[c] = -K[c] * s * invH;
+    }
+}
+
+template <typename T>
+__global__ void well_apply_kernel(int n, const int* __restrict__ node, const double* __restrict__ d,
+                                  T dt, const T* __restrict__ x, T* __restrict__ y,
+                                  const Scal* __restrict__ sc) {
+    if (sc && sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int id = node[i];
+        y[id] += dt * (T)d[i] * x[id];
+    }
+}
+
+__global__ void well_diag_kernel(int n, const int* __restrict__ node, const double* __restrict__ d,
+                                 double dt, double* __restrict__ D) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) D[node[i]] += dt * d[i];
+}
+
+__global__ void pile_load_kernel(int n_nodes, const int* __restrict__ node, const int* __restrict__ off,
+                                 const int* __restrict__ src, const double* __restrict__ w,
+                                 const ht_line_src* __restrict__ piles, double t,
+                                 const double* __restrict__ Fbase, double* __restrict__ F) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_nodes) {
+        const int id = node[i];
+        double s = Fbase[id];
+        for (int e = off[i]; e < off[i + 1]; ++e) {
+            const ht_line_src& pl = piles[src[e]];
+            const double a = pl.mean + pl.amp * sin(2.0 * 3.141592653589793 * t / pl.period + pl.phase);
+            s += a * w[e];
+        }
+        F[id] = s;
+    }
+}
+
+__global__ void add_kernel(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] + (b ? b[i] : 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kCXM = 16, kCYM = 16;
+
+Grid field_grid(const ht_ctx* c, int field) {
+    Grid g = c->grid;
+    g.dmask = c->dmask[field];
+    return g;
+}
+
+template <int P>
+void tile_dims(const ht_ctx* c, dim3* grid, int* ZC) {
+    using S = TileShape<P, kCXM, kCYM>;
+    const Grid& g = c->grid;
+    const int tx = (g.Nx + S::TX - 1) / S::TX, ty = (g.Ny + S::TY - 1) / S::TY;
+    const int target = 2 * (c->num_sms > 0 ? c->num_sms : 148);
+    int chunks = (target + tx * ty - 1) / (tx * ty);
+    chunks = chunks < 1 ? 1 : (chunks > g.ncz ? g.ncz : chunks);
+    int zc = (g.ncz + chunks - 1) / chunks;
+    chunks = (g.ncz + zc - 1) / zc;
+    *grid = dim3(tx, ty, chunks);
+    *ZC = zc;
+}
+
+template <int P, typename T, class Op>
+int launch_tile(ht_ctx* c, const Grid& g, const Op& op, double* dot_part, int* n_part,
+                const Scal* sc = nullptr) {
+    dim3 grid;
+    int ZC;
+    tile_dims<P>(c, &grid, &ZC);
+    constexpr int n = P + 1, NL = n * n * n;
+    const size_t smem = (size_t)kCXM * kCYM * NL * sizeof(T);
+    auto kern = tile_kernel<P, T, kCXM, kCYM, Op>;
+    static bool attr_done = false;   // per instantiation
+    if (!attr_done) {
+        HT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_done = true;
+    }
+    kern<<<grid, kCXM * kCYM, smem, c->stream>>>(g, op, ZC, dot_part, sc);
+    HT_CUDA(c, cudaGetLastError());
+    if (n_part) *n_part = (int)(grid.x * grid.y * grid.z);
+    return HT_OK;
+}
+
+template <typename T>
+const Elem<T>& elem_of(const ht_ctx* c);
+template <>
+const Elem<double>& elem_of<double>(const ht_ctx* c) { return c->e64; }
+template <>
+const Elem<float>& elem_of<float>(const ht_ctx* c) { return c->e32; }
+
+template <int P, typename T>
+int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int* n_part,
+            const Scal* sc) {
+    const Grid g = field_grid(c, field);
+    const bool f64 = sizeof(T) == 8;
+    if (field == HT_HEAD) {
+        HeadOp<P, T, MODE_APPLY> op{};
+        op.x = x; op.y = y;
+        op.K = f64 ? (const T*)c->K64 : (const T*)c->K32;
+        op.alpha = (T)c->Ss; op.dt = dt; op.e = elem_of<T>(c);
+        return launch_tile<P, T>(c, g, op, dot_part, n_part, sc);
+    }
+    HeatOp<P, T, MODE_APPLY> op{};
+    op.x = x; op.y = y;
+    op.qs = f64 ? (const T*)c->qs64 : (const T*)c->qs32;
+    op.cTc = f64 ? (const T*)c->cT64 : (const T*)c->cT32;
+    op.lamc = f64 ? (const T*)c->lam64 : (const T*)c->lam32;
+    op.cT_u = (T)c->cT_u; op.lam_u = (T)c->lam_u; op.dt = dt; op.cw = (T)c->cw;
+    op.e = elem_of<T>(c);
+    return launch_tile<P, T>(c, g, op, dot_part, n_part, sc);
+}
+
+}  // namespace
+
+int apply_tiles(const ht_ctx* c) {
+    dim3 grid;
+    int ZC;
+    if (c->grid.P == 1) tile_dims<1>(c, &grid, &ZC);
+    else tile_dims<2>(c, &grid, &ZC);
+    return (int)(grid.x * grid.y * grid.z);
+}
+
+int launch_apply64(ht_ctx* c, int field, double dt, const double* x, double* y, double* dot_part,
+                   int* n_part, const Scal* sc) {
+    int rc = c->grid.P == 1 ? apply_P<1, double>(c, field, dt, x, y, dot_part, n_part, sc)
+                            : apply_P<2, double>(c, field, dt, x, y, dot_part, n_part, sc);
+    if (rc != HT_OK) return rc;
+    if (field == HT_TEMP && c->n_well_nodes > 0) return launch_well_apply64(c, dt, x, y, sc);
+    return HT_OK;
+}
+
+int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y, double* dot_part,
+                   int* n_part, const Scal* sc) {
+    int rc = c->grid.P == 1 ? apply_P<1, float>(c, field, dt, x, y, dot_part, n_part, sc)
+                            : apply_P<2, float>(c, field, dt, x, y, dot_part, n_part, sc);
+    if (rc != HT_OK) return rc;
+    if (field == HT_TEMP && c->n_well_nodes > 0) return launch_well_apply32(c, dt, x, y, sc);
+    return HT_OK;
+}
+
+template <int P>
+static int rhs_P(ht_ctx* c, int field, double dt, const double* u_old, double* b) {
+    const Grid g = field_grid(c, field);
+    if (field == HT_HEAD) {
+        HeadOp<P, double, MODE_RHS> op{};
+        op.x = u_old; op.gD = c->g[field]; op.F = c->F[field]; op.y = b;
+        op.K = c->K64; op.alpha = c->Ss; op.dt = dt; op.e = c->e64;
+        return launch_tile<P, double>(c, g, op, nullptr, nullptr);
+    }
+    HeatOp<P, double, MODE_RHS> op{};
+    op.x = u_old; op.gD = c->g[field]; op.F = c->F[field]; op.y = b;
+    op.qs = c->qs64; op.cTc = c->cT64; op.lamc = c->lam64;
+    op.cT_u = c->cT_u; op.lam_u = c->lam_u; op.dt = dt; op.cw = c->cw; op.e = c->e64;
+    return launch_tile<P, double>(c, g, op, nullptr, nullptr);
+}
+
+int launch_rhs(ht_ctx* c, int field, double dt, const double* u_old, double* b) {
+    return c->grid.P == 1 ? rhs_P<1>(c, field, dt, u_old, b) : rhs_P<2>(c, field, dt, u_old, b);
+}
+
+template <int P>
+static int diag_P(ht_ctx* c, int field, double dt, double* D) {
+    const Grid g = field_grid(c, field);
+    if (field == HT_HEAD) {
+        HeadOp<P, double, MODE_DIAG> op{};
+        op.y = D; op.K = c->K64; op.alpha = c->Ss; op.dt = dt; op.e = c->e64;
+        return launch_tile<P, double>(c, g, op, nullptr, nullptr);
+    }
+    HeatOp<P, double, MODE_DIAG> op{};
+    op.y = D; op.qs = c->qs64; op.cTc = c->cT64; op.lamc = c->lam64;
+    op.cT_u = c->cT_u; op.lam_u = c->lam_u; op.dt = dt; op.cw = c->cw; op.e = c->e64;
+    return launch_tile<P, double>(c, g, op, nullptr, nullptr);
+}
+
+int launch_diag(ht_ctx* c, int field, double dt, double* D) {
+    int rc = c->grid.P == 1 ? diag_P<1>(c, field, dt, D) : diag_P<2>(c, field, dt, D);
+    if (rc != HT_OK) return rc;
+    if (field == HT_TEMP && c->n_well_nodes > 0) return launch_well_diag(c, dt, D);
+    return HT_OK;
+}
+
+int launch_darcy_qp(ht_ctx* c, const double* h) {
+    const Grid g = field_grid(c, HT_HEAD);
+    const int threads = 128;
+    long long blocks = (g.nc + threads - 1) / threads;
+    const long long cap = (long long)c->num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (c->grid.P == 1)
+        darcy_qp_kernel<1><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, c->e64, c->qs64, c->qs32);
+    else
+        darcy_qp_kernel<2><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, c->e64, c->qs64, c->qs32);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int launch_cell_flux(ht_ctx* c, const double* h, int comp, double* out) {
+    const Grid g = field_grid(c, HT_HEAD);
+    CentreBasis cb{};
+    if (c->grid.P == 1) {
+        cb.v[0] = 0.5; cb.v[1] = 0.5; cb.d[0] = -1.0; cb.d[1] = 1.0;
+    } else {
+        // Q2 basis on nodes {0, 1/2, 1} evaluated at the cell centre
+        cb.v[0] = 0.0; cb.v[1] = 1.0; cb.v[2] = 0.0;
+        cb.d[0] = -1.0; cb.d[1] = 0.0; cb.d[2] = 1.0;
+    }
+    const int threads = 256;
+    long long blocks = (g.nc + threads - 1) / threads;
+    const long long cap = (long long)c->num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    const double invH = 1.0 / c->H[comp];
+    if (c->grid.P == 1)
+        cell_flux_kernel<1><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, cb, invH, comp, out);
+    else
+        cell_flux_kernel<2><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, cb, invH, comp, out);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int launch_well_apply64(ht_ctx* c, double dt, const double* x, double* y, const Scal* sc) {
+    const int n = c->n_well_nodes;
+    well_apply_kernel<double><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, x, y, sc);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int launch_well_apply32(ht_ctx* c, float dt, const float* x, float* y, const Scal* sc) {
+    const int n = c->n_well_nodes;
+    well_apply_kernel<float><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, x, y, sc);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int launch_well_diag(ht_ctx* c, double dt, double* D) {
+    const int n = c->n_well_nodes;
+    well_diag_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, D);
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int launch_loads(ht_ctx* c, double t) {
+    const long long nn = c->grid.nn;
+    const int grid = vec_grid(c);
+    for (int f = 0; f < 2; ++f) {
+        add_kernel<<<grid, kVecThreads, 0, c->stream>>>(nn, c->Fstat[f], c->extra[f], c->F[f]);
+        HT_CUDA(c, cudaGetLastError());
+    }
+    if (c->n_pile_nodes > 0) {
+        // pile nodes: F_T = Fstat + extra + sum_s q_l,s(t) w_s (unique nodes)
+        const int n = c->n_pile_nodes;
+        pile_load_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->pile_node, c->pile_off, c->pile_src,
+                                                                 c->pile_w, c->d_piles, t, c->F[HT_TEMP],
+                                                                 c->F[HT_TEMP]);
+        HT_CUDA(c, cudaGetLastError());
+    }
+    return HT_OK;
+}
+
+}  // namespace ht

@@ -1,0 +1,142 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle on
+the same seeded inputs.
+
+Tolerances (derived in the design doc):
+* operator apply / diagonal / right-hand side: relative L2 <= 1e-12 and
+  max |diff| <= 1e-12 * max |y| (FP64 rounding of sums of <= 27*8 terms);
+* solutions of steps solved to relative residual 1e-13: relative L2 <= 1e-9;
+* FP32-inner / FP64-outer mixed precision solved to 1e-12: relative L2
+  <= 1e-9 as well (the outer loop is FP64);
+* Darcy flux at cell centres: 1e-12 relative.
+Mesh sizes span several CTA tiles with ragged tails (Q1 tiles own 15 x 15
+node columns, Q2 tiles 30 x 30) and several z chunks.
+"""
+import numpy as np
+import pytest
+
+import scenarios as S
+from oracle import fem
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    (1, 33, 20, 7, 11),
+    (2, 17, 9, 5, 12),
+    (1, 1, 1, 1, 13),
+    (2, 1, 1, 1, 14),
+    (2, 3, 1, 2, 15),
+    (1, 16, 16, 16, 16),
+]
+
+
+def _ids(c):
+    return f"q{c[0]}_{c[1]}x{c[2]}x{c[3]}"
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _close(got, ref, tol=1e-12):
+    assert _rel(got, ref) <= tol, _rel(got, ref)
+    assert np.max(np.abs(got - ref)) <= tol * max(np.max(np.abs(ref)), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def Sim(built_lib):
+    from paper_2103_00081_gb300 import hydro
+    return hydro.Simulator
+
+
+def _scenario(case, per_cell=False, wells=2, piles=3):
+    p, nx, ny, nz, seed = case
+    return S.random_small(seed, nx, ny, nz, p, n_piles=piles, n_wells=wells,
+                          per_cell_thermal=per_cell)
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+@pytest.mark.parametrize("per_cell", [False, True])
+def test_operator_apply_diag_rhs_match_oracle(Sim, case, per_cell):
+    sc = _scenario(case, per_cell)
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc)
+    rng = np.random.default_rng(100 + case[-1])
+    dt = sc.dt
+    x = rng.standard_normal(sc.n_nodes)
+    _close(sim.apply(S.HEAD, dt, x), o.apply_head(x, dt))
+    _close(sim.apply(S.TEMP, dt, x), o.apply_heat(x, o.h, dt))
+    _close(sim.diag(S.HEAD, dt), o.diag_head(dt))
+    _close(sim.diag(S.TEMP, dt), o.diag_heat(o.h, dt))
+    _close(sim.rhs(S.HEAD, dt), o.head_rhs(dt, dt))
+    _close(sim.rhs(S.TEMP, dt), o.heat_rhs(dt, dt, o.h))
+    for comp, field in enumerate((S.HEAD + 2, S.HEAD + 3, S.HEAD + 4)):
+        _close(sim.get_field(field), o.cell_flux()[comp])
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_steps_match_oracle_fp64(Sim, case):
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc, tol=1e-13, max_iter=50000)
+    for _ in range(3):
+        st = sim.step(sc.dt)
+        o.step(sc.dt)
+        assert st["res_head"] <= 1.001e-13 and st["res_heat"] <= 1.001e-13
+        assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
+        assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+    assert abs(sim.time - 3 * sc.dt) < 1e-6
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=_ids)
+def test_mixed_precision_matches_oracle(Sim, case):
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    from paper_2103_00081_gb300 import _lib as L
+    sim = Sim.from_scenario(sc, tol=1e-12, precision=L.HT_MIXED, inner_tol=1e-4)
+    for _ in range(2):
+        st = sim.step(sc.dt)
+        o.step(sc.dt)
+        assert st["outer_head"] >= 1
+        assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
+        assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+
+
+def test_config1_plain_workload_matches_oracle(Sim):
+    """The plain FP64 workload: 16^3 Q1 cube, line source, 10 days."""
+    sc = S.config1()
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc, tol=1e-13)
+    for _ in range(sc.n_steps):
+        sim.step(sc.dt)
+        o.step(sc.dt)
+    assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
+    assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+
+
+def test_bitwise_reproducible(Sim):
+    sc = _scenario(CASES[1])
+    out = []
+    for _ in range(2):
+        sim = Sim.from_scenario(sc, tol=1e-10)
+        for _ in range(2):
+            sim.step(sc.dt)
+        out.append((sim.get_field(S.HEAD), sim.get_field(S.TEMP)))
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_error_codes(Sim):
+    from paper_2103_00081_gb300 import hydro
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(CASES[2])
+    sim = Sim.from_scenario(sc)
+    with pytest.raises(hydro.HTError) as e:
+        sim.set_cells(np.zeros(sc.n_cells))
+    assert e.value.code == L.HT_EINVAL
+    with pytest.raises(hydro.HTError) as e:
+        sim.add_line_sources([[1e6, 0, 1, 0, 1, 0, 1, 0]])
+    assert e.value.code == L.HT_EINVAL
+    sc2 = _scenario(CASES[0])
+    sim2 = Sim.from_scenario(sc2, tol=1e-14, max_iter=1)
+    st = sim2.step(sc2.dt, check=False)
+    assert st["rc"] == L.HT_ENOCONV
