@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the hydrothermal time step on one GB300.
+
+Workload (default): the ATES-like layered aquifer, 200 m x 200 m x 50 m,
+128 x 128 x 32 Q2 cells (4,293,185 nodes per field), iid lognormal K in three
+layers, an injection / extraction well pair, dt = 0.5 day, both linear systems
+solved to relative residual 1e-10.  A "step" is one backward-Euler step:
+loads, head CG solve, heat BiCGStab solve.
+
+Printed metric: simulated years per hour of the FP32-inner / FP64-outer form
+(value), with the plain FP64 form beside it, operator GDoF/s and the roofline
+of the dominant kernel (the head operator apply).
+
+--impl reference times the CPU FP64 oracle (the plain assembled-matrix
+reference) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+if "--impl" in sys.argv and "reference" in sys.argv:
+    # the oracle arm runs single-threaded; say so truthfully in "cores"
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenarios as S  # noqa: E402
+
+YEAR = 365.0 * 86400.0
+METRIC = "simulated-years/hour at 1e-10 residual (FP32-inner/FP64-outer; plain FP64 beside it)"
+UNIT = "sim-years/h"
+
+
+def workload(name):
+    if name == "ates_q2":
+        return S.config2()
+    if name == "plain_q1":
+        return S.config1()
+    if name.startswith("ates_q2_"):          # e.g. ates_q2_32 -> 32x32x8 cells
+        n = int(name.split("_")[-1])
+        return S.config2(nx=n, ny=n, nz=max(2, n // 4))
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        out.update(hbm_gbs=float(d["hbm_gbs"]), source="measured",
+                   sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)))
+    # ALU peaks derived from unit counts and the maximum SM clock:
+    # FP32: 152 SMs x 128 lanes x 2 flop/FMA; FP64: GB300 nominal 1.25 TFLOP/s.
+    out["fp32_tflops"] = 152 * 128 * 2 * out["sm_max_mhz"] * 1e6 / 1e12
+    out["fp64_tflops"] = 1.25
+    return out
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def apply_flops_per_node(order):
+    """Algorithmic FLOPs of one head-operator apply per node (fast-
+    diagonalisation sum factorisation, counted in the design doc)."""
+    if order == 1:
+        return 242.0
+    return 143.0
+
+
+def apply_bytes_per_node(order, fp32):
+    w = 4 if fp32 else 8
+    cells_per_node = 1.0 if order == 1 else 1.0 / 8.0
+    return 2 * w + w * cells_per_node
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    backend = "nccl"
+    dist.init_process_group(backend=backend)
+    return dist.get_rank(), ws, dist
+
+
+def run_ours(args):
+    import torch
+    from paper_2103_00081_gb300 import build as B
+    B.build()
+    from paper_2103_00081_gb300 import hydro
+    from paper_2103_00081_gb300 import _lib as L
+
+    rank, world, dist = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    sc = workload(args.workload)
+    dt = sc.dt
+    nn = sc.n_nodes
+    stream = torch.cuda.Stream(device=local)
+    pk = peaks()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def timed_run(precision):
+        sim = hydro.Simulator.from_scenario(sc, device=local, stream=stream.cuda_stream,
+                                            tol=1e-10, precision=precision, inner_tol=args.inner_tol,
+                                            max_iter=200000)
+        for _ in range(args.warmup):
+            sim.step(dt)
+        torch.cuda.synchronize()
+        sim.profile(True)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        with Clocks(local) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                stats.append(sim.step(dt))
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        barrier()
+        prof = sim.profile_read()
+        sim.profile(False)
+        return sim, ms, stats, prof, clk.summary()
+
+    # --- mixed precision (the headline form) --------------------------------
+    sim, ms_mixed, st_mixed, prof_mixed, clk = timed_run(L.HT_MIXED)
+    # --- end to end through the C ABI with host buffers ---------------------
+    h_host = np.ascontiguousarray(sim.get_field(S.HEAD))
+    T_host = np.ascontiguousarray(sim.get_field(S.TEMP))
+    torch.cuda.synchronize()
+    t_now = sim.time
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.set_state(h_host, T_host, t_now)
+        sim.step(dt)
+        h_host = sim.get_field(S.HEAD)
+        T_host = sim.get_field(S.TEMP)
+        t_now += dt
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    sim.close()
+    # --- plain FP64 ----------------------------------------------------------
+    sim64, ms_fp64, st_fp64, prof_fp64, clk64 = timed_run(L.HT_FP64)
+    sim64.close()
+
+    def to_rate(ms, steps):
+        return (steps * dt / YEAR) / (ms / 1000.0 / 3600.0)
+
+    # max over ranks of the timed duration
+    if dist:
+        t = torch.tensor([ms_mixed, ms_fp64, e2e_s], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mixed, ms_fp64, e2e_s = t.tolist()
+    if rank != 0:
+        return
+    rate_mixed = to_rate(ms_mixed, args.steps) * world
+    rate_fp64 = to_rate(ms_fp64, args.steps) * world
+    rate_e2e = (args.steps * dt / YEAR) / (e2e_s / 3600.0) * world
+
+    order = sc.order
+    # dominant kernel: the head operator apply of the form measured
+    n32 = prof_mixed["head_applies_fp32"]
+    ms32 = prof_mixed["head_apply_ms_fp32"]
+    avg32 = ms32 / max(n32, 1)
+    n64 = prof_fp64["head_applies"]
+    avg64 = prof_fp64["head_apply_ms"] / max(n64, 1)
+    flops = apply_flops_per_node(order) * nn
+    bytes32 = apply_bytes_per_node(order, True) * nn
+    bytes64 = apply_bytes_per_node(order, False) * nn
+    roof = {
+        "kernel": "head operator apply (FP32, tile_kernel<HeadOp>)",
+        "bound": "alu",
+        "achieved": flops / (avg32 / 1e3) / 1e12,
+        "peak": pk["fp32_tflops"],
+        "unit": "TFLOP/s",
+        "frac": flops / (avg32 / 1e3) / 1e12 / pk["fp32_tflops"],
+        "traffic": None,
+        "avg_launch_us": avg32 * 1e3,
+        "launches": n32,
+        "hbm_achieved_gbs": bytes32 / (avg32 / 1e3) / 1e9,
+        "hbm_frac": bytes32 / (avg32 / 1e3) / 1e9 / pk["hbm_gbs"],
+        "peak_source": f"FP32 = 152 SM x 128 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz (derived); "
+                       f"HBM {pk['hbm_gbs']:.0f} GB/s ({pk['source']})",
+    }
+    roof_fp64 = {
+        "kernel": "head operator apply (FP64)",
+        "bound": "alu",
+        "achieved": flops / (avg64 / 1e3) / 1e12,
+        "peak": pk["fp64_tflops"],
+        "unit": "TFLOP/s",
+        "frac": flops / (avg64 / 1e3) / 1e12 / pk["fp64_tflops"],
+        "avg_launch_us": avg64 * 1e3,
+        "launches": n64,
+        "hbm_achieved_gbs": bytes64 / (avg64 / 1e3) / 1e9,
+        "hbm_frac": bytes64 / (avg64 / 1e3) / 1e9 / pk["hbm_gbs"],
+    }
+    its_h = [s["iters_head"] for s in st_mixed]
+    its_T = [s["iters_heat"] for s in st_mixed]
+    line = {
+        "metric": METRIC,
+        "value": rate_mixed,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_mixed / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32-inner/f64-outer",
+        "data": "synthetic (seeded lognormal K layers, well pair)",
+        "config": {"workload": f"{sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{order}, {nn} nodes/field, "
+                               f"dt={dt / 86400:g} d, tol 1e-10",
+                   "nodes_per_field": nn, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "working set per step > L2 (no flush needed)"},
+        "plain_fp64": {"value": rate_fp64, "unit": UNIT, "ms_per_step": ms_fp64 / args.steps,
+                       "iters_head": [s["iters_head"] for s in st_fp64],
+                       "iters_heat": [s["iters_heat"] for s in st_fp64],
+                       "roofline": roof_fp64, "clocks": clk64},
+        "speedup_vs_fp64": rate_mixed / rate_fp64 if rate_fp64 > 0 else None,
+        "iters_head": its_h, "iters_heat": its_T,
+        "outer_head": [s["outer_head"] for s in st_mixed],
+        "res_head": max(s["res_head"] for s in st_mixed), "res_heat": max(s["res_heat"] for s in st_mixed),
+        "operator_gdofs": {"fp32_head_apply": nn / (avg32 / 1e3) / 1e9,
+                           "fp64_head_apply": nn / (avg64 / 1e3) / 1e9},
+        "roofline": roof,
+        "e2e": {"value": rate_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nn * 8,
+                "d2h_bytes_per_step": 2 * nn * 8},
+        "gpu_launches": prof_mixed["launches"],
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, sc)
+    print(json.dumps(line))
+
+
+def _oracle_sample(sc_full, args):
+    """Bounded sample of the workload for the CPU oracle: the same layered
+    aquifer and well pair on a coarser mesh (same physics, fewer cells)."""
+    n = args.cpu_sample_cells
+    return S.config2(nx=n, ny=n, nz=max(2, n // 4)) if sc_full.order == 2 else S.config1(nx=n)
+
+
+def cpu_baseline(args, sc_full, steps=1, warm=0):
+    from oracle import fem
+    sc = _oracle_sample(sc_full, args)
+    o = fem.OracleSim(sc, solver="iterative", tol=1e-10)
+    for _ in range(warm):
+        o.step(sc.dt)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(sc.dt)
+    el = time.perf_counter() - t0
+    rate_sample = (steps * sc.dt / YEAR) / (el / 3600.0)
+    # extrapolate linearly in nodes per field to the full workload
+    rate = rate_sample * sc.n_nodes / sc_full.n_nodes
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} step(s) of {sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{sc.order} "
+                      f"({sc.n_nodes} nodes), Jacobi-PCG/BiCGStab to 1e-10 on assembled CSR, "
+                      f"{el:.1f} s; scaled linearly by node count to {sc_full.n_nodes} nodes",
+            "sample_rate": rate_sample, "seconds": el}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc_full = workload(args.workload)
+    from oracle import fem
+    sc = _oracle_sample(sc_full, args)
+    o = fem.OracleSim(sc, solver="iterative", tol=1e-10)
+    for _ in range(args.warmup):
+        o.step(sc.dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(sc.dt)
+    el = time.perf_counter() - t0
+    rate_sample = (args.steps * sc.dt / YEAR) / (el / 3600.0)
+    rate = rate_sample * sc.n_nodes / sc_full.n_nodes
+    cb = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"{args.steps} step(s) of {sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{sc.order} "
+                    f"({sc.n_nodes} nodes), scaled linearly by node count to {sc_full.n_nodes} nodes"}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"{sc_full.name} (sampled at {sc.nx}x{sc.ny}x{sc.nz})"},
+        "cpu_baseline": cb,
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ates_q2")
+    ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-4)
+    ap.add_argument("--cpu-sample-cells", dest="cpu_sample_cells", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -47,7 +47,7 @@ extern "C" {
 enum { HT_HEAD = 0, HT_TEMP = 1, HT_QX = 2, HT_QY = 3, HT_QZ = 4 };
 enum { HT_BC_NONE = 0, HT_BC_DIRICHLET = 1, HT_BC_FLUX = 2 };
 enum { HT_FP64 = 0, HT_MIXED = 1 };
-enum { HT_KRYLOV_BICGSTAB = 0 };
+enum { HT_KRYLOV_BICGSTAB = 0, HT_KRYLOV_GMRES = 1 };
 enum { HT_PREC_JACOBI = 0, HT_PREC_CHEBYSHEV = 1 };
 
 typedef struct ht_ctx ht_ctx;
@@ -67,24 +67,33 @@ typedef struct {
 } ht_line_src;
 
 /* Vertical well screened from z_bot to z_top at (x, y): volumetric rate Q
- * (m^3/s, > 0 injects) spread uniformly over the screen as a head source;
- * injected water carries temperature T_in (implicit lumped line term
- * c_w (Q/L) int N_i dz (T_in - T)); extraction adds no heat term because
- * Eq. 2 is in advective (q . grad T) form. */
+ * (m^3/s, > 0 injects) spread uniformly over the screen length L and
+ * laterally with profile s(x, y): the axis itself (sigma = 0, a line source)
+ * or a normal density of standard deviation sigma (m).  Head load
+ * (Q/L) int N_i s dV; injected water carries temperature T_in through the
+ * implicit lumped term c_w (Q/L) int N_i s dV (T_in - T); extraction adds no
+ * heat term because Eq. 2 is in advective (q . grad T) form.  The lateral
+ * integrals use a 10-point Gauss rule per cell within 10 sigma. */
 typedef struct {
-    double x, y, z_top, z_bot, Q, T_in;
+    double x, y, z_top, z_bot, Q, T_in, sigma;
 } ht_well;
 
 /* Solver options.  tol is the relative residual ||b - A x||_2 <= tol ||b||_2
- * on each linear system (head: preconditioned CG, heat: BiCGStab).
+ * on each linear system (head: preconditioned CG; heat: restarted GMRES(restart)
+ * with right Jacobi preconditioning (krylov HT_KRYLOV_GMRES, the default) or
+ * BiCGStab (HT_KRYLOV_BICGSTAB)).
  * precision HT_MIXED runs operator applies, preconditioner and inner Krylov
  * iterations in FP32 inside an FP64 defect-correction loop whose residuals,
  * dot products and norms are FP64.  precond HT_PREC_CHEBYSHEV uses a
- * Chebyshev polynomial of degree cheb_degree in D^-1 A for the head CG. */
+ * Chebyshev polynomial of degree cheb_degree in D^-1 A for the head CG.
+ * z_chunks > 0 fixes the number of z chunks of the operator tiles (0: the
+ * library picks it from the SM count); it changes performance, not results
+ * beyond rounding order. */
 typedef struct {
     double tol;
     int max_iter;
     int krylov;
+    int restart;
     int precond;
     int cheb_degree;
     int precision;
@@ -92,6 +101,7 @@ typedef struct {
     int max_outer;
     int check_every;
     int use_graphs;
+    int z_chunks;
 } ht_solver_opts;
 
 /* Per-step statistics: Krylov iterations (inner iterations in mixed mode),
@@ -173,6 +183,23 @@ int ht_get_time(const ht_ctx* ctx, double* t);
 int ht_apply(ht_ctx* ctx, int field, double dt, const double* x, double* y, int on_device);
 int ht_diag(ht_ctx* ctx, int field, double dt, double* d, int on_device);
 int ht_rhs(ht_ctx* ctx, int field, double dt, double* b, int on_device);
+
+/* Launch accounting and operator timing.  ht_profile(ctx, on) resets the
+ * counters; with on != 0 every operator-apply launch is bracketed by CUDA
+ * events on the context's stream.  ht_profile_read() synchronises the stream
+ * and returns: all kernels launched by the library since the reset, the
+ * number of head / heat apply launches that did work (launches that found
+ * the solve already converged and returned at once are excluded by duration)
+ * and their summed device time in milliseconds. */
+typedef struct {
+    long long launches;
+    long long head_applies, heat_applies;
+    double head_apply_ms, heat_apply_ms;
+    long long head_applies_fp32, heat_applies_fp32;
+    double head_apply_ms_fp32, heat_apply_ms_fp32;
+} ht_profile_stats;
+int ht_profile(ht_ctx* ctx, int on);
+int ht_profile_read(ht_ctx* ctx, ht_profile_stats* out);
 
 /* Bulk coefficients from the mixture rules of Section 2 and the storage of
  * Eq. 1: lambda = (1-phi) lambda_s + phi lambda_w, cT = (1-phi) c_s +

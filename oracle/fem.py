@@ -18,7 +18,8 @@ sum factorisation, no blocking, then a sparse direct solve):
   (M_cT + dt L_lambda + dt C(q) + dt D_w) T^{n+1} = M_cT T^n + dt F_T, with
   C_ij = sum_qp w c_w N_i (q . grad N_j) and q = -K_c grad h^{n+1} evaluated at
   the same Gauss points (Darcy's law, Section 2, q = -k (grad p + rho_w g)).
-  D_w is the lumped line term of an injection well, c_w (Q/L) int N_i dz.
+  D_w is the lumped term of an injection well, c_w (Q/L) int N_i s dV with s
+  the well's lateral profile (a line, or a normal density of width sigma).
 * Quadrature: (p+1)-point Gauss-Legendre per direction for order p.
 * Dirichlet nodes: rows replaced by the identity and the prescribed values
   moved to the right-hand side (columns eliminated, so the head operator stays
@@ -244,6 +245,68 @@ def line_weights(mesh: Mesh, x: float, y: float, z_top: float, z_bot: float) -> 
     return w
 
 
+def gaussian_cell_integrals(mesh: Mesh, axis: int, centre: float, sigma: float, nq: int = 10):
+    """I[(c, a)] = int_cell phi_a(x) g(x) dx with g the normal density of mean
+    `centre` and standard deviation `sigma` along `axis`, by an nq-point Gauss
+    rule on every cell within 10 sigma of the centre."""
+    p = mesh.p
+    xg, wg = gauss01(nq)
+    n = (mesh.nx, mesh.ny, mesh.nz)[axis]
+    H, o = mesh.H[axis], mesh.origin[axis]
+    out = {}
+    for c in range(n):
+        a0 = o + c * H
+        if a0 > centre + 10 * sigma or a0 + H < centre - 10 * sigma:
+            continue
+        for a in range(p + 1):
+            s = 0.0
+            for g in range(nq):
+                xx = a0 + H * xg[g]
+                dens = math.exp(-0.5 * ((xx - centre) / sigma) ** 2) / (math.sqrt(2 * math.pi) * sigma)
+                s += wg[g] * H * lagrange_value(p, a, xg[g]) * dens
+            out[(c, a)] = s
+    return out
+
+
+def segment_z_integrals(mesh: Mesh, z_top: float, z_bot: float):
+    """J[(cz, c)] = int over [z_bot, z_top] of phi_c on cell layer cz."""
+    p = mesh.p
+    z0, Hz = mesh.origin[2], mesh.H[2]
+    lo, hi = max(min(z_bot, z_top), z0), min(max(z_bot, z_top), z0 + mesh.extent[2])
+    xg, wg = gauss01(3)
+    out = {}
+    for cz in range(mesh.nz):
+        a0, a1 = z0 + cz * Hz, z0 + (cz + 1) * Hz
+        s0, s1 = max(a0, lo), min(a1, hi)
+        if s1 <= s0:
+            continue
+        for c in range(p + 1):
+            out[(cz, c)] = sum(wg[g] * (s1 - s0) * lagrange_value(p, c, (s0 + (s1 - s0) * xg[g] - a0) / Hz)
+                               for g in range(3))
+    return out
+
+
+def well_weights(mesh: Mesh, wl) -> Dict[int, float]:
+    """Source weights of a well: w_i = int N_i(x, y, z) s(x, y) dz dx dy over
+    the screen, with s a line (sigma = 0) or a lateral normal density of
+    standard deviation sigma (the well's spread), so that sum_i w_i equals the
+    screen length inside the box."""
+    sigma = float(wl[6]) if len(wl) > 6 else 0.0
+    if sigma <= 0.0:
+        return line_weights(mesh, wl[0], wl[1], wl[2], wl[3])
+    p = mesh.p
+    Ix = gaussian_cell_integrals(mesh, 0, wl[0], sigma)
+    Iy = gaussian_cell_integrals(mesh, 1, wl[1], sigma)
+    Jz = segment_z_integrals(mesh, wl[2], wl[3])
+    out: Dict[int, float] = {}
+    for (cz, c), vz in Jz.items():
+        for (cy, b), vy in Iy.items():
+            for (cx, a), vx in Ix.items():
+                nd = mesh.node_index(p * cx + a, p * cy + b, p * cz + c)
+                out[nd] = out.get(nd, 0.0) + vx * vy * vz
+    return out
+
+
 def face_load(mesh: Mesh, face: int, value: float) -> np.ndarray:
     """F_i = value * int_face N_i dS for a uniform normal flux into the domain."""
     p = mesh.p
@@ -351,11 +414,13 @@ class OracleSim:
         # wells: head source and lumped heat injection term
         self.d_well = np.zeros(m.n_nodes)
         self.Tin_well = np.zeros(m.n_nodes)       # sum d*T_in
-        for wl in np.asarray(sc.wells).reshape(-1, 6):
+        wells = np.asarray(sc.wells, dtype=np.float64)
+        wells = wells.reshape(-1, wells.shape[-1] if wells.size else 7)
+        for wl in wells:
             L = abs(wl[2] - wl[3])
             if L <= 0:
                 continue
-            wts = line_weights(m, wl[0], wl[1], wl[2], wl[3])
+            wts = well_weights(m, wl)
             for node, wv in wts.items():
                 self.F_static[HEAD][node] += wl[4] / L * wv
                 if wl[4] > 0:

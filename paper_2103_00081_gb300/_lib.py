@@ -16,7 +16,7 @@ HT_OK, HT_EINVAL, HT_ENOMEM, HT_ECUDA, HT_ENOCONV, HT_EBREAKDOWN, HT_ETIMEOUT = 
 HT_HEAD, HT_TEMP, HT_QX, HT_QY, HT_QZ = 0, 1, 2, 3, 4
 HT_BC_NONE, HT_BC_DIRICHLET, HT_BC_FLUX = 0, 1, 2
 HT_FP64, HT_MIXED = 0, 1
-HT_KRYLOV_BICGSTAB = 0
+HT_KRYLOV_BICGSTAB, HT_KRYLOV_GMRES = 0, 1
 HT_PREC_JACOBI, HT_PREC_CHEBYSHEV = 0, 1
 
 ERROR_NAMES = {0: "HT_OK", -1: "HT_EINVAL", -2: "HT_ENOMEM", -3: "HT_ECUDA", -4: "HT_ENOCONV",
@@ -30,9 +30,11 @@ class Mesh(ctypes.Structure):
 
 
 class SolverOpts(ctypes.Structure):
-    _fields_ = [("tol", c_double), ("max_iter", c_int), ("krylov", c_int), ("precond", c_int),
+    _fields_ = [("tol", c_double), ("max_iter", c_int), ("krylov", c_int), ("restart", c_int),
+                ("precond", c_int),
                 ("cheb_degree", c_int), ("precision", c_int), ("inner_tol", c_double),
-                ("max_outer", c_int), ("check_every", c_int), ("use_graphs", c_int)]
+                ("max_outer", c_int), ("check_every", c_int), ("use_graphs", c_int),
+                ("z_chunks", c_int)]
 
 
 class LineSrc(ctypes.Structure):
@@ -40,7 +42,7 @@ class LineSrc(ctypes.Structure):
 
 
 class Well(ctypes.Structure):
-    _fields_ = [(n, c_double) for n in ("x", "y", "z_top", "z_bot", "Q", "T_in")]
+    _fields_ = [(n, c_double) for n in ("x", "y", "z_top", "z_bot", "Q", "T_in", "sigma")]
 
 
 class StepStats(ctypes.Structure):
@@ -48,6 +50,17 @@ class StepStats(ctypes.Structure):
                 ("outer_heat", c_int), ("res_head", c_double), ("res_heat", c_double),
                 ("t", c_double), ("ms_loads", c_double), ("ms_head", c_double),
                 ("ms_heat", c_double), ("ms_total", c_double), ("status", c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class ProfileStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("head_applies", ctypes.c_longlong),
+                ("heat_applies", ctypes.c_longlong), ("head_apply_ms", c_double),
+                ("heat_apply_ms", c_double), ("head_applies_fp32", ctypes.c_longlong),
+                ("heat_applies_fp32", ctypes.c_longlong), ("head_apply_ms_fp32", c_double),
+                ("heat_apply_ms_fp32", c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -73,6 +86,8 @@ SIGNATURES = {
     "ht_apply": (c_int, [c_void_p, c_int, c_double, c_void_p, c_void_p, c_int]),
     "ht_diag": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
     "ht_rhs": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
+    "ht_profile": (c_int, [c_void_p, c_int]),
+    "ht_profile_read": (c_int, [c_void_p, POINTER(ProfileStats)]),
     "ht_mixture": (c_int, [c_double, c_double, c_double, c_double, c_double, POINTER(c_double), POINTER(c_double)]),
     "ht_specific_storage": (c_double, [c_double, c_double, c_double]),
 }

@@ -286,6 +286,86 @@ bool node_on_dirichlet(const ht_ctx* c, int field, long long id) {
            ((m & 8) && j == g.Ny - 1) || ((m & 16) && k == 0) || ((m & 32) && k == g.Nz - 1);
 }
 
+// n-point Gauss-Legendre rule on [0, 1]: Newton iteration on the Legendre
+// polynomial P_n from the standard cosine initial guesses.
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double t = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1.0 - t);
+        w[i] = 1.0 / ((1.0 - t * t) * dp * dp);   // (2 / ((1-t^2) P'^2)) / 2
+    }
+}
+
+// Source weights of a well: line weights (sigma = 0) or, for a lateral normal
+// density of standard deviation sigma, w_i = Ix(cx,a) Iy(cy,b) Jz(cz,c) with
+// the lateral cell integrals by a 10-point Gauss rule within 10 sigma.
+int well_weights(ht_ctx* c, const ht_well& wl, std::map<long long, double>& out) {
+    if (!(wl.sigma > 0)) return line_weights(c, wl.x, wl.y, wl.z_top, wl.z_bot, out, "well");
+    std::map<long long, double> probe;
+    HT_TRY(line_weights(c, wl.x, wl.y, wl.z_top, wl.z_bot, probe, "well"));   // validates the segment
+    const ht_mesh& m = c->mesh;
+    const int P = c->grid.P;
+    std::vector<double> xg, wg;
+    gauss_legendre01(10, xg, wg);
+    std::vector<std::pair<std::pair<int, int>, double>> I[2];
+    const double centre[2] = {wl.x, wl.y}, org[2] = {m.x0, m.y0};
+    const int ncs[2] = {m.nx, m.ny};
+    const double sg = wl.sigma;
+    for (int d = 0; d < 2; ++d) {
+        const double H = c->H[d];
+        for (int ci = 0; ci < ncs[d]; ++ci) {
+            const double a0 = org[d] + ci * H;
+            if (a0 > centre[d] + 10 * sg || a0 + H < centre[d] - 10 * sg) continue;
+            for (int a = 0; a <= P; ++a) {
+                double sum = 0.0;
+                for (int g = 0; g < 10; ++g) {
+                    const double xx = a0 + H * xg[g];
+                    const double u = (xx - centre[d]) / sg;
+                    sum += wg[g] * H * lag(P, a, xg[g]) * exp(-0.5 * u * u) / (sqrt(2.0 * M_PI) * sg);
+                }
+                I[d].push_back({{ci, a}, sum});
+            }
+        }
+    }
+    // z integrals over the screen
+    const double lo = std::max(wl.z_bot, m.z0), hi = std::min(wl.z_top, m.z0 + m.Lz);
+    const double Hz = c->H[2];
+    double xq[3], wq[3];
+    gauss01(3, xq, wq);
+    for (int cz = 0; cz < m.nz; ++cz) {
+        const double a0 = m.z0 + cz * Hz, a1 = a0 + Hz;
+        const double s0 = std::max(a0, lo), s1 = std::min(a1, hi);
+        if (s1 <= s0) continue;
+        for (int cc = 0; cc <= P; ++cc) {
+            double Iz = 0;
+            for (int g = 0; g < 3; ++g) Iz += wq[g] * (s1 - s0) * lag(P, cc, (s0 + (s1 - s0) * xq[g] - a0) / Hz);
+            for (auto& ey : I[1])
+                for (auto& ex : I[0]) {
+                    const long long i = (long long)P * ex.first.first + ex.first.second;
+                    const long long j = (long long)P * ey.first.first + ey.first.second;
+                    const long long k = (long long)P * cz + cc;
+                    out[i + (long long)c->grid.Nx * (j + (long long)c->grid.Ny * k)] += ex.second * ey.second * Iz;
+                }
+        }
+    }
+    return HT_OK;
+}
+
 // Rebuild Dirichlet values, static loads and source tables after changes.
 int finalize_setup(ht_ctx* c) {
     if (!c->cells_set) return fail(c, HT_EINVAL, "ht_set_cells must be called before stepping");
@@ -328,7 +408,7 @@ int finalize_setup(ht_ctx* c) {
     std::map<long long, double> wd;
     for (const ht_well& w : c->wells) {
         std::map<long long, double> lw;
-        HT_TRY(line_weights(c, w.x, w.y, w.z_top, w.z_bot, lw, "well"));
+        HT_TRY(well_weights(c, w, lw));
         const double L = std::min(w.z_top, c->mesh.z0 + c->mesh.Lz) - std::max(w.z_bot, c->mesh.z0);
         const double qlin = w.Q / (w.z_top - w.z_bot);
         (void)L;
@@ -426,6 +506,39 @@ int upload_cells(ht_ctx* c, double** d64, float** d32, const double* h, size_t n
 }
 
 }  // namespace
+
+int prof_flush(ht_ctx* c) {
+    if (c->ev_used == 0) return HT_OK;
+    HT_CUDA(c, cudaEventSynchronize(c->ev_pool[2 * c->ev_used - 1]));
+    for (size_t i = 0; i < c->ev_used; ++i) {
+        float ms = 0.f;
+        HT_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
+        c->prof_ms[c->ev_kind[i]].push_back(ms);
+    }
+    c->ev_used = 0;
+    c->ev_kind.clear();
+    return HT_OK;
+}
+
+int prof_begin(ht_ctx* c, int kind) {
+    if (!c->prof_on) return HT_OK;
+    if (c->ev_pool.empty()) {
+        c->ev_pool.resize(4096);
+        for (auto& e : c->ev_pool) HT_CUDA(c, cudaEventCreate(&e));
+    }
+    if (2 * c->ev_used + 2 > c->ev_pool.size()) HT_TRY(prof_flush(c));
+    HT_CUDA(c, cudaEventRecord(c->ev_pool[2 * c->ev_used], c->stream));
+    c->ev_kind.push_back(kind);
+    return HT_OK;
+}
+
+int prof_end(ht_ctx* c) {
+    if (!c->prof_on) return HT_OK;
+    HT_CUDA(c, cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], c->stream));
+    c->ev_used += 1;
+    return HT_OK;
+}
+
 }  // namespace ht
 
 using namespace ht;
@@ -437,7 +550,8 @@ int ht_default_solver(ht_solver_opts* o) {
     memset(o, 0, sizeof(*o));
     o->tol = 1e-10;
     o->max_iter = 20000;
-    o->krylov = HT_KRYLOV_BICGSTAB;
+    o->krylov = HT_KRYLOV_GMRES;
+    o->restart = 100;
     o->precond = HT_PREC_JACOBI;
     o->cheb_degree = 4;
     o->precision = HT_FP64;
@@ -505,7 +619,8 @@ int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream) 
     if (rc == HT_OK) rc = dalloc(c, &c->qs32, 3 * NQ * NC);
     const int G = vec_grid(c), tiles = apply_tiles(c);
     c->part_stride = std::max(G, tiles) + 32;
-    if (rc == HT_OK) rc = dalloc(c, &c->part, (size_t)8 * c->part_stride);
+    if (rc == HT_OK) rc = dalloc(c, &c->part, (size_t)(kMaxRestart + 8) * c->part_stride);
+    if (rc == HT_OK) rc = dalloc(c, &c->gm, 2);
     if (rc == HT_OK) rc = dalloc(c, &c->scal, 4);
     if (rc == HT_OK && cudaMallocHost(&c->scal_host, 4 * sizeof(Scal)) != cudaSuccess) rc = HT_ENOMEM;
     if (rc == HT_OK) {
@@ -538,7 +653,11 @@ void ht_destroy(ht_ctx* c) {
     for (float** pp : v32) dfree(*pp);
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
     dfree(c->scal);
+    dfree(c->gm);
+    dfree(c->V64);
+    dfree(c->V32);
     if (c->scal_host) cudaFreeHost(c->scal_host);
+    for (auto& e : c->ev_pool) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -620,7 +739,8 @@ int ht_add_line_sources(ht_ctx* c, int n, const ht_line_src* src) {
 int ht_add_wells(ht_ctx* c, int n, const ht_well* w) {
     if (!c || n < 0 || (n > 0 && !w)) return HT_EINVAL;
     for (int i = 0; i < n; ++i) {
-        if (!isfinite(w[i].Q) || !isfinite(w[i].T_in)) return fail(c, HT_EINVAL, "well %d: invalid parameters", i);
+        if (!isfinite(w[i].Q) || !isfinite(w[i].T_in) || !(w[i].sigma >= 0) || !isfinite(w[i].sigma))
+            return fail(c, HT_EINVAL, "well %d: invalid parameters", i);
         std::map<long long, double> probe;
         HT_TRY(line_weights(c, w[i].x, w[i].y, w[i].z_top, w[i].z_bot, probe, "well"));
     }
@@ -645,11 +765,15 @@ int ht_set_solver(ht_ctx* c, const ht_solver_opts* o) {
     if (!c || !o) return HT_EINVAL;
     if (!(o->tol > 0) || o->max_iter < 1) return fail(c, HT_EINVAL, "tol > 0 and max_iter >= 1 required");
     if (o->precision != HT_FP64 && o->precision != HT_MIXED) return fail(c, HT_EINVAL, "unknown precision");
-    if (o->krylov != HT_KRYLOV_BICGSTAB) return fail(c, HT_EINVAL, "unsupported Krylov method %d", o->krylov);
+    if (o->krylov != HT_KRYLOV_BICGSTAB && o->krylov != HT_KRYLOV_GMRES)
+        return fail(c, HT_EINVAL, "unsupported Krylov method %d", o->krylov);
+    if (o->krylov == HT_KRYLOV_GMRES && (o->restart < 2 || o->restart > ht::kMaxRestart))
+        return fail(c, HT_EINVAL, "GMRES restart must be 2..%d", ht::kMaxRestart);
     if (o->precond != HT_PREC_JACOBI && o->precond != HT_PREC_CHEBYSHEV)
         return fail(c, HT_EINVAL, "unknown preconditioner");
     if (o->precond == HT_PREC_CHEBYSHEV && (o->cheb_degree < 1 || o->cheb_degree > 32))
         return fail(c, HT_EINVAL, "cheb_degree must be 1..32");
+    if (o->z_chunks < 0) return fail(c, HT_EINVAL, "z_chunks must be >= 0");
     c->opts = *o;
     return HT_OK;
 }
@@ -761,6 +885,38 @@ int ht_rhs(ht_ctx* c, int field, double dt, double* b, int on_device) {
     if (field == HT_TEMP) HT_TRY(launch_darcy_qp(c, c->h));
     HT_TRY(launch_rhs(c, field, dt, field == HT_HEAD ? c->h : c->T, c->q));
     return copy_out(c, b, c->q, (size_t)c->grid.nn, on_device);
+}
+
+int ht_profile(ht_ctx* c, int on) {
+    if (!c) return HT_EINVAL;
+    cudaSetDevice(c->device);
+    HT_TRY(prof_flush(c));
+    c->prof_on = on;
+    c->n_launch = 0;
+    for (auto& v : c->prof_ms) v.clear();
+    return HT_OK;
+}
+
+int ht_profile_read(ht_ctx* c, ht_profile_stats* out) {
+    if (!c || !out) return HT_EINVAL;
+    cudaSetDevice(c->device);
+    HT_TRY(prof_flush(c));
+    memset(out, 0, sizeof(*out));
+    out->launches = c->n_launch;
+    long long* cnt[4] = {&out->head_applies, &out->heat_applies, &out->head_applies_fp32, &out->heat_applies_fp32};
+    double* ms[4] = {&out->head_apply_ms, &out->heat_apply_ms, &out->head_apply_ms_fp32, &out->heat_apply_ms_fp32};
+    for (int k = 0; k < 4; ++k) {
+        std::vector<float> v = c->prof_ms[k];
+        if (v.empty()) continue;
+        std::vector<float> srt = v;
+        std::nth_element(srt.begin(), srt.begin() + srt.size() / 2, srt.end());
+        const float med = srt[srt.size() / 2];
+        // launches that returned at once (solve already converged) take a tiny
+        // fraction of a working launch; leave them out of the average
+        for (float x : v)
+            if (x >= 0.25f * med) { *cnt[k] += 1; *ms[k] += x; }
+    }
+    return HT_OK;
 }
 
 int ht_mixture(double phi, double lambda_s, double lambda_w, double c_s, double c_w, double* lambda, double* cT) {

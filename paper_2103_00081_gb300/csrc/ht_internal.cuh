@@ -49,6 +49,18 @@ struct Scal {
     double rho, rho_old, omega, rv, ts, tt, rr0;
     double cheb_theta, cheb_delta;
     int done, iters, status, restarts;
+    int kdone, conv;
+};
+
+// GMRES(m) Hessenberg data (device resident).  H is column-major with
+// leading dimension kMaxRestart + 1: H[j + (kMaxRestart + 1) * k].
+constexpr int kMaxRestart = 512;
+constexpr int kDotChunk = 32;     // basis vectors per CTA row in the multi-dot
+struct Gmres {
+    double H[(kMaxRestart + 1) * kMaxRestart];
+    double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+    double hc[kMaxRestart + 1];   // second-pass corrections
+    double inv;                   // 1 / norm of the newest basis vector
 };
 
 enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NAN = 2 };
@@ -123,11 +135,23 @@ struct ht_ctx {
     int part_stride = 0;
     ht::Scal* scal = nullptr;
     ht::Scal* scal_host = nullptr;  // pinned mirror
+    ht::Gmres* gm = nullptr;        // [2]: FP64 solve, FP32 inner solve
+    double* V64 = nullptr;          // GMRES basis (restart+1 vectors), lazily allocated
+    float* V32 = nullptr;
+    int V_m = 0;
     double cheb_lmax[2] = {0, 0};
     double cheb_dt[2] = {-1, -1};
 
     ht_solver_opts opts{};
     std::string err;
+
+    // launch accounting / apply timing
+    long long n_launch = 0;
+    int prof_on = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;                 // pairs in use
+    std::vector<int> ev_kind;           // field + 2 * fp32 of each recorded pair
+    std::vector<std::vector<float>> prof_ms = std::vector<std::vector<float>>(4);
 };
 
 namespace ht {
@@ -177,6 +201,10 @@ int launch_well_diag(ht_ctx* c, double dt, double* D);
 // F[field] = Fstat + extra + pile loads at time t
 int launch_loads(ht_ctx* c, double t);
 int apply_tiles(const ht_ctx* c);
+// event bracketing of apply launches (kind = field + 2 * fp32)
+int prof_begin(ht_ctx* c, int kind);
+int prof_end(ht_ctx* c);
+int prof_flush(ht_ctx* c);
 
 // ---- Krylov (ht_krylov.cu) -------------------------------------------------
 int solve_head(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);

@@ -611,6 +611,7 @@ void tile_dims(const ht_ctx* c, dim3* grid, int* ZC) {
     const int tx = (g.Nx + S::TX - 1) / S::TX, ty = (g.Ny + S::TY - 1) / S::TY;
     const int target = 2 * (c->num_sms > 0 ? c->num_sms : 148);
     int chunks = (target + tx * ty - 1) / (tx * ty);
+    if (c->opts.z_chunks > 0) chunks = c->opts.z_chunks;
     chunks = chunks < 1 ? 1 : (chunks > g.ncz ? g.ncz : chunks);
     int zc = (g.ncz + chunks - 1) / chunks;
     chunks = (g.ncz + zc - 1) / zc;
@@ -632,7 +633,7 @@ int launch_tile(ht_ctx* c, const Grid& g, const Op& op, double* dot_part, int* n
         HT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_done = true;
     }
-    kern<<<grid, kCXM * kCYM, smem, c->stream>>>(g, op, ZC, dot_part, sc);
+    kern<<<grid, kCXM * kCYM, smem, c->stream>>>(g, op, ZC, dot_part, sc); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     if (n_part) *n_part = (int)(grid.x * grid.y * grid.z);
     return HT_OK;
@@ -679,18 +680,22 @@ int apply_tiles(const ht_ctx* c) {
 
 int launch_apply64(ht_ctx* c, int field, double dt, const double* x, double* y, double* dot_part,
                    int* n_part, const Scal* sc) {
+    HT_TRY(prof_begin(c, field));
     int rc = c->grid.P == 1 ? apply_P<1, double>(c, field, dt, x, y, dot_part, n_part, sc)
                             : apply_P<2, double>(c, field, dt, x, y, dot_part, n_part, sc);
     if (rc != HT_OK) return rc;
+    HT_TRY(prof_end(c));
     if (field == HT_TEMP && c->n_well_nodes > 0) return launch_well_apply64(c, dt, x, y, sc);
     return HT_OK;
 }
 
 int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y, double* dot_part,
                    int* n_part, const Scal* sc) {
+    HT_TRY(prof_begin(c, field + 2));
     int rc = c->grid.P == 1 ? apply_P<1, float>(c, field, dt, x, y, dot_part, n_part, sc)
                             : apply_P<2, float>(c, field, dt, x, y, dot_part, n_part, sc);
     if (rc != HT_OK) return rc;
+    HT_TRY(prof_end(c));
     if (field == HT_TEMP && c->n_well_nodes > 0) return launch_well_apply32(c, dt, x, y, sc);
     return HT_OK;
 }
@@ -746,6 +751,7 @@ int launch_darcy_qp(ht_ctx* c, const double* h) {
         darcy_qp_kernel<1><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, c->e64, c->qs64, c->qs32);
     else
         darcy_qp_kernel<2><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, c->e64, c->qs64, c->qs32);
+    ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }
@@ -769,27 +775,28 @@ int launch_cell_flux(ht_ctx* c, const double* h, int comp, double* out) {
         cell_flux_kernel<1><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, cb, invH, comp, out);
     else
         cell_flux_kernel<2><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, cb, invH, comp, out);
+    ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }
 
 int launch_well_apply64(ht_ctx* c, double dt, const double* x, double* y, const Scal* sc) {
     const int n = c->n_well_nodes;
-    well_apply_kernel<double><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, x, y, sc);
+    well_apply_kernel<double><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, x, y, sc); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }
 
 int launch_well_apply32(ht_ctx* c, float dt, const float* x, float* y, const Scal* sc) {
     const int n = c->n_well_nodes;
-    well_apply_kernel<float><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, x, y, sc);
+    well_apply_kernel<float><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, x, y, sc); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }
 
 int launch_well_diag(ht_ctx* c, double dt, double* D) {
     const int n = c->n_well_nodes;
-    well_diag_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, D);
+    well_diag_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, D); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }
@@ -798,7 +805,7 @@ int launch_loads(ht_ctx* c, double t) {
     const long long nn = c->grid.nn;
     const int grid = vec_grid(c);
     for (int f = 0; f < 2; ++f) {
-        add_kernel<<<grid, kVecThreads, 0, c->stream>>>(nn, c->Fstat[f], c->extra[f], c->F[f]);
+        add_kernel<<<grid, kVecThreads, 0, c->stream>>>(nn, c->Fstat[f], c->extra[f], c->F[f]); ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
     }
     if (c->n_pile_nodes > 0) {
@@ -806,7 +813,7 @@ int launch_loads(ht_ctx* c, double t) {
         const int n = c->n_pile_nodes;
         pile_load_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->pile_node, c->pile_off, c->pile_src,
                                                                  c->pile_w, c->d_piles, t, c->F[HT_TEMP],
-                                                                 c->F[HT_TEMP]);
+                                                                 c->F[HT_TEMP]); ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
     }
     return HT_OK;

@@ -107,9 +107,12 @@ class Simulator:
         return self._check(self._lib.ht_add_line_sources(self._h, rows.shape[0], arr))
 
     def add_wells(self, rows):
-        rows = np.asarray(rows, dtype=np.float64).reshape(-1, 6)
-        if rows.shape[0] == 0:
+        rows = np.asarray(rows, dtype=np.float64)
+        if rows.size == 0:
             return L.HT_OK
+        rows = rows.reshape(-1, rows.shape[-1])
+        if rows.shape[1] == 6:
+            rows = np.concatenate([rows, np.zeros((rows.shape[0], 1))], axis=1)
         arr = (L.Well * rows.shape[0])(*[L.Well(*map(float, r)) for r in rows])
         return self._check(self._lib.ht_add_wells(self._h, rows.shape[0], arr))
 
@@ -175,6 +178,15 @@ class Simulator:
 
     def rhs(self, field, dt):
         return self._vec_call(self._lib.ht_rhs, field, dt)
+
+    # -- profiling -------------------------------------------------------------
+    def profile(self, on=True):
+        return self._check(self._lib.ht_profile(self._h, int(on)))
+
+    def profile_read(self):
+        st = L.ProfileStats()
+        self._check(self._lib.ht_profile_read(self._h, byref(st)))
+        return st.as_dict()
 
     # -- scenario helper -----------------------------------------------------------
     @classmethod

@@ -23,8 +23,10 @@ Conventions
 * Faces: 0 x-min, 1 x-max, 2 y-min, 3 y-max, 4 z-min (bottom), 5 z-max (top).
 * Piles (line heat sources): rows [x, y, z_top, z_bot, mean, amp, period, phase]
   giving q_l(t) = mean + amp*sin(2*pi*t/period + phase) in W/m.
-* Wells: rows [x, y, z_top, z_bot, Q, T_in]; Q in m^3/s (+ injection) spread
-  uniformly along the screen; injected water enters at temperature T_in.
+* Wells: rows [x, y, z_top, z_bot, Q, T_in, sigma]; Q in m^3/s (+ injection)
+  spread uniformly along the screen and laterally either on the well axis
+  (sigma = 0, a line source) or as a normal density of standard deviation
+  sigma (m); injected water enters at temperature T_in.
 """
 from __future__ import annotations
 
@@ -59,7 +61,7 @@ class Scenario:
     Ss: float                          # specific storage, 1/m
     bc: Dict[int, Dict[int, Tuple[int, float]]]   # field -> face -> (type, value)
     piles: np.ndarray                  # [n, 8]
-    wells: np.ndarray                  # [n, 6]
+    wells: np.ndarray                  # [n, 7]
     h0: np.ndarray                     # [nodes] initial head, m
     T0: np.ndarray                     # [nodes] initial temperature
     dt: float                          # time step, s
@@ -169,12 +171,12 @@ def config1(nx: int = 16, ny: Optional[int] = None, nz: Optional[int] = None,
              {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
               3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
     return Scenario("plain_q1_cube", nx, ny, nz, order, (0.0, 0.0, 0.0), (L, L, L),
-                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 6)), h0, T0,
+                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 7)), h0, T0,
                     1.0 * DAY, n_steps)
 
 
 def config2(nx: int = 128, ny: int = 128, nz: int = 32, seed: int = 2,
-            n_steps: int = 180, order: int = 2) -> Scenario:
+            n_steps: int = 180, order: int = 2, well_sigma: float = 1.5) -> Scenario:
     """ATES-like layered aquifer: 200 m x 200 m x 50 m, Q2 cells, three
     horizontal layers (10/12/10 of 32 cell layers, scaled with nz) with iid
     lognormal K per cell (geometric means 1e-6 / 1e-4 / 1e-6 m/s, sigma_lnK =
@@ -197,9 +199,12 @@ def config2(nx: int = 128, ny: int = 128, nz: int = 32, seed: int = 2,
     hx, hy = Lx / (p * nx), Ly / (p * ny)
     def snap(v, h):
         return round(v / h) * h
+    # lateral spread of 1.5 m (about one cell of the 128 x 128 mesh): a line
+    # source makes the advective Galerkin heat system indefinite near the
+    # well (local Courant number ~40 at the Gauss points next to the axis)
     wells = np.array([
-        [snap(70.0, hx), snap(100.0, hy), z_hi, z_lo, +5.0e-3, T_amb + 10.0],
-        [snap(130.0, hx), snap(100.0, hy), z_hi, z_lo, -5.0e-3, T_amb + 10.0],
+        [snap(70.0, hx), snap(100.0, hy), z_hi, z_lo, +5.0e-3, T_amb + 10.0, well_sigma],
+        [snap(130.0, hx), snap(100.0, hy), z_hi, z_lo, -5.0e-3, T_amb + 10.0, well_sigma],
     ])
     Nn = (p * nx + 1) * (p * ny + 1) * (p * nz + 1)
     h0 = np.zeros(Nn)
@@ -246,7 +251,7 @@ def config3(nx: int = 256, ny: int = 256, nz: int = 64, seed: int = 3,
              {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
               3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
     return Scenario("pile_field_q1", nx, ny, nz, order, (0.0, 0.0, 0.0), extent,
-                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 6)), h0, T0,
+                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 7)), h0, T0,
                     1.0 * DAY, n_steps)
 
 
@@ -271,10 +276,13 @@ def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
                       rng.uniform(-20, 20, n_piles), rng.uniform(0, 40, n_piles),
                       np.full(n_piles, 30 * DAY), rng.uniform(0, 2 * np.pi, n_piles)], axis=1) \
         if n_piles else np.zeros((0, 8))
+    # even wells are line sources, odd wells spread laterally
     wells = np.stack([rng.uniform(0, Lx, n_wells), rng.uniform(0, Ly, n_wells),
                       rng.uniform(0.5 * Lz, Lz, n_wells), rng.uniform(0.0, 0.5 * Lz, n_wells),
                       np.where(np.arange(n_wells) % 2 == 0, 2e-3, -2e-3),
-                      np.full(n_wells, 25.0)], axis=1) if n_wells else np.zeros((0, 6))
+                      np.full(n_wells, 25.0),
+                      np.where(np.arange(n_wells) % 2 == 0, 0.0, rng.uniform(0.5, 3.0, n_wells))],
+                     axis=1) if n_wells else np.zeros((0, 7))
     bc = {HEAD: {f: (DIRICHLET, float(rng.uniform(-0.3, 0.3))) for f in faces_head},
           TEMP: {f: (DIRICHLET, float(rng.uniform(14, 16))) for f in faces_temp}}
     sc = Scenario(f"random_q{order}_{nx}x{ny}x{nz}_s{seed}", nx, ny, nz, order,

@@ -73,6 +73,21 @@ def test_operator_apply_diag_rhs_match_oracle(Sim, case, per_cell):
         _close(sim.get_field(field), o.cell_flux()[comp])
 
 
+@pytest.mark.parametrize("case", [(1, 20, 17, 9, 21), (2, 9, 16, 7, 22)], ids=_ids)
+@pytest.mark.parametrize("chunks", [1, 2, 3])
+def test_multi_layer_z_chunks_match_oracle(Sim, case, chunks):
+    """Tiles that march through several cell layers (1-3 z chunks)."""
+    sc = _scenario(case, per_cell=True)
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc, z_chunks=chunks)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(sc.n_nodes)
+    _close(sim.apply(S.HEAD, sc.dt, x), o.apply_head(x, sc.dt))
+    _close(sim.apply(S.TEMP, sc.dt, x), o.apply_heat(x, o.h, sc.dt))
+    _close(sim.diag(S.TEMP, sc.dt), o.diag_heat(o.h, sc.dt))
+    _close(sim.rhs(S.TEMP, sc.dt), o.heat_rhs(sc.dt, sc.dt, o.h))
+
+
 @pytest.mark.parametrize("case", CASES, ids=_ids)
 def test_steps_match_oracle_fp64(Sim, case):
     sc = _scenario(case)
@@ -85,6 +100,29 @@ def test_steps_match_oracle_fp64(Sim, case):
         assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
         assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
     assert abs(sim.time - 3 * sc.dt) < 1e-6
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=_ids)
+def test_bicgstab_heat_solver_matches_oracle(Sim, case):
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc, tol=1e-13, krylov=L.HT_KRYLOV_BICGSTAB)
+    for _ in range(2):
+        sim.step(sc.dt)
+        o.step(sc.dt)
+    assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=_ids)
+@pytest.mark.parametrize("restart", [2, 5, 40])
+def test_gmres_restart_lengths_match_oracle(Sim, case, restart):
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc, tol=1e-13, restart=restart, max_iter=100000)
+    sim.step(sc.dt)
+    o.step(sc.dt)
+    assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
 
 
 @pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=_ids)

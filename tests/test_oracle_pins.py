@@ -370,3 +370,33 @@ def test_mirror_symmetry_between_identical_piles():
         o.step(sc.dt)
     T = o.T.reshape(sc.node_dims[::-1])
     np.testing.assert_allclose(T, T[:, :, ::-1], rtol=0, atol=1e-12)
+
+
+def test_gaussian_well_integrals_match_erf_closed_forms():
+    """The lateral cell integrals of a spread well: summed over the local basis
+    they give the probability mass of the cell (partition of unity), and the
+    first moment sum_a x_a I_a equals int x g dx (linear reproduction), both
+    in closed form with erf."""
+    from scipy import special
+    for p in (1, 2):
+        m = fem.Mesh(20, 3, 2, p, (0.0, 0.0, 0.0), (30.0, 3.0, 2.0))
+        mu, sg = 13.7, 1.3
+        I = fem.gaussian_cell_integrals(m, 0, mu, sg)
+        H = m.H[0]
+        for c in range(m.nx):
+            a0, a1 = c * H, (c + 1) * H
+            if not any((c, a) in I for a in range(p + 1)):
+                continue
+            za, zb = (a0 - mu) / sg, (a1 - mu) / sg
+            mass = 0.5 * (special.erf(zb / math.sqrt(2)) - special.erf(za / math.sqrt(2)))
+            dens = lambda z: math.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+            first = mu * mass - sg * (dens(zb) - dens(za))
+            got_mass = sum(I[(c, a)] for a in range(p + 1))
+            got_first = sum(I[(c, a)] * (a0 + a * H / p) for a in range(p + 1))
+            assert abs(got_mass - mass) < 1e-13
+            assert abs(got_first - first) < 1e-12
+        # a well spread inside the box injects exactly Q (weights sum to L)
+        sc = S.random_small(3, 6, 6, 3, p, n_piles=0, n_wells=0)
+        wl = np.array([sc.extent[0] / 2, sc.extent[1] / 2, 15.0, 5.0, 1e-3, 20.0, 2.0])
+        w = fem.well_weights(fem.Mesh(sc.nx, sc.ny, sc.nz, p, sc.origin, sc.extent), wl)
+        assert abs(sum(w.values()) - 10.0) < 1e-9
