@@ -201,6 +201,36 @@ typedef struct {
 int ht_profile(ht_ctx* ctx, int on);
 int ht_profile_read(ht_ctx* ctx, ht_profile_stats* out);
 
+/* Allocation-free variant of the head-operator apply, for callers that
+ * cannot allocate device memory: a host application that has already handed
+ * all device memory to its own pool allocator and forbids other
+ * allocations, or a latency-critical stepping loop that must not call
+ * cudaMalloc because it can synchronise the device and stall.  Such a caller
+ * cannot create a context (ht_create allocates), so this entry point needs
+ * none.  The paper has no counterpart; it is an addition of this library.
+ *
+ * Computes y = A0 x for the constrained head operator S_s M + dt K_K of a
+ * structured mesh and *xAx = x^T y.  K [cells], x and y [nodes] and xAx [1]
+ * are device pointers owned by the caller on `device`; dirichlet_faces is a
+ * bit mask of the faces (bit f = face f) whose nodes are Dirichlet rows.
+ * Work is queued on cuda_stream (NULL: the legacy default stream); the call
+ * does not synchronise it.  On error a message is written into msg (msg_len
+ * bytes; msg may be NULL).
+ *
+ * Scratch: the per-tile partial sums of x^T y live in one static device
+ * array of 4096 doubles (32 KiB) that every GPU loading this library keeps
+ * until the process exits.  Meshes needing more than 4096 operator tiles are
+ * rejected with HT_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the array; every slot a call
+ * reads is written earlier by the same call, so nothing needs clearing, but
+ * calls whose kernels can run at the same time on one GPU (for example on
+ * two streams) race on it and must be serialised by the caller.  The
+ * function allocates no device or host memory. */
+int ht_head_apply_dot_noalloc(const ht_mesh* mesh, int dirichlet_faces, double Ss, double dt,
+                              const double* K, const double* x, double* y, double* xAx,
+                              int device, void* cuda_stream, char* msg, size_t msg_len);
+
 /* Bulk coefficients from the mixture rules of Section 2 and the storage of
  * Eq. 1: lambda = (1-phi) lambda_s + phi lambda_w, cT = (1-phi) c_s +
  * phi c_w, Ss = rho_w g / B_poro. */

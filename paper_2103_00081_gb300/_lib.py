@@ -88,6 +88,8 @@ SIGNATURES = {
     "ht_rhs": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
     "ht_profile": (c_int, [c_void_p, c_int]),
     "ht_profile_read": (c_int, [c_void_p, POINTER(ProfileStats)]),
+    "ht_head_apply_dot_noalloc": (c_int, [POINTER(Mesh), c_int, c_double, c_double, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_int, c_void_p, ctypes.c_char_p, c_size_t]),
     "ht_mixture": (c_int, [c_double, c_double, c_double, c_double, c_double, POINTER(c_double), POINTER(c_double)]),
     "ht_specific_storage": (c_double, [c_double, c_double, c_double]),
 }

@@ -187,6 +187,25 @@ void build_elem(ht_ctx* c) {
     for (size_t i = 0; i < sizeof(e) / sizeof(double); ++i) dst[i] = (float)src[i];
 }
 
+// Head-operator constants of a cell of size H (fast-diagonalisation factors,
+// eigenvalues and element diagonals) computed into a caller-owned struct; used
+// by the allocation-free entry point, which has no context.
+void head_elem_stack(int P, const double H[3], ht::Elem<double>& e) {
+    const int n = P + 1;
+    memset(&e, 0, sizeof(e));
+    double m[3][3][3], k[3][3][3];
+    for (int d = 0; d < 3; ++d) element_1d(P, H[d], m[d], k[d], e.G[d], e.Lam[d]);
+    for (int cc = 0; cc < n; ++cc)
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+                const int l = a + n * (b + n * cc);
+                e.dM[l] = m[0][a][a] * m[1][b][b] * m[2][cc][cc];
+                e.dK[l] = k[0][a][a] * m[1][b][b] * m[2][cc][cc] + m[0][a][a] * k[1][b][b] * m[2][cc][cc] +
+                          m[0][a][a] * m[1][b][b] * k[2][cc][cc];
+            }
+    for (int d = 0; d < 3; ++d) e.invH[d] = 1.0 / H[d];
+}
+
 // integral of phi_a over [0,1] (exact Gauss)
 double phi_int(int P, int a) {
     double xq[3], wq[3];
@@ -917,6 +936,34 @@ int ht_profile_read(ht_ctx* c, ht_profile_stats* out) {
             if (x >= 0.25f * med) { *cnt[k] += 1; *ms[k] += x; }
     }
     return HT_OK;
+}
+
+int ht_head_apply_dot_noalloc(const ht_mesh* mesh, int dirichlet_faces, double Ss, double dt, const double* K,
+                              const double* x, double* y, double* xAx, int device, void* cuda_stream, char* msg,
+                              size_t msg_len) {
+    if (msg && msg_len) msg[0] = 0;
+    if (!mesh || !K || !x || !y || !xAx) {
+        if (msg && msg_len) snprintf(msg, msg_len, "null argument");
+        return HT_EINVAL;
+    }
+    if ((mesh->order != 1 && mesh->order != 2) || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 ||
+        !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0) || !(Ss > 0) || !(dt > 0) ||
+        dirichlet_faces < 0 || dirichlet_faces > 63) {
+        if (msg && msg_len) snprintf(msg, msg_len, "invalid mesh, coefficient or face mask");
+        return HT_EINVAL;
+    }
+    Grid g{};
+    g.P = mesh->order;
+    g.ncx = mesh->nx; g.ncy = mesh->ny; g.ncz = mesh->nz;
+    g.Nx = g.P * g.ncx + 1; g.Ny = g.P * g.ncy + 1; g.Nz = g.P * g.ncz + 1;
+    g.nn = (long long)g.Nx * g.Ny * g.Nz;
+    g.nc = (long long)g.ncx * g.ncy * g.ncz;
+    g.dmask = dirichlet_faces;
+    // reference-element constants on the stack (no allocation)
+    const double H[3] = {mesh->Lx / mesh->nx, mesh->Ly / mesh->ny, mesh->Lz / mesh->nz};
+    Elem<double> e;
+    head_elem_stack(g.P, H, e);
+    return noalloc_head_apply_dot(g, e, Ss, dt, K, x, y, xAx, device, (cudaStream_t)cuda_stream, msg, msg_len);
 }
 
 int ht_mixture(double phi, double lambda_s, double lambda_w, double c_s, double c_w, double* lambda, double* cT) {

@@ -206,6 +206,13 @@ int prof_begin(ht_ctx* c, int kind);
 int prof_end(ht_ctx* c);
 int prof_flush(ht_ctx* c);
 
+// ---- allocation-free head apply (ht_ops.cu) ----------------------------------
+constexpr int kNoAllocMaxTiles = 4096;     // partial sums held by the static scratch
+constexpr int kNoAllocMaxDevices = 64;
+int noalloc_head_apply_dot(const Grid& g, const Elem<double>& e, double Ss, double dt, const double* K,
+                           const double* x, double* y, double* xAx, int device, cudaStream_t stream, char* msg,
+                           size_t msg_len);
+
 // ---- Krylov (ht_krylov.cu) -------------------------------------------------
 int solve_head(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);
 int solve_heat(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);

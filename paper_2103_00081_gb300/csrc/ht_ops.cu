@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "ht_internal.cuh"
 
 namespace ht {
@@ -817,6 +819,95 @@ int launch_loads(ht_ctx* c, double t) {
         HT_CUDA(c, cudaGetLastError());
     }
     return HT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free head apply with x^T A x (ht_head_apply_dot_noalloc).
+//
+// Scratch for the per-tile partial sums of x^T A x lives in this fixed,
+// file-scope device array instead of memory from cudaMalloc.  Every GPU that
+// loads the library holds it until the process exits.  Host code cannot use
+// the symbol itself as a device address: its device address is looked up
+// once per device with cudaGetSymbolAddress, with that device current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double ht_noalloc_part[kNoAllocMaxTiles];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+__global__ void noalloc_reduce_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+template <int P>
+int noalloc_P(const Grid& g, const Elem<double>& e, double Ss, double dt, const double* K, const double* x,
+              double* y, double* xAx, double* part, int num_sms, cudaStream_t stream, char* msg, size_t msg_len) {
+    using Sh = TileShape<P, kCXM, kCYM>;
+    const int tx = (g.Nx + Sh::TX - 1) / Sh::TX, ty = (g.Ny + Sh::TY - 1) / Sh::TY;
+    const int target = 2 * (num_sms > 0 ? num_sms : 148);
+    int chunks = (target + tx * ty - 1) / (tx * ty);
+    chunks = chunks < 1 ? 1 : (chunks > g.ncz ? g.ncz : chunks);
+    const int zc = (g.ncz + chunks - 1) / chunks;
+    chunks = (g.ncz + zc - 1) / zc;
+    const long long tiles = (long long)tx * ty * chunks;
+    if (tiles > kNoAllocMaxTiles) {
+        if (msg && msg_len) snprintf(msg, msg_len, "mesh needs %lld tiles; the static scratch holds %d", tiles,
+                                     kNoAllocMaxTiles);
+        return HT_EINVAL;
+    }
+    HeadOp<P, double, MODE_APPLY> op{};
+    op.x = x; op.y = y; op.K = K; op.alpha = Ss; op.dt = dt; op.e = e;
+    constexpr int n = P + 1, NL = n * n * n;
+    const size_t smem = (size_t)kCXM * kCYM * NL * sizeof(double);
+    auto kern = tile_kernel<P, double, kCXM, kCYM, HeadOp<P, double, MODE_APPLY>>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) {
+        kern<<<dim3(tx, ty, chunks), kCXM * kCYM, smem, stream>>>(g, op, zc, part, nullptr);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) {
+        noalloc_reduce_kernel<<<1, 256, 0, stream>>>(part, (int)tiles, xAx);
+        err = cudaGetLastError();
+    }
+    if (err != cudaSuccess) {
+        if (msg && msg_len) snprintf(msg, msg_len, "CUDA error: %s", cudaGetErrorString(err));
+        return HT_ECUDA;
+    }
+    return HT_OK;
+}
+}  // namespace
+
+int noalloc_head_apply_dot(const Grid& g, const Elem<double>& e, double Ss, double dt, const double* K,
+                           const double* x, double* y, double* xAx, int device, cudaStream_t stream, char* msg,
+                           size_t msg_len) {
+    if (device < 0 || device >= kNoAllocMaxDevices) {
+        if (msg && msg_len) snprintf(msg, msg_len, "device %d out of range", device);
+        return HT_EINVAL;
+    }
+    cudaError_t err = cudaSetDevice(device);
+    double* part = nullptr;
+    int num_sms = 0;
+    if (err == cudaSuccess) {
+        // one-time set-up per device: the device address of the static scratch
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[device]) {
+            void* addr = nullptr;
+            err = cudaGetSymbolAddress(&addr, ht_noalloc_part);
+            if (err == cudaSuccess) g_noalloc_addr[device] = static_cast<double*>(addr);
+        }
+        part = g_noalloc_addr[device];
+    }
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (err != cudaSuccess) {
+        if (msg && msg_len) snprintf(msg, msg_len, "CUDA error: %s", cudaGetErrorString(err));
+        return HT_ECUDA;
+    }
+    return g.P == 1 ? noalloc_P<1>(g, e, Ss, dt, K, x, y, xAx, part, num_sms, stream, msg, msg_len)
+                    : noalloc_P<2>(g, e, Ss, dt, K, x, y, xAx, part, num_sms, stream, msg, msg_len);
 }
 
 }  // namespace ht
