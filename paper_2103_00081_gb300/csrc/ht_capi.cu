@@ -715,6 +715,7 @@ int ht_set_cells(ht_ctx* c, const double* K, const double* lambda, const double*
     c->Ss = Ss;
     c->cells_set = true;
     c->loads_dirty = true;   // well heat terms depend on c_w
+    c->cheb_dt[0] = c->cheb_dt[1] = -1.0;   // operator changed: re-estimate the spectrum
     return HT_OK;
 }
 
@@ -727,6 +728,7 @@ int ht_set_bc(ht_ctx* c, int field, int face, int type, double value) {
     c->bc_type[field][face] = type;
     c->bc_val[field][face] = value;
     c->bc_dirty = true;
+    c->cheb_dt[field] = -1.0;
     return HT_OK;
 }
 

@@ -46,7 +46,7 @@ __device__ __forceinline__ double bsum(double v) {
 
 // ---- scalar kernel ----------------------------------------------------------
 enum {
-    SC_CG_INIT, SC_CG_ALPHA, SC_CG_BETA,
+    SC_CG_INIT, SC_CG_ALPHA, SC_CG_BETA, SC_FCG_BETA,
     SC_BI_INIT, SC_BI_ALPHA, SC_BI_OMEGA, SC_BI_BETA,
     SC_NORMS
 };
@@ -80,6 +80,14 @@ __global__ void scalar_kernel(int op, const double* __restrict__ part, int strid
         case SC_CG_BETA:  // a1 = r.z (new), a2 = r.r
             s->rz_new = a1; s->rr = a2;
             s->beta = a1 / s->rz;
+            s->rz = a1;
+            s->iters += 1;
+            if (!isfinite(a1) || !isfinite(a2)) { s->status = ST_NAN; s->done = 1; }
+            else if (a2 <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
+            break;
+        case SC_FCG_BETA:  // a0 = z.q, a1 = r.z (new), a2 = r.r; Polak-Ribiere beta
+            s->rz_new = a1; s->rr = a2;
+            s->beta = -s->alpha * a0 / s->rz;
             s->rz = a1;
             s->iters += 1;
             if (!isfinite(a1) || !isfinite(a2)) { s->status = ST_NAN; s->done = 1; }
@@ -478,6 +486,129 @@ __global__ void gm_scalar_kernel(int op, int k, const double* __restrict__ part,
     }
 }
 
+
+// ---- Chebyshev-Jacobi polynomial preconditioner ----------------------------------
+// z = p_k(D^-1 A) D^-1 r: k steps of the Chebyshev iteration for A z = r from
+// z = 0 on the interval [a, b] = [b / ratio, 1.2 lambda_max] of D^-1 A.  The
+// residual polynomial R = T_k((theta - lambda) / delta) / T_k(theta / delta)
+// lies in (-1, 1) for every lambda in (0, b] (below a the argument stays in
+// (1, theta / delta)), so lambda p_k(lambda) = 1 - R > 0: the preconditioner
+// is symmetric positive definite, as CG requires, and on [a, b] the
+// preconditioned spectrum is within 1 -+ 1 / T_k(theta / delta).
+template <typename T>
+__global__ void cheb_init_kernel(long long n, const T* __restrict__ r, const T* __restrict__ Dinv,
+                                 T* __restrict__ d, T* __restrict__ z, T inv_theta, const Scal* __restrict__ s) {
+    if (s && s->done) return;
+    GRID_LOOP(i, n) {
+        const T v = Dinv[i] * r[i] * inv_theta;
+        d[i] = v;
+        z[i] = v;
+    }
+}
+
+// d = c1 d + c2 Dinv (r - w); z += d
+template <typename T>
+__global__ void cheb_step_kernel(long long n, const T* __restrict__ r, const T* __restrict__ w,
+                                 const T* __restrict__ Dinv, T* __restrict__ d, T* __restrict__ z, T c1, T c2,
+                                 const Scal* __restrict__ s) {
+    if (s && s->done) return;
+    GRID_LOOP(i, n) {
+        const T di = fma(c1, d[i], c2 * Dinv[i] * (r[i] - w[i]));
+        d[i] = di;
+        z[i] += di;
+    }
+}
+
+// CG with an explicit preconditioned vector z:
+// x += alpha p; r -= alpha q.  part[2] = r.r
+template <typename T>
+__global__ void cgz_update_kernel(long long n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                  const T* __restrict__ q, const Scal* __restrict__ s, double* __restrict__ part,
+                                  int stride) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha;
+    T rr = 0;
+    GRID_LOOP(i, n) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+    }
+    write3<T>(part, stride, T(0), T(0), rr);
+}
+
+// part[slot] = r.z (the other slots keep what the update / init wrote); with
+// q != nullptr also part[0] = z.q for the flexible (Polak-Ribiere) beta
+template <typename T>
+__global__ void cgz_dot_kernel(long long n, const T* __restrict__ r, const T* __restrict__ z,
+                               const T* __restrict__ q, double* __restrict__ part, int stride, int slot,
+                               const Scal* __restrict__ s) {
+    if (s->done) return;
+    T rz = 0, zq = 0;
+    GRID_LOOP(i, n) {
+        const T zi = z[i];
+        rz = fma(r[i], zi, rz);
+        if (q) zq = fma(zi, q[i], zq);
+    }
+    const double v = bsum((double)rz);
+    const double u = bsum((double)zq);
+    if (threadIdx.x == 0) {
+        part[(size_t)slot * stride + blockIdx.x] = v;
+        if (q) part[blockIdx.x] = u;
+    }
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void cgz_pupdate_kernel(long long n, const T* __restrict__ z, T* __restrict__ p,
+                                   const Scal* __restrict__ s) {
+    if (s->done) return;
+    const T beta = (T)s->beta;
+    GRID_LOOP(i, n) p[i] = fma(beta, p[i], z[i]);
+}
+
+// r = b - q, z-independent init: part: 0, r.r, b.b  (r.z comes from cgz_dot)
+template <typename T>
+__global__ void cgz_init_kernel(long long n, const T* __restrict__ b, const T* __restrict__ q,
+                                T* __restrict__ r, double* __restrict__ part, int stride) {
+    T rr = 0, bb = 0;
+    GRID_LOOP(i, n) {
+        const T bi = b[i];
+        const T ri = bi - q[i];
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    write3<T>(part, stride, T(0), rr, bb);
+}
+
+template <typename T>
+__global__ void copy_kernel(long long n, const T* __restrict__ a, T* __restrict__ b) {
+    GRID_LOOP(i, n) b[i] = a[i];
+}
+
+// power iteration on D^-1 A: v = D^-1 w / |.|, part[0] = |D^-1 w|^2, part[1] = v.v
+__global__ void power_kernel(long long n, const double* __restrict__ w, const double* __restrict__ Dinv,
+                             double* __restrict__ v, double inv_norm, double* __restrict__ part, int stride) {
+    double a = 0, b = 0;
+    GRID_LOOP(i, n) {
+        const double vi = Dinv[i] * w[i] * inv_norm;
+        v[i] = vi;
+        a = fma(vi, vi, a);
+    }
+    write3<double>(part, stride, a, b, 0.0);
+}
+
+__global__ void seed_kernel(long long n, double* __restrict__ v) {
+    GRID_LOOP(i, n) {
+        unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ULL + 0x632BE59BD9B4E019ULL;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        v[i] = 2.0 * (double)(z >> 11) * (1.0 / 9007199254740992.0) - 1.0;   // zero-mean, all frequencies
+    }
+}
+
 // ---- mixed precision helpers ---------------------------------------------------
 // r = b - q (FP64); r32 = (float) r.  part: r.r, b.b
 __global__ void resid_kernel(long long n, const double* __restrict__ b, const double* __restrict__ q,
@@ -737,6 +868,107 @@ int run_gmres(ht_ctx* c, double dt, const V& w, const T* b, int slot, double tol
     return HT_OK;
 }
 
+
+constexpr double kChebRatio = 30.0;
+
+// largest eigenvalue of D^-1 A (head operator) by power iteration, cached per dt
+int cheb_lambda_max(ht_ctx* c, double dt, double* lmax) {
+    if (c->cheb_dt[HT_HEAD] == dt && c->cheb_lmax[HT_HEAD] > 0) {
+        *lmax = c->cheb_lmax[HT_HEAD];
+        return HT_OK;
+    }
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c);
+    const int S = c->part_stride;
+    double* v = c->rh;
+    double* w = c->s;
+    seed_kernel<<<G, kVecThreads, 0, c->stream>>>(n, v); ++c->n_launch;
+    double norm = 1.0, lam = 0.0;
+    for (int it = 0; it < 50; ++it) {
+        HT_TRY(launch_apply64(c, HT_HEAD, dt, v, w, nullptr, nullptr, nullptr));
+        power_kernel<<<G, kVecThreads, 0, c->stream>>>(n, w, c->D, v, 1.0 / norm, c->part, S); ++c->n_launch;
+        scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, S, G, c->scal + 3, 0.0, 0); ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+        HT_TRY(sync_scal(c, 3));
+        // v now holds D^-1 A v_prev / |v_prev|: its norm estimates lambda_max
+        const double nv = sqrt(c->scal_host[3].rr);
+        if (it > 0) lam = nv;
+        norm = nv > 0 ? nv : 1.0;
+    }
+    // power iteration approaches lambda_max from below; the margin keeps the
+    // top of the spectrum inside the Chebyshev interval
+    *lmax = 1.2 * lam;
+    c->cheb_lmax[HT_HEAD] = *lmax;
+    c->cheb_dt[HT_HEAD] = dt;
+    return HT_OK;
+}
+
+template <typename T, class V>
+int cheb_apply(ht_ctx* c, double dt, const V& w, const T* r, T* z, T* d, T* tmp, double lmax, const Scal* sc) {
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c);
+    const int k = c->opts.cheb_degree > 0 ? c->opts.cheb_degree : 4;
+    const double b = lmax, a = lmax / kChebRatio;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+    cheb_init_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, r, w.Dinv, d, z, (T)(1.0 / theta), sc); ++c->n_launch;
+    double rho_prev = 1.0 / sigma;
+    for (int j = 1; j < k; ++j) {
+        const double rho = 1.0 / (2.0 * sigma - rho_prev);
+        HT_TRY(apply_T<T>(c, HT_HEAD, dt, z, tmp, nullptr, nullptr, sc));
+        cheb_step_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, r, tmp, w.Dinv, d, z, (T)(rho * rho_prev),
+                                                              (T)(2.0 * rho / delta), sc); ++c->n_launch;
+        rho_prev = rho;
+    }
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+// CG preconditioned by the Chebyshev-Jacobi polynomial.  beta takes the
+// flexible (Polak-Ribiere) form -alpha z_new.q / r_old.z_old, equal to the
+// usual r_new.z_new / r_old.z_old in exact arithmetic but robust to the
+// rounding of a degree-k polynomial applied in FP32.
+template <typename T, class V>
+int run_cg_cheb(ht_ctx* c, double dt, const V& w, T* z, T* d, T* tmp, const T* b, int slot, double tol,
+                int max_iter, int* iters) {
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c);
+    const int S = c->part_stride;
+    Scal* sc = c->scal + slot;
+    double lmax = 0;
+    HT_TRY(cheb_lambda_max(c, dt, &lmax));
+    int np = 0;
+    HT_TRY(apply_T<T>(c, HT_HEAD, dt, w.x, w.q, nullptr, nullptr, nullptr));
+    cgz_init_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, b, w.q, w.r, c->part, S); ++c->n_launch;
+    HT_CUDA(c, cudaMemsetAsync(sc, 0, sizeof(Scal), c->stream));
+    HT_TRY((cheb_apply<T, V>(c, dt, w, w.r, z, d, tmp, lmax, nullptr)));
+    cgz_dot_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, z, (const T*)nullptr, c->part, S, 0, sc); ++c->n_launch;
+    HT_TRY(scalar(c, SC_CG_INIT, G, slot, tol, max_iter));
+    copy_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, z, w.p); ++c->n_launch;
+    HT_TRY(sync_scal(c, slot));
+    if (c->scal_host[slot].bb == 0.0) {
+        fill_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, T(0)); ++c->n_launch;
+        *iters = 0;
+        return HT_OK;
+    }
+    int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
+    while (!c->scal_host[slot].done) {
+        for (int it = 0; it < chunk; ++it) {
+            HT_TRY(apply_T<T>(c, HT_HEAD, dt, w.p, w.q, c->part, &np, sc));
+            HT_TRY(scalar(c, SC_CG_ALPHA, np, slot, tol, max_iter));
+            cgz_update_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, w.r, w.p, w.q, sc, c->part, S); ++c->n_launch;
+            HT_TRY((cheb_apply<T, V>(c, dt, w, w.r, z, d, tmp, lmax, sc)));
+            cgz_dot_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, z, w.q, c->part, S, 1, sc); ++c->n_launch;
+            HT_TRY(scalar(c, SC_FCG_BETA, G, slot, tol, max_iter));
+            cgz_pupdate_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, z, w.p, sc); ++c->n_launch;
+        }
+        HT_CUDA(c, cudaGetLastError());
+        HT_TRY(sync_scal(c, slot));
+        if (chunk < 32) chunk *= 2;
+    }
+    *iters = c->scal_host[slot].iters;
+    return HT_OK;
+}
+
 int prepare_diag(ht_ctx* c, int field, double dt) {
     HT_TRY(launch_diag(c, field, dt, c->z));
     inv_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, c->z, c->D, c->D32); ++c->n_launch;
@@ -769,7 +1001,9 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
         // restarts from the current iterate.
         for (int pass = 0; pass < 4; ++pass) {
             int it = 0;
-            if (field == HT_HEAD) HT_TRY((run_cg<double, Vecs64>(c, dt, w, b, 0, tol, max_iter - total, &it)));
+            if (field == HT_HEAD && c->opts.precond == HT_PREC_CHEBYSHEV)
+                HT_TRY((run_cg_cheb<double, Vecs64>(c, dt, w, c->z, c->z2, c->v, b, 0, tol, max_iter - total, &it)));
+            else if (field == HT_HEAD) HT_TRY((run_cg<double, Vecs64>(c, dt, w, b, 0, tol, max_iter - total, &it)));
             else if (c->opts.krylov == HT_KRYLOV_GMRES)
                 HT_TRY((run_gmres<double, Vecs64>(c, dt, w, b, 0, tol, max_iter - total, &it)));
             else HT_TRY((run_bicgstab<double, Vecs64>(c, dt, w, b, 0, tol, max_iter - total, &it)));
@@ -815,7 +1049,10 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
         fill_kernel<float><<<G, kVecThreads, 0, c->stream>>>(n, c->d32, 0.0f); ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
         int it = 0;
-        if (field == HT_HEAD)
+        if (field == HT_HEAD && c->opts.precond == HT_PREC_CHEBYSHEV)
+            HT_TRY((run_cg_cheb<float, Vecs32>(c, dt, w, c->z32, c->zz32, c->v32, c->r32, 1, inner_tol,
+                                               max_iter - total, &it)));
+        else if (field == HT_HEAD)
             HT_TRY((run_cg<float, Vecs32>(c, dt, w, c->r32, 1, inner_tol, max_iter - total, &it)));
         else if (c->opts.krylov == HT_KRYLOV_GMRES)
             HT_TRY((run_gmres<float, Vecs32>(c, dt, w, c->r32, 1, inner_tol, max_iter - total, &it)));

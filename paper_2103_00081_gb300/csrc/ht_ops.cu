@@ -143,18 +143,8 @@ struct HeadOp {
         }
         if (MODE == MODE_APPLY) {
             gather<P, T>(g, x, cx, cy, cz, true, res);
-            sweep<n, 0, false>(res, e.G[0]);
-            sweep<n, 1, false>(res, e.G[1]);
-            sweep<n, 2, false>(res, e.G[2]);
-#pragma unroll
-            for (int c2 = 0; c2 < n; ++c2)
-#pragma unroll
-                for (int b = 0; b < n; ++b)
-#pragma unroll
-                    for (int a = 0; a < n; ++a) {
-                        const int l = a + n * (b + n * c2);
-                        res[l] *= fma(beta, e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][c2], alpha);
-                    }
+            fdm(res, beta);
+            return;
         } else {  // RHS: alpha M (u_old - g_D) - beta K g_D
             T us[NL];
             const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
@@ -193,6 +183,32 @@ struct HeadOp {
         sweep<n, 0, true>(res, e.G[0]);
     }
 
+    // res <- (G^T)^3 diag(alpha + beta (Lx+Ly+Lz)) G^3 res, in place
+    __device__ __forceinline__ void fdm(T (&res)[NL], const T beta) const {
+        sweep<n, 0, false>(res, e.G[0]);
+        sweep<n, 1, false>(res, e.G[1]);
+        sweep<n, 2, false>(res, e.G[2]);
+#pragma unroll
+        for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+            for (int b = 0; b < n; ++b)
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    const int l = a + n * (b + n * c2);
+                    res[l] *= fma(beta, e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][c2], alpha);
+                }
+        sweep<n, 2, true>(res, e.G[2]);
+        sweep<n, 1, true>(res, e.G[1]);
+        sweep<n, 0, true>(res, e.G[0]);
+    }
+
+    // element result of the apply from the (masked) element vector u
+    __device__ __forceinline__ void compute(const T (&u)[NL], long long c, T (&res)[NL]) const {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) res[l] = u[l];
+        fdm(res, dt * ldro(K + c));
+    }
+
     __device__ __forceinline__ void emit(const Grid& g, int i, int j, int k, T val, T& dot) const {
         const long long id = nidx(g, i, j, k);
         const bool d = on_dir(g, i, j, k);
@@ -222,6 +238,14 @@ struct HeatOp {
     T cT_u, lam_u, dt, cw;
     Elem<T> e;
 
+    // element result of the apply from the (masked) element vector u
+    __device__ __forceinline__ void compute(const T (&u)[NL], long long c, T (&res)[NL]) const {
+        const T cT = cTc ? ldro(cTc + c) : cT_u;
+        const T dtlam = dt * (lamc ? ldro(lamc + c) : lam_u);
+        core(u, u, T(1), cT, dtlam, dt * cw, c, g_nc, res);
+    }
+    long long g_nc;
+
     __device__ __forceinline__ void cell(const Grid& g, int cx, int cy, int cz, long long c,
                                          T (&res)[NL]) const {
         const T cT = cTc ? ldro(cTc + c) : cT_u;
@@ -229,29 +253,55 @@ struct HeatOp {
         const T dtcw = dt * cw;
         const long long nc = g.nc;
         if (MODE == MODE_DIAG) {
+            // mass + diffusion diagonals, then the advective diagonal
+            //   sum_q W c_w N_l (q . grad N_l) = sum_d sum_q f_d(q) M^x_a M^y_b M^z_c
+            // with f_d = W q_d / H_d and 1D factors B*D (direction d) or B*B,
+            // contracted direction by direction (sum factorisation)
 #pragma unroll
             for (int l = 0; l < NL; ++l) res[l] = fma(dtlam, e.dK[l], cT * e.dM[l]);
-            for (int qz = 0; qz < n; ++qz)
-                for (int qy = 0; qy < n; ++qy)
-                    for (int qx = 0; qx < n; ++qx) {
-                        const int qi = qx + n * (qy + n * qz);
-                        const T w = e.W[qi] * dtcw;
-                        const T q0 = ldro(qs + (0 * NQ + qi) * nc + c);
-                        const T q1 = ldro(qs + (1 * NQ + qi) * nc + c);
-                        const T q2 = ldro(qs + (2 * NQ + qi) * nc + c);
 #pragma unroll
-                        for (int c2 = 0; c2 < n; ++c2)
+            for (int d = 0; d < 3; ++d) {
+                T f[NQ];
 #pragma unroll
-                            for (int b = 0; b < n; ++b)
+                for (int qi = 0; qi < NQ; ++qi) f[qi] = dtcw * e.W[qi] * e.invH[d] * ldro(qs + (d * NQ + qi) * nc + c);
+                // x: f1[qz][qy][a] = sum_qx Mx[qx][a] f[qz][qy][qx]
+                T f1[NQ];
 #pragma unroll
-                                for (int a = 0; a < n; ++a) {
-                                    const T Nv = e.B[qx][a] * e.B[qy][b] * e.B[qz][c2];
-                                    const T gx = e.D[qx][a] * e.B[qy][b] * e.B[qz][c2] * e.invH[0];
-                                    const T gy = e.B[qx][a] * e.D[qy][b] * e.B[qz][c2] * e.invH[1];
-                                    const T gz = e.B[qx][a] * e.B[qy][b] * e.D[qz][c2] * e.invH[2];
-                                    res[a + n * (b + n * c2)] += w * Nv * (q0 * gx + q1 * gy + q2 * gz);
-                                }
+                for (int zy = 0; zy < n * n; ++zy)
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int qx = 0; qx < n; ++qx)
+                            acc = fma(e.B[qx][a] * (d == 0 ? e.D[qx][a] : e.B[qx][a]), f[zy * n + qx], acc);
+                        f1[zy * n + a] = acc;
                     }
+                // y: f2[qz][b][a] = sum_qy My[qy][b] f1[qz][qy][a]
+                T f2[NQ];
+#pragma unroll
+                for (int qz = 0; qz < n; ++qz)
+#pragma unroll
+                    for (int b = 0; b < n; ++b)
+#pragma unroll
+                        for (int a = 0; a < n; ++a) {
+                            T acc = T(0);
+#pragma unroll
+                            for (int qy = 0; qy < n; ++qy)
+                                acc = fma(e.B[qy][b] * (d == 1 ? e.D[qy][b] : e.B[qy][b]), f1[(qz * n + qy) * n + a], acc);
+                            f2[(qz * n + b) * n + a] = acc;
+                        }
+                // z: res[c][b][a] += sum_qz Mz[qz][c] f2[qz][b][a]
+#pragma unroll
+                for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                    for (int ba = 0; ba < n * n; ++ba) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int qz = 0; qz < n; ++qz)
+                            acc = fma(e.B[qz][c2] * (d == 2 ? e.D[qz][c2] : e.B[qz][c2]), f2[qz * n * n + ba], acc);
+                        res[ba + n * n * c2] += acc;
+                    }
+            }
             return;
         }
         // input(s): APPLY: um = us = masked x; RHS: um = T_old - g_D, us = g_D
@@ -479,6 +529,193 @@ __global__ void __launch_bounds__(CXM* CYM) tile_kernel(const Grid g, const Op o
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The operator-apply kernel: like tile_kernel, but the node planes of each
+// cell layer are staged in shared memory by asynchronous copies (cp.async,
+// zero-filled for Dirichlet nodes) issued one layer ahead of the compute, so
+// every node value is read from global memory once per tile and the copies
+// of layer cz+1 overlap the cell work of layer cz.
+//   shared memory: slab [2P+1 plane slots][P*CYM+1][P*CXM+1] of T, then the
+//   element results E [CXM*CYM][(P+1)^3].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, int bytes, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <int P, int CXM, int CYM, typename T>
+struct ApplySmem {
+    static constexpr int n = P + 1, NL = n * n * n;
+    static constexpr int SX = P * CXM + 1, SY = P * CYM + 1, NS = 2 * P + 1;
+    static constexpr size_t slab_elems = (size_t)NS * SX * SY;
+    static constexpr size_t bytes = (slab_elems + (size_t)CXM * CYM * NL) * sizeof(T);
+};
+
+template <int P, typename T, int CXM, int CYM, class Op>
+__global__ void __launch_bounds__(CXM* CYM) apply_kernel(const Grid g, const Op op, const int ZC,
+                                                         const T* __restrict__ x, T* __restrict__ y,
+                                                         double* __restrict__ dot_part,
+                                                         const Scal* __restrict__ sc) {
+    if (sc && sc->done) return;
+    using S = TileShape<P, CXM, CYM>;
+    using M = ApplySmem<P, CXM, CYM, T>;
+    constexpr int n = P + 1, NL = n * n * n;
+    constexpr int SX = M::SX, SY = M::SY, NS = M::NS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* slab = reinterpret_cast<T*>(smem_raw);
+    T* E = slab + M::slab_elems;
+
+    const int ix0 = blockIdx.x * S::TX, iy0 = blockIdx.y * S::TY;
+    const int ix1 = min(ix0 + S::TX, g.Nx), iy1 = min(iy0 + S::TY, g.Ny);
+    const int cx_lo = max(ix0 / P - 1, 0), cy_lo = max(iy0 / P - 1, 0);
+    const int cx_hi = min((ix1 - 1) / P, g.ncx - 1), cy_hi = min((iy1 - 1) / P, g.ncy - 1);
+    const int CX = cx_hi - cx_lo + 1, CY = cy_hi - cy_lo + 1;
+    const int TXo = ix1 - ix0, TYo = iy1 - iy0;
+    const int last = (blockIdx.z == gridDim.z - 1);
+    const int k0 = blockIdx.z * ZC * P;
+    const int k1 = last ? g.Nz : min(k0 + ZC * P, g.Nz);
+    const int cz_lo = max((int)blockIdx.z * ZC - 1, 0);
+    const int cz_hi = last ? g.ncz - 1 : min((int)blockIdx.z * ZC + ZC - 1, g.ncz - 1);
+    const int i0 = P * cx_lo, j0 = P * cy_lo;
+    const int NXs = P * CX + 1, NYs = P * CY + 1;
+    const int plane = g.Nx * g.Ny;           // node counts fit in 32 bits
+    const bool tile_dir = g.dmask != 0 &&
+                          ((cx_lo == 0 && (g.dmask & 1)) || (cx_hi == g.ncx - 1 && (g.dmask & 2)) ||
+                           (cy_lo == 0 && (g.dmask & 4)) || (cy_hi == g.ncy - 1 && (g.dmask & 8)) ||
+                           (cz_lo == 0 && (g.dmask & 16)) || (cz_hi == g.ncz - 1 && (g.dmask & 32)));
+
+    // copies of node planes ka..kb into their slots (k mod NS); Dirichlet
+    // nodes are zero-filled
+    auto issue = [&](int ka, int kb) {
+        const int per = NXs * NYs;
+        const int cnt = (kb - ka + 1) * per;
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int pl = t / per, r = t - pl * per;
+            const int ly = r / NXs, lx = r - ly * NXs;
+            const int k = ka + pl, i = i0 + lx, j = j0 + ly;
+            T* dst = slab + ((k % NS) * SY + ly) * SX + lx;
+            const T* src = x + (i + g.Nx * j + plane * k);
+            const bool z = tile_dir && on_dir(g, i, j, k);
+            cp_async_elem(dst, src, (int)sizeof(T), z ? 0 : (int)sizeof(T));
+        }
+        cp_async_commit();
+    };
+
+    // per owned column: element-result offsets of its (up to 4) cells, slot
+    // xx + 2*yy for the lower/upper neighbour cell in x / y (-1: none)
+    int offs[S::CPT][4], gcol[S::CPT];
+#pragma unroll
+    for (int s = 0; s < S::CPT; ++s) {
+        gcol[s] = -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) offs[s][q] = -1;
+        const int col = threadIdx.x + s * S::NT;
+        if (col < TXo * TYo) {
+            const int ix = ix0 + col % TXo, iy = iy0 + col / TXo;
+            int cxs[2] = {-1, -1}, axs[2] = {0, 0}, cys[2] = {-1, -1}, bys[2] = {0, 0};
+            if (ix % P == 0) {
+                if (ix / P - 1 >= 0) { cxs[0] = ix / P - 1; axs[0] = P; }
+                if (ix / P < g.ncx) { cxs[1] = ix / P; axs[1] = 0; }
+            } else { cxs[0] = ix / P; axs[0] = ix % P; }
+            if (iy % P == 0) {
+                if (iy / P - 1 >= 0) { cys[0] = iy / P - 1; bys[0] = P; }
+                if (iy / P < g.ncy) { cys[1] = iy / P; bys[1] = 0; }
+            } else { cys[0] = iy / P; bys[0] = iy % P; }
+#pragma unroll
+            for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+                for (int xx = 0; xx < 2; ++xx)
+                    if (cxs[xx] >= 0 && cys[yy] >= 0)
+                        offs[s][xx + 2 * yy] = ((cxs[xx] - cx_lo) + CX * (cys[yy] - cy_lo)) * NL + axs[xx] + n * bys[yy];
+            gcol[s] = ix + g.Nx * iy;
+        }
+    }
+
+    T carry[S::CPT];
+#pragma unroll
+    for (int s = 0; s < S::CPT; ++s) carry[s] = T(0);
+    T dot = T(0);
+
+    issue(P * cz_lo, P * cz_lo + P);
+    for (int cz = cz_lo; cz <= cz_hi; ++cz) {
+        if (cz < cz_hi) issue(P * cz + P + 1, P * cz + 2 * P);
+        else cp_async_commit();
+        cp_async_wait_1();
+        __syncthreads();
+        {
+            const int cidx = threadIdx.x;
+            if (cidx < CX * CY) {
+                const int lx = cidx % CX, ly = cidx / CX;
+                const long long c = (long long)(cx_lo + lx) + (long long)g.ncx * ((cy_lo + ly) + (long long)g.ncy * cz);
+                T u[NL];
+#pragma unroll
+                for (int c2 = 0; c2 < n; ++c2) {
+                    const T* pl = slab + ((P * cz + c2) % NS) * SY * SX;
+#pragma unroll
+                    for (int b = 0; b < n; ++b)
+#pragma unroll
+                        for (int a = 0; a < n; ++a) u[a + n * (b + n * c2)] = pl[(P * ly + b) * SX + P * lx + a];
+                }
+                T res[NL];
+                op.compute(u, c, res);
+                T* e = E + (size_t)cidx * NL;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) e[l] = res[l];
+            }
+        }
+        __syncthreads();
+        const int kb = P * cz;
+#pragma unroll
+        for (int s = 0; s < S::CPT; ++s) {
+            if (gcol[s] < 0) continue;
+            T sj[P + 1];
+#pragma unroll
+            for (int j = 0; j <= P; ++j) sj[j] = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (offs[s][q] < 0) continue;
+                const T* base = E + offs[s][q];
+#pragma unroll
+                for (int j = 0; j <= P; ++j) sj[j] += base[n * n * j];
+            }
+            const int col = threadIdx.x + s * S::NT;
+            const int lxn = ix0 + col % TXo - i0, lyn = iy0 + col / TXo - j0;
+#pragma unroll
+            for (int j = 0; j <= P; ++j) {
+                const int k = kb + j;
+                T val;
+                bool emit_it;
+                if (j == 0) { val = carry[s] + sj[0]; emit_it = k >= k0 && k < k1; }
+                else if (j < P) { val = sj[j]; emit_it = k >= k0 && k < k1; }
+                else { carry[s] = sj[P]; val = carry[s]; emit_it = (cz == g.ncz - 1) && k >= k0 && k < k1; }
+                if (emit_it) {
+                    const int id = gcol[s] + plane * k;
+                    T xv = slab[((k % NS) * SY + lyn) * SX + lxn];
+                    T yv = val;
+                    if (tile_dir && on_dir(g, ix0 + col % TXo, iy0 + col / TXo, k)) {
+                        xv = x[id];   // Dirichlet row: identity, unmasked value
+                        yv = xv;
+                    }
+                    y[id] = yv;
+                    dot = fma(xv, yv, dot);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (dot_part) {
+        const double tot = block_sum((double)dot);
+        if (threadIdx.x == 0)
+            dot_part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Other per-cell kernels
 // ---------------------------------------------------------------------------
@@ -494,21 +731,46 @@ __global__ void darcy_qp_kernel(const Grid g, const double* __restrict__ h,
         double u[NL];
         gather<P, double>(g, h, cx, cy, cz, false, u);
         const double Kc = K[c];
+        // gradient at the Gauss points by sum factorisation: z, then y, then x
+        double zB[NQ], zD[NQ];   // [qz][b][a]
+#pragma unroll
         for (int qz = 0; qz < n; ++qz)
-            for (int qy = 0; qy < n; ++qy)
+#pragma unroll
+            for (int ba = 0; ba < n * n; ++ba) {
+                double sb = 0, sd = 0;
+#pragma unroll
+                for (int c2 = 0; c2 < n; ++c2) {
+                    sb = fma(e.B[qz][c2], u[ba + n * n * c2], sb);
+                    sd = fma(e.D[qz][c2], u[ba + n * n * c2], sd);
+                }
+                zB[qz * n * n + ba] = sb;
+                zD[qz * n * n + ba] = sd;
+            }
+#pragma unroll
+        for (int qz = 0; qz < n; ++qz)
+#pragma unroll
+            for (int qy = 0; qy < n; ++qy) {
+                double yBB[n], yDB[n], yBD[n];
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    double v0 = 0, v1 = 0, v2 = 0;
+#pragma unroll
+                    for (int b = 0; b < n; ++b) {
+                        v0 = fma(e.B[qy][b], zB[qz * n * n + a + n * b], v0);
+                        v1 = fma(e.D[qy][b], zB[qz * n * n + a + n * b], v1);
+                        v2 = fma(e.B[qy][b], zD[qz * n * n + a + n * b], v2);
+                    }
+                    yBB[a] = v0; yDB[a] = v1; yBD[a] = v2;
+                }
+#pragma unroll
                 for (int qx = 0; qx < n; ++qx) {
                     double gx = 0, gy = 0, gz = 0;
 #pragma unroll
-                    for (int c2 = 0; c2 < n; ++c2)
-#pragma unroll
-                        for (int b = 0; b < n; ++b)
-#pragma unroll
-                            for (int a = 0; a < n; ++a) {
-                                const double v = u[a + n * (b + n * c2)];
-                                gx += e.D[qx][a] * e.B[qy][b] * e.B[qz][c2] * v;
-                                gy += e.B[qx][a] * e.D[qy][b] * e.B[qz][c2] * v;
-                                gz += e.B[qx][a] * e.B[qy][b] * e.D[qz][c2] * v;
-                            }
+                    for (int a = 0; a < n; ++a) {
+                        gx = fma(e.D[qx][a], yBB[a], gx);
+                        gy = fma(e.B[qx][a], yDB[a], gy);
+                        gz = fma(e.B[qx][a], yBD[a], gz);
+                    }
                     const int qi = qx + n * (qy + n * qz);
                     const double q0 = -Kc * gx * e.invH[0];
                     const double q1 = -Kc * gy * e.invH[1];
@@ -520,6 +782,7 @@ __global__ void darcy_qp_kernel(const Grid g, const double* __restrict__ h,
                     qs32[(1 * NQ + qi) * g.nc + c] = (float)q1;
                     qs32[(2 * NQ + qi) * g.nc + c] = (float)q2;
                 }
+            }
     }
 }
 
@@ -641,6 +904,25 @@ int launch_tile(ht_ctx* c, const Grid& g, const Op& op, double* dot_part, int* n
     return HT_OK;
 }
 
+template <int P, typename T, class Op>
+int launch_apply_staged(ht_ctx* c, const Grid& g, const Op& op, const T* x, T* y, double* dot_part,
+                        int* n_part, const Scal* sc) {
+    dim3 grid;
+    int ZC;
+    tile_dims<P>(c, &grid, &ZC);
+    const size_t smem = ApplySmem<P, kCXM, kCYM, T>::bytes;
+    auto kern = apply_kernel<P, T, kCXM, kCYM, Op>;
+    static bool attr_done = false;   // per instantiation
+    if (!attr_done) {
+        HT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_done = true;
+    }
+    kern<<<grid, kCXM * kCYM, smem, c->stream>>>(g, op, ZC, x, y, dot_part, sc); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    if (n_part) *n_part = (int)(grid.x * grid.y * grid.z);
+    return HT_OK;
+}
+
 template <typename T>
 const Elem<T>& elem_of(const ht_ctx* c);
 template <>
@@ -658,7 +940,7 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
         op.x = x; op.y = y;
         op.K = f64 ? (const T*)c->K64 : (const T*)c->K32;
         op.alpha = (T)c->Ss; op.dt = dt; op.e = elem_of<T>(c);
-        return launch_tile<P, T>(c, g, op, dot_part, n_part, sc);
+        return launch_apply_staged<P, T>(c, g, op, x, y, dot_part, n_part, sc);
     }
     HeatOp<P, T, MODE_APPLY> op{};
     op.x = x; op.y = y;
@@ -667,7 +949,8 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
     op.lamc = f64 ? (const T*)c->lam64 : (const T*)c->lam32;
     op.cT_u = (T)c->cT_u; op.lam_u = (T)c->lam_u; op.dt = dt; op.cw = (T)c->cw;
     op.e = elem_of<T>(c);
-    return launch_tile<P, T>(c, g, op, dot_part, n_part, sc);
+    op.g_nc = g.nc;
+    return launch_apply_staged<P, T>(c, g, op, x, y, dot_part, n_part, sc);
 }
 
 }  // namespace

@@ -125,6 +125,24 @@ def test_gmres_restart_lengths_match_oracle(Sim, case, restart):
     assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
 
 
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4]], ids=_ids)
+@pytest.mark.parametrize("degree", [1, 3, 6])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_chebyshev_preconditioned_cg_matches_oracle(Sim, case, degree, mixed):
+    """Head CG with the Chebyshev-Jacobi polynomial preconditioner."""
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc, tol=1e-12, precond=L.HT_PREC_CHEBYSHEV, cheb_degree=degree,
+                            precision=L.HT_MIXED if mixed else L.HT_FP64)
+    for _ in range(2):
+        st = sim.step(sc.dt)
+        o.step(sc.dt)
+        assert st["res_head"] <= 1e-12
+        assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
+        assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+
+
 @pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=_ids)
 def test_mixed_precision_matches_oracle(Sim, case):
     sc = _scenario(case)
