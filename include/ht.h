@@ -49,6 +49,7 @@ enum { HT_BC_NONE = 0, HT_BC_DIRICHLET = 1, HT_BC_FLUX = 2 };
 enum { HT_FP64 = 0, HT_MIXED = 1 };
 enum { HT_KRYLOV_BICGSTAB = 0, HT_KRYLOV_GMRES = 1 };
 enum { HT_PREC_JACOBI = 0, HT_PREC_CHEBYSHEV = 1 };
+enum { HT_APPLY_AUTO = 0, HT_APPLY_TILED = 1, HT_APPLY_TWO_PASS = 2 };
 
 typedef struct ht_ctx ht_ctx;
 
@@ -87,8 +88,11 @@ typedef struct {
  * dot products and norms are FP64.  precond HT_PREC_CHEBYSHEV uses a
  * Chebyshev polynomial of degree cheb_degree in D^-1 A for the head CG.
  * z_chunks > 0 fixes the number of z chunks of the operator tiles (0: the
- * library picks it from the SM count); it changes performance, not results
- * beyond rounding order. */
+ * library picks it from the SM count).  apply_variant selects the operator
+ * kernel: HT_APPLY_TILED (one fused owner-computes tile kernel),
+ * HT_APPLY_TWO_PASS (cells into an element buffer, then a node gather) or
+ * HT_APPLY_AUTO (two-pass in FP32, tiled in FP64).  Both change performance,
+ * not results beyond rounding order. */
 typedef struct {
     double tol;
     int max_iter;
@@ -102,6 +106,7 @@ typedef struct {
     int check_every;
     int use_graphs;
     int z_chunks;
+    int apply_variant;
 } ht_solver_opts;
 
 /* Per-step statistics: Krylov iterations (inner iterations in mixed mode),

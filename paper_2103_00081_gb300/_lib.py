@@ -18,6 +18,7 @@ HT_BC_NONE, HT_BC_DIRICHLET, HT_BC_FLUX = 0, 1, 2
 HT_FP64, HT_MIXED = 0, 1
 HT_KRYLOV_BICGSTAB, HT_KRYLOV_GMRES = 0, 1
 HT_PREC_JACOBI, HT_PREC_CHEBYSHEV = 0, 1
+HT_APPLY_AUTO, HT_APPLY_TILED, HT_APPLY_TWO_PASS = 0, 1, 2
 
 ERROR_NAMES = {0: "HT_OK", -1: "HT_EINVAL", -2: "HT_ENOMEM", -3: "HT_ECUDA", -4: "HT_ENOCONV",
                -5: "HT_EBREAKDOWN", -6: "HT_ETIMEOUT"}
@@ -34,7 +35,7 @@ class SolverOpts(ctypes.Structure):
                 ("precond", c_int),
                 ("cheb_degree", c_int), ("precision", c_int), ("inner_tol", c_double),
                 ("max_outer", c_int), ("check_every", c_int), ("use_graphs", c_int),
-                ("z_chunks", c_int)]
+                ("z_chunks", c_int), ("apply_variant", c_int)]
 
 
 class LineSrc(ctypes.Structure):

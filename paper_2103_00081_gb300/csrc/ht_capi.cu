@@ -178,6 +178,7 @@ void build_elem(ht_ctx* c) {
                 e.dM[l] = m[0][a][a] * m[1][b][b] * m[2][cc][cc];
                 e.dK[l] = k[0][a][a] * m[1][b][b] * m[2][cc][cc] + m[0][a][a] * k[1][b][b] * m[2][cc][cc] +
                           m[0][a][a] * m[1][b][b] * k[2][cc][cc];
+                e.LS[l] = e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][cc];
             }
     // FP32 copy
     ht::Elem<float>& f = c->e32;
@@ -202,6 +203,7 @@ void head_elem_stack(int P, const double H[3], ht::Elem<double>& e) {
                 e.dM[l] = m[0][a][a] * m[1][b][b] * m[2][cc][cc];
                 e.dK[l] = k[0][a][a] * m[1][b][b] * m[2][cc][cc] + m[0][a][a] * k[1][b][b] * m[2][cc][cc] +
                           m[0][a][a] * m[1][b][b] * k[2][cc][cc];
+                e.LS[l] = e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][cc];
             }
     for (int d = 0; d < 3; ++d) e.invH[d] = 1.0 / H[d];
 }
@@ -636,8 +638,12 @@ int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream) 
         if (rc == HT_OK) rc = dalloc(c, pp, N);
     if (rc == HT_OK) rc = dalloc(c, &c->qs64, 3 * NQ * NC);
     if (rc == HT_OK) rc = dalloc(c, &c->qs32, 3 * NQ * NC);
+    if (rc == HT_OK) rc = dalloc(c, &c->E32, NQ * NC);
+    if (rc == HT_OK) rc = dalloc(c, &c->E64, NQ * NC);
     const int G = vec_grid(c), tiles = apply_tiles(c);
-    c->part_stride = std::max(G, tiles) + 32;
+    // the two-pass node gather writes one partial per (32 x 4) node column block and z split
+    const int node_blocks = ((g.Nx + 31) / 32) * ((g.Ny + 3) / 4) + 8 * std::max(c->num_sms, 148);
+    c->part_stride = std::max(std::max(G, tiles), node_blocks) + 32;
     if (rc == HT_OK) rc = dalloc(c, &c->part, (size_t)(kMaxRestart + 8) * c->part_stride);
     if (rc == HT_OK) rc = dalloc(c, &c->gm, 2);
     if (rc == HT_OK) rc = dalloc(c, &c->scal, 4);
@@ -665,10 +671,11 @@ void ht_destroy(ht_ctx* c) {
     double** v64[] = {&c->h, &c->T, &c->g[0], &c->g[1], &c->Fstat[0], &c->Fstat[1], &c->F[0], &c->F[1],
                       &c->extra[0], &c->extra[1], &c->x, &c->r, &c->z, &c->p, &c->q, &c->b, &c->D,
                       &c->rh, &c->v, &c->s, &c->tv, &c->ph, &c->sh, &c->z2, &c->K64, &c->lam64,
-                      &c->cT64, &c->qs64, &c->part, &c->pile_w, &c->well_d};
+                      &c->cT64, &c->qs64, &c->part, &c->pile_w, &c->well_d, &c->E64};
     for (double** pp : v64) dfree(*pp);
     float** v32[] = {&c->x32, &c->r32, &c->z32, &c->p32, &c->q32, &c->D32, &c->rh32, &c->v32, &c->s32,
-                     &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32, &c->K32, &c->lam32, &c->cT32, &c->qs32};
+                     &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32, &c->K32, &c->lam32, &c->cT32, &c->qs32,
+                     &c->E32};
     for (float** pp : v32) dfree(*pp);
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
     dfree(c->scal);
@@ -795,6 +802,8 @@ int ht_set_solver(ht_ctx* c, const ht_solver_opts* o) {
     if (o->precond == HT_PREC_CHEBYSHEV && (o->cheb_degree < 1 || o->cheb_degree > 32))
         return fail(c, HT_EINVAL, "cheb_degree must be 1..32");
     if (o->z_chunks < 0) return fail(c, HT_EINVAL, "z_chunks must be >= 0");
+    if (o->apply_variant < HT_APPLY_AUTO || o->apply_variant > HT_APPLY_TWO_PASS)
+        return fail(c, HT_EINVAL, "unknown apply variant %d", o->apply_variant);
     c->opts = *o;
     return HT_OK;
 }

@@ -41,6 +41,7 @@ struct Elem {
     T invH[3];
     T dM[27];
     T dK[27];
+    T LS[27];      // Lx[a] + Ly[b] + Lz[c] per mode l = a + n(b + n c)
 };
 
 // Device-resident scalars of one Krylov solve.
@@ -50,6 +51,7 @@ struct Scal {
     double cheb_theta, cheb_delta;
     int done, iters, status, restarts;
     int kdone, conv;
+    double rz2[2];   // r.z of the fused CG, indexed by iteration parity
 };
 
 // GMRES(m) Hessenberg data (device resident).  H is column-major with
@@ -123,6 +125,9 @@ struct ht_ctx {
     // Darcy flux at Gauss points [3*nq^3][cells]
     double* qs64 = nullptr;
     float* qs32 = nullptr;
+    // element-result buffers of the two-pass apply [(p+1)^3][cells]
+    double* E64 = nullptr;
+    float* E32 = nullptr;
 
     // Krylov workspace
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;

@@ -68,6 +68,7 @@ __global__ void scalar_kernel(int op, const double* __restrict__ part, int strid
     switch (op) {
         case SC_CG_INIT:  // a0 = r.z, a1 = r.r, a2 = b.b
             s->rz = a0; s->rr = a1; s->bb = a2; s->rr0 = a1;
+            s->rz2[0] = a0;
             s->iters = 0; s->status = ST_OK;
             s->done = (a1 <= tol2 * a2 || a2 == 0.0) ? 1 : 0;
             if (!isfinite(a0) || !isfinite(a1)) { s->status = ST_NAN; s->done = 1; }
@@ -189,6 +190,67 @@ __global__ void cg_pupdate_kernel(long long n, const T* __restrict__ r, const T*
                                   T* __restrict__ p, const Scal* __restrict__ s) {
     if (s->done) return;
     const T beta = (T)s->beta;
+    GRID_LOOP(i, n) p[i] = fma(beta, p[i], Dinv[i] * r[i]);
+}
+
+
+// ---- fused CG iteration (Jacobi) ------------------------------------------------
+// alpha and beta are reduced redundantly, in a fixed order, by every CTA of the
+// kernel that needs them, so a CG iteration is three launches: apply (with
+// the p.Ap partials), x/r update, p update.  r.z is double-buffered by the
+// iteration parity so that the CTA that stores the new value never races the
+// CTAs that still read the old one.
+template <typename T>
+__global__ void cgf_update_kernel(long long n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                  const T* __restrict__ q, const T* __restrict__ Dinv, Scal* __restrict__ s,
+                                  double* __restrict__ part, int stride, int np, int par) {
+    if (s->done) return;
+    __shared__ double sh_alpha;
+    const double pq = reduce_part(part, np);
+    if (threadIdx.x == 0) sh_alpha = pq;
+    __syncthreads();
+    const double pqv = sh_alpha;
+    if (!(pqv > 0.0) || !isfinite(pqv)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) { s->status = ST_BREAKDOWN; s->done = 1; }
+        return;
+    }
+    const T alpha = (T)(s->rz2[par] / pqv);
+    T rz = 0, rr = 0;
+    GRID_LOOP(i, n) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rz = fma(ri, Dinv[i] * ri, rz);
+        rr = fma(ri, ri, rr);
+    }
+    const double a = bsum((double)rz);
+    const double b = bsum((double)rr);
+    if (threadIdx.x == 0) {
+        part[(size_t)stride + blockIdx.x] = a;
+        part[(size_t)2 * stride + blockIdx.x] = b;
+    }
+}
+
+template <typename T>
+__global__ void cgf_pupdate_kernel(long long n, const T* __restrict__ r, const T* __restrict__ Dinv,
+                                   T* __restrict__ p, Scal* __restrict__ s, const double* __restrict__ part,
+                                   int stride, int np, int par, double tol2, int max_iter) {
+    if (s->done) return;
+    __shared__ double sh[2];
+    const double rz = reduce_part(part + (size_t)stride, np);
+    if (threadIdx.x == 0) sh[0] = rz;
+    const double rr = reduce_part(part + (size_t)2 * stride, np);
+    if (threadIdx.x == 0) sh[1] = rr;
+    __syncthreads();
+    const double rzn = sh[0], rrn = sh[1];
+    const T beta = (T)(rzn / s->rz2[par]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s->rz2[par ^ 1] = rzn;
+        s->rr = rrn;
+        s->iters += 1;
+        if (!isfinite(rzn) || !isfinite(rrn)) { s->status = ST_NAN; s->done = 1; }
+        else if (rrn <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
+    }
     GRID_LOOP(i, n) p[i] = fma(beta, p[i], Dinv[i] * r[i]);
 }
 
@@ -714,13 +776,15 @@ int run_cg(ht_ctx* c, double dt, const V& w, const T* b, int slot, double tol, i
         *iters = 0;
         return HT_OK;
     }
+    int it_enq = 0;
     while (!c->scal_host[slot].done) {
-        for (int k = 0; k < chunk; ++k) {
+        for (int k = 0; k < chunk; ++k, ++it_enq) {
+            const int par = it_enq & 1;
             HT_TRY(apply_T<T>(c, HT_HEAD, dt, w.p, w.q, c->part, &np, sc));
-            HT_TRY(scalar(c, SC_CG_ALPHA, np, slot, tol, max_iter));
-            cg_update_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, w.r, w.p, w.q, w.Dinv, sc, c->part, S); ++c->n_launch;
-            HT_TRY(scalar(c, SC_CG_BETA, G, slot, tol, max_iter));
-            cg_pupdate_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, w.Dinv, w.p, sc); ++c->n_launch;
+            cgf_update_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.x, w.r, w.p, w.q, w.Dinv, sc, c->part, S, np,
+                                                                   par); ++c->n_launch;
+            cgf_pupdate_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, w.Dinv, w.p, sc, c->part, S, G, par,
+                                                                    tol * tol, max_iter); ++c->n_launch;
         }
         HT_CUDA(c, cudaGetLastError());
         HT_TRY(sync_scal(c, slot));

@@ -53,16 +53,19 @@ __device__ __forceinline__ long long nidx(const Grid& g, int i, int j, int k) {
 template <typename T>
 __device__ __forceinline__ T ldro(const T* p) { return __ldg(p); }
 
+// Sum over the CTA (1D, 2D or 3D blocks whose size is a multiple of 32);
+// the result is valid in the thread with linear index 0.
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double ws[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, wid = tid >> 5;
     __syncthreads();
     if (lane == 0) ws[wid] = v;
     __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    v = (threadIdx.x < nw) ? ws[lane] : 0.0;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+    v = (tid < nw) ? ws[lane] : 0.0;
     if (wid == 0) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -189,14 +192,7 @@ struct HeadOp {
         sweep<n, 1, false>(res, e.G[1]);
         sweep<n, 2, false>(res, e.G[2]);
 #pragma unroll
-        for (int c2 = 0; c2 < n; ++c2)
-#pragma unroll
-            for (int b = 0; b < n; ++b)
-#pragma unroll
-                for (int a = 0; a < n; ++a) {
-                    const int l = a + n * (b + n * c2);
-                    res[l] *= fma(beta, e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][c2], alpha);
-                }
+        for (int l = 0; l < NL; ++l) res[l] *= fma(beta, e.LS[l], alpha);
         sweep<n, 2, true>(res, e.G[2]);
         sweep<n, 1, true>(res, e.G[1]);
         sweep<n, 0, true>(res, e.G[0]);
@@ -590,19 +586,23 @@ __global__ void __launch_bounds__(CXM* CYM) apply_kernel(const Grid g, const Op 
                            (cy_lo == 0 && (g.dmask & 4)) || (cy_hi == g.ncy - 1 && (g.dmask & 8)) ||
                            (cz_lo == 0 && (g.dmask & 16)) || (cz_hi == g.ncz - 1 && (g.dmask & 32)));
 
-    // copies of node planes ka..kb into their slots (k mod NS); Dirichlet
-    // nodes are zero-filled
+    // copies of node planes ka..kb into their slots (k mod NS), one row per
+    // warp and one node per lane; Dirichlet nodes are zero-filled
     auto issue = [&](int ka, int kb) {
-        const int per = NXs * NYs;
-        const int cnt = (kb - ka + 1) * per;
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const int pl = t / per, r = t - pl * per;
-            const int ly = r / NXs, lx = r - ly * NXs;
-            const int k = ka + pl, i = i0 + lx, j = j0 + ly;
-            T* dst = slab + ((k % NS) * SY + ly) * SX + lx;
-            const T* src = x + (i + g.Nx * j + plane * k);
-            const bool z = tile_dir && on_dir(g, i, j, k);
-            cp_async_elem(dst, src, (int)sizeof(T), z ? 0 : (int)sizeof(T));
+        const int rows = (kb - ka + 1) * NYs;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int r = wid; r < rows; r += nw) {
+            const int pl = r / NYs, ly = r - pl * NYs;
+            const int k = ka + pl, j = j0 + ly;
+            T* drow = slab + ((k % NS) * SY + ly) * SX;
+            const T* srow = x + (g.Nx * j + plane * k);
+            const bool rowdir = tile_dir && (((g.dmask & 4) && j == 0) || ((g.dmask & 8) && j == g.Ny - 1) ||
+                                             ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1));
+            for (int lx = lane; lx < NXs; lx += 32) {
+                const int i = i0 + lx;
+                const bool z = rowdir || (tile_dir && (((g.dmask & 1) && i == 0) || ((g.dmask & 2) && i == g.Nx - 1)));
+                cp_async_elem(drow + lx, srow + i, (int)sizeof(T), z ? 0 : (int)sizeof(T));
+            }
         }
         cp_async_commit();
     };
@@ -712,6 +712,134 @@ __global__ void __launch_bounds__(CXM* CYM) apply_kernel(const Grid g, const Op 
     if (dot_part) {
         const double tot = block_sum((double)dot);
         if (threadIdx.x == 0)
+            dot_part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Two-pass operator apply (variant used for FP32): pass 1 computes every
+// cell once (one thread per cell, no barriers) into an element-result buffer
+// E laid out component-major, E[l * nc + c], which stays in L2 for the mesh
+// sizes of interest; pass 2 gives every node its own thread, which sums the
+// contributions of its cells in a fixed order (deterministic, no atomics),
+// applies the Dirichlet identity rows and accumulates the fused dot product.
+// ---------------------------------------------------------------------------
+// Thread (cx, cy) of a (32 x 4) block marches through its share of the cell
+// layers; all indices are 32-bit and advance incrementally.
+template <int P, typename T, class Op>
+__global__ void __launch_bounds__(128) cell_pass_kernel(const Grid g, const Op op, const T* __restrict__ x,
+                                                        T* __restrict__ E, const int zlen,
+                                                        const Scal* __restrict__ sc) {
+    if (sc && sc->done) return;
+    constexpr int n = P + 1, NL = n * n * n;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cx >= g.ncx || cy >= g.ncy) return;
+    const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
+    const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+    const int NX = g.Nx, NXY = g.Nx * g.Ny;
+    int off[n * n];   // offsets of the (b, c) node rows of a cell
+#pragma unroll
+    for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+        for (int b = 0; b < n; ++b) off[b + n * c2] = NX * b + NXY * c2;
+    const bool edge_xy = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1);
+    int base = P * cx + NX * P * cy + NXY * P * cz0;
+    int c = cx + g.ncx * cy + layer * cz0;
+    for (int cz = cz0; cz < cz1; ++cz, base += NXY * P, c += layer) {
+        T u[NL];
+#pragma unroll
+        for (int bc = 0; bc < n * n; ++bc)
+#pragma unroll
+            for (int a2 = 0; a2 < n; ++a2) u[a2 + n * bc] = ldro(x + base + off[bc] + a2);
+        if (edge_xy || (g.dmask & 48 && (cz == 0 || cz == g.ncz - 1))) {
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a2 = 0; a2 < n; ++a2)
+                        if (on_dir(g, P * cx + a2, P * cy + b, P * cz + c2)) u[a2 + n * (b + n * c2)] = T(0);
+        }
+        T res[NL];
+        op.compute(u, c, res);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) E[l * nc + c] = res[l];
+    }
+}
+
+// Thread (i, j) of a (32 x 4) block sums, for each node plane of its share,
+// the contributions of the node's cells in a fixed order.
+template <int P, typename T>
+__global__ void __launch_bounds__(128) node_pass_kernel(const Grid g, const T* __restrict__ E,
+                                                        const T* __restrict__ x, T* __restrict__ y,
+                                                        const int klen, double* __restrict__ dot_part,
+                                                        const Scal* __restrict__ sc) {
+    if (sc && sc->done) return;
+    constexpr int n = P + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    T dot = T(0);
+    if (i < g.Nx && j < g.Ny) {
+        const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+        // neighbour cells in x and y (slot xx + 2 yy, lower/upper), their cell
+        // index part and local index part; invalid slots read nothing
+        int cxy[4], lxy[4];
+        bool vxy[4];
+        {
+            int cxs[2] = {0, 0}, axs[2] = {0, 0}, cys[2] = {0, 0}, bys[2] = {0, 0};
+            bool vx[2] = {false, false}, vy[2] = {false, false};
+            if (i % P == 0) {
+                if (i / P - 1 >= 0) { cxs[0] = i / P - 1; axs[0] = P; vx[0] = true; }
+                if (i / P < g.ncx) { cxs[1] = i / P; axs[1] = 0; vx[1] = true; }
+            } else { cxs[0] = i / P; axs[0] = i % P; vx[0] = true; }
+            if (j % P == 0) {
+                if (j / P - 1 >= 0) { cys[0] = j / P - 1; bys[0] = P; vy[0] = true; }
+                if (j / P < g.ncy) { cys[1] = j / P; bys[1] = 0; vy[1] = true; }
+            } else { cys[0] = j / P; bys[0] = j % P; vy[0] = true; }
+#pragma unroll
+            for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+                for (int xx = 0; xx < 2; ++xx) {
+                    const int q = xx + 2 * yy;
+                    vxy[q] = vx[xx] && vy[yy];
+                    cxy[q] = cxs[xx] + g.ncx * cys[yy];
+                    lxy[q] = axs[xx] + n * bys[yy];
+                }
+        }
+        const bool dir_xy = ((g.dmask & 1) && i == 0) || ((g.dmask & 2) && i == g.Nx - 1) ||
+                            ((g.dmask & 4) && j == 0) || ((g.dmask & 8) && j == g.Ny - 1);
+        const int k0 = blockIdx.z * klen, k1 = min(k0 + klen, g.Nz);
+        int id = i + g.Nx * j + g.Nx * g.Ny * k0;
+        const int NXY = g.Nx * g.Ny;
+        for (int k = k0; k < k1; ++k, id += NXY) {
+            // lower (slot 0) and upper (slot 1) cell layer of the node plane
+            int czs[2] = {0, 0}, czl[2] = {0, 0};
+            bool vz[2] = {false, false};
+            if (k % P == 0) {
+                if (k / P - 1 >= 0) { czs[0] = k / P - 1; czl[0] = P; vz[0] = true; }
+                if (k / P < g.ncz) { czs[1] = k / P; czl[1] = 0; vz[1] = true; }
+            } else { czs[0] = k / P; czl[0] = k % P; vz[0] = true; }
+            T v[8];
+#pragma unroll
+            for (int zz = 0; zz < 2; ++zz) {
+                const int cz = layer * czs[zz], lz = n * n * czl[zz];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    v[q + 4 * zz] = (vz[zz] && vxy[q]) ? __ldg(E + (lxy[q] + lz) * nc + cxy[q] + cz) : T(0);
+            }
+            T sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+            const T xv = x[id];
+            const bool d = dir_xy || ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1);
+            const T yv = d ? xv : sum;
+            y[id] = yv;
+            dot = fma(xv, yv, dot);
+        }
+    }
+    if (dot_part) {
+        const double tot = block_sum((double)dot);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
             dot_part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
     }
 }
@@ -924,6 +1052,51 @@ int launch_apply_staged(ht_ctx* c, const Grid& g, const Op& op, const T* x, T* y
 }
 
 template <typename T>
+T* elem_buffer(ht_ctx* c);
+template <>
+double* elem_buffer<double>(ht_ctx* c) { return c->E64; }
+template <>
+float* elem_buffer<float>(ht_ctx* c) { return c->E32; }
+
+template <int P, typename T, class Op>
+int launch_apply_two_pass(ht_ctx* c, const Grid& g, const Op& op, const T* x, T* y, double* dot_part,
+                          int* n_part, const Scal* sc) {
+    T* E = elem_buffer<T>(c);
+    const int sms = c->num_sms > 0 ? c->num_sms : 148;
+    // cell pass: (32 x 4) thread columns, z split so that ~8 blocks per SM
+    const dim3 cb(32, 4);
+    const int gx = (g.ncx + 31) / 32, gy = (g.ncy + 3) / 4;
+    int zs = (8 * sms + gx * gy - 1) / (gx * gy);
+    zs = zs < 1 ? 1 : (zs > g.ncz ? g.ncz : zs);
+    const int zlen = (g.ncz + zs - 1) / zs;
+    zs = (g.ncz + zlen - 1) / zlen;
+    cell_pass_kernel<P, T, Op><<<dim3(gx, gy, zs), cb, 0, c->stream>>>(g, op, x, E, zlen, sc); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    // node pass: (32 x 4) node columns; the block count bounds the partial sums
+    const int nx = (g.Nx + 31) / 32, ny = (g.Ny + 3) / 4;
+    int ks = (8 * sms + nx * ny - 1) / (nx * ny);
+    const int kmax = c->part_stride / (nx * ny);
+    ks = ks < 1 ? 1 : (ks > g.Nz ? g.Nz : ks);
+    if (ks > kmax) ks = kmax > 0 ? kmax : 1;
+    const int klen = (g.Nz + ks - 1) / ks;
+    ks = (g.Nz + klen - 1) / klen;
+    if (dot_part && nx * ny * ks > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
+    node_pass_kernel<P, T><<<dim3(nx, ny, ks), cb, 0, c->stream>>>(g, E, x, y, klen, dot_part, sc); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    if (n_part) *n_part = nx * ny * ks;
+    return HT_OK;
+}
+
+template <typename T>
+bool use_two_pass(const ht_ctx* c) {
+    const int v = c->opts.apply_variant;
+    if (v == HT_APPLY_TILED) return false;
+    if (!elem_buffer<T>(const_cast<ht_ctx*>(c))) return false;
+    if (v == HT_APPLY_TWO_PASS) return true;
+    return sizeof(T) == 4;   // automatic choice: two-pass for FP32, tiled for FP64
+}
+
+template <typename T>
 const Elem<T>& elem_of(const ht_ctx* c);
 template <>
 const Elem<double>& elem_of<double>(const ht_ctx* c) { return c->e64; }
@@ -940,6 +1113,7 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
         op.x = x; op.y = y;
         op.K = f64 ? (const T*)c->K64 : (const T*)c->K32;
         op.alpha = (T)c->Ss; op.dt = dt; op.e = elem_of<T>(c);
+        if (use_two_pass<T>(c)) return launch_apply_two_pass<P, T>(c, g, op, x, y, dot_part, n_part, sc);
         return launch_apply_staged<P, T>(c, g, op, x, y, dot_part, n_part, sc);
     }
     HeatOp<P, T, MODE_APPLY> op{};
@@ -950,6 +1124,7 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
     op.cT_u = (T)c->cT_u; op.lam_u = (T)c->lam_u; op.dt = dt; op.cw = (T)c->cw;
     op.e = elem_of<T>(c);
     op.g_nc = g.nc;
+    if (use_two_pass<T>(c)) return launch_apply_two_pass<P, T>(c, g, op, x, y, dot_part, n_part, sc);
     return launch_apply_staged<P, T>(c, g, op, x, y, dot_part, n_part, sc);
 }
 

@@ -73,6 +73,18 @@ def test_operator_apply_diag_rhs_match_oracle(Sim, case, per_cell):
         _close(sim.get_field(field), o.cell_flux()[comp])
 
 
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_two_pass_apply_variant_matches_oracle(Sim, case):
+    """Operator applies through the two-pass (element buffer + node gather) kernels."""
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(case, per_cell=True)
+    o = fem.OracleSim(sc)
+    sim = Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TWO_PASS)
+    x = np.random.default_rng(5).standard_normal(sc.n_nodes)
+    _close(sim.apply(S.HEAD, sc.dt, x), o.apply_head(x, sc.dt))
+    _close(sim.apply(S.TEMP, sc.dt, x), o.apply_heat(x, o.h, sc.dt))
+
+
 @pytest.mark.parametrize("case", [(1, 20, 17, 9, 21), (2, 9, 16, 7, 22)], ids=_ids)
 @pytest.mark.parametrize("chunks", [1, 2, 3])
 def test_multi_layer_z_chunks_match_oracle(Sim, case, chunks):
