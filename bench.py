@@ -167,10 +167,23 @@ def run_ours(args):
         if dist:
             dist.barrier()
 
+    tuned = {}
+    tune_table = []
+    if not args.no_autotune:
+        from paper_2103_00081_gb300 import autotune as AT
+
+        def factory(opts):
+            return hydro.Simulator.from_scenario(sc, device=local, stream=stream.cuda_stream, tol=1e-10,
+                                                 precision=L.HT_MIXED, inner_tol=args.inner_tol,
+                                                 max_iter=200000, **opts)
+        tuned, tune_table = AT.tune(factory, dt, AT.signature(sc.nx, sc.ny, sc.nz, sc.order, L.HT_MIXED),
+                                    force=args.retune)
+
     def timed_run(precision):
+        extra = tuned if precision == L.HT_MIXED else {}
         sim = hydro.Simulator.from_scenario(sc, device=local, stream=stream.cuda_stream,
                                             tol=1e-10, precision=precision, inner_tol=args.inner_tol,
-                                            max_iter=200000)
+                                            max_iter=200000, **extra)
         for _ in range(args.warmup):
             sim.step(dt)
         torch.cuda.synchronize()
@@ -296,6 +309,7 @@ def run_ours(args):
         "e2e": {"value": rate_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nn * 8,
                 "d2h_bytes_per_step": 2 * nn * 8},
         "gpu_launches": prof_mixed["launches"],
+        "autotuned": {"opts": tuned, "candidates": [[o, t, st] for o, t, st in tune_table]},
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
@@ -369,6 +383,8 @@ def main():
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-4)
     ap.add_argument("--cpu-sample-cells", dest="cpu_sample_cells", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="no_autotune", action="store_true")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuning cache")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
