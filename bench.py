@@ -373,6 +373,55 @@ def run_reference(args):
     }))
 
 
+def run_batch(args):
+    """Batched workload: 64 independent Q1 problems (32x32x16 .. 96x96x48)
+    advanced together by ht_batch_step, against the same problems stepped one
+    after another; value = simulated years per hour summed over problems."""
+    import torch
+    from paper_2103_00081_gb300 import build as B
+    B.build()
+    from paper_2103_00081_gb300 import hydro
+    from paper_2103_00081_gb300 import _lib as L
+    torch.cuda.set_device(0)
+    scs = S.config4(n_problems=args.batch_size)
+    opts = dict(tol=1e-10, precision=L.HT_MIXED, inner_tol=args.inner_tol, krylov=L.HT_KRYLOV_BICGSTAB)
+    sims = [hydro.Simulator.from_scenario(sc, **opts) for sc in scs]
+    dt = scs[0].dt
+    batch = hydro.Batch(sims)
+    for _ in range(args.warmup):
+        batch.step(dt)
+    for sm in sims:
+        sm.profile(True)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        stats = batch.step(dt)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - w0
+    launches = sum(sm.profile_read()["launches"] for sm in sims)
+    # the same problems stepped one by one through ht_step
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        for sm in sims:
+            sm.step(dt)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - w0
+    batch.close()
+    years = args.steps * dt / YEAR * len(scs)
+    nodes = sum(sc.n_nodes for sc in scs)
+    print(json.dumps({
+        "metric": "simulated-years/hour summed over the batch at 1e-10 residual", "value": years / (t_batch / 3600),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic (seeded GRF lnK, piles)",
+        "config": {"workload": f"{len(scs)} Q1 problems, {nodes} nodes in total, dt=1 d, tol 1e-10",
+                   "sizes": sorted(set(f"{sc.nx}x{sc.ny}x{sc.nz}" for sc in scs))[:8]},
+        "sequential": {"value": years / (t_seq / 3600), "ms_per_step": t_seq / args.steps * 1e3},
+        "speedup_vs_sequential": t_seq / t_batch,
+        "iters_head": [st["iters_head"] for st in stats][:8], "gpu_launches": launches,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,11 +434,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuning cache")
+    ap.add_argument("--batch-size", dest="batch_size", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -189,6 +189,24 @@ int ht_apply(ht_ctx* ctx, int field, double dt, const double* x, double* y, int 
 int ht_diag(ht_ctx* ctx, int field, double dt, double* d, int on_device);
 int ht_rhs(ht_ctx* ctx, int field, double dt, double* b, int on_device);
 
+/* Batched steps of independent problems (same device, same element order,
+ * any mesh sizes; each problem is a context set up as usual and configured
+ * with precision HT_MIXED and the Jacobi preconditioner).  ht_batch_step
+ * advances every problem by dt: loads, right-hand sides, FP64 defect-
+ * correction residuals and heat solves run per problem, while the inner FP32
+ * head CG of all problems runs as one kernel launch per phase over a work
+ * list of (problem, block) items with per-problem scalars and convergence
+ * flags; a chunk of CG iterations is captured once in a CUDA graph (per dt)
+ * and replayed until every problem has converged.  stats may be NULL or
+ * point to n entries.  The batch does not own the contexts; destroy it
+ * before them.  Errors: HT_EINVAL (mixed devices or orders, wrong solver
+ * options), HT_ENOMEM, HT_ECUDA, HT_ENOCONV. */
+typedef struct ht_batch ht_batch;
+int ht_batch_create(ht_batch** out, int n, ht_ctx* const* problems);
+void ht_batch_destroy(ht_batch* batch);
+int ht_batch_step(ht_batch* batch, double dt, ht_step_stats* stats);
+const char* ht_batch_last_error(const ht_batch* batch);
+
 /* Launch accounting and operator timing.  ht_profile(ctx, on) resets the
  * counters; with on != 0 every operator-apply launch is bracketed by CUDA
  * events on the context's stream.  ht_profile_read() synchronises the stream

@@ -87,6 +87,10 @@ SIGNATURES = {
     "ht_apply": (c_int, [c_void_p, c_int, c_double, c_void_p, c_void_p, c_int]),
     "ht_diag": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
     "ht_rhs": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
+    "ht_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
+    "ht_batch_destroy": (None, [c_void_p]),
+    "ht_batch_step": (c_int, [c_void_p, c_double, c_void_p]),
+    "ht_batch_last_error": (ctypes.c_char_p, [c_void_p]),
     "ht_profile": (c_int, [c_void_p, c_int]),
     "ht_profile_read": (c_int, [c_void_p, POINTER(ProfileStats)]),
     "ht_head_apply_dot_noalloc": (c_int, [POINTER(Mesh), c_int, c_double, c_double, c_void_p, c_void_p,

@@ -528,6 +528,36 @@ int upload_cells(ht_ctx* c, double** d64, float** d32, const double* h, size_t n
 
 }  // namespace
 
+int batch_prepare_diag(ht_ctx* c, double dt);
+
+// first part of a batched step: loads at t + dt, head right-hand side,
+// initial iterate with Dirichlet values, diagonal
+int batch_head_begin(ht_ctx* c, double dt) {
+    HT_TRY(finalize_setup(c));
+    HT_TRY(launch_loads(c, c->t + dt));
+    HT_TRY(launch_rhs(c, HT_HEAD, dt, c->h, c->b));
+    HT_CUDA(c, cudaMemcpyAsync(c->x, c->h, (size_t)c->grid.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    HT_TRY(set_dirichlet_values(c, HT_HEAD, c->x));
+    return batch_prepare_diag(c, dt);
+}
+
+// last part of a batched step: store the head, then the heat solve with the
+// Darcy flux of the new head (single-problem path)
+int batch_head_end_and_heat(ht_ctx* c, double dt, ht_step_stats* st) {
+    const size_t n = (size_t)c->grid.nn;
+    HT_CUDA(c, cudaMemcpyAsync(c->h, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    HT_TRY(launch_darcy_qp(c, c->h));
+    HT_TRY(launch_rhs(c, HT_TEMP, dt, c->T, c->b));
+    HT_CUDA(c, cudaMemcpyAsync(c->x, c->T, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    HT_TRY(set_dirichlet_values(c, HT_TEMP, c->x));
+    HT_TRY(solve_heat(c, dt, c->x, c->b, &st->iters_heat, &st->outer_heat, &st->res_heat));
+    HT_CUDA(c, cudaMemcpyAsync(c->T, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->t += dt;
+    st->t = c->t;
+    return HT_OK;
+}
+
 int prof_flush(ht_ctx* c) {
     if (c->ev_used == 0) return HT_OK;
     HT_CUDA(c, cudaEventSynchronize(c->ev_pool[2 * c->ev_used - 1]));

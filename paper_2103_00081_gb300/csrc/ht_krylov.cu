@@ -1165,4 +1165,48 @@ int solve_heat(ht_ctx* c, double dt, double* x, const double* b, int* iters, int
     return solve_field(c, HT_TEMP, dt, x, b, iters, outer, res);
 }
 
+
+// ---- pieces of the head solve used by the batched step (ht_batch.cu) ----------------
+int batch_prepare_diag(ht_ctx* c, double dt) { return prepare_diag(c, HT_HEAD, dt); }
+
+// FP64 residual r = b - A x of the head system; r32 = (float) r; convergence test
+int batch_outer_residual(ht_ctx* c, double dt, double tol, int* converged, double* res) {
+    const int G = vec_grid(c);
+    HT_TRY(launch_apply64(c, HT_HEAD, dt, c->x, c->q, nullptr, nullptr, nullptr));
+    resid_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid.nn, c->b, c->q, nullptr, c->r32, c->part, c->part_stride); ++c->n_launch;
+    scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, c->part_stride, G, c->scal + 2, 0.0, 0); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    HT_TRY(sync_scal(c, 2));
+    const Scal s = c->scal_host[2];
+    if (!isfinite(s.rr)) return fail(c, HT_EINVAL, "head solve: non-finite residual");
+    *res = s.bb > 0 ? sqrt(s.rr / s.bb) : 0.0;
+    *converged = (s.rr <= tol * tol * s.bb) ? 1 : 0;
+    return HT_OK;
+}
+
+// start the inner FP32 CG on A32 d = r32 (d = 0); scalars in slot 1
+int batch_inner_init(ht_ctx* c, double dt, double inner_tol, int max_iter) {
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c);
+    fill_kernel<float><<<G, kVecThreads, 0, c->stream>>>(n, c->d32, 0.0f); ++c->n_launch;
+    HT_TRY(launch_apply32(c, HT_HEAD, (float)dt, c->d32, c->q32, nullptr, nullptr, nullptr));
+    cg_init_kernel<float><<<G, kVecThreads, 0, c->stream>>>(n, c->r32, c->q32, c->D32, c->r32, c->p32, c->part,
+                                                            c->part_stride); ++c->n_launch;
+    HT_CUDA(c, cudaMemsetAsync(c->scal + 1, 0, sizeof(Scal), c->stream));
+    scalar_kernel<<<1, 256, 0, c->stream>>>(SC_CG_INIT, c->part, c->part_stride, G, c->scal + 1,
+                                            inner_tol * inner_tol, max_iter); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+// x += d after the batched inner solve; reads back the inner scalars
+int batch_outer_update(ht_ctx* c) {
+    HT_TRY(sync_scal(c, 1));
+    if (c->scal_host[1].status == ST_NAN) return fail(c, HT_EINVAL, "head solve: FP32 inner solve produced non-finite values");
+    add_f32_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, c->x, c->d32); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
 }  // namespace ht
+

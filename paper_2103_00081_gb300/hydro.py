@@ -202,3 +202,40 @@ class Simulator:
         if solver:
             s.set_solver(**solver)
         return s
+
+
+class Batch:
+    """Batched steps of several Simulators (ht_batch_*): the inner FP32 head
+    CG of all problems runs in shared launches captured in a CUDA graph."""
+
+    def __init__(self, sims):
+        self._lib = L.lib()
+        self.sims = list(sims)
+        arr = (c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
+        h = c_void_p()
+        rc = self._lib.ht_batch_create(byref(h), len(self.sims), arr)
+        if rc != L.HT_OK:
+            raise HTError(rc, "ht_batch_create failed")
+        self._h = h
+
+    def step(self, dt, check=True):
+        n = len(self.sims)
+        stats = (L.StepStats * n)()
+        rc = self._lib.ht_batch_step(self._h, float(dt), ctypes.cast(stats, c_void_p))
+        if check and rc != L.HT_OK:
+            raise HTError(rc, self._lib.ht_batch_last_error(self._h).decode())
+        out = [s.as_dict() for s in stats]
+        for d in out:
+            d["rc"] = rc
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ht_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -292,3 +292,35 @@ def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
         sc.lam_cells = lam * np.exp(0.3 * rng.standard_normal(nc))
         sc.cT_cells = cT * np.exp(0.2 * rng.standard_normal(nc))
     return sc
+
+
+def config4(n_problems: int = 64, seed0: int = 1000, n_steps: int = 30,
+            size_range=(16, 48), extent=(400.0, 400.0, 100.0)) -> list:
+    """Batched scenarios: independent Q1 problems with nz ~ U{16..48} and
+    nx = ny = 2 nz cells (32x32x16 .. 96x96x48) over the same box, each with
+    its own Gaussian-random lnK (sigma_lnK ~ U(0.5, 1.5), correlation length
+    50 m) and 10-200 piles with random seasonal loads; dt = 1 day."""
+    out = []
+    for i in range(n_problems):
+        rng = np.random.default_rng(seed0 + i)
+        nz = int(rng.integers(size_range[0], size_range[1] + 1))
+        nx = ny = 2 * nz
+        lam, cT, cw, Ss = _sand()
+        Lx, Ly, Lz = extent
+        sig = float(rng.uniform(0.5, 1.5))
+        lnK = math.log(1e-5) + gaussian_field_fft((nz, ny, nx), (Lz / nz, Ly / ny, Lx / nx), 50.0, sig, rng)
+        K = np.exp(lnK).reshape(-1)
+        npl = int(rng.integers(10, 201))
+        piles = np.stack([rng.uniform(0.1 * Lx, 0.9 * Lx, npl), rng.uniform(0.1 * Ly, 0.9 * Ly, npl),
+                          np.full(npl, Lz), np.full(npl, Lz - 30.0), rng.uniform(-5, 5, npl),
+                          rng.uniform(10, 40, npl), np.full(npl, 365 * DAY),
+                          rng.uniform(0, 2 * np.pi, npl)], axis=1)
+        grad = 5.0 / (RHO_W * G_ACC)
+        h0 = _linear_x(None, (0, 0, 0), extent, 1, grad * Lx, -grad, nx, ny, nz)
+        T0 = np.full(h0.size, 15.0)
+        bc = _bc({0: (DIRICHLET, grad * Lx), 1: (DIRICHLET, 0.0)},
+                 {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
+                  3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
+        out.append(Scenario(f"batch_q1_{nx}x{ny}x{nz}_s{seed0 + i}", nx, ny, nz, 1, (0.0, 0.0, 0.0), extent,
+                            K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 7)), h0, T0, 1.0 * DAY, n_steps))
+    return out
