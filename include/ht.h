@@ -207,6 +207,31 @@ void ht_batch_destroy(ht_batch* batch);
 int ht_batch_step(ht_batch* batch, double dt, ht_step_stats* stats);
 const char* ht_batch_last_error(const ht_batch* batch);
 
+/* Learned warm start: a small 3D U-Net (2 levels, 16 / 32 channels) with
+ * hand-written forward, backward and Adam kernels; BF16 weights in the
+ * convolutions, FP32 accumulation and FP32 master weights.  The paper has no
+ * learned component; the network predicts step increments that serve as
+ * Krylov initial guesses (ht_step_learned_guess).
+ *   e1 = relu(conv3(x; cin->16)), p1 = avgpool2(e1), e2 = relu(conv3(p1; 16->32)),
+ *   d1 = relu(conv3([e1, upsample2(e2)]; 48->16)), y = conv1(d1; 16->cout)
+ * Tensors are device FP32 arrays [channel][D][H][W] (W fastest) with even
+ * D, H, W.  Parameters (host FP32, ht_unet_num_params values): per layer the
+ * weights [co][ci][27 or 1] then the biases [co].  cout must be 2. */
+typedef struct ht_unet ht_unet;
+int ht_unet_create(ht_unet** out, int cin, int cout, int device, void* cuda_stream);
+void ht_unet_destroy(ht_unet* net);
+int ht_unet_num_params(const ht_unet* net);
+const char* ht_unet_last_error(const ht_unet* net);
+int ht_unet_set_params(ht_unet* net, const float* theta);
+int ht_unet_get_params(ht_unet* net, float* theta);
+int ht_unet_forward(ht_unet* net, const float* x, int D, int H, int W, float* y);
+/* Mean squared error against target and its gradient (host, optional). */
+int ht_unet_loss_grad(ht_unet* net, const float* x, const float* target, int D, int H, int W,
+                      double* loss, float* grad);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the mean squared error. */
+int ht_unet_train_step(ht_unet* net, const float* x, const float* target, int D, int H, int W,
+                       float lr, double* loss);
+
 /* Launch accounting and operator timing.  ht_profile(ctx, on) resets the
  * counters; with on != 0 every operator-apply launch is bracketed by CUDA
  * events on the context's stream.  ht_profile_read() synchronises the stream

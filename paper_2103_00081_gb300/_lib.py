@@ -91,6 +91,16 @@ SIGNATURES = {
     "ht_batch_destroy": (None, [c_void_p]),
     "ht_batch_step": (c_int, [c_void_p, c_double, c_void_p]),
     "ht_batch_last_error": (ctypes.c_char_p, [c_void_p]),
+    "ht_unet_create": (c_int, [POINTER(c_void_p), c_int, c_int, c_int, c_void_p]),
+    "ht_unet_destroy": (None, [c_void_p]),
+    "ht_unet_num_params": (c_int, [c_void_p]),
+    "ht_unet_last_error": (ctypes.c_char_p, [c_void_p]),
+    "ht_unet_set_params": (c_int, [c_void_p, c_void_p]),
+    "ht_unet_get_params": (c_int, [c_void_p, c_void_p]),
+    "ht_unet_forward": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "ht_unet_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, POINTER(c_double), c_void_p]),
+    "ht_unet_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, ctypes.c_float,
+                                   POINTER(c_double)]),
     "ht_profile": (c_int, [c_void_p, c_int]),
     "ht_profile_read": (c_int, [c_void_p, POINTER(ProfileStats)]),
     "ht_head_apply_dot_noalloc": (c_int, [POINTER(Mesh), c_int, c_double, c_double, c_void_p, c_void_p,
