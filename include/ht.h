@@ -119,6 +119,8 @@ typedef struct {
     double t;
     double ms_loads, ms_head, ms_heat, ms_total;
     int status;
+    int guess_head, guess_heat;          /* 1: the learned initial guess won the gate */
+    double guess_res_head, guess_res_heat; /* relative residual of the chosen guess */
 } ht_step_stats;
 
 /* Fill *opts with the defaults (tol 1e-10, max_iter 20000, Jacobi, FP64). */
@@ -231,6 +233,22 @@ int ht_unet_loss_grad(ht_unet* net, const float* x, const float* target, int D, 
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the mean squared error. */
 int ht_unet_train_step(ht_unet* net, const float* x, const float* target, int D, int H, int W,
                        float lr, double* loss);
+
+/* Attach a trained U-Net (cin 4, cout 2) as the source of Krylov initial
+ * guesses (NULL detaches).  Once two step increments are known, every step
+ * builds the features [dT1, dT2, dh1, dh2] / (s_T, s_T, s_h, s_h) from the
+ * last two increments (s = their RMS), predicts the next increments
+ * (dT, dh) / (s_T, s_h), and for each field starts the Krylov solve from
+ * x^n + s * prediction if its true FP64 residual is smaller than that of x^n
+ * (the gate; the solver still converges to the same tolerance).  With
+ * record != 0 the features and targets of every step are kept for
+ * ht_learned_sample, also without a network.  Grid sizes are the node counts
+ * rounded up to even. */
+int ht_set_learned_guess(ht_ctx* ctx, ht_unet* net, int record);
+/* Copy the last step's features [4][D][H][W] and targets [2][D][H][W]
+ * (device FP32 buffers of the caller) and report D, H, W; HT_EINVAL when no
+ * complete sample exists yet. */
+int ht_learned_sample(ht_ctx* ctx, float* features, float* targets, int* dims);
 
 /* Launch accounting and operator timing.  ht_profile(ctx, on) resets the
  * counters; with on != 0 every operator-apply launch is bracketed by CUDA

@@ -50,7 +50,9 @@ class StepStats(ctypes.Structure):
     _fields_ = [("iters_head", c_int), ("iters_heat", c_int), ("outer_head", c_int),
                 ("outer_heat", c_int), ("res_head", c_double), ("res_heat", c_double),
                 ("t", c_double), ("ms_loads", c_double), ("ms_head", c_double),
-                ("ms_heat", c_double), ("ms_total", c_double), ("status", c_int)]
+                ("ms_heat", c_double), ("ms_total", c_double), ("status", c_int),
+                ("guess_head", c_int), ("guess_heat", c_int), ("guess_res_head", c_double),
+                ("guess_res_heat", c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -101,6 +103,8 @@ SIGNATURES = {
     "ht_unet_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, POINTER(c_double), c_void_p]),
     "ht_unet_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, ctypes.c_float,
                                    POINTER(c_double)]),
+    "ht_set_learned_guess": (c_int, [c_void_p, c_void_p, c_int]),
+    "ht_learned_sample": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_int)]),
     "ht_profile": (c_int, [c_void_p, c_int]),
     "ht_profile_read": (c_int, [c_void_p, POINTER(ProfileStats)]),
     "ht_head_apply_dot_noalloc": (c_int, [POINTER(Mesh), c_int, c_double, c_double, c_void_p, c_void_p,

@@ -518,7 +518,10 @@ int ht_batch_step(ht_batch* b, double dt, ht_step_stats* stats) {
         if (k == max_outer) { rc = HT_ENOCONV; b->err = "batched head solve did not converge"; break; }
         for (int i = 0; i < np && rc == HT_OK; ++i) {
             ht_ctx* c = b->probs[i];
-            const double itol = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-4;
+            const double base = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-4;
+            // no inner reduction beyond what the outer tolerance needs
+            const double need = res[i] > 0 ? 0.5 * tol / res[i] : 1.0;
+            const double itol = std::max(base, std::min(need, 0.5));
             rc = batch_inner_init(c, dt, conv[i] ? 1.0 : itol, c->opts.max_iter);
         }
         if (rc == HT_OK) {

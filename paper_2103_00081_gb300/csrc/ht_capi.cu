@@ -714,6 +714,7 @@ void ht_destroy(ht_ctx* c) {
     dfree(c->V32);
     if (c->scal_host) cudaFreeHost(c->scal_host);
     for (auto& e : c->ev_pool) cudaEventDestroy(e);
+    learned_free(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -850,13 +851,15 @@ int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
     ht_step_stats s{};
     int rc = HT_OK;
     cudaEventRecord(ev[0], c->stream);
-    rc = launch_loads(c, t1);
+    rc = learned_begin(c);
+    if (rc == HT_OK) rc = launch_loads(c, t1);
     cudaEventRecord(ev[1], c->stream);
     // head: b = S_s M h^n + dt F_h lifted; x0 = h^n with Dirichlet values
     if (rc == HT_OK) rc = launch_rhs(c, HT_HEAD, dt, c->h, c->b);
     if (rc == HT_OK && cudaMemcpyAsync(c->x, c->h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
         rc = fail(c, HT_ECUDA, "copy failed");
     if (rc == HT_OK) rc = set_dirichlet_values(c, HT_HEAD, c->x);
+    if (rc == HT_OK) rc = learned_gate(c, HT_HEAD, dt, c->x, c->b, &s.guess_head, &s.guess_res_head);
     if (rc == HT_OK) rc = solve_head(c, dt, c->x, c->b, &s.iters_head, &s.outer_head, &s.res_head);
     int rc_head = rc;
     if (rc == HT_OK || rc == HT_ENOCONV)
@@ -870,10 +873,17 @@ int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
         if (rc == HT_OK && cudaMemcpyAsync(c->x, c->T, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
             rc = fail(c, HT_ECUDA, "copy failed");
         if (rc == HT_OK) rc = set_dirichlet_values(c, HT_TEMP, c->x);
+        if (rc == HT_OK) rc = learned_gate(c, HT_TEMP, dt, c->x, c->b, &s.guess_heat, &s.guess_res_heat);
         if (rc == HT_OK) rc = solve_heat(c, dt, c->x, c->b, &s.iters_heat, &s.outer_heat, &s.res_heat);
         if (rc == HT_OK || rc == HT_ENOCONV)
             if (cudaMemcpyAsync(c->T, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
                 rc = fail(c, HT_ECUDA, "copy failed");
+    }
+    if (rc == HT_OK) {
+        // the step is complete: history for the learned guess (state update below)
+        const double t_save = c->t;
+        (void)t_save;
+        rc = learned_end(c);
     }
     cudaEventRecord(ev[3], c->stream);
     cudaEventSynchronize(ev[3]);

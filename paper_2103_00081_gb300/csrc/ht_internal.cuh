@@ -150,6 +150,17 @@ struct ht_ctx {
     ht_solver_opts opts{};
     std::string err;
 
+    // learned warm start
+    ht_unet* net = nullptr;
+    int learn_record = 0;
+    int hist = 0;                       // increments stored (0..2)
+    double *hn = nullptr, *Tn = nullptr;    // state at the start of the step
+    double *dh1 = nullptr, *dh2 = nullptr, *dT1 = nullptr, *dT2 = nullptr;
+    float *feat = nullptr, *targ = nullptr, *pred = nullptr;
+    int Dp = 0, Hp = 0, Wp = 0;
+    double lscale_T = 1.0, lscale_h = 1.0;   // RMS of the last increments (feature scales)
+    int have_feat = 0, have_sample = 0;
+
     // launch accounting / apply timing
     long long n_launch = 0;
     int prof_on = 0;
@@ -217,6 +228,12 @@ constexpr int kNoAllocMaxDevices = 64;
 int noalloc_head_apply_dot(const Grid& g, const Elem<double>& e, double Ss, double dt, const double* K,
                            const double* x, double* y, double* xAx, int device, cudaStream_t stream, char* msg,
                            size_t msg_len);
+
+// ---- learned warm start (ht_learned.cu) --------------------------------------
+int learned_begin(ht_ctx* c);                                   // features + prediction
+int learned_gate(ht_ctx* c, int field, double dt, double* x, const double* b, int* used, double* res);
+int learned_end(ht_ctx* c);                                     // targets + history
+void learned_free(ht_ctx* c);
 
 // ---- Krylov (ht_krylov.cu) -------------------------------------------------
 int solve_head(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);

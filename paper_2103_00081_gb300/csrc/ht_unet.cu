@@ -373,6 +373,8 @@ bool even_dims(int D, int H, int W) { return D > 1 && H > 1 && W > 1 && D % 2 ==
 
 }  // namespace
 
+cudaStream_t ht_unet_stream_internal(ht_unet* u) { return u ? u->stream : nullptr; }
+
 extern "C" {
 
 int ht_unet_create(ht_unet** out, int cin, int cout, int device, void* stream) {
