@@ -671,8 +671,9 @@ int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream) 
     if (rc == HT_OK) rc = dalloc(c, &c->E32, NQ * NC);
     if (rc == HT_OK) rc = dalloc(c, &c->E64, NQ * NC);
     const int G = vec_grid(c), tiles = apply_tiles(c);
-    // the two-pass node gather writes one partial per (32 x 4) node column block and z split
-    const int node_blocks = ((g.Nx + 31) / 32) * ((g.Ny + 3) / 4) + 8 * std::max(c->num_sms, 148);
+    // the two-pass node gather writes one partial per 128-node run of a layer and
+    // layer split, at most one wave of 128-thread CTAs (16 per SM) beyond one split
+    const int node_blocks = ((g.Nx + 31) / 32) * ((g.Ny + 3) / 4) + 16 * std::max(c->num_sms, 148);
     c->part_stride = std::max(std::max(G, tiles), node_blocks) + 32;
     if (rc == HT_OK) rc = dalloc(c, &c->part, (size_t)(kMaxRestart + 8) * c->part_stride);
     if (rc == HT_OK) rc = dalloc(c, &c->gm, 2);

@@ -52,6 +52,7 @@ struct Scal {
     int done, iters, status, restarts;
     int kdone, conv;
     double rz2[2];   // r.z of the fused CG, indexed by iteration parity
+    unsigned ticket; // CTAs done in the running fused-CG kernel (the last one resets it)
 };
 
 // GMRES(m) Hessenberg data (device resident).  H is column-major with
@@ -217,6 +218,12 @@ int launch_well_diag(ht_ctx* c, double dt, double* D);
 // F[field] = Fstat + extra + pile loads at time t
 int launch_loads(ht_ctx* c, double t);
 int apply_tiles(const ht_ctx* c);
+// fused two-pass Jacobi-CG iteration of the head system (ht_ops.cu)
+int fused_cg_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* Dinv, double* p, Scal* sc,
+                         int first, double tol2, int max_iter);
+int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* Dinv, float* p, Scal* sc,
+                         int first, double tol2, int max_iter);
+bool fused_cg_available(const ht_ctx* c, int fp32);
 // event bracketing of apply launches (kind = field + 2 * fp32)
 int prof_begin(ht_ctx* c, int kind);
 int prof_end(ht_ctx* c);

@@ -754,6 +754,15 @@ int apply_T<float>(ht_ctx* c, int field, double dt, const float* x, float* y, do
     return launch_apply32(c, field, (float)dt, x, y, part, np, sc);
 }
 
+inline int fused_cg_iteration(ht_ctx* c, double dt, const Vecs64& w, Scal* sc, int first, double tol2,
+                              int max_iter) {
+    return fused_cg_iteration64(c, dt, w.x, w.r, w.Dinv, w.p, sc, first, tol2, max_iter);
+}
+inline int fused_cg_iteration(ht_ctx* c, double dt, const Vecs32& w, Scal* sc, int first, double tol2,
+                              int max_iter) {
+    return fused_cg_iteration32(c, (float)dt, w.x, w.r, w.Dinv, w.p, sc, first, tol2, max_iter);
+}
+
 // Preconditioned CG on A0 x = b (x holds the initial guess).  Returns
 // iterations in *iters; status in c->scal[slot].
 template <typename T, class V>
@@ -777,6 +786,18 @@ int run_cg(ht_ctx* c, double dt, const V& w, const T* b, int slot, double tol, i
         return HT_OK;
     }
     int it_enq = 0;
+    if (fused_cg_available(c, sizeof(T) == 4)) {
+        // two launches per iteration: the p update rides in the element pass,
+        // the x / r update and the next dot products in the node gather
+        while (!c->scal_host[slot].done) {
+            for (int k = 0; k < chunk; ++k, ++it_enq)
+                HT_TRY(fused_cg_iteration(c, dt, w, sc, it_enq == 0, tol * tol, max_iter));
+            HT_TRY(sync_scal(c, slot));
+            if (chunk < 64) chunk *= 2;
+        }
+        *iters = c->scal_host[slot].iters;
+        return HT_OK;
+    }
     while (!c->scal_host[slot].done) {
         for (int k = 0; k < chunk; ++k, ++it_enq) {
             const int par = it_enq & 1;

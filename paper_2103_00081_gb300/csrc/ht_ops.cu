@@ -769,78 +769,285 @@ __global__ void __launch_bounds__(128) cell_pass_kernel(const Grid g, const Op o
     }
 }
 
-// Thread (i, j) of a (32 x 4) block sums, for each node plane of its share,
-// the contributions of the node's cells in a fixed order.
+// The element contributions of node (i, j, k): up to 2 x 2 x 2 cells share
+// it.  E[l * nc + c] splits into an xy part fixed per thread (eb[q] for the 4
+// cell columns q = xx + 2 yy around the node) and a z part that is the same
+// for every node of a layer (ez[zz] for the cell layers below and above).
+template <int P>
+struct NodeXY {
+    int eb[4];
+    bool vxy[4];
+    bool dir;
+    __device__ __forceinline__ NodeXY(const Grid& g, int i, int j) {
+        constexpr int n = P + 1;
+        const int nc = (int)g.nc;
+        int cxs[2] = {0, 0}, axs[2] = {0, 0}, cys[2] = {0, 0}, bys[2] = {0, 0};
+        bool vx[2] = {false, false}, vy[2] = {false, false};
+        if (i % P == 0) {
+            if (i / P - 1 >= 0) { cxs[0] = i / P - 1; axs[0] = P; vx[0] = true; }
+            if (i / P < g.ncx) { cxs[1] = i / P; axs[1] = 0; vx[1] = true; }
+        } else { cxs[0] = i / P; axs[0] = i % P; vx[0] = true; }
+        if (j % P == 0) {
+            if (j / P - 1 >= 0) { cys[0] = j / P - 1; bys[0] = P; vy[0] = true; }
+            if (j / P < g.ncy) { cys[1] = j / P; bys[1] = 0; vy[1] = true; }
+        } else { cys[0] = j / P; bys[0] = j % P; vy[0] = true; }
+#pragma unroll
+        for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+            for (int xx = 0; xx < 2; ++xx) {
+                const int q = xx + 2 * yy;
+                vxy[q] = vx[xx] && vy[yy];
+                eb[q] = (axs[xx] + n * bys[yy]) * nc + cxs[xx] + g.ncx * cys[yy];
+            }
+        dir = ((g.dmask & 1) && i == 0) || ((g.dmask & 2) && i == g.Nx - 1) ||
+              ((g.dmask & 4) && j == 0) || ((g.dmask & 8) && j == g.Ny - 1);
+    }
+
+    // the 8 (possibly absent) element contributions at node layer k
+    template <typename T>
+    __device__ __forceinline__ void load(const Grid& g, const T* __restrict__ E, int k, T (&v)[8]) const {
+        constexpr int n = P + 1;
+        const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+        int ez[2];
+        bool vz[2];
+        if (k % P == 0) {
+            ez[0] = n * n * P * nc + layer * (k / P - 1);
+            vz[0] = k > 0;
+            ez[1] = layer * (k / P);
+            vz[1] = k / P < g.ncz;
+        } else {
+            ez[0] = n * n * (k % P) * nc + layer * (k / P);
+            vz[0] = true;
+            ez[1] = 0;
+            vz[1] = false;
+        }
+#pragma unroll
+        for (int zz = 0; zz < 2; ++zz)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q + 4 * zz] = (vz[zz] && vxy[q]) ? __ldg(E + (eb[q] + ez[zz])) : T(0);
+    }
+};
+
+// Node pass of the two-pass apply: y = sum of the element contributions at
+// each node in a fixed order (x at Dirichlet nodes), optional partial sums of
+// x.y.  128 nodes of a layer per CTA (a linear run of node indices, so the
+// vector accesses are coalesced), each thread marching klen layers two at a
+// time so that twice the loads are in flight.
 template <int P, typename T>
 __global__ void __launch_bounds__(128) node_pass_kernel(const Grid g, const T* __restrict__ E,
                                                         const T* __restrict__ x, T* __restrict__ y,
                                                         const int klen, double* __restrict__ dot_part,
                                                         const Scal* __restrict__ sc) {
     if (sc && sc->done) return;
-    constexpr int n = P + 1;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int NXY = g.Nx * g.Ny;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
     T dot = T(0);
-    if (i < g.Nx && j < g.Ny) {
-        const int nc = (int)g.nc, layer = g.ncx * g.ncy;
-        // neighbour cells in x and y (slot xx + 2 yy, lower/upper), their cell
-        // index part and local index part; invalid slots read nothing
-        int cxy[4], lxy[4];
-        bool vxy[4];
-        {
-            int cxs[2] = {0, 0}, axs[2] = {0, 0}, cys[2] = {0, 0}, bys[2] = {0, 0};
-            bool vx[2] = {false, false}, vy[2] = {false, false};
-            if (i % P == 0) {
-                if (i / P - 1 >= 0) { cxs[0] = i / P - 1; axs[0] = P; vx[0] = true; }
-                if (i / P < g.ncx) { cxs[1] = i / P; axs[1] = 0; vx[1] = true; }
-            } else { cxs[0] = i / P; axs[0] = i % P; vx[0] = true; }
-            if (j % P == 0) {
-                if (j / P - 1 >= 0) { cys[0] = j / P - 1; bys[0] = P; vy[0] = true; }
-                if (j / P < g.ncy) { cys[1] = j / P; bys[1] = 0; vy[1] = true; }
-            } else { cys[0] = j / P; bys[0] = j % P; vy[0] = true; }
-#pragma unroll
-            for (int yy = 0; yy < 2; ++yy)
-#pragma unroll
-                for (int xx = 0; xx < 2; ++xx) {
-                    const int q = xx + 2 * yy;
-                    vxy[q] = vx[xx] && vy[yy];
-                    cxy[q] = cxs[xx] + g.ncx * cys[yy];
-                    lxy[q] = axs[xx] + n * bys[yy];
-                }
-        }
-        const bool dir_xy = ((g.dmask & 1) && i == 0) || ((g.dmask & 2) && i == g.Nx - 1) ||
-                            ((g.dmask & 4) && j == 0) || ((g.dmask & 8) && j == g.Ny - 1);
-        const int k0 = blockIdx.z * klen, k1 = min(k0 + klen, g.Nz);
-        int id = i + g.Nx * j + g.Nx * g.Ny * k0;
-        const int NXY = g.Nx * g.Ny;
-        for (int k = k0; k < k1; ++k, id += NXY) {
-            // lower (slot 0) and upper (slot 1) cell layer of the node plane
-            int czs[2] = {0, 0}, czl[2] = {0, 0};
-            bool vz[2] = {false, false};
-            if (k % P == 0) {
-                if (k / P - 1 >= 0) { czs[0] = k / P - 1; czl[0] = P; vz[0] = true; }
-                if (k / P < g.ncz) { czs[1] = k / P; czl[1] = 0; vz[1] = true; }
-            } else { czs[0] = k / P; czl[0] = k % P; vz[0] = true; }
-            T v[8];
-#pragma unroll
-            for (int zz = 0; zz < 2; ++zz) {
-                const int cz = layer * czs[zz], lz = n * n * czl[zz];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    v[q + 4 * zz] = (vz[zz] && vxy[q]) ? __ldg(E + (lxy[q] + lz) * nc + cxy[q] + cz) : T(0);
-            }
-            T sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-            const T xv = x[id];
-            const bool d = dir_xy || ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1);
+    if (m < NXY) {
+        const NodeXY<P> nx(g, m % g.Nx, m / g.Nx);
+        const int k0 = blockIdx.y * klen, k1 = min(k0 + klen, g.Nz);
+        auto finish = [&](int k, int id, const T (&v)[8], T xv) {
+            const bool d = nx.dir || ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1);
+            const T sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
             const T yv = d ? xv : sum;
             y[id] = yv;
             dot = fma(xv, yv, dot);
+        };
+        int k = k0, id = m + NXY * k0;
+        for (; k + 1 < k1; k += 2, id += 2 * NXY) {
+            T v0[8], v1[8];
+            nx.load(g, E, k, v0);
+            nx.load(g, E, k + 1, v1);
+            const T x0 = x[id], x1 = x[id + NXY];
+            finish(k, id, v0, x0);
+            finish(k + 1, id + NXY, v1, x1);
+        }
+        if (k < k1) {
+            T v0[8];
+            nx.load(g, E, k, v0);
+            finish(k, id, v0, x[id]);
         }
     }
     if (dot_part) {
         const double tot = block_sum((double)dot);
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            dot_part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+        if (threadIdx.x == 0) dot_part[blockIdx.x + gridDim.x * blockIdx.y] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused Jacobi-CG iteration over the two-pass apply (head operator), two
+// launches per iteration:
+//   cell pass:  p_e = Dinv r + beta p_old at the cell's nodes (Dirichlet
+//               nodes zero), E = A_e p_e, partial of sum_e p_e . A_e p_e;
+//               the last CTA to finish reduces the partials in a fixed order
+//               and sets alpha = r.z / p.Ap (or flags a breakdown).
+//   node pass:  q = sum of the element contributions, p = Dinv r + beta p_old
+//               (the same formula, so the same value), x += alpha p,
+//               r -= alpha q; partials of r.Dinv.r and r.r; the last CTA
+//               reduces them, tests convergence and sets beta for the next
+//               iteration.
+// A CTA learns that it is last from an atomic ticket in s (the classic
+// threadfence reduction): no CTA waits for another, and the sums do not
+// depend on the order in which CTAs finish.
+// ---------------------------------------------------------------------------
+// thread 0 publishes the CTA's partial sums and takes a ticket; the result is
+// true in every thread of the CTA that finished last
+__device__ __forceinline__ bool publish_and_ticket(Scal* s, double* part_slot, const double* vals, int nv,
+                                                   int stride, unsigned nblk) {
+    __shared__ bool last;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tid == 0) {
+        for (int k = 0; k < nv; ++k) part_slot[(size_t)k * stride + blk] = vals[k];
+        __threadfence();
+        last = atomicAdd(&s->ticket, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    return last;
+}
+
+// sum of part[0..n) in a fixed order (valid in thread 0); reads bypass L1
+__device__ __forceinline__ double last_cta_sum(const double* part, int n) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    double a = 0.0;
+    for (int i = tid; i < n; i += nt) a += __ldcg(part + i);
+    return block_sum(a);
+}
+
+template <int P, typename T, class Op>
+__global__ void __launch_bounds__(128) fcg_cell_kernel(const Grid g, const Op op, const T* __restrict__ r,
+                                                       const T* __restrict__ Dinv, const T* __restrict__ p,
+                                                       T* __restrict__ E, const int zlen, Scal* s,
+                                                       double* __restrict__ part, const int first) {
+    if (s->done) return;
+    const T beta = first ? T(0) : (T)s->beta;
+    constexpr int n = P + 1, NL = n * n * n, NF = n * n;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    T pap = T(0);
+    if (cx < g.ncx && cy < g.ncy) {
+        const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
+        const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+        const int NX = g.Nx, NXY = g.Nx * g.Ny;
+        const bool edge_xy = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1);
+        int base = P * cx + NX * P * cy + NXY * P * cz0;
+        int c = cx + g.ncx * cy + layer * cz0;
+        T u[NL];
+        // p at the bottom face of the first cell; later cells take it from the
+        // top face of the cell below (the same nodes, so the same values)
+#pragma unroll
+        for (int b = 0; b < n; ++b)
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                const int id = base + NX * b + a;
+                u[a + n * b] = fma(beta, ldro(p + id), ldro(Dinv + id) * ldro(r + id));
+            }
+        for (int cz = cz0; cz < cz1; ++cz, base += NXY * P, c += layer) {
+#pragma unroll
+            for (int c2 = 1; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        const int id = base + NX * b + NXY * c2 + a;
+                        u[a + n * (b + n * c2)] = fma(beta, ldro(p + id), ldro(Dinv + id) * ldro(r + id));
+                    }
+            if (edge_xy || (g.dmask & 48 && (cz == 0 || cz == g.ncz - 1))) {
+#pragma unroll
+                for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                    for (int b = 0; b < n; ++b)
+#pragma unroll
+                        for (int a = 0; a < n; ++a)
+                            if (on_dir(g, P * cx + a, P * cy + b, P * cz + c2)) u[a + n * (b + n * c2)] = T(0);
+            }
+            T res[NL];
+            op.compute(u, c, res);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                E[l * nc + c] = res[l];
+                pap = fma(u[l], res[l], pap);
+            }
+            // the top face becomes the next bottom face; a node zeroed as a
+            // Dirichlet node is zero in the next cell too
+#pragma unroll
+            for (int f = 0; f < NF; ++f) u[f] = u[f + NF * P];
+        }
+    }
+    const double v = block_sum((double)pap);
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    if (!publish_and_ticket(s, part, &v, 1, 0, nblk)) return;
+    const double tot = last_cta_sum(part, (int)nblk);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        s->ticket = 0;
+        s->pq = tot;
+        if (!(tot > 0.0) || !isfinite(tot)) { s->status = ST_BREAKDOWN; s->done = 1; }
+        else s->alpha = s->rz / tot;
+    }
+}
+
+// node pass of the fused CG: 128 nodes of a layer per CTA (a linear run of
+// node indices, so the vector accesses are fully coalesced), each thread
+// marching klen layers two at a time so that twice the loads are in flight
+template <int P, typename T>
+__global__ void __launch_bounds__(128) fcg_node_kernel(const Grid g, const T* __restrict__ E, T* __restrict__ x,
+                                                       T* __restrict__ r, const T* __restrict__ Dinv,
+                                                       T* __restrict__ p, const int klen, Scal* s,
+                                                       double* __restrict__ part, const int stride,
+                                                       const int first, const double tol2, const int max_iter) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha;
+    const T beta = first ? T(0) : (T)s->beta;
+    const int NXY = g.Nx * g.Ny;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    T rzp = T(0), rrp = T(0);
+    if (m < NXY) {
+        const NodeXY<P> nx(g, m % g.Nx, m / g.Nx);
+        const int k0 = blockIdx.y * klen, k1 = min(k0 + klen, g.Nz);
+        auto finish = [&](int k, int id, const T (&v)[8], T di, T ri, T pi, T xi) {
+            const bool d = nx.dir || ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1);
+            T pn = fma(beta, pi, di * ri);
+            if (d) pn = T(0);
+            const T q = d ? pn : ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+            p[id] = pn;
+            x[id] = fma(alpha, pn, xi);
+            const T rn = fma(-alpha, q, ri);
+            r[id] = rn;
+            rzp = fma(rn, di * rn, rzp);
+            rrp = fma(rn, rn, rrp);
+        };
+        int k = k0, id = m + NXY * k0;
+        for (; k + 1 < k1; k += 2, id += 2 * NXY) {
+            T v0[8], v1[8];
+            nx.load(g, E, k, v0);
+            nx.load(g, E, k + 1, v1);
+            const T d0 = Dinv[id], r0 = r[id], p0 = p[id], x0 = x[id];
+            const T d1 = Dinv[id + NXY], r1 = r[id + NXY], p1 = p[id + NXY], x1 = x[id + NXY];
+            finish(k, id, v0, d0, r0, p0, x0);
+            finish(k + 1, id + NXY, v1, d1, r1, p1, x1);
+        }
+        if (k < k1) {
+            T v0[8];
+            nx.load(g, E, k, v0);
+            finish(k, id, v0, Dinv[id], r[id], p[id], x[id]);
+        }
+    }
+    double v[2];
+    v[0] = block_sum((double)rzp);
+    v[1] = block_sum((double)rrp);
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    if (!publish_and_ticket(s, part + stride, v, 2, stride, nblk)) return;
+    const double rz = last_cta_sum(part + stride, (int)nblk);
+    const double rr = last_cta_sum(part + 2 * (size_t)stride, (int)nblk);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        s->ticket = 0;
+        s->rr = rr;
+        s->rz_new = rz;
+        s->iters += 1;
+        if (!isfinite(rz) || !isfinite(rr)) { s->status = ST_NAN; s->done = 1; }
+        else if (rr <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
+        s->beta = rz / s->rz;
+        s->rz = rz;
     }
 }
 
@@ -1058,32 +1265,70 @@ double* elem_buffer<double>(ht_ctx* c) { return c->E64; }
 template <>
 float* elem_buffer<float>(ht_ctx* c) { return c->E32; }
 
+// resident 128-thread CTAs of a kernel per SM (queried once per kernel)
+template <auto Kernel>
+int resident_per_sm() {
+    static const int n = [] {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, Kernel, 128, 0) != cudaSuccess || v < 1) v = 1;
+        return v;
+    }();
+    return n;
+}
+
+// Split of a marching range of n layers over `cols` thread columns: the split
+// z minimises (waves of resident CTAs) x (layers per CTA + 1), the "+ 1" being
+// the start-up of a CTA; ties go to fewer CTAs.  zmax bounds the split.
+int pick_split(int n, int cols, int resident, int zmax) {
+    int best = 1;
+    long long best_cost = -1;
+    for (int z = 1; z <= n && z <= zmax; ++z) {
+        const int len = (n + z - 1) / z;
+        if (z > 1 && (n + len - 1) / len != z) continue;  // same as a smaller split
+        const long long waves = ((long long)cols * z + resident - 1) / resident;
+        const long long cost = waves * (len + 1);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = z; }
+    }
+    return best;
+}
+
+// cell-pass grid of the two-pass kernels, shared by the apply and the fused
+// CG: (32 x 4) cell columns marching in z
+void cell_pass_dims(const ht_ctx* c, const Grid& g, int cell_per_sm, dim3* grid, int* zlen) {
+    const int sms = c->num_sms > 0 ? c->num_sms : 148;
+    const int gx = (g.ncx + 31) / 32, gy = (g.ncy + 3) / 4;
+    int zs = pick_split(g.ncz, gx * gy, cell_per_sm * sms, c->part_stride / (gx * gy));
+    *zlen = (g.ncz + zs - 1) / zs;
+    zs = (g.ncz + *zlen - 1) / *zlen;
+    *grid = dim3(gx, gy, zs);
+}
+
+// node-pass grid: 128-node runs of a layer x a split of the layers; the block
+// count bounds the partial sums
+void layer_node_dims(const ht_ctx* c, const Grid& g, int node_per_sm, dim3* grid, int* klen) {
+    const int sms = c->num_sms > 0 ? c->num_sms : 148;
+    const int runs = (g.Nx * g.Ny + 127) / 128;
+    int ks = pick_split(g.Nz, runs, node_per_sm * sms, c->part_stride / runs);
+    *klen = (g.Nz + ks - 1) / ks;
+    ks = (g.Nz + *klen - 1) / *klen;
+    *grid = dim3(runs, ks);
+}
+
 template <int P, typename T, class Op>
 int launch_apply_two_pass(ht_ctx* c, const Grid& g, const Op& op, const T* x, T* y, double* dot_part,
                           int* n_part, const Scal* sc) {
     T* E = elem_buffer<T>(c);
-    const int sms = c->num_sms > 0 ? c->num_sms : 148;
-    // cell pass: (32 x 4) thread columns, z split so that ~8 blocks per SM
-    const dim3 cb(32, 4);
-    const int gx = (g.ncx + 31) / 32, gy = (g.ncy + 3) / 4;
-    int zs = (8 * sms + gx * gy - 1) / (gx * gy);
-    zs = zs < 1 ? 1 : (zs > g.ncz ? g.ncz : zs);
-    const int zlen = (g.ncz + zs - 1) / zs;
-    zs = (g.ncz + zlen - 1) / zlen;
-    cell_pass_kernel<P, T, Op><<<dim3(gx, gy, zs), cb, 0, c->stream>>>(g, op, x, E, zlen, sc); ++c->n_launch;
+    dim3 cgrid, ngrid;
+    int zlen, klen;
+    cell_pass_dims(c, g, resident_per_sm<cell_pass_kernel<P, T, Op>>(), &cgrid, &zlen);
+    layer_node_dims(c, g, resident_per_sm<node_pass_kernel<P, T>>(), &ngrid, &klen);
+    const int nb = (int)(ngrid.x * ngrid.y);
+    if (dot_part && nb > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
+    cell_pass_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zlen, sc); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
-    // node pass: (32 x 4) node columns; the block count bounds the partial sums
-    const int nx = (g.Nx + 31) / 32, ny = (g.Ny + 3) / 4;
-    int ks = (8 * sms + nx * ny - 1) / (nx * ny);
-    const int kmax = c->part_stride / (nx * ny);
-    ks = ks < 1 ? 1 : (ks > g.Nz ? g.Nz : ks);
-    if (ks > kmax) ks = kmax > 0 ? kmax : 1;
-    const int klen = (g.Nz + ks - 1) / ks;
-    ks = (g.Nz + klen - 1) / klen;
-    if (dot_part && nx * ny * ks > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
-    node_pass_kernel<P, T><<<dim3(nx, ny, ks), cb, 0, c->stream>>>(g, E, x, y, klen, dot_part, sc); ++c->n_launch;
+    node_pass_kernel<P, T><<<ngrid, 128, 0, c->stream>>>(g, E, x, y, klen, dot_part, sc); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
-    if (n_part) *n_part = nx * ny * ks;
+    if (n_part) *n_part = nb;
     return HT_OK;
 }
 
@@ -1102,6 +1347,35 @@ template <>
 const Elem<double>& elem_of<double>(const ht_ctx* c) { return c->e64; }
 template <>
 const Elem<float>& elem_of<float>(const ht_ctx* c) { return c->e32; }
+
+template <int P, typename T>
+int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal* sc, int first, double tol2,
+                         int max_iter) {
+    using Op = HeadOp<P, T, MODE_APPLY>;
+    const Grid g = field_grid(c, HT_HEAD);
+    Op op{};
+    op.K = sizeof(T) == 8 ? (const T*)c->K64 : (const T*)c->K32;
+    op.alpha = (T)c->Ss;
+    op.dt = dt;
+    op.e = elem_of<T>(c);
+    T* E = elem_buffer<T>(c);
+    dim3 cgrid, ngrid;
+    int zlen, klen;
+    cell_pass_dims(c, g, resident_per_sm<fcg_cell_kernel<P, T, Op>>(), &cgrid, &zlen);
+    layer_node_dims(c, g, resident_per_sm<fcg_node_kernel<P, T>>(), &ngrid, &klen);
+    if ((int)(cgrid.x * cgrid.y * cgrid.z) > c->part_stride || (int)(ngrid.x * ngrid.y) > c->part_stride)
+        return fail(c, HT_EINVAL, "too many partial sums");
+    HT_TRY(prof_begin(c, sizeof(T) == 8 ? HT_HEAD : HT_HEAD + 2));
+    fcg_cell_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, r, Dinv, p, E, zlen, sc, c->part, first);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    fcg_node_kernel<P, T><<<ngrid, 128, 0, c->stream>>>(g, E, x, r, Dinv, p, klen, sc, c->part, c->part_stride,
+                                                        first, tol2, max_iter);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    HT_TRY(prof_end(c));
+    return HT_OK;
+}
 
 template <int P, typename T>
 int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int* n_part,
@@ -1129,6 +1403,21 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
 }
 
 }  // namespace
+
+// one fused CG iteration of the head system (see fcg_cell_kernel)
+int fused_cg_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* Dinv, double* p, Scal* sc,
+                         int first, double tol2, int max_iter) {
+    return c->grid.P == 1 ? fused_cg_iteration_P<1, double>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter)
+                          : fused_cg_iteration_P<2, double>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter);
+}
+int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* Dinv, float* p, Scal* sc,
+                         int first, double tol2, int max_iter) {
+    return c->grid.P == 1 ? fused_cg_iteration_P<1, float>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter)
+                          : fused_cg_iteration_P<2, float>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter);
+}
+bool fused_cg_available(const ht_ctx* c, int fp32) {
+    return fp32 ? use_two_pass<float>(c) : use_two_pass<double>(c);
+}
 
 int apply_tiles(const ht_ctx* c) {
     dim3 grid;

@@ -169,6 +169,29 @@ def test_mixed_precision_matches_oracle(Sim, case):
         assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
 
 
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_fused_two_pass_cg_steps_match_oracle(Sim, case, mixed):
+    """Head CG fused into the two-pass kernels (two launches per iteration):
+    the same answer as the oracle, and in FP64 the same iteration count as the
+    unfused CG over the tiled apply, up to rounding (2 iterations or 2%)."""
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    prec = dict(tol=1e-12, precision=L.HT_MIXED, inner_tol=1e-4) if mixed else dict(tol=1e-13)
+    sim = Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TWO_PASS, max_iter=50000, **prec)
+    ref = None if mixed else Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TILED, max_iter=50000, **prec)
+    for _ in range(3):
+        st = sim.step(sc.dt)
+        o.step(sc.dt)
+        assert st["res_head"] <= prec["tol"] * 1.001
+        assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
+        assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+        if ref is not None:
+            st_ref = ref.step(sc.dt)
+            assert abs(st["iters_head"] - st_ref["iters_head"]) <= max(2, 0.02 * st_ref["iters_head"])
+
+
 def test_config1_plain_workload_matches_oracle(Sim):
     """The plain FP64 workload: 16^3 Q1 cube, line source, 10 days."""
     sc = S.config1()
