@@ -458,6 +458,19 @@ int finalize_setup(ht_ctx* c) {
         HT_CUDA(c, cudaMemcpyAsync(c->well_node, wn.data(), wn.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
         HT_CUDA(c, cudaMemcpyAsync(c->well_d, wv.data(), wv.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     }
+    // the same coefficients as dense per-node arrays (zero off the wells)
+    dfree(c->wdn64);
+    dfree(c->wdn32);
+    if (!wn.empty()) {
+        std::vector<double> d64(nn, 0.0);
+        std::vector<float> d32(nn, 0.0f);
+        for (auto& kv : wd) { d64[kv.first] = kv.second; d32[kv.first] = (float)kv.second; }
+        HT_TRY(dalloc(c, &c->wdn64, nn));
+        HT_TRY(dalloc(c, &c->wdn32, nn));
+        HT_CUDA(c, cudaMemcpyAsync(c->wdn64, d64.data(), nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaMemcpyAsync(c->wdn32, d32.data(), nn * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
     // pile tables: CSR over unique nodes
     std::map<long long, std::vector<std::pair<int, double>>> pm;
     for (size_t s = 0; s < c->piles.size(); ++s) {
@@ -702,11 +715,11 @@ void ht_destroy(ht_ctx* c) {
     double** v64[] = {&c->h, &c->T, &c->g[0], &c->g[1], &c->Fstat[0], &c->Fstat[1], &c->F[0], &c->F[1],
                       &c->extra[0], &c->extra[1], &c->x, &c->r, &c->z, &c->p, &c->q, &c->b, &c->D,
                       &c->rh, &c->v, &c->s, &c->tv, &c->ph, &c->sh, &c->z2, &c->K64, &c->lam64,
-                      &c->cT64, &c->qs64, &c->part, &c->pile_w, &c->well_d, &c->E64};
+                      &c->cT64, &c->qs64, &c->part, &c->pile_w, &c->well_d, &c->E64, &c->wdn64};
     for (double** pp : v64) dfree(*pp);
     float** v32[] = {&c->x32, &c->r32, &c->z32, &c->p32, &c->q32, &c->D32, &c->rh32, &c->v32, &c->s32,
                      &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32, &c->K32, &c->lam32, &c->cT32, &c->qs32,
-                     &c->E32};
+                     &c->E32, &c->wdn32};
     for (float** pp : v32) dfree(*pp);
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
     dfree(c->scal);

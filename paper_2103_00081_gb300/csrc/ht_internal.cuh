@@ -122,6 +122,8 @@ struct ht_ctx {
     int n_well_nodes = 0;
     int* well_node = nullptr;
     double* well_d = nullptr;               // c_w Q/L int N_i dz (heat, injection)
+    double* wdn64 = nullptr;                // the same per node (0 elsewhere), for the fused solvers
+    float* wdn32 = nullptr;
 
     // Darcy flux at Gauss points [3*nq^3][cells]
     double* qs64 = nullptr;
@@ -207,6 +209,8 @@ int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y,
 int launch_rhs(ht_ctx* c, int field, double dt, const double* u_old, double* b);
 // D = diagonal of A0.
 int launch_diag(ht_ctx* c, int field, double dt, double* D);
+// the same in FP32 (the Jacobi scaling of the FP32 inner solves)
+int launch_diag32(ht_ctx* c, int field, double dt, float* D);
 // qs = -K grad h at Gauss points (both precisions).
 int launch_darcy_qp(ht_ctx* c, const double* h);
 // q at cell centres for output, component comp (0..2)
@@ -224,6 +228,11 @@ int fused_cg_iteration64(ht_ctx* c, double dt, double* x, double* r, const doubl
 int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* Dinv, float* p, Scal* sc,
                          int first, double tol2, int max_iter);
 bool fused_cg_available(const ht_ctx* c, int fp32);
+// fused two-pass Jacobi-BiCGStab iteration of the heat system (ht_ops.cu)
+int fused_bicgstab_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* rh, double* p, double* v,
+                               double* t, const double* Dinv, Scal* sc, double tol2, int max_iter);
+int fused_bicgstab_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* rh, float* p, float* v,
+                               float* t, const float* Dinv, Scal* sc, double tol2, int max_iter);
 // event bracketing of apply launches (kind = field + 2 * fp32)
 int prof_begin(ht_ctx* c, int kind);
 int prof_end(ht_ctx* c);

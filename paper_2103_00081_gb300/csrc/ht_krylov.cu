@@ -763,6 +763,13 @@ inline int fused_cg_iteration(ht_ctx* c, double dt, const Vecs32& w, Scal* sc, i
     return fused_cg_iteration32(c, (float)dt, w.x, w.r, w.Dinv, w.p, sc, first, tol2, max_iter);
 }
 
+inline int fused_bicgstab_iteration(ht_ctx* c, double dt, const Vecs64& w, Scal* sc, double tol2, int max_iter) {
+    return fused_bicgstab_iteration64(c, dt, w.x, w.r, w.rh, w.p, w.v, w.t, w.Dinv, sc, tol2, max_iter);
+}
+inline int fused_bicgstab_iteration(ht_ctx* c, double dt, const Vecs32& w, Scal* sc, double tol2, int max_iter) {
+    return fused_bicgstab_iteration32(c, (float)dt, w.x, w.r, w.rh, w.p, w.v, w.t, w.Dinv, sc, tol2, max_iter);
+}
+
 // Preconditioned CG on A0 x = b (x holds the initial guess).  Returns
 // iterations in *iters; status in c->scal[slot].
 template <typename T, class V>
@@ -836,8 +843,11 @@ int run_bicgstab(ht_ctx* c, double dt, const V& w, const T* b, int slot, double 
             break;
         }
         int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
+        const bool fused = fused_cg_available(c, sizeof(T) == 4);
         while (!c->scal_host[slot].done) {
-            for (int k = 0; k < chunk; ++k) {
+            for (int k = 0; fused && k < chunk; ++k)
+                HT_TRY(fused_bicgstab_iteration(c, dt, w, sc, tol * tol, max_iter - total));
+            for (int k = 0; !fused && k < chunk; ++k) {
                 bi_p_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, w.p, w.v, w.Dinv, w.ph, sc); ++c->n_launch;
                 HT_TRY(apply_T<T>(c, HT_TEMP, dt, w.ph, w.v, nullptr, nullptr, sc));
                 dot_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.rh, w.v, c->part, S, sc); ++c->n_launch;
@@ -1054,7 +1064,20 @@ int run_cg_cheb(ht_ctx* c, double dt, const V& w, T* z, T* d, T* tmp, const T* b
     return HT_OK;
 }
 
+__global__ void inv32_kernel(long long n, const float* __restrict__ D, float* __restrict__ Dinv32) {
+    GRID_LOOP(i, n) Dinv32[i] = 1.0f / D[i];
+}
+
 int prepare_diag(ht_ctx* c, int field, double dt) {
+    // The FP32 inner solves of the mixed form use only the FP32 inverse
+    // diagonal, so it is computed in FP32; the Chebyshev bounds of the head
+    // CG come from the FP64 diagonal.
+    if (c->opts.precision == HT_MIXED && !(field == HT_HEAD && c->opts.precond == HT_PREC_CHEBYSHEV)) {
+        HT_TRY(launch_diag32(c, field, dt, c->z32));
+        inv32_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, c->z32, c->D32); ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+        return HT_OK;
+    }
     HT_TRY(launch_diag(c, field, dt, c->z));
     inv_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, c->z, c->D, c->D32); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());

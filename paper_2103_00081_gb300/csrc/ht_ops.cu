@@ -148,6 +148,15 @@ struct HeadOp {
             gather<P, T>(g, x, cx, cy, cz, true, res);
             fdm(res, beta);
             return;
+        } else if (!cell_touches_dir(g, cx, cy, cz)) {
+            // RHS of a cell without Dirichlet nodes: g_D vanishes on it, so
+            // the element result is alpha M u_old = alpha (G^T)^3 G^3 u_old
+            gather<P, T>(g, x, cx, cy, cz, false, res);
+            sweep<n, 0, false>(res, e.G[0]);
+            sweep<n, 1, false>(res, e.G[1]);
+            sweep<n, 2, false>(res, e.G[2]);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) res[l] *= alpha;
         } else {  // RHS: alpha M (u_old - g_D) - beta K g_D
             T us[NL];
             const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
@@ -305,6 +314,19 @@ struct HeatOp {
             T um[NL];
             gather<P, T>(g, x, cx, cy, cz, true, um);
             core(um, um, T(1), cT, dtlam, dtcw, c, nc, res);
+        } else if (!cell_touches_dir(g, cx, cy, cz)) {
+            // RHS of a cell without Dirichlet nodes: g_D vanishes on it, so
+            // only the storage term cT M T_old remains; the consistent mass
+            // factors as M = (G^T)^3 G^3 (the 1D mass is G^T G)
+            gather<P, T>(g, x, cx, cy, cz, false, res);
+            sweep<n, 0, false>(res, e.G[0]);
+            sweep<n, 1, false>(res, e.G[1]);
+            sweep<n, 2, false>(res, e.G[2]);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) res[l] *= cT;
+            sweep<n, 2, true>(res, e.G[2]);
+            sweep<n, 1, true>(res, e.G[1]);
+            sweep<n, 0, true>(res, e.G[0]);
         } else {
             T um[NL], us[NL];
             const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
@@ -914,66 +936,79 @@ __device__ __forceinline__ double last_cta_sum(const double* part, int n) {
     return block_sum(a);
 }
 
+// Column march of the fused Krylov cell passes: thread (cx, cy) walks cells
+// cz0..cz1 of its column, forms the operator input at the cell's nodes with
+// nv(id) (Dirichlet nodes zero), writes E = A_e u and returns sum_e u . A_e u
+// when DOT.  The bottom face of a cell is the top face of the cell below (the
+// same nodes, so the same values): it is carried, not re-read.
+template <int P, typename T, class Op, class NV, bool DOT>
+__device__ __forceinline__ T march_cells(const Grid& g, const Op& op, const NV& nv, T* __restrict__ E,
+                                         const int zlen) {
+    constexpr int n = P + 1, NL = n * n * n, NF = n * n;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    T dot = T(0);
+    if (cx >= g.ncx || cy >= g.ncy) return dot;
+    const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
+    const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+    const int NX = g.Nx, NXY = g.Nx * g.Ny;
+    const bool edge_xy = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1);
+    int base = P * cx + NX * P * cy + NXY * P * cz0;
+    int c = cx + g.ncx * cy + layer * cz0;
+    T u[NL];
+#pragma unroll
+    for (int b = 0; b < n; ++b)
+#pragma unroll
+        for (int a = 0; a < n; ++a) u[a + n * b] = nv(base + NX * b + a);
+    for (int cz = cz0; cz < cz1; ++cz, base += NXY * P, c += layer) {
+#pragma unroll
+        for (int c2 = 1; c2 < n; ++c2)
+#pragma unroll
+            for (int b = 0; b < n; ++b)
+#pragma unroll
+                for (int a = 0; a < n; ++a) u[a + n * (b + n * c2)] = nv(base + NX * b + NXY * c2 + a);
+        if (edge_xy || (g.dmask & 48 && (cz == 0 || cz == g.ncz - 1))) {
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a)
+                        if (on_dir(g, P * cx + a, P * cy + b, P * cz + c2)) u[a + n * (b + n * c2)] = T(0);
+        }
+        T res[NL];
+        op.compute(u, c, res);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            E[l * nc + c] = res[l];
+            if (DOT) dot = fma(u[l], res[l], dot);
+        }
+        // the top face becomes the next bottom face; a node zeroed as a
+        // Dirichlet node is zero in the next cell too
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u[f] = u[f + NF * P];
+    }
+    return dot;
+}
+
+// CG search direction at a node: p = Dinv r + beta p_old
+template <typename T>
+struct CgDir {
+    const T* r;
+    const T* Dinv;
+    const T* p;
+    T beta;
+    __device__ __forceinline__ T operator()(int id) const { return fma(beta, ldro(p + id), ldro(Dinv + id) * ldro(r + id)); }
+};
+
 template <int P, typename T, class Op>
 __global__ void __launch_bounds__(128) fcg_cell_kernel(const Grid g, const Op op, const T* __restrict__ r,
                                                        const T* __restrict__ Dinv, const T* __restrict__ p,
                                                        T* __restrict__ E, const int zlen, Scal* s,
                                                        double* __restrict__ part, const int first) {
     if (s->done) return;
-    const T beta = first ? T(0) : (T)s->beta;
-    constexpr int n = P + 1, NL = n * n * n, NF = n * n;
-    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
-    T pap = T(0);
-    if (cx < g.ncx && cy < g.ncy) {
-        const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
-        const int nc = (int)g.nc, layer = g.ncx * g.ncy;
-        const int NX = g.Nx, NXY = g.Nx * g.Ny;
-        const bool edge_xy = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1);
-        int base = P * cx + NX * P * cy + NXY * P * cz0;
-        int c = cx + g.ncx * cy + layer * cz0;
-        T u[NL];
-        // p at the bottom face of the first cell; later cells take it from the
-        // top face of the cell below (the same nodes, so the same values)
-#pragma unroll
-        for (int b = 0; b < n; ++b)
-#pragma unroll
-            for (int a = 0; a < n; ++a) {
-                const int id = base + NX * b + a;
-                u[a + n * b] = fma(beta, ldro(p + id), ldro(Dinv + id) * ldro(r + id));
-            }
-        for (int cz = cz0; cz < cz1; ++cz, base += NXY * P, c += layer) {
-#pragma unroll
-            for (int c2 = 1; c2 < n; ++c2)
-#pragma unroll
-                for (int b = 0; b < n; ++b)
-#pragma unroll
-                    for (int a = 0; a < n; ++a) {
-                        const int id = base + NX * b + NXY * c2 + a;
-                        u[a + n * (b + n * c2)] = fma(beta, ldro(p + id), ldro(Dinv + id) * ldro(r + id));
-                    }
-            if (edge_xy || (g.dmask & 48 && (cz == 0 || cz == g.ncz - 1))) {
-#pragma unroll
-                for (int c2 = 0; c2 < n; ++c2)
-#pragma unroll
-                    for (int b = 0; b < n; ++b)
-#pragma unroll
-                        for (int a = 0; a < n; ++a)
-                            if (on_dir(g, P * cx + a, P * cy + b, P * cz + c2)) u[a + n * (b + n * c2)] = T(0);
-            }
-            T res[NL];
-            op.compute(u, c, res);
-#pragma unroll
-            for (int l = 0; l < NL; ++l) {
-                E[l * nc + c] = res[l];
-                pap = fma(u[l], res[l], pap);
-            }
-            // the top face becomes the next bottom face; a node zeroed as a
-            // Dirichlet node is zero in the next cell too
-#pragma unroll
-            for (int f = 0; f < NF; ++f) u[f] = u[f + NF * P];
-        }
-    }
+    const CgDir<T> nv{r, Dinv, p, first ? T(0) : (T)s->beta};
+    const T pap = march_cells<P, T, Op, CgDir<T>, true>(g, op, nv, E, zlen);
     const double v = block_sum((double)pap);
     const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     if (!publish_and_ticket(s, part, &v, 1, 0, nblk)) return;
@@ -1048,6 +1083,207 @@ __global__ void __launch_bounds__(128) fcg_node_kernel(const Grid g, const T* __
         else if (rr <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
         s->beta = rz / s->rz;
         s->rz = rz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused Jacobi-BiCGStab iteration over the two-pass apply (heat operator),
+// five launches per iteration instead of thirteen:
+//   cell A: ph = Dinv (r + beta (p - omega v)) at the cell's nodes, E = A_e ph
+//   node A: p = r + beta (p - omega v) (the same formula), v = A ph;
+//           last CTA: alpha = rho / rh.v
+//   cell B: sh = Dinv (r - alpha v), E = A_e sh
+//   node B: t = A sh; last CTA: omega = t.s / t.t
+//   update: x += alpha Dinv p + omega Dinv s, r = s - omega t with
+//           s = r - alpha v; last CTA: convergence, beta, rho
+// The lumped injection-well term of the heat operator (dt d_i on the
+// diagonal of well nodes) is added in the node passes from a dense per-node
+// array wd (null when there are no wells).  Dirichlet rows are identity rows:
+// the node passes return the input there, as the plain apply does.
+// Partial slots: 0 = rh.v; 1, 2 = t.s, t.t; 3, 4 = rh.r, r.r.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BiDirP {   // ph = Dinv (r + beta (p - omega v))
+    const T* r;
+    const T* p;
+    const T* v;
+    const T* Dinv;
+    T beta, omega;
+    __device__ __forceinline__ T val(int id) const { return fma(beta, fma(-omega, ldro(v + id), ldro(p + id)), ldro(r + id)); }
+    __device__ __forceinline__ T operator()(int id) const { return ldro(Dinv + id) * val(id); }
+};
+template <typename T>
+struct BiDirS {   // sh = Dinv (r - alpha v)
+    const T* r;
+    const T* v;
+    const T* Dinv;
+    T alpha;
+    __device__ __forceinline__ T operator()(int id) const { return ldro(Dinv + id) * fma(-alpha, ldro(v + id), ldro(r + id)); }
+};
+
+template <int P, typename T, class Op>
+__global__ void __launch_bounds__(128) fbi_cell_a_kernel(const Grid g, const Op op, const T* __restrict__ r,
+                                                         const T* __restrict__ p, const T* __restrict__ v,
+                                                         const T* __restrict__ Dinv, T* __restrict__ E,
+                                                         const int zlen, const Scal* s) {
+    if (s->done) return;
+    const BiDirP<T> nv{r, p, v, Dinv, (T)s->beta, (T)s->omega};
+    march_cells<P, T, Op, BiDirP<T>, false>(g, op, nv, E, zlen);
+}
+
+template <int P, typename T, class Op>
+__global__ void __launch_bounds__(128) fbi_cell_b_kernel(const Grid g, const Op op, const T* __restrict__ r,
+                                                         const T* __restrict__ v, const T* __restrict__ Dinv,
+                                                         T* __restrict__ E, const int zlen, const Scal* s) {
+    if (s->done) return;
+    const BiDirS<T> nv{r, v, Dinv, (T)s->alpha};
+    march_cells<P, T, Op, BiDirS<T>, false>(g, op, nv, E, zlen);
+}
+
+// node A: p, v = A ph, partials of rh.v
+template <int P, typename T>
+__global__ void __launch_bounds__(128) fbi_node_a_kernel(const Grid g, const T* __restrict__ E, const T* __restrict__ r,
+                                                         T* __restrict__ p, T* __restrict__ v, const T* __restrict__ Dinv,
+                                                         const T* __restrict__ rh, const T* __restrict__ wd, const T dt,
+                                                         const int klen, Scal* s, double* __restrict__ part) {
+    if (s->done) return;
+    const T beta = (T)s->beta, omega = (T)s->omega;
+    const int NXY = g.Nx * g.Ny;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    T rv = T(0);
+    if (m < NXY) {
+        const NodeXY<P> nx(g, m % g.Nx, m / g.Nx);
+        const int k0 = blockIdx.y * klen, k1 = min(k0 + klen, g.Nz);
+        auto finish = [&](int k, int id, const T (&e)[8]) {
+            const bool d = nx.dir || ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1);
+            const T pn = fma(beta, fma(-omega, v[id], p[id]), r[id]);
+            const T ph = Dinv[id] * pn;
+            T vn = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]));
+            if (wd) vn += dt * wd[id] * ph;
+            if (d) vn = ph;
+            p[id] = pn;
+            v[id] = vn;
+            rv = fma(rh[id], vn, rv);
+        };
+        int k = k0, id = m + NXY * k0;
+        for (; k + 1 < k1; k += 2, id += 2 * NXY) {
+            T e0[8], e1[8];
+            nx.load(g, E, k, e0);
+            nx.load(g, E, k + 1, e1);
+            finish(k, id, e0);
+            finish(k + 1, id + NXY, e1);
+        }
+        if (k < k1) {
+            T e0[8];
+            nx.load(g, E, k, e0);
+            finish(k, id, e0);
+        }
+    }
+    const double tot = block_sum((double)rv);
+    const unsigned nblk = gridDim.x * gridDim.y;
+    if (!publish_and_ticket(s, part, &tot, 1, 0, nblk)) return;
+    const double a = last_cta_sum(part, (int)nblk);
+    if (threadIdx.x == 0) {
+        s->ticket = 0;
+        s->rv = a;
+        if (a == 0.0 || !isfinite(a)) { s->status = ST_BREAKDOWN; s->done = 1; }
+        else s->alpha = s->rho / a;
+    }
+}
+
+// node B: t = A sh, partials of t.s and t.t
+template <int P, typename T>
+__global__ void __launch_bounds__(128) fbi_node_b_kernel(const Grid g, const T* __restrict__ E, const T* __restrict__ r,
+                                                         const T* __restrict__ v, T* __restrict__ t,
+                                                         const T* __restrict__ Dinv, const T* __restrict__ wd,
+                                                         const T dt, const int klen, Scal* s,
+                                                         double* __restrict__ part, const int stride) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha;
+    const int NXY = g.Nx * g.Ny;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    T ts = T(0), tt = T(0);
+    if (m < NXY) {
+        const NodeXY<P> nx(g, m % g.Nx, m / g.Nx);
+        const int k0 = blockIdx.y * klen, k1 = min(k0 + klen, g.Nz);
+        auto finish = [&](int k, int id, const T (&e)[8]) {
+            const bool d = nx.dir || ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1);
+            const T si = fma(-alpha, v[id], r[id]);
+            const T sh = Dinv[id] * si;
+            T tn = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]));
+            if (wd) tn += dt * wd[id] * sh;
+            if (d) tn = sh;
+            t[id] = tn;
+            ts = fma(tn, si, ts);
+            tt = fma(tn, tn, tt);
+        };
+        int k = k0, id = m + NXY * k0;
+        for (; k + 1 < k1; k += 2, id += 2 * NXY) {
+            T e0[8], e1[8];
+            nx.load(g, E, k, e0);
+            nx.load(g, E, k + 1, e1);
+            finish(k, id, e0);
+            finish(k + 1, id + NXY, e1);
+        }
+        if (k < k1) {
+            T e0[8];
+            nx.load(g, E, k, e0);
+            finish(k, id, e0);
+        }
+    }
+    double vals[2];
+    vals[0] = block_sum((double)ts);
+    vals[1] = block_sum((double)tt);
+    const unsigned nblk = gridDim.x * gridDim.y;
+    if (!publish_and_ticket(s, part + stride, vals, 2, stride, nblk)) return;
+    const double a = last_cta_sum(part + stride, (int)nblk);
+    const double b = last_cta_sum(part + 2 * (size_t)stride, (int)nblk);
+    if (threadIdx.x == 0) {
+        s->ticket = 0;
+        s->ts = a;
+        s->tt = b;
+        s->omega = b == 0.0 ? 0.0 : a / b;   // s = 0 exactly: x += alpha ph is the solution
+    }
+}
+
+// update: x, r; partials of rh.r and r.r; convergence and the next beta
+template <typename T>
+__global__ void __launch_bounds__(256) fbi_update_kernel(long long n, T* __restrict__ x, T* __restrict__ r,
+                                                         const T* __restrict__ p, const T* __restrict__ v,
+                                                         const T* __restrict__ t, const T* __restrict__ Dinv,
+                                                         const T* __restrict__ rh, Scal* s,
+                                                         double* __restrict__ part, const int stride,
+                                                         const double tol2, const int max_iter) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha, omega = (T)s->omega;
+    T rhr = T(0), rr = T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T di = Dinv[i];
+        const T si = fma(-alpha, v[i], r[i]);
+        x[i] = fma(alpha, di * p[i], fma(omega, di * si, x[i]));
+        const T ri = fma(-omega, t[i], si);
+        r[i] = ri;
+        rhr = fma(rh[i], ri, rhr);
+        rr = fma(ri, ri, rr);
+    }
+    double vals[2];
+    vals[0] = block_sum((double)rhr);
+    vals[1] = block_sum((double)rr);
+    const unsigned nblk = gridDim.x;
+    if (!publish_and_ticket(s, part + 3 * (size_t)stride, vals, 2, stride, nblk)) return;
+    const double a0 = last_cta_sum(part + 3 * (size_t)stride, (int)nblk);
+    const double a1 = last_cta_sum(part + 4 * (size_t)stride, (int)nblk);
+    if (threadIdx.x == 0) {
+        s->ticket = 0;
+        s->rr = a1;
+        s->iters += 1;
+        if (!isfinite(a0) || !isfinite(a1)) { s->status = ST_NAN; s->done = 1; }
+        else if (a1 <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
+        else if (a0 == 0.0 || s->omega == 0.0) { s->status = ST_BREAKDOWN; s->done = 1; }
+        else {
+            s->beta = (a0 / s->rho) * (s->alpha / s->omega);
+            s->rho = a0;
+        }
     }
 }
 
@@ -1161,10 +1397,11 @@ __global__ void well_apply_kernel(int n, const int* __restrict__ node, const dou
     }
 }
 
+template <typename T>
 __global__ void well_diag_kernel(int n, const int* __restrict__ node, const double* __restrict__ d,
-                                 double dt, double* __restrict__ D) {
+                                 double dt, T* __restrict__ D) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) D[node[i]] += dt * d[i];
+    if (i < n) D[node[i]] += (T)(dt * d[i]);
 }
 
 __global__ void pile_load_kernel(int n_nodes, const int* __restrict__ node, const int* __restrict__ off,
@@ -1377,6 +1614,50 @@ int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal*
     return HT_OK;
 }
 
+template <typename T>
+const T* well_dense(const ht_ctx* c);
+template <>
+const double* well_dense<double>(const ht_ctx* c) { return c->wdn64; }
+template <>
+const float* well_dense<float>(const ht_ctx* c) { return c->wdn32; }
+
+template <int P, typename T>
+int fused_bicgstab_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* rh, T* p, T* v, T* t, const T* Dinv,
+                               Scal* sc, double tol2, int max_iter) {
+    using Op = HeatOp<P, T, MODE_APPLY>;
+    const Grid g = field_grid(c, HT_TEMP);
+    const bool f64 = sizeof(T) == 8;
+    Op op{};
+    op.qs = f64 ? (const T*)c->qs64 : (const T*)c->qs32;
+    op.cTc = f64 ? (const T*)c->cT64 : (const T*)c->cT32;
+    op.lamc = f64 ? (const T*)c->lam64 : (const T*)c->lam32;
+    op.cT_u = (T)c->cT_u; op.lam_u = (T)c->lam_u; op.dt = dt; op.cw = (T)c->cw;
+    op.e = elem_of<T>(c);
+    op.g_nc = g.nc;
+    T* E = elem_buffer<T>(c);
+    const T* wd = well_dense<T>(c);
+    dim3 ca, cb, na, nb;
+    int za, zb, ka, kb;
+    cell_pass_dims(c, g, resident_per_sm<fbi_cell_a_kernel<P, T, Op>>(), &ca, &za);
+    cell_pass_dims(c, g, resident_per_sm<fbi_cell_b_kernel<P, T, Op>>(), &cb, &zb);
+    layer_node_dims(c, g, resident_per_sm<fbi_node_a_kernel<P, T>>(), &na, &ka);
+    layer_node_dims(c, g, resident_per_sm<fbi_node_b_kernel<P, T>>(), &nb, &kb);
+    const int G = vec_grid(c);
+    if ((int)(na.x * na.y) > c->part_stride || (int)(nb.x * nb.y) > c->part_stride || G > c->part_stride)
+        return fail(c, HT_EINVAL, "too many partial sums");
+    const int S = c->part_stride;
+    HT_TRY(prof_begin(c, f64 ? HT_TEMP : HT_TEMP + 2));
+    fbi_cell_a_kernel<P, T, Op><<<ca, dim3(32, 4), 0, c->stream>>>(g, op, r, p, v, Dinv, E, za, sc); ++c->n_launch;
+    fbi_node_a_kernel<P, T><<<na, 128, 0, c->stream>>>(g, E, r, p, v, Dinv, rh, wd, dt, ka, sc, c->part); ++c->n_launch;
+    fbi_cell_b_kernel<P, T, Op><<<cb, dim3(32, 4), 0, c->stream>>>(g, op, r, v, Dinv, E, zb, sc); ++c->n_launch;
+    fbi_node_b_kernel<P, T><<<nb, 128, 0, c->stream>>>(g, E, r, v, t, Dinv, wd, dt, kb, sc, c->part, S); ++c->n_launch;
+    HT_TRY(prof_end(c));
+    fbi_update_kernel<T><<<G, 256, 0, c->stream>>>(c->grid.nn, x, r, p, v, t, Dinv, rh, sc, c->part, S, tol2,
+                                                   max_iter); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
 template <int P, typename T>
 int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int* n_part,
             const Scal* sc) {
@@ -1414,6 +1695,16 @@ int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* D
                          int first, double tol2, int max_iter) {
     return c->grid.P == 1 ? fused_cg_iteration_P<1, float>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter)
                           : fused_cg_iteration_P<2, float>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter);
+}
+int fused_bicgstab_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* rh, double* p, double* v,
+                               double* t, const double* Dinv, Scal* sc, double tol2, int max_iter) {
+    return c->grid.P == 1 ? fused_bicgstab_iteration_P<1, double>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter)
+                          : fused_bicgstab_iteration_P<2, double>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter);
+}
+int fused_bicgstab_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* rh, float* p, float* v,
+                               float* t, const float* Dinv, Scal* sc, double tol2, int max_iter) {
+    return c->grid.P == 1 ? fused_bicgstab_iteration_P<1, float>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter)
+                          : fused_bicgstab_iteration_P<2, float>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter);
 }
 bool fused_cg_available(const ht_ctx* c, int fp32) {
     return fp32 ? use_two_pass<float>(c) : use_two_pass<double>(c);
@@ -1483,6 +1774,32 @@ static int diag_P(ht_ctx* c, int field, double dt, double* D) {
     return launch_tile<P, double>(c, g, op, nullptr, nullptr);
 }
 
+template <int P>
+static int diag32_P(ht_ctx* c, int field, float dt, float* D) {
+    const Grid g = field_grid(c, field);
+    if (field == HT_HEAD) {
+        HeadOp<P, float, MODE_DIAG> op{};
+        op.y = D; op.K = c->K32; op.alpha = (float)c->Ss; op.dt = dt; op.e = c->e32;
+        return launch_tile<P, float>(c, g, op, nullptr, nullptr);
+    }
+    HeatOp<P, float, MODE_DIAG> op{};
+    op.y = D; op.qs = c->qs32; op.cTc = c->cT32; op.lamc = c->lam32;
+    op.cT_u = (float)c->cT_u; op.lam_u = (float)c->lam_u; op.dt = dt; op.cw = (float)c->cw; op.e = c->e32;
+    return launch_tile<P, float>(c, g, op, nullptr, nullptr);
+}
+
+int launch_diag32(ht_ctx* c, int field, double dt, float* D) {
+    int rc = c->grid.P == 1 ? diag32_P<1>(c, field, (float)dt, D) : diag32_P<2>(c, field, (float)dt, D);
+    if (rc != HT_OK) return rc;
+    if (field == HT_TEMP && c->n_well_nodes > 0) {
+        const int n = c->n_well_nodes;
+        well_diag_kernel<float><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, D);
+        ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+    }
+    return HT_OK;
+}
+
 int launch_diag(ht_ctx* c, int field, double dt, double* D) {
     int rc = c->grid.P == 1 ? diag_P<1>(c, field, dt, D) : diag_P<2>(c, field, dt, D);
     if (rc != HT_OK) return rc;
@@ -1545,7 +1862,7 @@ int launch_well_apply32(ht_ctx* c, float dt, const float* x, float* y, const Sca
 
 int launch_well_diag(ht_ctx* c, double dt, double* D) {
     const int n = c->n_well_nodes;
-    well_diag_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, D); ++c->n_launch;
+    well_diag_kernel<double><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->well_node, c->well_d, dt, D); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }

@@ -192,6 +192,31 @@ def test_fused_two_pass_cg_steps_match_oracle(Sim, case, mixed):
             assert abs(st["iters_head"] - st_ref["iters_head"]) <= max(2, 0.02 * st_ref["iters_head"])
 
 
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_fused_two_pass_bicgstab_steps_match_oracle(Sim, case, mixed):
+    """Heat BiCGStab fused into the two-pass kernels (five launches per
+    iteration, wells added in the node passes): the same answer as the
+    oracle, and in FP64 an iteration count close to the unfused BiCGStab over
+    the tiled apply (rounding differs, so within 2 iterations or 10%)."""
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    prec = dict(tol=1e-12, precision=L.HT_MIXED, inner_tol=1e-4) if mixed else dict(tol=1e-13)
+    common = dict(krylov=L.HT_KRYLOV_BICGSTAB, max_iter=50000, **prec)
+    sim = Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TWO_PASS, **common)
+    ref = None if mixed else Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TILED, **common)
+    for _ in range(2):
+        st = sim.step(sc.dt)
+        o.step(sc.dt)
+        assert st["res_heat"] <= prec["tol"] * 1.001
+        assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
+        assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+        if ref is not None:
+            st_ref = ref.step(sc.dt)
+            assert abs(st["iters_heat"] - st_ref["iters_heat"]) <= max(2, 0.1 * st_ref["iters_heat"])
+
+
 def test_config1_plain_workload_matches_oracle(Sim):
     """The plain FP64 workload: 16^3 Q1 cube, line source, 10 days."""
     sc = S.config1()
