@@ -256,13 +256,19 @@ int ht_learned_sample(ht_ctx* ctx, float* features, float* targets, int* dims);
  * and returns: all kernels launched by the library since the reset, the
  * number of head / heat apply launches that did work (launches that found
  * the solve already converged and returned at once are excluded by duration)
- * and their summed device time in milliseconds. */
+ * and their summed device time in milliseconds.  The fused Krylov
+ * iterations of the two-pass variant (both element and node passes of one CG
+ * iteration of the head system; all five launches of one BiCGStab iteration
+ * of the heat system) are counted and timed as units of their own and not as
+ * applies. */
 typedef struct {
     long long launches;
     long long head_applies, heat_applies;
     double head_apply_ms, heat_apply_ms;
     long long head_applies_fp32, heat_applies_fp32;
     double head_apply_ms_fp32, heat_apply_ms_fp32;
+    long long cg_iters, bicgstab_iters;
+    double cg_iter_ms, bicgstab_iter_ms;
 } ht_profile_stats;
 int ht_profile(ht_ctx* ctx, int on);
 int ht_profile_read(ht_ctx* ctx, ht_profile_stats* out);

@@ -63,7 +63,9 @@ class ProfileStats(ctypes.Structure):
                 ("heat_applies", ctypes.c_longlong), ("head_apply_ms", c_double),
                 ("heat_apply_ms", c_double), ("head_applies_fp32", ctypes.c_longlong),
                 ("heat_applies_fp32", ctypes.c_longlong), ("head_apply_ms_fp32", c_double),
-                ("heat_apply_ms_fp32", c_double)]
+                ("heat_apply_ms_fp32", c_double), ("cg_iters", ctypes.c_longlong),
+                ("bicgstab_iters", ctypes.c_longlong), ("cg_iter_ms", c_double),
+                ("bicgstab_iter_ms", c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -324,7 +324,7 @@ int batch_prepare(ht_batch* b, double dt) {
         pr.Ss = (float)c->Ss;
         pr.dt = (float)dt;
         pr.K = c->K32;
-        pr.x = c->d32; pr.r = c->r32; pr.p = c->p32; pr.q = c->q32; pr.Dinv = c->D32; pr.E = c->E32;
+        pr.x = c->d32; pr.r = c->r32; pr.p = c->p32; pr.q = c->q32; pr.Dinv = c->D32; pr.E = c->E32 + kElemPad;
         pr.part = c->part;
         pr.stride = c->part_stride;
         pr.sc = c->scal + 1;

@@ -681,8 +681,13 @@ int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream) 
         if (rc == HT_OK) rc = dalloc(c, pp, N);
     if (rc == HT_OK) rc = dalloc(c, &c->qs64, 3 * NQ * NC);
     if (rc == HT_OK) rc = dalloc(c, &c->qs32, 3 * NQ * NC);
-    if (rc == HT_OK) rc = dalloc(c, &c->E32, NQ * NC);
-    if (rc == HT_OK) rc = dalloc(c, &c->E64, NQ * NC);
+    // element buffers of the two-pass kernels behind kElemPad zeros: node
+    // gathers read E[-1] for absent neighbour cells, element passes write
+    // only E[0 .. NQ * NC)
+    if (rc == HT_OK) rc = dalloc(c, &c->E32, NQ * NC + kElemPad);
+    if (rc == HT_OK) rc = dalloc(c, &c->E64, NQ * NC + kElemPad);
+    if (rc == HT_OK && cudaMemsetAsync(c->E32, 0, (NQ * NC + kElemPad) * sizeof(float), c->stream) != cudaSuccess) rc = HT_ECUDA;
+    if (rc == HT_OK && cudaMemsetAsync(c->E64, 0, (NQ * NC + kElemPad) * sizeof(double), c->stream) != cudaSuccess) rc = HT_ECUDA;
     const int G = vec_grid(c), tiles = apply_tiles(c);
     // the two-pass node gather writes one partial per 128-node run of a layer and
     // layer split, at most one wave of 128-thread CTAs (16 per SM) beyond one split
@@ -987,9 +992,11 @@ int ht_profile_read(ht_ctx* c, ht_profile_stats* out) {
     HT_TRY(prof_flush(c));
     memset(out, 0, sizeof(*out));
     out->launches = c->n_launch;
-    long long* cnt[4] = {&out->head_applies, &out->heat_applies, &out->head_applies_fp32, &out->heat_applies_fp32};
-    double* ms[4] = {&out->head_apply_ms, &out->heat_apply_ms, &out->head_apply_ms_fp32, &out->heat_apply_ms_fp32};
-    for (int k = 0; k < 4; ++k) {
+    long long* cnt[HT_PROF_KINDS] = {&out->head_applies, &out->heat_applies, &out->head_applies_fp32,
+                                  &out->heat_applies_fp32, &out->cg_iters, &out->bicgstab_iters};
+    double* ms[HT_PROF_KINDS] = {&out->head_apply_ms, &out->heat_apply_ms, &out->head_apply_ms_fp32,
+                              &out->heat_apply_ms_fp32, &out->cg_iter_ms, &out->bicgstab_iter_ms};
+    for (int k = 0; k < HT_PROF_KINDS; ++k) {
         std::vector<float> v = c->prof_ms[k];
         if (v.empty()) continue;
         std::vector<float> srt = v;

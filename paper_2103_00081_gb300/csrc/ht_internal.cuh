@@ -70,6 +70,12 @@ enum { ST_OK = 0, ST_BREAKDOWN = 1, ST_NAN = 2 };
 
 }  // namespace ht
 
+// zeros in front of the element buffers (E[-1] is the zero slot of node gathers)
+constexpr int kElemPad = 64;
+
+// profiling kinds: field (FP64 apply), field + 2 (FP32 apply), fused iterations
+enum { HT_PROF_CG_ITER = 4, HT_PROF_BICGSTAB_ITER = 5, HT_PROF_KINDS = 6 };
+
 // ---------------------------------------------------------------------------
 // The context behind the opaque ht_ctx handle.
 // ---------------------------------------------------------------------------
@@ -129,7 +135,7 @@ struct ht_ctx {
     double* qs64 = nullptr;
     float* qs32 = nullptr;
     // element-result buffers of the two-pass apply [(p+1)^3][cells]
-    double* E64 = nullptr;
+    double* E64 = nullptr;                  // element buffers: kElemPad zeros, then (P+1)^3 nc entries
     float* E32 = nullptr;
 
     // Krylov workspace
@@ -170,7 +176,7 @@ struct ht_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;                 // pairs in use
     std::vector<int> ev_kind;           // field + 2 * fp32 of each recorded pair
-    std::vector<std::vector<float>> prof_ms = std::vector<std::vector<float>>(4);
+    std::vector<std::vector<float>> prof_ms = std::vector<std::vector<float>>(HT_PROF_KINDS);
 };
 
 namespace ht {

@@ -825,7 +825,9 @@ struct NodeXY {
               ((g.dmask & 4) && j == 0) || ((g.dmask & 8) && j == g.Ny - 1);
     }
 
-    // the 8 (possibly absent) element contributions at node layer k
+    // the 8 element contributions at node layer k; an absent one (no cell on
+    // that side) reads the zero slot E[-1] in front of the element buffer, so
+    // every load is unconditional
     template <typename T>
     __device__ __forceinline__ void load(const Grid& g, const T* __restrict__ E, int k, T (&v)[8]) const {
         constexpr int n = P + 1;
@@ -847,7 +849,7 @@ struct NodeXY {
         for (int zz = 0; zz < 2; ++zz)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                v[q + 4 * zz] = (vz[zz] && vxy[q]) ? __ldg(E + (eb[q] + ez[zz])) : T(0);
+                v[q + 4 * zz] = __ldg(E + ((vz[zz] && vxy[q]) ? eb[q] + ez[zz] : -1));
     }
 };
 
@@ -857,7 +859,7 @@ struct NodeXY {
 // vector accesses are coalesced), each thread marching klen layers two at a
 // time so that twice the loads are in flight.
 template <int P, typename T>
-__global__ void __launch_bounds__(128) node_pass_kernel(const Grid g, const T* __restrict__ E,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) node_pass_kernel(const Grid g, const T* __restrict__ E,
                                                         const T* __restrict__ x, T* __restrict__ y,
                                                         const int klen, double* __restrict__ dot_part,
                                                         const Scal* __restrict__ sc) {
@@ -1025,7 +1027,7 @@ __global__ void __launch_bounds__(128) fcg_cell_kernel(const Grid g, const Op op
 // node indices, so the vector accesses are fully coalesced), each thread
 // marching klen layers two at a time so that twice the loads are in flight
 template <int P, typename T>
-__global__ void __launch_bounds__(128) fcg_node_kernel(const Grid g, const T* __restrict__ E, T* __restrict__ x,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fcg_node_kernel(const Grid g, const T* __restrict__ E, T* __restrict__ x,
                                                        T* __restrict__ r, const T* __restrict__ Dinv,
                                                        T* __restrict__ p, const int klen, Scal* s,
                                                        double* __restrict__ part, const int stride,
@@ -1142,7 +1144,7 @@ __global__ void __launch_bounds__(128) fbi_cell_b_kernel(const Grid g, const Op 
 
 // node A: p, v = A ph, partials of rh.v
 template <int P, typename T>
-__global__ void __launch_bounds__(128) fbi_node_a_kernel(const Grid g, const T* __restrict__ E, const T* __restrict__ r,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fbi_node_a_kernel(const Grid g, const T* __restrict__ E, const T* __restrict__ r,
                                                          T* __restrict__ p, T* __restrict__ v, const T* __restrict__ Dinv,
                                                          const T* __restrict__ rh, const T* __restrict__ wd, const T dt,
                                                          const int klen, Scal* s, double* __restrict__ part) {
@@ -1193,7 +1195,7 @@ __global__ void __launch_bounds__(128) fbi_node_a_kernel(const Grid g, const T* 
 
 // node B: t = A sh, partials of t.s and t.t
 template <int P, typename T>
-__global__ void __launch_bounds__(128) fbi_node_b_kernel(const Grid g, const T* __restrict__ E, const T* __restrict__ r,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fbi_node_b_kernel(const Grid g, const T* __restrict__ E, const T* __restrict__ r,
                                                          const T* __restrict__ v, T* __restrict__ t,
                                                          const T* __restrict__ Dinv, const T* __restrict__ wd,
                                                          const T dt, const int klen, Scal* s,
@@ -1498,9 +1500,9 @@ int launch_apply_staged(ht_ctx* c, const Grid& g, const Op& op, const T* x, T* y
 template <typename T>
 T* elem_buffer(ht_ctx* c);
 template <>
-double* elem_buffer<double>(ht_ctx* c) { return c->E64; }
+double* elem_buffer<double>(ht_ctx* c) { return c->E64 ? c->E64 + kElemPad : nullptr; }
 template <>
-float* elem_buffer<float>(ht_ctx* c) { return c->E32; }
+float* elem_buffer<float>(ht_ctx* c) { return c->E32 ? c->E32 + kElemPad : nullptr; }
 
 // resident 128-thread CTAs of a kernel per SM (queried once per kernel)
 template <auto Kernel>
@@ -1602,7 +1604,7 @@ int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal*
     layer_node_dims(c, g, resident_per_sm<fcg_node_kernel<P, T>>(), &ngrid, &klen);
     if ((int)(cgrid.x * cgrid.y * cgrid.z) > c->part_stride || (int)(ngrid.x * ngrid.y) > c->part_stride)
         return fail(c, HT_EINVAL, "too many partial sums");
-    HT_TRY(prof_begin(c, sizeof(T) == 8 ? HT_HEAD : HT_HEAD + 2));
+    HT_TRY(prof_begin(c, HT_PROF_CG_ITER));
     fcg_cell_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, r, Dinv, p, E, zlen, sc, c->part, first);
     ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
@@ -1646,15 +1648,15 @@ int fused_bicgstab_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* rh, T* p, T
     if ((int)(na.x * na.y) > c->part_stride || (int)(nb.x * nb.y) > c->part_stride || G > c->part_stride)
         return fail(c, HT_EINVAL, "too many partial sums");
     const int S = c->part_stride;
-    HT_TRY(prof_begin(c, f64 ? HT_TEMP : HT_TEMP + 2));
+    HT_TRY(prof_begin(c, HT_PROF_BICGSTAB_ITER));
     fbi_cell_a_kernel<P, T, Op><<<ca, dim3(32, 4), 0, c->stream>>>(g, op, r, p, v, Dinv, E, za, sc); ++c->n_launch;
     fbi_node_a_kernel<P, T><<<na, 128, 0, c->stream>>>(g, E, r, p, v, Dinv, rh, wd, dt, ka, sc, c->part); ++c->n_launch;
     fbi_cell_b_kernel<P, T, Op><<<cb, dim3(32, 4), 0, c->stream>>>(g, op, r, v, Dinv, E, zb, sc); ++c->n_launch;
     fbi_node_b_kernel<P, T><<<nb, 128, 0, c->stream>>>(g, E, r, v, t, Dinv, wd, dt, kb, sc, c->part, S); ++c->n_launch;
-    HT_TRY(prof_end(c));
     fbi_update_kernel<T><<<G, 256, 0, c->stream>>>(c->grid.nn, x, r, p, v, t, Dinv, rh, sc, c->part, S, tol2,
                                                    max_iter); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
+    HT_TRY(prof_end(c));
     return HT_OK;
 }
 
