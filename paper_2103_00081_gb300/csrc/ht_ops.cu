@@ -149,14 +149,8 @@ struct HeadOp {
             fdm(res, beta);
             return;
         } else if (!cell_touches_dir(g, cx, cy, cz)) {
-            // RHS of a cell without Dirichlet nodes: g_D vanishes on it, so
-            // the element result is alpha M u_old = alpha (G^T)^3 G^3 u_old
-            gather<P, T>(g, x, cx, cy, cz, false, res);
-            sweep<n, 0, false>(res, e.G[0]);
-            sweep<n, 1, false>(res, e.G[1]);
-            sweep<n, 2, false>(res, e.G[2]);
-#pragma unroll
-            for (int l = 0; l < NL; ++l) res[l] *= alpha;
+            rhs_interior(g, cx, cy, cz, res);
+            return;
         } else {  // RHS: alpha M (u_old - g_D) - beta K g_D
             T us[NL];
             const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
@@ -190,6 +184,20 @@ struct HeadOp {
                                  beta * (e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][c2]) * us[l];
                     }
         }
+        sweep<n, 2, true>(res, e.G[2]);
+        sweep<n, 1, true>(res, e.G[1]);
+        sweep<n, 0, true>(res, e.G[0]);
+    }
+
+    // RHS of a cell without Dirichlet nodes: g_D vanishes on it, so the
+    // element result is alpha M u_old = alpha (G^T)^3 G^3 u_old
+    __device__ __forceinline__ void rhs_interior(const Grid& g, int cx, int cy, int cz, T (&res)[NL]) const {
+        gather<P, T>(g, x, cx, cy, cz, false, res);
+        sweep<n, 0, false>(res, e.G[0]);
+        sweep<n, 1, false>(res, e.G[1]);
+        sweep<n, 2, false>(res, e.G[2]);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) res[l] *= alpha;
         sweep<n, 2, true>(res, e.G[2]);
         sweep<n, 1, true>(res, e.G[1]);
         sweep<n, 0, true>(res, e.G[0]);
@@ -315,18 +323,7 @@ struct HeatOp {
             gather<P, T>(g, x, cx, cy, cz, true, um);
             core(um, um, T(1), cT, dtlam, dtcw, c, nc, res);
         } else if (!cell_touches_dir(g, cx, cy, cz)) {
-            // RHS of a cell without Dirichlet nodes: g_D vanishes on it, so
-            // only the storage term cT M T_old remains; the consistent mass
-            // factors as M = (G^T)^3 G^3 (the 1D mass is G^T G)
-            gather<P, T>(g, x, cx, cy, cz, false, res);
-            sweep<n, 0, false>(res, e.G[0]);
-            sweep<n, 1, false>(res, e.G[1]);
-            sweep<n, 2, false>(res, e.G[2]);
-#pragma unroll
-            for (int l = 0; l < NL; ++l) res[l] *= cT;
-            sweep<n, 2, true>(res, e.G[2]);
-            sweep<n, 1, true>(res, e.G[1]);
-            sweep<n, 0, true>(res, e.G[0]);
+            rhs_interior(g, cx, cy, cz, res);
         } else {
             T um[NL], us[NL];
             const int i0 = P * cx, j0 = P * cy, k0 = P * cz;
@@ -345,6 +342,23 @@ struct HeatOp {
                     }
             core(um, us, T(-1), cT, dtlam, dtcw, c, nc, res);
         }
+    }
+
+    // RHS of a cell without Dirichlet nodes: g_D vanishes on it, so only the
+    // storage term cT M T_old remains; the consistent mass factors as
+    // M = (G^T)^3 G^3 (the 1D mass is G^T G)
+    __device__ __forceinline__ void rhs_interior(const Grid& g, int cx, int cy, int cz, T (&res)[NL]) const {
+        const long long c = (long long)cx + (long long)g.ncx * ((long long)cy + (long long)g.ncy * cz);
+        const T cT = cTc ? ldro(cTc + c) : cT_u;
+        gather<P, T>(g, x, cx, cy, cz, false, res);
+        sweep<n, 0, false>(res, e.G[0]);
+        sweep<n, 1, false>(res, e.G[1]);
+        sweep<n, 2, false>(res, e.G[2]);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) res[l] *= cT;
+        sweep<n, 2, true>(res, e.G[2]);
+        sweep<n, 1, true>(res, e.G[1]);
+        sweep<n, 0, true>(res, e.G[0]);
     }
 
     // sum-factorised quadrature: res = cT M um + sgn (dt lam K + dt C) us
@@ -1290,6 +1304,90 @@ __global__ void __launch_bounds__(256) fbi_update_kernel(long long n, T* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Right-hand sides through the element buffer.  Cells without Dirichlet nodes
+// need only the mass term (light kernel); the few cells with Dirichlet nodes
+// take the full lifted element RHS (heavy kernel, launched over the same
+// columns but doing work only on those cells).  The node pass sums the
+// contributions in a fixed order and emits through the operator (g_D on
+// Dirichlet rows, the sum plus dt F elsewhere).
+// ---------------------------------------------------------------------------
+template <int P, typename T, class Op>
+__global__ void __launch_bounds__(128) rhs_interior_kernel(const Grid g, const Op op, T* __restrict__ E,
+                                                           const int zlen) {
+    constexpr int n = P + 1, NL = n * n * n;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cx >= g.ncx || cy >= g.ncy) return;
+    const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
+    const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+    for (int cz = cz0; cz < cz1; ++cz) {
+        if (cell_touches_dir(g, cx, cy, cz)) continue;
+        const int c = cx + g.ncx * cy + layer * cz;
+        T res[NL];
+        op.rhs_interior(g, cx, cy, cz, res);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) E[l * nc + c] = res[l];
+    }
+}
+
+// Cells of the slab next to a Dirichlet face: candidate t enumerates face 0's
+// slab, then face 1's, ...; a cell in several slabs belongs to the first of
+// them whose face is Dirichlet, so each boundary cell is done exactly once.
+__device__ __forceinline__ bool face_cell(const Grid& g, long long t, int* cx, int* cy, int* cz) {
+    const int dims[3] = {g.ncx, g.ncy, g.ncz};
+    for (int f = 0; f < 6; ++f) {
+        const int ax = f >> 1, u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
+        const long long sz = (long long)dims[u] * dims[v];
+        if (t >= sz) { t -= sz; continue; }
+        if (!((g.dmask >> f) & 1)) return false;
+        int c3[3];
+        c3[ax] = (f & 1) ? dims[ax] - 1 : 0;
+        c3[u] = (int)(t % dims[u]);
+        c3[v] = (int)(t / dims[u]);
+        for (int f2 = 0; f2 < f; ++f2) {
+            const int ax2 = f2 >> 1;
+            if (((g.dmask >> f2) & 1) && c3[ax2] == ((f2 & 1) ? dims[ax2] - 1 : 0)) return false;
+        }
+        *cx = c3[0]; *cy = c3[1]; *cz = c3[2];
+        return true;
+    }
+    return false;
+}
+
+template <int P, typename T, class Op>
+__global__ void __launch_bounds__(128) rhs_boundary_kernel(const Grid g, const Op op, T* __restrict__ E,
+                                                           const long long n_cand) {
+    constexpr int n = P + 1, NL = n * n * n;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int cx, cy, cz;
+    if (t >= n_cand || !face_cell(g, t, &cx, &cy, &cz)) return;
+    const int nc = (int)g.nc;
+    const int c = cx + g.ncx * (cy + g.ncy * cz);
+    T res[NL];
+    op.cell(g, cx, cy, cz, c, res);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) E[l * nc + c] = res[l];
+}
+
+template <int P, typename T, class Op>
+__global__ void __launch_bounds__(128) node_emit_kernel(const Grid g, const T* __restrict__ E, const Op op,
+                                                        const int klen) {
+    const int NXY = g.Nx * g.Ny;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= NXY) return;
+    const int i = m % g.Nx, j = m / g.Nx;
+    const NodeXY<P> nx(g, i, j);
+    const int k0 = blockIdx.y * klen, k1 = min(k0 + klen, g.Nz);
+    T dot = T(0);
+    for (int k = k0; k < k1; ++k) {
+        T v[8];
+        nx.load(g, E, k, v);
+        const T sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        op.emit(g, i, j, k, sum, dot);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Other per-cell kernels
 // ---------------------------------------------------------------------------
 // q = -K_c grad h at the Gauss points; qs[(d*NQ + q)*nc + c]
@@ -1742,19 +1840,40 @@ int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y, dou
     return HT_OK;
 }
 
+template <int P, class Op>
+static int launch_rhs_two_pass(ht_ctx* c, const Grid& g, const Op& op) {
+    double* E = elem_buffer<double>(c);
+    dim3 ci, ng;
+    int zi, kl;
+    cell_pass_dims(c, g, resident_per_sm<rhs_interior_kernel<P, double, Op>>(), &ci, &zi);
+    layer_node_dims(c, g, resident_per_sm<node_emit_kernel<P, double, Op>>(), &ng, &kl);
+    rhs_interior_kernel<P, double, Op><<<ci, dim3(32, 4), 0, c->stream>>>(g, op, E, zi); ++c->n_launch;
+    if (g.dmask) {
+        const long long n_cand = 2LL * ((long long)g.ncy * g.ncz + (long long)g.ncx * g.ncz + (long long)g.ncx * g.ncy);
+        rhs_boundary_kernel<P, double, Op><<<(unsigned)((n_cand + 127) / 128), 128, 0, c->stream>>>(g, op, E, n_cand);
+        ++c->n_launch;
+    }
+    node_emit_kernel<P, double, Op><<<ng, 128, 0, c->stream>>>(g, E, op, kl); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
 template <int P>
 static int rhs_P(ht_ctx* c, int field, double dt, const double* u_old, double* b) {
     const Grid g = field_grid(c, field);
+    const bool two_pass = elem_buffer<double>(c) != nullptr;
     if (field == HT_HEAD) {
         HeadOp<P, double, MODE_RHS> op{};
         op.x = u_old; op.gD = c->g[field]; op.F = c->F[field]; op.y = b;
         op.K = c->K64; op.alpha = c->Ss; op.dt = dt; op.e = c->e64;
+        if (two_pass) return launch_rhs_two_pass<P>(c, g, op);
         return launch_tile<P, double>(c, g, op, nullptr, nullptr);
     }
     HeatOp<P, double, MODE_RHS> op{};
     op.x = u_old; op.gD = c->g[field]; op.F = c->F[field]; op.y = b;
     op.qs = c->qs64; op.cTc = c->cT64; op.lamc = c->lam64;
     op.cT_u = c->cT_u; op.lam_u = c->lam_u; op.dt = dt; op.cw = c->cw; op.e = c->e64;
+    if (two_pass) return launch_rhs_two_pass<P>(c, g, op);
     return launch_tile<P, double>(c, g, op, nullptr, nullptr);
 }
 
