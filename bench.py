@@ -204,6 +204,7 @@ def run_ours(args):
         def factory(opts):
             return hydro.Simulator.from_scenario(sc, device=local, stream=stream.cuda_stream, tol=1e-10,
                                                  precision=L.HT_MIXED, inner_tol=args.inner_tol,
+                                                 inner_tol_heat=args.inner_tol_heat,
                                                  max_iter=200000, **opts)
         tuned, tune_table = AT.tune(factory, dt, AT.signature(sc.nx, sc.ny, sc.nz, sc.order, L.HT_MIXED),
                                     force=args.retune)
@@ -212,6 +213,7 @@ def run_ours(args):
         extra = tuned if precision == L.HT_MIXED else {}
         sim = hydro.Simulator.from_scenario(sc, device=local, stream=stream.cuda_stream,
                                             tol=1e-10, precision=precision, inner_tol=args.inner_tol,
+                                            inner_tol_heat=args.inner_tol_heat,
                                             max_iter=200000, **extra)
         for _ in range(args.warmup):
             sim.step(dt)
@@ -418,7 +420,7 @@ def run_batch(args):
     from paper_2103_00081_gb300 import _lib as L
     torch.cuda.set_device(0)
     scs = S.config4(n_problems=args.batch_size)
-    opts = dict(tol=1e-10, precision=L.HT_MIXED, inner_tol=args.inner_tol, krylov=L.HT_KRYLOV_BICGSTAB)
+    opts = dict(tol=1e-10, precision=L.HT_MIXED, inner_tol=1e-4, krylov=L.HT_KRYLOV_BICGSTAB)
     sims = [hydro.Simulator.from_scenario(sc, **opts) for sc in scs]
     dt = scs[0].dt
     batch = hydro.Batch(sims)
@@ -463,7 +465,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ates_q2")
-    ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-4)
+    ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-5,
+                    help="FP32 inner-solve reduction floor, head system")
+    ap.add_argument("--inner-tol-heat", dest="inner_tol_heat", type=float, default=1e-4,
+                    help="FP32 inner-solve reduction floor, heat system")
     ap.add_argument("--cpu-sample-cells", dest="cpu_sample_cells", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true")

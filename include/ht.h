@@ -92,7 +92,15 @@ typedef struct {
  * kernel: HT_APPLY_TILED (one fused owner-computes tile kernel),
  * HT_APPLY_TWO_PASS (cells into an element buffer, then a node gather) or
  * HT_APPLY_AUTO (two-pass in FP32, tiled in FP64).  Both change performance,
- * not results beyond rounding order. */
+ * not results beyond rounding order.
+ * inner_tol is the smallest relative residual reduction asked of one FP32
+ * inner solve of the head system (the solve stops earlier when the outer
+ * tolerance needs less); inner_tol_heat is the same for the heat system
+ * (0: inner_tol).
+ * outer_fp64 != 0 computes the outer residuals b - A x of the mixed form
+ * with the operator in FP64; 0 (the default) applies it in float-float
+ * arithmetic on the FP32 pipes (about 48 significant bits, relative error of
+ * order 1e-14 in A x), with b, x and r kept in FP64. */
 typedef struct {
     double tol;
     int max_iter;
@@ -107,6 +115,8 @@ typedef struct {
     int use_graphs;
     int z_chunks;
     int apply_variant;
+    double inner_tol_heat;
+    int outer_fp64;
 } ht_solver_opts;
 
 /* Per-step statistics: Krylov iterations (inner iterations in mixed mode),
@@ -190,6 +200,14 @@ int ht_get_time(const ht_ctx* ctx, double* t);
 int ht_apply(ht_ctx* ctx, int field, double dt, const double* x, double* y, int on_device);
 int ht_diag(ht_ctx* ctx, int field, double dt, double* d, int on_device);
 int ht_rhs(ht_ctx* ctx, int field, double dt, double* b, int on_device);
+/* Relative residual *rel = ||b - A0 x||_2 / ||b||_2 of the head or heat
+ * operator (the heat one with q from the current head), with A0 x computed in
+ * FP64 (emulated = 0) or in the float-float arithmetic of the mixed form's
+ * outer residuals (emulated = 1).  x and b are [nodes], on the device when
+ * on_device != 0; nothing is written back.  A parity hook for the emulated
+ * outer residual (the residual definition of the stopping test of R4). */
+int ht_residual(ht_ctx* ctx, int field, double dt, const double* x, const double* b, int emulated,
+                int on_device, double* rel);
 
 /* Batched steps of independent problems (same device, same element order,
  * any mesh sizes; each problem is a context set up as usual and configured

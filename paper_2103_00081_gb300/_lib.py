@@ -35,7 +35,8 @@ class SolverOpts(ctypes.Structure):
                 ("precond", c_int),
                 ("cheb_degree", c_int), ("precision", c_int), ("inner_tol", c_double),
                 ("max_outer", c_int), ("check_every", c_int), ("use_graphs", c_int),
-                ("z_chunks", c_int), ("apply_variant", c_int)]
+                ("z_chunks", c_int), ("apply_variant", c_int), ("inner_tol_heat", c_double),
+                ("outer_fp64", c_int)]
 
 
 class LineSrc(ctypes.Structure):
@@ -89,6 +90,7 @@ SIGNATURES = {
     "ht_get_field": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
     "ht_get_time": (c_int, [c_void_p, POINTER(c_double)]),
     "ht_apply": (c_int, [c_void_p, c_int, c_double, c_void_p, c_void_p, c_int]),
+    "ht_residual": (c_int, [c_void_p, c_int, c_double, c_void_p, c_void_p, c_int, c_int, POINTER(c_double)]),
     "ht_diag": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
     "ht_rhs": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
     "ht_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),

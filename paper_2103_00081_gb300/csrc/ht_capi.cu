@@ -186,6 +186,13 @@ void build_elem(ht_ctx* c) {
     float* dst = reinterpret_cast<float*>(&f);
     static_assert(sizeof(ht::Elem<double>) == 2 * sizeof(ht::Elem<float>), "Elem layout");
     for (size_t i = 0; i < sizeof(e) / sizeof(double); ++i) dst[i] = (float)src[i];
+    // float-float copy: hi = nearest float, lo = nearest float to the remainder
+    ht::df64* dd = reinterpret_cast<ht::df64*>(&c->edf);
+    static_assert(sizeof(ht::Elem<double>) == sizeof(ht::Elem<ht::df64>), "Elem layout");
+    for (size_t i = 0; i < sizeof(e) / sizeof(double); ++i) {
+        const float hi = (float)src[i];
+        dd[i] = ht::df64(hi, (float)(src[i] - (double)hi));
+    }
 }
 
 // Head-operator constants of a cell of size H (fast-diagonalisation factors,
@@ -852,6 +859,8 @@ int ht_set_solver(ht_ctx* c, const ht_solver_opts* o) {
     if (o->precond == HT_PREC_CHEBYSHEV && (o->cheb_degree < 1 || o->cheb_degree > 32))
         return fail(c, HT_EINVAL, "cheb_degree must be 1..32");
     if (o->z_chunks < 0) return fail(c, HT_EINVAL, "z_chunks must be >= 0");
+    if (!(o->inner_tol >= 0 && o->inner_tol < 1) || !(o->inner_tol_heat >= 0 && o->inner_tol_heat < 1))
+        return fail(c, HT_EINVAL, "inner tolerances must be in [0, 1)");
     if (o->apply_variant < HT_APPLY_AUTO || o->apply_variant > HT_APPLY_TWO_PASS)
         return fail(c, HT_EINVAL, "unknown apply variant %d", o->apply_variant);
     c->opts = *o;
@@ -963,6 +972,32 @@ int ht_diag(ht_ctx* c, int field, double dt, double* d, int on_device) {
     if (field == HT_TEMP) HT_TRY(launch_darcy_qp(c, c->h));
     HT_TRY(launch_diag(c, field, dt, c->q));
     return copy_out(c, d, c->q, (size_t)c->grid.nn, on_device);
+}
+
+int ht_residual(ht_ctx* c, int field, double dt, const double* x, const double* b, int emulated, int on_device,
+                double* rel) {
+    if (!c || !x || !b || !rel) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    if (!(dt > 0)) return fail(c, HT_EINVAL, "dt must be positive");
+    cudaSetDevice(c->device);
+    HT_TRY(finalize_setup(c));
+    const size_t n = (size_t)c->grid.nn;
+    HT_TRY(copy_in(c, c->z, x, n, on_device));
+    HT_TRY(copy_in(c, c->v, b, n, on_device));
+    if (field == HT_TEMP) HT_TRY(launch_darcy_qp(c, c->h));
+    int np = 0;
+    if (emulated) {
+        HT_TRY(launch_resid_df(c, field, dt, c->z, c->v, c->r32, c->part, &np));
+    } else {
+        HT_TRY(launch_apply64(c, field, dt, c->z, c->q, nullptr, nullptr, nullptr));
+        HT_TRY(launch_resid64(c, c->v, c->q, c->part, &np));
+    }
+    HT_TRY(launch_norms(c, np, 3));
+    HT_CUDA(c, cudaMemcpyAsync(c->scal_host + 3, c->scal + 3, sizeof(ht::Scal), cudaMemcpyDeviceToHost, c->stream));
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    const ht::Scal s = c->scal_host[3];
+    *rel = s.bb > 0 ? sqrt(s.rr / s.bb) : sqrt(s.rr);
+    return HT_OK;
 }
 
 int ht_rhs(ht_ctx* c, int field, double dt, double* b, int on_device) {

@@ -44,6 +44,15 @@ struct Elem {
     T LS[27];      // Lx[a] + Ly[b] + Lz[c] per mode l = a + n(b + n c)
 };
 
+// A float-float value hi + lo (|lo| <= ulp(hi)/2, about 48 significant bits),
+// the arithmetic of the emulated-FP64 outer residuals (operators in ht_ops.cu).
+struct df64 {
+    float hi, lo;
+    df64() = default;
+    __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr df64(int v) : hi((float)v), lo(0.0f) {}
+};
+
 // Device-resident scalars of one Krylov solve.
 struct Scal {
     double bb, rr, rz, rz_new, pq, alpha, beta;
@@ -88,6 +97,7 @@ struct ht_ctx {
     double H[3] = {0, 0, 0};
     ht::Elem<double> e64{};
     ht::Elem<float> e32{};
+    ht::Elem<ht::df64> edf{};               // e64 split into float pairs
     int num_sms = 0;
 
     // coefficients
@@ -217,6 +227,15 @@ int launch_rhs(ht_ctx* c, int field, double dt, const double* u_old, double* b);
 int launch_diag(ht_ctx* c, int field, double dt, double* D);
 // the same in FP32 (the Jacobi scaling of the FP32 inner solves)
 int launch_diag32(ht_ctx* c, int field, double dt, float* D);
+// outer residual of the mixed form with the operator applied in float-float
+// arithmetic: r32 = (float)(b - A x), partial sums of r.r and b.b in part
+// (slots 0 and 1, *n_part entries); false if the two-pass buffers are absent
+int launch_resid_df(ht_ctx* c, int field, double dt, const double* x, const double* b, float* r32,
+                    double* part, int* n_part);
+// r = b - q in FP64 with partial sums of r.r and b.b (slots 0, 1); reduction
+// of those partial sums into c->scal[slot] (ht_krylov.cu)
+int launch_resid64(ht_ctx* c, const double* b, const double* q, double* part, int* n_part);
+int launch_norms(ht_ctx* c, int n_part, int slot);
 // qs = -K grad h at Gauss points (both precisions).
 int launch_darcy_qp(ht_ctx* c, const double* h);
 // q at cell centres for output, component comp (0..2)

@@ -1135,15 +1135,21 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
     const long long n = c->grid.nn;
     const int G = vec_grid(c);
     const int S = c->part_stride;
-    const double inner_tol = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-4;
+    const double inner_head = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-4;
+    const double inner_tol = field == HT_TEMP && c->opts.inner_tol_heat > 0 ? c->opts.inner_tol_heat : inner_head;
     const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 30;
     Vecs32 w{c->d32, c->r32, c->p32, c->q32, c->D32, c->rh32, c->v32, c->s32, c->t32, c->ph32, c->sh32};
     int total = 0;
     for (int k = 0; k <= max_outer; ++k) {
-        HT_TRY(launch_apply64(c, field, dt, x, c->q, nullptr, nullptr, nullptr));
-        resid_kernel<<<G, kVecThreads, 0, c->stream>>>(n, b, c->q, nullptr, c->r32, c->part, S); ++c->n_launch;
-        HT_CUDA(c, cudaGetLastError());
-        scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, S, G, c->scal + 2, 0.0, 0); ++c->n_launch;
+        int np = G;
+        if (c->opts.outer_fp64) {
+            HT_TRY(launch_apply64(c, field, dt, x, c->q, nullptr, nullptr, nullptr));
+            resid_kernel<<<G, kVecThreads, 0, c->stream>>>(n, b, c->q, nullptr, c->r32, c->part, S); ++c->n_launch;
+            HT_CUDA(c, cudaGetLastError());
+        } else {
+            HT_TRY(launch_resid_df(c, field, dt, x, b, c->r32, c->part, &np));
+        }
+        scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, S, np, c->scal + 2, 0.0, 0); ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
         HT_TRY(sync_scal(c, 2));
         const Scal s = c->scal_host[2];
@@ -1193,6 +1199,24 @@ int true_residual(ht_ctx* c, int field, double dt, const double* x, const double
     HT_TRY(sync_scal(c, 3));
     const Scal s = c->scal_host[3];
     *rel = s.bb > 0 ? sqrt(s.rr / s.bb) : sqrt(s.rr);
+    return HT_OK;
+}
+
+// r = b - q, partial sums of r.r and b.b (slots 0 and 1); *n_part entries
+int launch_resid64(ht_ctx* c, const double* b, const double* q, double* part, int* n_part) {
+    const int G = vec_grid(c);
+    resid_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid.nn, b, q, nullptr, nullptr, part, c->part_stride);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    *n_part = G;
+    return HT_OK;
+}
+
+// reduce the r.r / b.b partial sums into c->scal[slot] (rr, bb)
+int launch_norms(ht_ctx* c, int n_part, int slot) {
+    scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, c->part_stride, n_part, c->scal + slot, 0.0, 0);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }
 

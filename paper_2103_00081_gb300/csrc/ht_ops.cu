@@ -53,6 +53,69 @@ __device__ __forceinline__ long long nidx(const Grid& g, int i, int j, int k) {
 template <typename T>
 __device__ __forceinline__ T ldro(const T* p) { return __ldg(p); }
 
+// ---------------------------------------------------------------------------
+// Float-float arithmetic (emulated FP64 on the FP32 pipes, which GB300 runs
+// at 64x its FP64 rate).  Error-free transformations: TwoSum (Knuth, TAOCP
+// vol. 2, 4.2.2), FastTwoSum for |a| >= |b| (Dekker 1971) and TwoProduct
+// with a fused multiply-add; the compound addition adds the low parts
+// without a second TwoSum (Dekker's addition), so its error is of order
+// 2^-46 (|a| + |b|) and the product's 2^-46 |ab|.  The _rn intrinsics keep
+// the compiler from contracting the steps into other fused operations.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df64(s, e);
+}
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+    const df64 s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+using ::fma;   // keep the float and double overloads visible beside the float-float one
+__device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) { return a * b + c; }
+__device__ __forceinline__ df64 df_from(double d) {
+    const float hi = __double2float_rn(d);
+    return df64(hi, __double2float_rn(d - (double)hi));
+}
+__device__ __forceinline__ double df_to(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// read-only load of any of the element types
+template <typename T>
+__device__ __forceinline__ T ldg_any(const T* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ df64 ldg_any<df64>(const df64* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return df64(v.x, v.y);
+}
+
+// value of storage type S in compute type T
+template <typename T, typename S>
+struct Cvt {
+    __device__ __forceinline__ static T f(S v) { return (T)v; }
+};
+template <>
+struct Cvt<df64, double> {
+    __device__ __forceinline__ static df64 f(double v) { return df_from(v); }
+};
+template <typename T, typename S>
+__device__ __forceinline__ T cvt(S v) { return Cvt<T, S>::f(v); }
+
 // Sum over the CTA (1D, 2D or 3D blocks whose size is a multiple of 32);
 // the result is valid in the thread with linear index 0.
 __device__ __forceinline__ double block_sum(double v) {
@@ -125,20 +188,20 @@ __device__ __forceinline__ void sweep(T (&u)[n * n * n], const T (&M)[3][3]) {
 // ---------------------------------------------------------------------------
 // Operators (cell computation + node emission)
 // ---------------------------------------------------------------------------
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, typename S = T>
 struct HeadOp {
     static constexpr int n = P + 1, NL = n * n * n;
     const T* x;        // APPLY: input; RHS: u_old
     const double* gD;  // RHS: Dirichlet values
     const double* F;   // RHS: loads
     T* y;
-    const T* K;
+    const S* K;        // per cell, in storage type S (converted to T on load)
     T alpha, dt;
     Elem<T> e;
 
     __device__ __forceinline__ void cell(const Grid& g, int cx, int cy, int cz, long long c,
                                          T (&res)[NL]) const {
-        const T beta = dt * ldro(K + c);
+        const T beta = dt * cvt<T>(ldro(K + c));
         if (MODE == MODE_DIAG) {
 #pragma unroll
             for (int l = 0; l < NL; ++l) res[l] = fma(beta, e.dK[l], alpha * e.dM[l]);
@@ -219,7 +282,7 @@ struct HeadOp {
     __device__ __forceinline__ void compute(const T (&u)[NL], long long c, T (&res)[NL]) const {
 #pragma unroll
         for (int l = 0; l < NL; ++l) res[l] = u[l];
-        fdm(res, dt * ldro(K + c));
+        fdm(res, dt * cvt<T>(ldro(K + c)));
     }
 
     __device__ __forceinline__ void emit(const Grid& g, int i, int j, int k, T val, T& dot) const {
@@ -238,31 +301,31 @@ struct HeadOp {
     }
 };
 
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, typename S = T>
 struct HeatOp {
     static constexpr int n = P + 1, NL = n * n * n, NQ = n * n * n;
     const T* x;        // APPLY: input; RHS: T_old
     const double* gD;
     const double* F;
     T* y;
-    const T* qs;       // [3*NQ][nc]
-    const T* cTc;      // optional per-cell
-    const T* lamc;
+    const S* qs;       // [3*NQ][nc], in storage type S (converted to T on load)
+    const S* cTc;      // optional per-cell
+    const S* lamc;
     T cT_u, lam_u, dt, cw;
     Elem<T> e;
 
     // element result of the apply from the (masked) element vector u
     __device__ __forceinline__ void compute(const T (&u)[NL], long long c, T (&res)[NL]) const {
-        const T cT = cTc ? ldro(cTc + c) : cT_u;
-        const T dtlam = dt * (lamc ? ldro(lamc + c) : lam_u);
+        const T cT = cTc ? cvt<T>(ldro(cTc + c)) : cT_u;
+        const T dtlam = dt * (lamc ? cvt<T>(ldro(lamc + c)) : lam_u);
         core(u, u, T(1), cT, dtlam, dt * cw, c, g_nc, res);
     }
     long long g_nc;
 
     __device__ __forceinline__ void cell(const Grid& g, int cx, int cy, int cz, long long c,
                                          T (&res)[NL]) const {
-        const T cT = cTc ? ldro(cTc + c) : cT_u;
-        const T dtlam = dt * (lamc ? ldro(lamc + c) : lam_u);
+        const T cT = cTc ? cvt<T>(ldro(cTc + c)) : cT_u;
+        const T dtlam = dt * (lamc ? cvt<T>(ldro(lamc + c)) : lam_u);
         const T dtcw = dt * cw;
         const long long nc = g.nc;
         if (MODE == MODE_DIAG) {
@@ -276,7 +339,7 @@ struct HeatOp {
             for (int d = 0; d < 3; ++d) {
                 T f[NQ];
 #pragma unroll
-                for (int qi = 0; qi < NQ; ++qi) f[qi] = dtcw * e.W[qi] * e.invH[d] * ldro(qs + (d * NQ + qi) * nc + c);
+                for (int qi = 0; qi < NQ; ++qi) f[qi] = dtcw * e.W[qi] * e.invH[d] * cvt<T>(ldro(qs + (d * NQ + qi) * nc + c));
                 // x: f1[qz][qy][a] = sum_qx Mx[qx][a] f[qz][qy][qx]
                 T f1[NQ];
 #pragma unroll
@@ -349,7 +412,7 @@ struct HeatOp {
     // M = (G^T)^3 G^3 (the 1D mass is G^T G)
     __device__ __forceinline__ void rhs_interior(const Grid& g, int cx, int cy, int cz, T (&res)[NL]) const {
         const long long c = (long long)cx + (long long)g.ncx * ((long long)cy + (long long)g.ncy * cz);
-        const T cT = cTc ? ldro(cTc + c) : cT_u;
+        const T cT = cTc ? cvt<T>(ldro(cTc + c)) : cT_u;
         gather<P, T>(g, x, cx, cy, cz, false, res);
         sweep<n, 0, false>(res, e.G[0]);
         sweep<n, 1, false>(res, e.G[1]);
@@ -419,9 +482,9 @@ struct HeatOp {
                     gy *= e.invH[1];
                     gz *= e.invH[2];
                     const int qi = qx + n * (qy + n * qz);
-                    const T q0 = ldro(qs + (0 * NQ + qi) * nc + c);
-                    const T q1 = ldro(qs + (1 * NQ + qi) * nc + c);
-                    const T q2 = ldro(qs + (2 * NQ + qi) * nc + c);
+                    const T q0 = cvt<T>(ldro(qs + (0 * NQ + qi) * nc + c));
+                    const T q1 = cvt<T>(ldro(qs + (1 * NQ + qi) * nc + c));
+                    const T q2 = cvt<T>(ldro(qs + (2 * NQ + qi) * nc + c));
                     const T W = e.W[qi];
                     const T v = W * fma(cT, val, sgn * dtcw * (q0 * gx + q1 * gy + q2 * gz));
                     const T f = sgn * W * dtlam;
@@ -863,7 +926,7 @@ struct NodeXY {
         for (int zz = 0; zz < 2; ++zz)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                v[q + 4 * zz] = __ldg(E + ((vz[zz] && vxy[q]) ? eb[q] + ez[zz] : -1));
+                v[q + 4 * zz] = ldg_any(E + ((vz[zz] && vxy[q]) ? eb[q] + ez[zz] : -1));
     }
 };
 
@@ -1384,6 +1447,89 @@ __global__ void __launch_bounds__(128) node_emit_kernel(const Grid g, const T* _
         nx.load(g, E, k, v);
         const T sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
         op.emit(g, i, j, k, sum, dot);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Outer residual of the mixed form in float-float arithmetic: the element pass
+// splits the FP64 iterate into float pairs (Dirichlet nodes zero) and applies
+// the element operator in float-float; the node pass sums the contributions
+// in float-float, returns to FP64 for r = b - A x (and the lumped well term),
+// and writes (float) r for the next inner solve and partial sums of r.r and
+// b.b.  The element buffer is the FP64 one, read as float pairs.
+// ---------------------------------------------------------------------------
+template <int P, class Op>
+__global__ void __launch_bounds__(128) df_cell_kernel(const Grid g, const Op op, const double* __restrict__ x,
+                                                      df64* __restrict__ E, const int zlen) {
+    constexpr int n = P + 1, NL = n * n * n;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cx >= g.ncx || cy >= g.ncy) return;
+    const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
+    const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+    const int NX = g.Nx, NXY = g.Nx * g.Ny;
+    const bool edge_xy = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1);
+    int base = P * cx + NX * P * cy + NXY * P * cz0;
+    int c = cx + g.ncx * cy + layer * cz0;
+    for (int cz = cz0; cz < cz1; ++cz, base += NXY * P, c += layer) {
+        df64 u[NL];
+#pragma unroll
+        for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+            for (int b = 0; b < n; ++b)
+#pragma unroll
+                for (int a = 0; a < n; ++a) u[a + n * (b + n * c2)] = df_from(ldro(x + base + NX * b + NXY * c2 + a));
+        if (edge_xy || (g.dmask & 48 && (cz == 0 || cz == g.ncz - 1))) {
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a)
+                        if (on_dir(g, P * cx + a, P * cy + b, P * cz + c2)) u[a + n * (b + n * c2)] = df64(0);
+        }
+        df64 res[NL];
+        op.compute(u, c, res);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) E[l * nc + c] = res[l];
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) df_resid_node_kernel(const Grid g, const df64* __restrict__ E,
+                                                            const double* __restrict__ x,
+                                                            const double* __restrict__ b,
+                                                            const double* __restrict__ wd, const double dt,
+                                                            float* __restrict__ r32, double* __restrict__ part,
+                                                            const int stride, const int klen) {
+    const int NXY = g.Nx * g.Ny;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    double rr = 0.0, bb = 0.0;
+    if (m < NXY) {
+        const NodeXY<P> nx(g, m % g.Nx, m / g.Nx);
+        const int k0 = blockIdx.y * klen, k1 = min(k0 + klen, g.Nz);
+        for (int k = k0; k < k1; ++k) {
+            const int id = m + NXY * k;
+            df64 v[8];
+            nx.load(g, E, k, v);
+            const df64 sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+            const bool d = nx.dir || ((g.dmask & 16) && k == 0) || ((g.dmask & 32) && k == g.Nz - 1);
+            const double xi = x[id];
+            double y = d ? xi : df_to(sum);
+            if (wd && !d) y = fma(dt * wd[id], xi, y);
+            const double bi = b[id];
+            const double ri = bi - y;
+            r32[id] = (float)ri;
+            rr = fma(ri, ri, rr);
+            bb = fma(bi, bi, bb);
+        }
+    }
+    const double a0 = block_sum(rr);
+    const double a1 = block_sum(bb);
+    if (threadIdx.x == 0) {
+        const int blk = blockIdx.x + gridDim.x * blockIdx.y;
+        part[blk] = a0;
+        part[(size_t)stride + blk] = a1;
     }
 }
 
@@ -1919,6 +2065,52 @@ int launch_diag32(ht_ctx* c, int field, double dt, float* D) {
         HT_CUDA(c, cudaGetLastError());
     }
     return HT_OK;
+}
+
+template <int P, class Op>
+static int resid_df_P(ht_ctx* c, const Grid& g, const Op& op, const double* x, const double* b, float* r32,
+                      double* part, int* n_part, double dt, const double* wd) {
+    df64* E = reinterpret_cast<df64*>(elem_buffer<double>(c));
+    dim3 cg, ng;
+    int zl, kl;
+    cell_pass_dims(c, g, resident_per_sm<df_cell_kernel<P, Op>>(), &cg, &zl);
+    layer_node_dims(c, g, resident_per_sm<df_resid_node_kernel<P>>(), &ng, &kl);
+    if ((int)(ng.x * ng.y) > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
+    df_cell_kernel<P, Op><<<cg, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zl); ++c->n_launch;
+    df_resid_node_kernel<P><<<ng, 128, 0, c->stream>>>(g, E, x, b, wd, dt, r32, part, c->part_stride, kl);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    *n_part = (int)(ng.x * ng.y);
+    return HT_OK;
+}
+
+static df64 df_split(double d) {
+    const float hi = (float)d;
+    return df64(hi, (float)(d - (double)hi));
+}
+
+template <int P>
+static int resid_df_field(ht_ctx* c, int field, double dt, const double* x, const double* b, float* r32,
+                          double* part, int* n_part) {
+    const Grid g = field_grid(c, field);
+    if (field == HT_HEAD) {
+        HeadOp<P, df64, MODE_APPLY, double> op{};
+        op.K = c->K64; op.alpha = df_split(c->Ss); op.dt = df_split(dt); op.e = c->edf;
+        return resid_df_P<P>(c, g, op, x, b, r32, part, n_part, dt, nullptr);
+    }
+    HeatOp<P, df64, MODE_APPLY, double> op{};
+    op.qs = c->qs64; op.cTc = c->cT64; op.lamc = c->lam64;
+    op.cT_u = df_split(c->cT_u); op.lam_u = df_split(c->lam_u); op.dt = df_split(dt); op.cw = df_split(c->cw);
+    op.e = c->edf;
+    op.g_nc = g.nc;
+    return resid_df_P<P>(c, g, op, x, b, r32, part, n_part, dt, c->wdn64);
+}
+
+int launch_resid_df(ht_ctx* c, int field, double dt, const double* x, const double* b, float* r32,
+                    double* part, int* n_part) {
+    if (!c->E64) return fail(c, HT_EINVAL, "no element buffer");
+    return c->grid.P == 1 ? resid_df_field<1>(c, field, dt, x, b, r32, part, n_part)
+                          : resid_df_field<2>(c, field, dt, x, b, r32, part, n_part);
 }
 
 int launch_diag(ht_ctx* c, int field, double dt, double* D) {

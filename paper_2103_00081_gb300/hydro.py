@@ -173,6 +173,15 @@ class Simulator:
     def apply(self, field, dt, x):
         return self._vec_call(self._lib.ht_apply, field, dt, x)
 
+    def residual(self, field, dt, x, b, emulated=False):
+        """||b - A x|| / ||b|| with A x in FP64 or in float-float (emulated)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        rel = c_double()
+        self._check(self._lib.ht_residual(self._h, int(field), float(dt), x.ctypes.data_as(c_void_p),
+                                          b.ctypes.data_as(c_void_p), int(bool(emulated)), 0, byref(rel)))
+        return rel.value
+
     def diag(self, field, dt):
         return self._vec_call(self._lib.ht_diag, field, dt)
 

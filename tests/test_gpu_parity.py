@@ -217,6 +217,43 @@ def test_fused_two_pass_bicgstab_steps_match_oracle(Sim, case, mixed):
             assert abs(st["iters_heat"] - st_ref["iters_heat"]) <= max(2, 0.1 * st_ref["iters_heat"])
 
 
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[5]], ids=_ids)
+def test_float_float_outer_residual_matches_fp64(Sim, case):
+    """The mixed form computes its outer residuals b - A x with the operator
+    in float-float arithmetic (about 48 bits).  On the systems of a step and
+    the solutions returned, that residual must equal the FP64 one to 1e-13
+    relative to ||b||, equal the residual the step reported, and the FP64
+    residual must meet the tolerance to within that margin; the solutions
+    agree with the FP64-residual variant and the oracle."""
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(case)
+    o = fem.OracleSim(sc)
+    tol = 1e-12
+    common = dict(tol=tol, precision=L.HT_MIXED, inner_tol=1e-4)
+    sim = Sim.from_scenario(sc, **common)
+    ref = Sim.from_scenario(sc, outer_fp64=1, **common)
+    dt = sc.dt
+    for _ in range(2):
+        t0 = sim.time
+        T0 = sim.get_field(S.TEMP)
+        bh = sim.rhs(S.HEAD, dt)
+        st = sim.step(dt)
+        ref.step(dt)
+        o.step(dt)
+        h1, T1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP)
+        sim.set_state(h1, T0, t0)          # heat system of this step: T^n with h^{n+1}
+        bT = sim.rhs(S.TEMP, dt)
+        for field, x, b, rep in ((S.HEAD, h1, bh, st["res_head"]), (S.TEMP, T1, bT, st["res_heat"])):
+            r_df = sim.residual(field, dt, x, b, emulated=True)
+            r_64 = sim.residual(field, dt, x, b, emulated=False)
+            assert abs(r_df - r_64) <= 1e-13, (field, r_df, r_64)
+            assert abs(r_df - rep) <= 1e-15, (field, r_df, rep)
+            assert r_64 <= tol + 1e-13, (field, r_64)
+        sim.set_state(h1, T1, t0 + dt)
+        assert _rel(h1, o.h) <= 1e-9 and _rel(T1, o.T) <= 1e-9
+        assert _rel(h1, ref.get_field(S.HEAD)) <= 1e-9 and _rel(T1, ref.get_field(S.TEMP)) <= 1e-9
+
+
 def test_config1_plain_workload_matches_oracle(Sim):
     """The plain FP64 workload: 16^3 Q1 cube, line source, 10 days."""
     sc = S.config1()
