@@ -585,9 +585,11 @@ int prof_flush(ht_ctx* c) {
         float ms = 0.f;
         HT_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
         c->prof_ms[c->ev_kind[i]].push_back(ms);
+        c->prof_w[c->ev_kind[i]].push_back((float)c->ev_weight[i]);
     }
     c->ev_used = 0;
     c->ev_kind.clear();
+    c->ev_weight.clear();
     return HT_OK;
 }
 
@@ -600,6 +602,7 @@ int prof_begin(ht_ctx* c, int kind) {
     if (2 * c->ev_used + 2 > c->ev_pool.size()) HT_TRY(prof_flush(c));
     HT_CUDA(c, cudaEventRecord(c->ev_pool[2 * c->ev_used], c->stream));
     c->ev_kind.push_back(kind);
+    c->ev_weight.push_back(1);
     return HT_OK;
 }
 
@@ -608,6 +611,19 @@ int prof_end(ht_ctx* c) {
     HT_CUDA(c, cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], c->stream));
     c->ev_used += 1;
     return HT_OK;
+}
+
+int prof_end_weighted(ht_ctx* c, int weight) {
+    if (!c->prof_on) return HT_OK;
+    c->ev_weight.back() = weight;
+    return prof_end(c);
+}
+
+void prof_drop_last(ht_ctx* c) {
+    if (c->ev_used == 0 || c->ev_kind.empty()) return;
+    c->ev_used -= 1;
+    c->ev_kind.pop_back();
+    c->ev_weight.pop_back();
 }
 
 }  // namespace ht
@@ -629,7 +645,7 @@ int ht_default_solver(ht_solver_opts* o) {
     o->inner_tol = 1e-4;
     o->max_outer = 30;
     o->check_every = 8;
-    o->use_graphs = 0;
+    o->use_graphs = 1;
     return HT_OK;
 }
 
@@ -724,6 +740,8 @@ void ht_destroy(ht_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto* gr : {&c->g_cg[0], &c->g_cg[1], &c->g_bi[0], &c->g_bi[1]})
+        if (gr->exec) cudaGraphExecDestroy(gr->exec);
     double** v64[] = {&c->h, &c->T, &c->g[0], &c->g[1], &c->Fstat[0], &c->Fstat[1], &c->F[0], &c->F[1],
                       &c->extra[0], &c->extra[1], &c->x, &c->r, &c->z, &c->p, &c->q, &c->b, &c->D,
                       &c->rh, &c->v, &c->s, &c->tv, &c->ph, &c->sh, &c->z2, &c->K64, &c->lam64,
@@ -1018,6 +1036,7 @@ int ht_profile(ht_ctx* c, int on) {
     c->prof_on = on;
     c->n_launch = 0;
     for (auto& v : c->prof_ms) v.clear();
+    for (auto& v : c->prof_w) v.clear();
     return HT_OK;
 }
 
@@ -1034,6 +1053,14 @@ int ht_profile_read(ht_ctx* c, ht_profile_stats* out) {
     for (int k = 0; k < HT_PROF_KINDS; ++k) {
         std::vector<float> v = c->prof_ms[k];
         if (v.empty()) continue;
+        if (k == HT_PROF_CG_ITER || k == HT_PROF_BICGSTAB_ITER) {
+            // timed check intervals in which every iteration did work
+            for (size_t i = 0; i < v.size(); ++i) {
+                *cnt[k] += (long long)c->prof_w[k][i];
+                *ms[k] += v[i];
+            }
+            continue;
+        }
         std::vector<float> srt = v;
         std::nth_element(srt.begin(), srt.begin() + srt.size() / 2, srt.end());
         const float med = srt[srt.size() / 2];

@@ -62,6 +62,8 @@ struct Scal {
     int kdone, conv;
     double rz2[2];   // r.z of the fused CG, indexed by iteration parity
     unsigned ticket; // CTAs done in the running fused-CG kernel (the last one resets it)
+    double tol2;     // squared relative tolerance and iteration limit of the
+    int max_iter;    // running solve (read by the fused kernels)
 };
 
 // GMRES(m) Hessenberg data (device resident).  H is column-major with
@@ -186,6 +188,17 @@ struct ht_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;                 // pairs in use
     std::vector<int> ev_kind;           // field + 2 * fp32 of each recorded pair
+    std::vector<int> ev_weight;         // iterations covered by each recorded pair
+    std::vector<std::vector<float>> prof_w = std::vector<std::vector<float>>(HT_PROF_KINDS);
+    // CUDA graphs of kGraphIters fused Krylov iterations, recaptured when the
+    // pointers or dt they were captured with change ([0] FP64, [1] FP32)
+    struct FusedGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* key[8] = {};
+        double dt = 0.0;
+        double ss = 0.0;                // operator scalars baked into the captured launches
+    };
+    FusedGraph g_cg[2], g_bi[2];
     std::vector<std::vector<float>> prof_ms = std::vector<std::vector<float>>(HT_PROF_KINDS);
 };
 
@@ -249,18 +262,20 @@ int launch_loads(ht_ctx* c, double t);
 int apply_tiles(const ht_ctx* c);
 // fused two-pass Jacobi-CG iteration of the head system (ht_ops.cu)
 int fused_cg_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* Dinv, double* p, Scal* sc,
-                         int first, double tol2, int max_iter);
+                         int first);
 int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* Dinv, float* p, Scal* sc,
-                         int first, double tol2, int max_iter);
+                         int first);
 bool fused_cg_available(const ht_ctx* c, int fp32);
 // fused two-pass Jacobi-BiCGStab iteration of the heat system (ht_ops.cu)
 int fused_bicgstab_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* rh, double* p, double* v,
-                               double* t, const double* Dinv, Scal* sc, double tol2, int max_iter);
+                               double* t, const double* Dinv, Scal* sc);
 int fused_bicgstab_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* rh, float* p, float* v,
-                               float* t, const float* Dinv, Scal* sc, double tol2, int max_iter);
+                               float* t, const float* Dinv, Scal* sc);
 // event bracketing of apply launches (kind = field + 2 * fp32)
 int prof_begin(ht_ctx* c, int kind);
 int prof_end(ht_ctx* c);
+int prof_end_weighted(ht_ctx* c, int weight);   // the pair covers `weight` iterations
+void prof_drop_last(ht_ctx* c);                 // forget the last pair (not yet flushed)
 int prof_flush(ht_ctx* c);
 
 // ---- allocation-free head apply (ht_ops.cu) ----------------------------------

@@ -67,6 +67,7 @@ __global__ void scalar_kernel(int op, const double* __restrict__ part, int strid
     if (threadIdx.x != 0) return;
     switch (op) {
         case SC_CG_INIT:  // a0 = r.z, a1 = r.r, a2 = b.b
+            s->tol2 = tol2; s->max_iter = max_iter;
             s->rz = a0; s->rr = a1; s->bb = a2; s->rr0 = a1;
             s->rz2[0] = a0;
             s->iters = 0; s->status = ST_OK;
@@ -95,6 +96,7 @@ __global__ void scalar_kernel(int op, const double* __restrict__ part, int strid
             else if (a2 <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
             break;
         case SC_BI_INIT:  // a0 = rh.r, a1 = r.r, a2 = b.b
+            s->tol2 = tol2; s->max_iter = max_iter;
             s->rho = a0; s->rr = a1; s->bb = a2; s->rr0 = a1;
             s->alpha = 1.0; s->omega = 1.0; s->beta = 0.0;
             s->iters = 0; s->status = ST_OK;
@@ -754,20 +756,93 @@ int apply_T<float>(ht_ctx* c, int field, double dt, const float* x, float* y, do
     return launch_apply32(c, field, (float)dt, x, y, part, np, sc);
 }
 
-inline int fused_cg_iteration(ht_ctx* c, double dt, const Vecs64& w, Scal* sc, int first, double tol2,
-                              int max_iter) {
-    return fused_cg_iteration64(c, dt, w.x, w.r, w.Dinv, w.p, sc, first, tol2, max_iter);
+inline int fused_cg_iteration(ht_ctx* c, double dt, const Vecs64& w, Scal* sc, int first) {
+    return fused_cg_iteration64(c, dt, w.x, w.r, w.Dinv, w.p, sc, first);
 }
-inline int fused_cg_iteration(ht_ctx* c, double dt, const Vecs32& w, Scal* sc, int first, double tol2,
-                              int max_iter) {
-    return fused_cg_iteration32(c, (float)dt, w.x, w.r, w.Dinv, w.p, sc, first, tol2, max_iter);
+inline int fused_cg_iteration(ht_ctx* c, double dt, const Vecs32& w, Scal* sc, int first) {
+    return fused_cg_iteration32(c, (float)dt, w.x, w.r, w.Dinv, w.p, sc, first);
+}
+inline int fused_bicgstab_iteration(ht_ctx* c, double dt, const Vecs64& w, Scal* sc) {
+    return fused_bicgstab_iteration64(c, dt, w.x, w.r, w.rh, w.p, w.v, w.t, w.Dinv, sc);
+}
+inline int fused_bicgstab_iteration(ht_ctx* c, double dt, const Vecs32& w, Scal* sc) {
+    return fused_bicgstab_iteration32(c, (float)dt, w.x, w.r, w.rh, w.p, w.v, w.t, w.Dinv, sc);
 }
 
-inline int fused_bicgstab_iteration(ht_ctx* c, double dt, const Vecs64& w, Scal* sc, double tol2, int max_iter) {
-    return fused_bicgstab_iteration64(c, dt, w.x, w.r, w.rh, w.p, w.v, w.t, w.Dinv, sc, tol2, max_iter);
+// Fused iterations per CUDA graph replay.
+constexpr int kGraphIters = 8;
+
+// Capture kGraphIters calls of iter() into gr (kernel launches only; the
+// context's launch counter is restored, replays count their launches).
+template <class Iter>
+int capture_fused(ht_ctx* c, ht_ctx::FusedGraph& gr, Iter&& iter) {
+    if (gr.exec) { cudaGraphExecDestroy(gr.exec); gr.exec = nullptr; }
+    const long long nl = c->n_launch;
+    HT_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = HT_OK;
+    for (int k = 0; k < kGraphIters && rc == HT_OK; ++k) rc = iter();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->n_launch = nl;
+    if (rc != HT_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != HT_OK) return rc;
+        HT_CUDA(c, e);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&gr.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { gr.exec = nullptr; HT_CUDA(c, ie); }
+    return HT_OK;
 }
-inline int fused_bicgstab_iteration(ht_ctx* c, double dt, const Vecs32& w, Scal* sc, double tol2, int max_iter) {
-    return fused_bicgstab_iteration32(c, (float)dt, w.x, w.r, w.rh, w.p, w.v, w.t, w.Dinv, sc, tol2, max_iter);
+
+// Drive fused Krylov iterations until the device flags convergence.  iter(1)
+// is the first iteration, iter(0) every later one.  With graphs on, later
+// iterations are replays of a graph of kGraphIters iterations, captured once
+// per key (the vectors, the step size and the operator scalars); iterations
+// launched after convergence return at once.  The host checks convergence
+// every 8..64 iterations.  When profiling, each check interval is timed with
+// CUDA events and kept only if every iteration in it did work (counted per
+// iteration in ht_profile_read).
+template <class Iter>
+int drive_fused(ht_ctx* c, int slot, ht_ctx::FusedGraph& gr, const void* const* key, int nkey, double dt,
+                int kind, int launches_per_iter, Iter&& iter) {
+    HT_TRY(iter(1));
+    bool graphs = c->opts.use_graphs != 0;
+    if (graphs) {
+        bool same = gr.exec != nullptr && gr.dt == dt;
+        for (int k = 0; k < nkey && same; ++k) same = gr.key[k] == key[k];
+        if (!same) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+                cudaGetLastError();
+                graphs = false;       // the caller is capturing this stream: launch directly
+            } else {
+                HT_TRY(capture_fused(c, gr, [&] { return iter(0); }));
+                for (int k = 0; k < nkey; ++k) gr.key[k] = key[k];
+                gr.dt = dt;
+            }
+        }
+    }
+    int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
+    if (graphs) chunk = (chunk + kGraphIters - 1) / kGraphIters * kGraphIters;
+    HT_TRY(sync_scal(c, slot));
+    while (!c->scal_host[slot].done) {
+        const int before = c->scal_host[slot].iters;
+        if (c->prof_on) HT_TRY(prof_begin(c, kind));
+        if (graphs) {
+            for (int k = 0; k < chunk; k += kGraphIters) {
+                HT_CUDA(c, cudaGraphLaunch(gr.exec, c->stream));
+                c->n_launch += (long long)kGraphIters * launches_per_iter;
+            }
+        } else {
+            for (int k = 0; k < chunk; ++k) HT_TRY(iter(0));
+        }
+        if (c->prof_on) HT_TRY(prof_end_weighted(c, chunk));
+        HT_TRY(sync_scal(c, slot));
+        if (c->prof_on && c->scal_host[slot].iters - before != chunk) prof_drop_last(c);
+        if (chunk < 64) chunk *= 2;
+    }
+    return HT_OK;
 }
 
 // Preconditioned CG on A0 x = b (x holds the initial guess).  Returns
@@ -796,12 +871,13 @@ int run_cg(ht_ctx* c, double dt, const V& w, const T* b, int slot, double tol, i
     if (fused_cg_available(c, sizeof(T) == 4)) {
         // two launches per iteration: the p update rides in the element pass,
         // the x / r update and the next dot products in the node gather
-        while (!c->scal_host[slot].done) {
-            for (int k = 0; k < chunk; ++k, ++it_enq)
-                HT_TRY(fused_cg_iteration(c, dt, w, sc, it_enq == 0, tol * tol, max_iter));
-            HT_TRY(sync_scal(c, slot));
-            if (chunk < 64) chunk *= 2;
-        }
+        const double ss = c->Ss;
+        const void* key[5] = {w.x, w.r, w.Dinv, w.p, sc};
+        ht_ctx::FusedGraph& gr = c->g_cg[sizeof(T) == 4];
+        if (gr.exec && gr.ss != ss) gr.dt = -1.0;   // operator scalar changed: recapture
+        HT_TRY(drive_fused(c, slot, gr, key, 5, dt, HT_PROF_CG_ITER, 2,
+                           [&](int first) { return fused_cg_iteration(c, dt, w, sc, first); }));
+        gr.ss = ss;
         *iters = c->scal_host[slot].iters;
         return HT_OK;
     }
@@ -844,9 +920,18 @@ int run_bicgstab(ht_ctx* c, double dt, const V& w, const T* b, int slot, double 
         }
         int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
         const bool fused = fused_cg_available(c, sizeof(T) == 4);
+        if (fused) {
+            // five launches per iteration (two element / node pass pairs and
+            // the update); the first iteration needs no special form
+            const double ss = c->cT_u + 3.0 * c->lam_u + 7.0 * c->cw;
+            const void* key[8] = {w.x, w.r, w.rh, w.p, w.v, w.t, w.Dinv, sc};
+            ht_ctx::FusedGraph& gr = c->g_bi[sizeof(T) == 4];
+            if (gr.exec && gr.ss != ss) gr.dt = -1.0;
+            HT_TRY(drive_fused(c, slot, gr, key, 8, dt, HT_PROF_BICGSTAB_ITER, 5,
+                               [&](int) { return fused_bicgstab_iteration(c, dt, w, sc); }));
+            gr.ss = ss;
+        }
         while (!c->scal_host[slot].done) {
-            for (int k = 0; fused && k < chunk; ++k)
-                HT_TRY(fused_bicgstab_iteration(c, dt, w, sc, tol * tol, max_iter - total));
             for (int k = 0; !fused && k < chunk; ++k) {
                 bi_p_kernel<T><<<G, kVecThreads, 0, c->stream>>>(n, w.r, w.p, w.v, w.Dinv, w.ph, sc); ++c->n_launch;
                 HT_TRY(apply_T<T>(c, HT_TEMP, dt, w.ph, w.v, nullptr, nullptr, sc));

@@ -191,6 +191,7 @@ __device__ __forceinline__ void sweep(T (&u)[n * n * n], const T (&M)[3][3]) {
 template <int P, typename T, int MODE, typename S = T>
 struct HeadOp {
     static constexpr int n = P + 1, NL = n * n * n;
+    static constexpr bool kPlanes = false;
     const T* x;        // APPLY: input; RHS: u_old
     const double* gD;  // RHS: Dirichlet values
     const double* F;   // RHS: loads
@@ -304,6 +305,7 @@ struct HeadOp {
 template <int P, typename T, int MODE, typename S = T>
 struct HeatOp {
     static constexpr int n = P + 1, NL = n * n * n, NQ = n * n * n;
+    static constexpr bool kPlanes = true;   // element pass: one thread per Gauss plane
     const T* x;        // APPLY: input; RHS: T_old
     const double* gD;
     const double* F;
@@ -422,6 +424,94 @@ struct HeatOp {
         sweep<n, 2, true>(res, e.G[2]);
         sweep<n, 1, true>(res, e.G[1]);
         sweep<n, 0, true>(res, e.G[0]);
+    }
+
+    // Contribution of Gauss plane qz to the element result of the apply
+    // (cT M + dt lam K + dt C) u, written to out[l] for all (P+1)^3 l: the
+    // z-sweep is restricted to plane qz and the transposed z-sweep scatters to
+    // every layer; the planes' contributions add up to compute()'s result
+    // (one thread per plane, u and out in shared memory).
+    __device__ __forceinline__ void plane(const T* u, const long long c, const long long nc, const int qz,
+                                          T* out) const {
+        const T cT = cTc ? cvt<T>(ldro(cTc + c)) : cT_u;
+        const T dtlam = dt * (lamc ? cvt<T>(ldro(lamc + c)) : lam_u);
+        const T dtcw = dt * cw;
+        T zB[n * n], zD[n * n];
+#pragma unroll
+        for (int ba = 0; ba < n * n; ++ba) {
+            T sb = T(0), sd = T(0);
+#pragma unroll
+            for (int c2 = 0; c2 < n; ++c2) {
+                const T uv = u[ba + n * n * c2];
+                sb = fma(e.B[qz][c2], uv, sb);
+                sd = fma(e.D[qz][c2], uv, sd);
+            }
+            zB[ba] = sb;
+            zD[ba] = sd;
+        }
+        T s1[n * n], s2[n * n];
+#pragma unroll
+        for (int ba = 0; ba < n * n; ++ba) { s1[ba] = T(0); s2[ba] = T(0); }
+#pragma unroll
+        for (int qy = 0; qy < n; ++qy) {
+            T yBB[n], yDB[n], yBD[n];
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                T v0 = T(0), v2 = T(0), v3 = T(0);
+#pragma unroll
+                for (int b = 0; b < n; ++b) {
+                    v0 = fma(e.B[qy][b], zB[a + n * b], v0);
+                    v2 = fma(e.D[qy][b], zB[a + n * b], v2);
+                    v3 = fma(e.B[qy][b], zD[a + n * b], v3);
+                }
+                yBB[a] = v0; yDB[a] = v2; yBD[a] = v3;
+            }
+            T t1[n], t2[n], t3[n];
+#pragma unroll
+            for (int a = 0; a < n; ++a) { t1[a] = T(0); t2[a] = T(0); t3[a] = T(0); }
+#pragma unroll
+            for (int qx = 0; qx < n; ++qx) {
+                T val = T(0), gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    val = fma(e.B[qx][a], yBB[a], val);
+                    gx = fma(e.D[qx][a], yBB[a], gx);
+                    gy = fma(e.B[qx][a], yDB[a], gy);
+                    gz = fma(e.B[qx][a], yBD[a], gz);
+                }
+                gx *= e.invH[0];
+                gy *= e.invH[1];
+                gz *= e.invH[2];
+                const int qi = qx + n * (qy + n * qz);
+                const T q0 = cvt<T>(ldro(qs + (0 * NQ + qi) * nc + c));
+                const T q1 = cvt<T>(ldro(qs + (1 * NQ + qi) * nc + c));
+                const T q2 = cvt<T>(ldro(qs + (2 * NQ + qi) * nc + c));
+                const T W = e.W[qi];
+                const T v = W * fma(cT, val, dtcw * (q0 * gx + q1 * gy + q2 * gz));
+                const T f = W * dtlam;
+                const T gxs = f * gx * e.invH[0];
+                const T gys = f * gy * e.invH[1];
+                const T gzs = f * gz * e.invH[2];
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    t1[a] = fma(e.B[qx][a], v, fma(e.D[qx][a], gxs, t1[a]));
+                    t2[a] = fma(e.B[qx][a], gys, t2[a]);
+                    t3[a] = fma(e.B[qx][a], gzs, t3[a]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < n; ++b)
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    s1[a + n * b] = fma(e.B[qy][b], t1[a], fma(e.D[qy][b], t2[a], s1[a + n * b]));
+                    s2[a + n * b] = fma(e.B[qy][b], t3[a], s2[a + n * b]);
+                }
+        }
+#pragma unroll
+        for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+            for (int ba = 0; ba < n * n; ++ba)
+                out[ba + n * n * c2] = fma(e.B[qz][c2], s1[ba], e.D[qz][c2] * s2[ba]);
     }
 
     // sum-factorised quadrature: res = cT M um + sgn (dt lam K + dt C) us
@@ -1108,7 +1198,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fcg_node_kernel(
                                                        T* __restrict__ r, const T* __restrict__ Dinv,
                                                        T* __restrict__ p, const int klen, Scal* s,
                                                        double* __restrict__ part, const int stride,
-                                                       const int first, const double tol2, const int max_iter) {
+                                                       const int first) {
     if (s->done) return;
     const T alpha = (T)s->alpha;
     const T beta = first ? T(0) : (T)s->beta;
@@ -1159,7 +1249,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fcg_node_kernel(
         s->rz_new = rz;
         s->iters += 1;
         if (!isfinite(rz) || !isfinite(rr)) { s->status = ST_NAN; s->done = 1; }
-        else if (rr <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
+        else if (rr <= s->tol2 * s->bb || s->iters >= s->max_iter) s->done = 1;
         s->beta = rz / s->rz;
         s->rz = rz;
     }
@@ -1188,6 +1278,7 @@ struct BiDirP {   // ph = Dinv (r + beta (p - omega v))
     const T* v;
     const T* Dinv;
     T beta, omega;
+    __device__ __forceinline__ void init(const Scal* s) { beta = (T)s->beta; omega = (T)s->omega; }
     __device__ __forceinline__ T val(int id) const { return fma(beta, fma(-omega, ldro(v + id), ldro(p + id)), ldro(r + id)); }
     __device__ __forceinline__ T operator()(int id) const { return ldro(Dinv + id) * val(id); }
 };
@@ -1197,6 +1288,7 @@ struct BiDirS {   // sh = Dinv (r - alpha v)
     const T* v;
     const T* Dinv;
     T alpha;
+    __device__ __forceinline__ void init(const Scal* s) { alpha = (T)s->alpha; }
     __device__ __forceinline__ T operator()(int id) const { return ldro(Dinv + id) * fma(-alpha, ldro(v + id), ldro(r + id)); }
 };
 
@@ -1331,8 +1423,7 @@ __global__ void __launch_bounds__(256) fbi_update_kernel(long long n, T* __restr
                                                          const T* __restrict__ p, const T* __restrict__ v,
                                                          const T* __restrict__ t, const T* __restrict__ Dinv,
                                                          const T* __restrict__ rh, Scal* s,
-                                                         double* __restrict__ part, const int stride,
-                                                         const double tol2, const int max_iter) {
+                                                         double* __restrict__ part, const int stride) {
     if (s->done) return;
     const T alpha = (T)s->alpha, omega = (T)s->omega;
     T rhr = T(0), rr = T(0);
@@ -1357,7 +1448,7 @@ __global__ void __launch_bounds__(256) fbi_update_kernel(long long n, T* __restr
         s->rr = a1;
         s->iters += 1;
         if (!isfinite(a0) || !isfinite(a1)) { s->status = ST_NAN; s->done = 1; }
-        else if (a1 <= tol2 * s->bb || s->iters >= max_iter) s->done = 1;
+        else if (a1 <= s->tol2 * s->bb || s->iters >= s->max_iter) s->done = 1;
         else if (a0 == 0.0 || s->omega == 0.0) { s->status = ST_BREAKDOWN; s->done = 1; }
         else {
             s->beta = (a0 / s->rho) * (s->alpha / s->omega);
@@ -1531,6 +1622,84 @@ __global__ void __launch_bounds__(128) df_resid_node_kernel(const Grid g, const 
         part[blk] = a0;
         part[(size_t)stride + blk] = a1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Heat element pass with one thread per Gauss plane: a CTA of 32 x (P+1)
+// threads takes 32 cells of a row and marches them in z.  Thread (tx, qz)
+// forms the operator input at node layer qz of its cell (nv(id), Dirichlet
+// nodes zero) in shared memory, computes the contribution of plane qz
+// (HeatOp::plane) into shared memory, and finally sums the planes'
+// contributions to node layer qz in a fixed order and writes them to E.
+// The three planes split the work and the registers of one cell.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LoadNodes {   // plain operator input
+    const T* x;
+    __device__ __forceinline__ void init(const Scal*) {}
+    __device__ __forceinline__ T operator()(int id) const { return ldro(x + id); }
+};
+struct LoadSplit {   // FP64 input split into float pairs
+    const double* x;
+    __device__ __forceinline__ void init(const Scal*) {}
+    __device__ __forceinline__ df64 operator()(int id) const { return df_from(ldro(x + id)); }
+};
+
+template <int P, typename T, class Op, class NV>
+__global__ void __launch_bounds__(32 * (P + 1)) heat_plane_kernel(const Grid g, const Op op, NV nv,
+                                                                  T* __restrict__ E, const int zlen,
+                                                                  const Scal* s) {
+    if (s && s->done) return;
+    if (s) nv.init(s);
+    constexpr int n = P + 1, NL = n * n * n;
+    __shared__ T su[32][NL];
+    __shared__ T sp[n][32][NL];
+    const int tx = threadIdx.x, qz = threadIdx.y;
+    const int cx = blockIdx.x * 32 + tx, cy = blockIdx.y;
+    const bool valid = cx < g.ncx;
+    const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
+    const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+    const int NX = g.Nx, NXY = g.Nx * g.Ny;
+    const bool edge_xy = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1);
+    int base = P * cx + NX * P * cy + NXY * P * cz0;
+    int c = cx + g.ncx * cy + layer * cz0;
+    for (int cz = cz0; cz < cz1; ++cz, base += NXY * P, c += layer) {
+        if (valid) {
+            const bool chk = edge_xy || ((g.dmask & 48) && (cz == 0 || cz == g.ncz - 1));
+#pragma unroll
+            for (int b = 0; b < n; ++b)
+#pragma unroll
+                for (int a = 0; a < n; ++a) {
+                    T u = nv(base + NX * b + NXY * qz + a);
+                    if (chk && on_dir(g, P * cx + a, P * cy + b, P * cz + qz)) u = T(0);
+                    su[tx][a + n * (b + n * qz)] = u;
+                }
+        }
+        __syncthreads();
+        if (valid) op.plane(&su[tx][0], c, nc, qz, &sp[qz][tx][0]);
+        __syncthreads();
+        if (valid) {
+#pragma unroll
+            for (int ba = 0; ba < n * n; ++ba) {
+                const int l = ba + n * n * qz;
+                T v = sp[0][tx][l];
+#pragma unroll
+                for (int q = 1; q < n; ++q) v = v + sp[q][tx][l];
+                E[l * nc + c] = v;
+            }
+        }
+    }
+}
+
+// grid of heat_plane_kernel: 32-cell row segments x rows x a split of the layers
+template <auto Kernel>
+int resident_per_sm_threads(int threads) {
+    static const int r = [threads] {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, Kernel, threads, 0) != cudaSuccess || v < 1) v = 1;
+        return v;
+    }();
+    return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -1786,6 +1955,29 @@ void cell_pass_dims(const ht_ctx* c, const Grid& g, int cell_per_sm, dim3* grid,
     *grid = dim3(gx, gy, zs);
 }
 
+// grid of heat_plane_kernel: 32-cell row segments x rows x a split of the layers
+void plane_pass_dims(const ht_ctx* c, const Grid& g, int cta_per_sm, dim3* grid, int* zlen) {
+    const int sms = c->num_sms > 0 ? c->num_sms : 148;
+    const int gx = (g.ncx + 31) / 32;
+    int zs = pick_split(g.ncz, gx * g.ncy, cta_per_sm * sms, g.ncz);
+    *zlen = (g.ncz + zs - 1) / zs;
+    zs = (g.ncz + *zlen - 1) / *zlen;
+    *grid = dim3(gx, g.ncy, zs);
+}
+
+// launch of the element pass of a heat operator with input functor nv
+template <int P, typename T, class Op, class NV>
+int launch_heat_planes(ht_ctx* c, const Grid& g, const Op& op, const NV& nv, T* E, const Scal* sc) {
+    constexpr int threads = 32 * (P + 1);
+    dim3 grid;
+    int zlen;
+    plane_pass_dims(c, g, resident_per_sm_threads<heat_plane_kernel<P, T, Op, NV>>(threads), &grid, &zlen);
+    heat_plane_kernel<P, T, Op, NV><<<grid, dim3(32, P + 1), 0, c->stream>>>(g, op, nv, E, zlen, sc);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
 // node-pass grid: 128-node runs of a layer x a split of the layers; the block
 // count bounds the partial sums
 void layer_node_dims(const ht_ctx* c, const Grid& g, int node_per_sm, dim3* grid, int* klen) {
@@ -1807,8 +1999,12 @@ int launch_apply_two_pass(ht_ctx* c, const Grid& g, const Op& op, const T* x, T*
     layer_node_dims(c, g, resident_per_sm<node_pass_kernel<P, T>>(), &ngrid, &klen);
     const int nb = (int)(ngrid.x * ngrid.y);
     if (dot_part && nb > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
-    cell_pass_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zlen, sc); ++c->n_launch;
-    HT_CUDA(c, cudaGetLastError());
+    if constexpr (Op::kPlanes) {
+        HT_TRY((launch_heat_planes<P, T>(c, g, op, LoadNodes<T>{x}, E, sc)));
+    } else {
+        cell_pass_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zlen, sc); ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+    }
     node_pass_kernel<P, T><<<ngrid, 128, 0, c->stream>>>(g, E, x, y, klen, dot_part, sc); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     if (n_part) *n_part = nb;
@@ -1832,8 +2028,7 @@ template <>
 const Elem<float>& elem_of<float>(const ht_ctx* c) { return c->e32; }
 
 template <int P, typename T>
-int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal* sc, int first, double tol2,
-                         int max_iter) {
+int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal* sc, int first) {
     using Op = HeadOp<P, T, MODE_APPLY>;
     const Grid g = field_grid(c, HT_HEAD);
     Op op{};
@@ -1848,15 +2043,13 @@ int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal*
     layer_node_dims(c, g, resident_per_sm<fcg_node_kernel<P, T>>(), &ngrid, &klen);
     if ((int)(cgrid.x * cgrid.y * cgrid.z) > c->part_stride || (int)(ngrid.x * ngrid.y) > c->part_stride)
         return fail(c, HT_EINVAL, "too many partial sums");
-    HT_TRY(prof_begin(c, HT_PROF_CG_ITER));
     fcg_cell_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, r, Dinv, p, E, zlen, sc, c->part, first);
     ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     fcg_node_kernel<P, T><<<ngrid, 128, 0, c->stream>>>(g, E, x, r, Dinv, p, klen, sc, c->part, c->part_stride,
-                                                        first, tol2, max_iter);
+                                                        first);
     ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
-    HT_TRY(prof_end(c));
     return HT_OK;
 }
 
@@ -1869,7 +2062,7 @@ const float* well_dense<float>(const ht_ctx* c) { return c->wdn32; }
 
 template <int P, typename T>
 int fused_bicgstab_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* rh, T* p, T* v, T* t, const T* Dinv,
-                               Scal* sc, double tol2, int max_iter) {
+                               Scal* sc) {
     using Op = HeatOp<P, T, MODE_APPLY>;
     const Grid g = field_grid(c, HT_TEMP);
     const bool f64 = sizeof(T) == 8;
@@ -1882,25 +2075,21 @@ int fused_bicgstab_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* rh, T* p, T
     op.g_nc = g.nc;
     T* E = elem_buffer<T>(c);
     const T* wd = well_dense<T>(c);
-    dim3 ca, cb, na, nb;
-    int za, zb, ka, kb;
-    cell_pass_dims(c, g, resident_per_sm<fbi_cell_a_kernel<P, T, Op>>(), &ca, &za);
-    cell_pass_dims(c, g, resident_per_sm<fbi_cell_b_kernel<P, T, Op>>(), &cb, &zb);
+    dim3 na, nb;
+    int ka, kb;
     layer_node_dims(c, g, resident_per_sm<fbi_node_a_kernel<P, T>>(), &na, &ka);
     layer_node_dims(c, g, resident_per_sm<fbi_node_b_kernel<P, T>>(), &nb, &kb);
     const int G = vec_grid(c);
     if ((int)(na.x * na.y) > c->part_stride || (int)(nb.x * nb.y) > c->part_stride || G > c->part_stride)
         return fail(c, HT_EINVAL, "too many partial sums");
     const int S = c->part_stride;
-    HT_TRY(prof_begin(c, HT_PROF_BICGSTAB_ITER));
-    fbi_cell_a_kernel<P, T, Op><<<ca, dim3(32, 4), 0, c->stream>>>(g, op, r, p, v, Dinv, E, za, sc); ++c->n_launch;
+    HT_TRY((launch_heat_planes<P, T>(c, g, op, BiDirP<T>{r, p, v, Dinv, T(0), T(0)}, E, sc)));
     fbi_node_a_kernel<P, T><<<na, 128, 0, c->stream>>>(g, E, r, p, v, Dinv, rh, wd, dt, ka, sc, c->part); ++c->n_launch;
-    fbi_cell_b_kernel<P, T, Op><<<cb, dim3(32, 4), 0, c->stream>>>(g, op, r, v, Dinv, E, zb, sc); ++c->n_launch;
+    HT_TRY((launch_heat_planes<P, T>(c, g, op, BiDirS<T>{r, v, Dinv, T(0)}, E, sc)));
     fbi_node_b_kernel<P, T><<<nb, 128, 0, c->stream>>>(g, E, r, v, t, Dinv, wd, dt, kb, sc, c->part, S); ++c->n_launch;
-    fbi_update_kernel<T><<<G, 256, 0, c->stream>>>(c->grid.nn, x, r, p, v, t, Dinv, rh, sc, c->part, S, tol2,
-                                                   max_iter); ++c->n_launch;
+    fbi_update_kernel<T><<<G, 256, 0, c->stream>>>(c->grid.nn, x, r, p, v, t, Dinv, rh, sc, c->part, S);
+    ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
-    HT_TRY(prof_end(c));
     return HT_OK;
 }
 
@@ -1933,24 +2122,24 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
 
 // one fused CG iteration of the head system (see fcg_cell_kernel)
 int fused_cg_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* Dinv, double* p, Scal* sc,
-                         int first, double tol2, int max_iter) {
-    return c->grid.P == 1 ? fused_cg_iteration_P<1, double>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter)
-                          : fused_cg_iteration_P<2, double>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter);
+                         int first) {
+    return c->grid.P == 1 ? fused_cg_iteration_P<1, double>(c, dt, x, r, Dinv, p, sc, first)
+                          : fused_cg_iteration_P<2, double>(c, dt, x, r, Dinv, p, sc, first);
 }
 int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* Dinv, float* p, Scal* sc,
-                         int first, double tol2, int max_iter) {
-    return c->grid.P == 1 ? fused_cg_iteration_P<1, float>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter)
-                          : fused_cg_iteration_P<2, float>(c, dt, x, r, Dinv, p, sc, first, tol2, max_iter);
+                         int first) {
+    return c->grid.P == 1 ? fused_cg_iteration_P<1, float>(c, dt, x, r, Dinv, p, sc, first)
+                          : fused_cg_iteration_P<2, float>(c, dt, x, r, Dinv, p, sc, first);
 }
 int fused_bicgstab_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* rh, double* p, double* v,
-                               double* t, const double* Dinv, Scal* sc, double tol2, int max_iter) {
-    return c->grid.P == 1 ? fused_bicgstab_iteration_P<1, double>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter)
-                          : fused_bicgstab_iteration_P<2, double>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter);
+                               double* t, const double* Dinv, Scal* sc) {
+    return c->grid.P == 1 ? fused_bicgstab_iteration_P<1, double>(c, dt, x, r, rh, p, v, t, Dinv, sc)
+                          : fused_bicgstab_iteration_P<2, double>(c, dt, x, r, rh, p, v, t, Dinv, sc);
 }
 int fused_bicgstab_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* rh, float* p, float* v,
-                               float* t, const float* Dinv, Scal* sc, double tol2, int max_iter) {
-    return c->grid.P == 1 ? fused_bicgstab_iteration_P<1, float>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter)
-                          : fused_bicgstab_iteration_P<2, float>(c, dt, x, r, rh, p, v, t, Dinv, sc, tol2, max_iter);
+                               float* t, const float* Dinv, Scal* sc) {
+    return c->grid.P == 1 ? fused_bicgstab_iteration_P<1, float>(c, dt, x, r, rh, p, v, t, Dinv, sc)
+                          : fused_bicgstab_iteration_P<2, float>(c, dt, x, r, rh, p, v, t, Dinv, sc);
 }
 bool fused_cg_available(const ht_ctx* c, int fp32) {
     return fp32 ? use_two_pass<float>(c) : use_two_pass<double>(c);
@@ -2076,7 +2265,11 @@ static int resid_df_P(ht_ctx* c, const Grid& g, const Op& op, const double* x, c
     cell_pass_dims(c, g, resident_per_sm<df_cell_kernel<P, Op>>(), &cg, &zl);
     layer_node_dims(c, g, resident_per_sm<df_resid_node_kernel<P>>(), &ng, &kl);
     if ((int)(ng.x * ng.y) > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
-    df_cell_kernel<P, Op><<<cg, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zl); ++c->n_launch;
+    if constexpr (Op::kPlanes) {
+        HT_TRY((launch_heat_planes<P, df64>(c, g, op, LoadSplit{x}, E, nullptr)));
+    } else {
+        df_cell_kernel<P, Op><<<cg, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zl); ++c->n_launch;
+    }
     df_resid_node_kernel<P><<<ng, 128, 0, c->stream>>>(g, E, x, b, wd, dt, r32, part, c->part_stride, kl);
     ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
