@@ -699,7 +699,7 @@ int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream) 
     for (double** pp : v64)
         if (rc == HT_OK) rc = dalloc(c, pp, N);
     float** v32[] = {&c->x32, &c->r32, &c->z32, &c->p32, &c->q32, &c->D32, &c->rh32, &c->v32,
-                     &c->s32, &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32};
+                     &c->s32, &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32, &c->h32};
     for (float** pp : v32)
         if (rc == HT_OK) rc = dalloc(c, pp, N);
     if (rc == HT_OK) rc = dalloc(c, &c->qs64, 3 * NQ * NC);
@@ -749,7 +749,7 @@ void ht_destroy(ht_ctx* c) {
     for (double** pp : v64) dfree(*pp);
     float** v32[] = {&c->x32, &c->r32, &c->z32, &c->p32, &c->q32, &c->D32, &c->rh32, &c->v32, &c->s32,
                      &c->t32, &c->ph32, &c->sh32, &c->zz32, &c->d32, &c->K32, &c->lam32, &c->cT32, &c->qs32,
-                     &c->E32, &c->wdn32};
+                     &c->E32, &c->wdn32, &c->h32};
     for (float** pp : v32) dfree(*pp);
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
     dfree(c->scal);

@@ -105,6 +105,7 @@ struct ht_ctx {
     // coefficients
     double* K64 = nullptr;
     float* K32 = nullptr;
+    float* h32 = nullptr;                   // FP32 copy of h^{n+1} for the FP32 heat operator
     double* lam64 = nullptr;    // optional per-cell
     double* cT64 = nullptr;
     float* lam32 = nullptr;

@@ -690,6 +690,10 @@ __global__ void resid_kernel(long long n, const double* __restrict__ b, const do
     write3<double>(part, stride, rr, bb, 0.0);
 }
 
+__global__ void to_f32_kernel(long long n, const double* __restrict__ a, float* __restrict__ b) {
+    GRID_LOOP(i, n) b[i] = (float)a[i];
+}
+
 __global__ void add_f32_kernel(long long n, double* __restrict__ x, const float* __restrict__ d) {
     GRID_LOOP(i, n) x[i] += (double)d[i];
 }
@@ -1220,6 +1224,11 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
     const long long n = c->grid.nn;
     const int G = vec_grid(c);
     const int S = c->part_stride;
+    if (field == HT_TEMP) {
+        // the FP32 heat operator forms its velocity from an FP32 copy of h^{n+1}
+        to_f32_kernel<<<G, kVecThreads, 0, c->stream>>>(n, c->h, c->h32); ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+    }
     const double inner_head = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-4;
     const double inner_tol = field == HT_TEMP && c->opts.inner_tol_heat > 0 ? c->opts.inner_tol_heat : inner_head;
     const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 30;

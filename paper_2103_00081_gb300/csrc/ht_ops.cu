@@ -313,6 +313,7 @@ struct HeatOp {
     const S* qs;       // [3*NQ][nc], in storage type S (converted to T on load)
     const S* cTc;      // optional per-cell
     const S* lamc;
+    const S* Kq;       // per-cell K_c for a velocity formed from the head in plane()
     T cT_u, lam_u, dt, cw;
     Elem<T> e;
 
@@ -431,12 +432,18 @@ struct HeatOp {
     // z-sweep is restricted to plane qz and the transposed z-sweep scatters to
     // every layer; the planes' contributions add up to compute()'s result
     // (one thread per plane, u and out in shared memory).
-    __device__ __forceinline__ void plane(const T* u, const long long c, const long long nc, const int qz,
-                                          T* out) const {
+    // With HQ the Darcy velocity q = -K_c grad h at the plane's Gauss points
+    // is formed here from the head values hv of the cell (in shared memory)
+    // instead of being read from qs.
+    template <bool HQ = false>
+    __device__ __forceinline__ void plane(const T* u, const T* hv, const long long c, const long long nc,
+                                          const int qz, T* out) const {
         const T cT = cTc ? cvt<T>(ldro(cTc + c)) : cT_u;
         const T dtlam = dt * (lamc ? cvt<T>(ldro(lamc + c)) : lam_u);
         const T dtcw = dt * cw;
+        const T mK = HQ ? -cvt<T>(ldro(Kq + c)) : T(0);
         T zB[n * n], zD[n * n];
+        T hzB[HQ ? n * n : 1], hzD[HQ ? n * n : 1];
 #pragma unroll
         for (int ba = 0; ba < n * n; ++ba) {
             T sb = T(0), sd = T(0);
@@ -448,6 +455,17 @@ struct HeatOp {
             }
             zB[ba] = sb;
             zD[ba] = sd;
+            if (HQ) {
+                T hb = T(0), hd = T(0);
+#pragma unroll
+                for (int c2 = 0; c2 < n; ++c2) {
+                    const T hh = hv[ba + n * n * c2];
+                    hb = fma(e.B[qz][c2], hh, hb);
+                    hd = fma(e.D[qz][c2], hh, hd);
+                }
+                hzB[ba] = hb;
+                hzD[ba] = hd;
+            }
         }
         T s1[n * n], s2[n * n];
 #pragma unroll
@@ -455,6 +473,7 @@ struct HeatOp {
 #pragma unroll
         for (int qy = 0; qy < n; ++qy) {
             T yBB[n], yDB[n], yBD[n];
+            T hBB[HQ ? n : 1], hDB[HQ ? n : 1], hBD[HQ ? n : 1];
 #pragma unroll
             for (int a = 0; a < n; ++a) {
                 T v0 = T(0), v2 = T(0), v3 = T(0);
@@ -465,6 +484,16 @@ struct HeatOp {
                     v3 = fma(e.B[qy][b], zD[a + n * b], v3);
                 }
                 yBB[a] = v0; yDB[a] = v2; yBD[a] = v3;
+                if (HQ) {
+                    T w0 = T(0), w2 = T(0), w3 = T(0);
+#pragma unroll
+                    for (int b = 0; b < n; ++b) {
+                        w0 = fma(e.B[qy][b], hzB[a + n * b], w0);
+                        w2 = fma(e.D[qy][b], hzB[a + n * b], w2);
+                        w3 = fma(e.B[qy][b], hzD[a + n * b], w3);
+                    }
+                    hBB[a] = w0; hDB[a] = w2; hBD[a] = w3;
+                }
             }
             T t1[n], t2[n], t3[n];
 #pragma unroll
@@ -483,9 +512,23 @@ struct HeatOp {
                 gy *= e.invH[1];
                 gz *= e.invH[2];
                 const int qi = qx + n * (qy + n * qz);
-                const T q0 = cvt<T>(ldro(qs + (0 * NQ + qi) * nc + c));
-                const T q1 = cvt<T>(ldro(qs + (1 * NQ + qi) * nc + c));
-                const T q2 = cvt<T>(ldro(qs + (2 * NQ + qi) * nc + c));
+                T q0, q1, q2;
+                if (HQ) {
+                    T hx = T(0), hy = T(0), hz = T(0);
+#pragma unroll
+                    for (int a = 0; a < n; ++a) {
+                        hx = fma(e.D[qx][a], hBB[a], hx);
+                        hy = fma(e.B[qx][a], hDB[a], hy);
+                        hz = fma(e.B[qx][a], hBD[a], hz);
+                    }
+                    q0 = mK * (hx * e.invH[0]);
+                    q1 = mK * (hy * e.invH[1]);
+                    q2 = mK * (hz * e.invH[2]);
+                } else {
+                    q0 = cvt<T>(ldro(qs + (0 * NQ + qi) * nc + c));
+                    q1 = cvt<T>(ldro(qs + (1 * NQ + qi) * nc + c));
+                    q2 = cvt<T>(ldro(qs + (2 * NQ + qi) * nc + c));
+                }
                 const T W = e.W[qi];
                 const T v = W * fma(cT, val, dtcw * (q0 * gx + q1 * gy + q2 * gz));
                 const T f = W * dtlam;
@@ -1645,14 +1688,15 @@ struct LoadSplit {   // FP64 input split into float pairs
     __device__ __forceinline__ df64 operator()(int id) const { return df_from(ldro(x + id)); }
 };
 
-template <int P, typename T, class Op, class NV>
+template <int P, typename T, class Op, class NV, bool HQ>
 __global__ void __launch_bounds__(32 * (P + 1)) heat_plane_kernel(const Grid g, const Op op, NV nv,
-                                                                  T* __restrict__ E, const int zlen,
-                                                                  const Scal* s) {
+                                                                  const T* __restrict__ hq, T* __restrict__ E,
+                                                                  const int zlen, const Scal* s) {
     if (s && s->done) return;
     if (s) nv.init(s);
     constexpr int n = P + 1, NL = n * n * n;
     __shared__ T su[32][NL];
+    __shared__ T sh[HQ ? 32 : 1][NL];
     __shared__ T sp[n][32][NL];
     const int tx = threadIdx.x, qz = threadIdx.y;
     const int cx = blockIdx.x * 32 + tx, cy = blockIdx.y;
@@ -1670,13 +1714,15 @@ __global__ void __launch_bounds__(32 * (P + 1)) heat_plane_kernel(const Grid g, 
             for (int b = 0; b < n; ++b)
 #pragma unroll
                 for (int a = 0; a < n; ++a) {
-                    T u = nv(base + NX * b + NXY * qz + a);
+                    const int id = base + NX * b + NXY * qz + a;
+                    T u = nv(id);
                     if (chk && on_dir(g, P * cx + a, P * cy + b, P * cz + qz)) u = T(0);
                     su[tx][a + n * (b + n * qz)] = u;
+                    if constexpr (HQ) sh[tx][a + n * (b + n * qz)] = ldg_any(hq + id);
                 }
         }
         __syncthreads();
-        if (valid) op.plane(&su[tx][0], c, nc, qz, &sp[qz][tx][0]);
+        if (valid) op.template plane<HQ>(&su[tx][0], HQ ? &sh[HQ ? tx : 0][0] : nullptr, c, nc, qz, &sp[qz][tx][0]);
         __syncthreads();
         if (valid) {
 #pragma unroll
@@ -1967,12 +2013,20 @@ void plane_pass_dims(const ht_ctx* c, const Grid& g, int cta_per_sm, dim3* grid,
 
 // launch of the element pass of a heat operator with input functor nv
 template <int P, typename T, class Op, class NV>
-int launch_heat_planes(ht_ctx* c, const Grid& g, const Op& op, const NV& nv, T* E, const Scal* sc) {
+int launch_heat_planes(ht_ctx* c, const Grid& g, const Op& op, const NV& nv, T* E, const Scal* sc,
+                       const T* hq = nullptr) {
     constexpr int threads = 32 * (P + 1);
     dim3 grid;
     int zlen;
-    plane_pass_dims(c, g, resident_per_sm_threads<heat_plane_kernel<P, T, Op, NV>>(threads), &grid, &zlen);
-    heat_plane_kernel<P, T, Op, NV><<<grid, dim3(32, P + 1), 0, c->stream>>>(g, op, nv, E, zlen, sc);
+    if (hq) {
+        plane_pass_dims(c, g, resident_per_sm_threads<heat_plane_kernel<P, T, Op, NV, true>>(threads), &grid, &zlen);
+        heat_plane_kernel<P, T, Op, NV, true><<<grid, dim3(32, P + 1), 0, c->stream>>>(g, op, nv, hq, E, zlen, sc);
+        ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+        return HT_OK;
+    }
+    plane_pass_dims(c, g, resident_per_sm_threads<heat_plane_kernel<P, T, Op, NV, false>>(threads), &grid, &zlen);
+    heat_plane_kernel<P, T, Op, NV, false><<<grid, dim3(32, P + 1), 0, c->stream>>>(g, op, nv, hq, E, zlen, sc);
     ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
@@ -2000,7 +2054,11 @@ int launch_apply_two_pass(ht_ctx* c, const Grid& g, const Op& op, const T* x, T*
     const int nb = (int)(ngrid.x * ngrid.y);
     if (dot_part && nb > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
     if constexpr (Op::kPlanes) {
-        HT_TRY((launch_heat_planes<P, T>(c, g, op, LoadNodes<T>{x}, E, sc)));
+        // FP32: the velocity is formed from the FP32 head, as in the fused BiCGStab
+        Op opq = op;
+        const T* hq = sizeof(T) == 4 ? (const T*)c->h32 : nullptr;
+        if (hq) opq.Kq = (const T*)c->K32;
+        HT_TRY((launch_heat_planes<P, T>(c, g, opq, LoadNodes<T>{x}, E, sc, hq)));
     } else {
         cell_pass_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zlen, sc); ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
@@ -2083,9 +2141,12 @@ int fused_bicgstab_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* rh, T* p, T
     if ((int)(na.x * na.y) > c->part_stride || (int)(nb.x * nb.y) > c->part_stride || G > c->part_stride)
         return fail(c, HT_EINVAL, "too many partial sums");
     const int S = c->part_stride;
-    HT_TRY((launch_heat_planes<P, T>(c, g, op, BiDirP<T>{r, p, v, Dinv, T(0), T(0)}, E, sc)));
+    // FP32: the velocity is formed from the FP32 head in the element pass
+    const T* hq = f64 ? nullptr : (const T*)c->h32;
+    if (hq) op.Kq = (const T*)c->K32;
+    HT_TRY((launch_heat_planes<P, T>(c, g, op, BiDirP<T>{r, p, v, Dinv, T(0), T(0)}, E, sc, hq)));
     fbi_node_a_kernel<P, T><<<na, 128, 0, c->stream>>>(g, E, r, p, v, Dinv, rh, wd, dt, ka, sc, c->part); ++c->n_launch;
-    HT_TRY((launch_heat_planes<P, T>(c, g, op, BiDirS<T>{r, v, Dinv, T(0)}, E, sc)));
+    HT_TRY((launch_heat_planes<P, T>(c, g, op, BiDirS<T>{r, v, Dinv, T(0)}, E, sc, hq)));
     fbi_node_b_kernel<P, T><<<nb, 128, 0, c->stream>>>(g, E, r, v, t, Dinv, wd, dt, kb, sc, c->part, S); ++c->n_launch;
     fbi_update_kernel<T><<<G, 256, 0, c->stream>>>(c->grid.nn, x, r, p, v, t, Dinv, rh, sc, c->part, S);
     ++c->n_launch;
