@@ -37,6 +37,40 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def _fwd_tol(o, dt, res_tol, floor=1e-9, max_nodes=1000):
+    """Forward-error tolerances (head, heat) for solutions whose relative
+    residual is at most res_tol, after o.step(dt).  The forward error is
+    bounded by amp * res_tol with amp = ||A0^-1|| ||A0 x|| / ||x||; on the
+    regular parity meshes amp is small and the floor 1e-9 applies, but on a
+    mesh of one or two cells where most rows are Dirichlet identity rows amp
+    reaches 1e9, so small systems take the bound computed from the oracle's
+    own matrices (dense, hence the size limit)."""
+    out = []
+    for A, x in ((fem.constrain(o.head_matrix(dt), o.dmask[fem.HEAD]), o.h),
+                 (fem.constrain(o.heat_matrix(dt, o.h), o.dmask[fem.TEMP]), o.T)):
+        if A.shape[0] > max_nodes:
+            out.append(floor)
+            continue
+        Ad = A.toarray()
+        amp = np.linalg.norm(np.linalg.inv(Ad), 2) * np.linalg.norm(Ad @ x) / np.linalg.norm(x)
+        out.append(max(floor, 2.0 * amp * res_tol))
+    return out
+
+
+def _backward(o, dt, t1, h_prev, T_prev, h1, T1):
+    """Relative residuals (head, heat) of the GPU solutions h1, T1 in the
+    oracle's systems of the step, built from the GPU's own previous state
+    (h_prev, T_prev) and, for heat, the GPU's h1."""
+    h_now, T_now = o.h, o.T
+    o.h, o.T = h_prev, T_prev
+    bh = o.head_rhs(dt, t1)
+    bT = o.heat_rhs(dt, t1, h1)
+    o.h, o.T = h_now, T_now
+    rh = np.linalg.norm(bh - o.apply_head(h1, dt)) / np.linalg.norm(bh)
+    rT = np.linalg.norm(bT - o.apply_heat(T1, h1, dt)) / np.linalg.norm(bT)
+    return rh, rT
+
+
 def _close(got, ref, tol=1e-12):
     assert _rel(got, ref) <= tol, _rel(got, ref)
     assert np.max(np.abs(got - ref)) <= tol * max(np.max(np.abs(ref)), 1e-300)
@@ -182,11 +216,16 @@ def test_fused_two_pass_cg_steps_match_oracle(Sim, case, mixed):
     sim = Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TWO_PASS, max_iter=50000, **prec)
     ref = None if mixed else Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TILED, max_iter=50000, **prec)
     for _ in range(3):
+        h_prev, T_prev, t1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP), o.t + sc.dt
         st = sim.step(sc.dt)
         o.step(sc.dt)
+        h1, T1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP)
+        tol_h, tol_T = _fwd_tol(o, sc.dt, prec["tol"])
         assert st["res_head"] <= prec["tol"] * 1.001
-        assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
-        assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+        assert _rel(h1, o.h) <= tol_h
+        assert _rel(T1, o.T) <= tol_T
+        rh, rT = _backward(o, sc.dt, t1, h_prev, T_prev, h1, T1)
+        assert rh <= 10 * prec["tol"] and rT <= 10 * prec["tol"], (rh, rT)
         if ref is not None:
             st_ref = ref.step(sc.dt)
             assert abs(st["iters_head"] - st_ref["iters_head"]) <= max(2, 0.02 * st_ref["iters_head"])
@@ -207,11 +246,16 @@ def test_fused_two_pass_bicgstab_steps_match_oracle(Sim, case, mixed):
     sim = Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TWO_PASS, **common)
     ref = None if mixed else Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TILED, **common)
     for _ in range(2):
+        h_prev, T_prev, t1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP), o.t + sc.dt
         st = sim.step(sc.dt)
         o.step(sc.dt)
+        h1, T1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP)
+        tol_h, tol_T = _fwd_tol(o, sc.dt, prec["tol"])
         assert st["res_heat"] <= prec["tol"] * 1.001
-        assert _rel(sim.get_field(S.HEAD), o.h) <= 1e-9
-        assert _rel(sim.get_field(S.TEMP), o.T) <= 1e-9
+        assert _rel(h1, o.h) <= tol_h
+        assert _rel(T1, o.T) <= tol_T
+        rh, rT = _backward(o, sc.dt, t1, h_prev, T_prev, h1, T1)
+        assert rh <= 10 * prec["tol"] and rT <= 10 * prec["tol"], (rh, rT)
         if ref is not None:
             st_ref = ref.step(sc.dt)
             assert abs(st["iters_heat"] - st_ref["iters_heat"]) <= max(2, 0.1 * st_ref["iters_heat"])
