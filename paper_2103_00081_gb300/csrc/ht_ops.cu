@@ -118,6 +118,13 @@ __device__ __forceinline__ T cvt(S v) { return Cvt<T, S>::f(v); }
 
 // Sum over the CTA (1D, 2D or 3D blocks whose size is a multiple of 32);
 // the result is valid in the thread with linear index 0.
+// Block sum of per-thread partials of a T-typed kernel: the warp stage runs
+// in T (for FP32 kernels this keeps the shuffles and adds off the FP64 pipe,
+// which GB300 runs at 1/64 of the FP32 rate), the per-warp results are
+// combined in FP64 by block_sum.  Valid in thread 0; fixed order.
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v);
+
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double ws[32];
 #pragma unroll
@@ -134,6 +141,25 @@ __device__ __forceinline__ double block_sum(double v) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     }
     return v;
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v) {
+    if constexpr (sizeof(T) == 8) return block_sum((double)v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ double wsum[32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, wid = tid >> 5;
+    __syncthreads();
+    if (lane == 0) wsum[wid] = (double)v;
+    __syncthreads();
+    double d = 0.0;
+    if (tid == 0) {
+        const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+        for (int w = 0; w < nw; ++w) d += wsum[w];
+    }
+    return d;
 }
 
 // gather the element vector of cell (cx,cy,cz) from a nodal vector; nodes on
@@ -751,7 +777,7 @@ __global__ void __launch_bounds__(CXM* CYM) tile_kernel(const Grid g, const Op o
         __syncthreads();
     }
     if (dot_part) {
-        const double tot = block_sum((double)dot);
+        const double tot = block_sum_t(dot);
         if (threadIdx.x == 0)
             dot_part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
     }
@@ -942,7 +968,7 @@ __global__ void __launch_bounds__(CXM* CYM) apply_kernel(const Grid g, const Op 
         __syncthreads();
     }
     if (dot_part) {
-        const double tot = block_sum((double)dot);
+        const double tot = block_sum_t(dot);
         if (threadIdx.x == 0)
             dot_part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
     }
@@ -1103,7 +1129,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) node_pass_kernel
         }
     }
     if (dot_part) {
-        const double tot = block_sum((double)dot);
+        const double tot = block_sum_t(dot);
         if (threadIdx.x == 0) dot_part[blockIdx.x + gridDim.x * blockIdx.y] = tot;
     }
 }
@@ -1221,7 +1247,7 @@ __global__ void __launch_bounds__(128) fcg_cell_kernel(const Grid g, const Op op
     if (s->done) return;
     const CgDir<T> nv{r, Dinv, p, first ? T(0) : (T)s->beta};
     const T pap = march_cells<P, T, Op, CgDir<T>, true>(g, op, nv, E, zlen);
-    const double v = block_sum((double)pap);
+    const double v = block_sum_t(pap);
     const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     if (!publish_and_ticket(s, part, &v, 1, 0, nblk)) return;
     const double tot = last_cta_sum(part, (int)nblk);
@@ -1280,8 +1306,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fcg_node_kernel(
         }
     }
     double v[2];
-    v[0] = block_sum((double)rzp);
-    v[1] = block_sum((double)rrp);
+    v[0] = block_sum_t(rzp);
+    v[1] = block_sum_t(rrp);
     const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     if (!publish_and_ticket(s, part + stride, v, 2, stride, nblk)) return;
     const double rz = last_cta_sum(part + stride, (int)nblk);
@@ -1393,7 +1419,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fbi_node_a_kerne
             finish(k, id, e0);
         }
     }
-    const double tot = block_sum((double)rv);
+    const double tot = block_sum_t(rv);
     const unsigned nblk = gridDim.x * gridDim.y;
     if (!publish_and_ticket(s, part, &tot, 1, 0, nblk)) return;
     const double a = last_cta_sum(part, (int)nblk);
@@ -1446,8 +1472,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fbi_node_b_kerne
         }
     }
     double vals[2];
-    vals[0] = block_sum((double)ts);
-    vals[1] = block_sum((double)tt);
+    vals[0] = block_sum_t(ts);
+    vals[1] = block_sum_t(tt);
     const unsigned nblk = gridDim.x * gridDim.y;
     if (!publish_and_ticket(s, part + stride, vals, 2, stride, nblk)) return;
     const double a = last_cta_sum(part + stride, (int)nblk);
@@ -1480,8 +1506,8 @@ __global__ void __launch_bounds__(256) fbi_update_kernel(long long n, T* __restr
         rr = fma(ri, ri, rr);
     }
     double vals[2];
-    vals[0] = block_sum((double)rhr);
-    vals[1] = block_sum((double)rr);
+    vals[0] = block_sum_t(rhr);
+    vals[1] = block_sum_t(rr);
     const unsigned nblk = gridDim.x;
     if (!publish_and_ticket(s, part + 3 * (size_t)stride, vals, 2, stride, nblk)) return;
     const double a0 = last_cta_sum(part + 3 * (size_t)stride, (int)nblk);
