@@ -1328,9 +1328,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) fcg_node_kernel(
 // Fused Jacobi-BiCGStab iteration over the two-pass apply (heat operator),
 // five launches per iteration instead of thirteen:
 //   cell A: ph = Dinv (r + beta (p - omega v)) at the cell's nodes, E = A_e ph
+//           (heat_plane_kernel with the BiDirP input)
 //   node A: p = r + beta (p - omega v) (the same formula), v = A ph;
 //           last CTA: alpha = rho / rh.v
-//   cell B: sh = Dinv (r - alpha v), E = A_e sh
+//   cell B: sh = Dinv (r - alpha v), E = A_e sh (heat_plane_kernel, BiDirS)
 //   node B: t = A sh; last CTA: omega = t.s / t.t
 //   update: x += alpha Dinv p + omega Dinv s, r = s - omega t with
 //           s = r - alpha v; last CTA: convergence, beta, rho
@@ -1360,25 +1361,6 @@ struct BiDirS {   // sh = Dinv (r - alpha v)
     __device__ __forceinline__ void init(const Scal* s) { alpha = (T)s->alpha; }
     __device__ __forceinline__ T operator()(int id) const { return ldro(Dinv + id) * fma(-alpha, ldro(v + id), ldro(r + id)); }
 };
-
-template <int P, typename T, class Op>
-__global__ void __launch_bounds__(128) fbi_cell_a_kernel(const Grid g, const Op op, const T* __restrict__ r,
-                                                         const T* __restrict__ p, const T* __restrict__ v,
-                                                         const T* __restrict__ Dinv, T* __restrict__ E,
-                                                         const int zlen, const Scal* s) {
-    if (s->done) return;
-    const BiDirP<T> nv{r, p, v, Dinv, (T)s->beta, (T)s->omega};
-    march_cells<P, T, Op, BiDirP<T>, false>(g, op, nv, E, zlen);
-}
-
-template <int P, typename T, class Op>
-__global__ void __launch_bounds__(128) fbi_cell_b_kernel(const Grid g, const Op op, const T* __restrict__ r,
-                                                         const T* __restrict__ v, const T* __restrict__ Dinv,
-                                                         T* __restrict__ E, const int zlen, const Scal* s) {
-    if (s->done) return;
-    const BiDirS<T> nv{r, v, Dinv, (T)s->alpha};
-    march_cells<P, T, Op, BiDirS<T>, false>(g, op, nv, E, zlen);
-}
 
 // node A: p, v = A ph, partials of rh.v
 template <int P, typename T>
@@ -2073,9 +2055,8 @@ template <int P, typename T, class Op>
 int launch_apply_two_pass(ht_ctx* c, const Grid& g, const Op& op, const T* x, T* y, double* dot_part,
                           int* n_part, const Scal* sc) {
     T* E = elem_buffer<T>(c);
-    dim3 cgrid, ngrid;
-    int zlen, klen;
-    cell_pass_dims(c, g, resident_per_sm<cell_pass_kernel<P, T, Op>>(), &cgrid, &zlen);
+    dim3 ngrid;
+    int klen;
     layer_node_dims(c, g, resident_per_sm<node_pass_kernel<P, T>>(), &ngrid, &klen);
     const int nb = (int)(ngrid.x * ngrid.y);
     if (dot_part && nb > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
@@ -2086,6 +2067,9 @@ int launch_apply_two_pass(ht_ctx* c, const Grid& g, const Op& op, const T* x, T*
         if (hq) opq.Kq = (const T*)c->K32;
         HT_TRY((launch_heat_planes<P, T>(c, g, opq, LoadNodes<T>{x}, E, sc, hq)));
     } else {
+        dim3 cgrid;
+        int zlen;
+        cell_pass_dims(c, g, resident_per_sm<cell_pass_kernel<P, T, Op>>(), &cgrid, &zlen);
         cell_pass_kernel<P, T, Op><<<cgrid, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zlen, sc); ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
     }
@@ -2347,14 +2331,16 @@ template <int P, class Op>
 static int resid_df_P(ht_ctx* c, const Grid& g, const Op& op, const double* x, const double* b, float* r32,
                       double* part, int* n_part, double dt, const double* wd) {
     df64* E = reinterpret_cast<df64*>(elem_buffer<double>(c));
-    dim3 cg, ng;
-    int zl, kl;
-    cell_pass_dims(c, g, resident_per_sm<df_cell_kernel<P, Op>>(), &cg, &zl);
+    dim3 ng;
+    int kl;
     layer_node_dims(c, g, resident_per_sm<df_resid_node_kernel<P>>(), &ng, &kl);
     if ((int)(ng.x * ng.y) > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
     if constexpr (Op::kPlanes) {
         HT_TRY((launch_heat_planes<P, df64>(c, g, op, LoadSplit{x}, E, nullptr)));
     } else {
+        dim3 cg;
+        int zl;
+        cell_pass_dims(c, g, resident_per_sm<df_cell_kernel<P, Op>>(), &cg, &zl);
         df_cell_kernel<P, Op><<<cg, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zl); ++c->n_launch;
     }
     df_resid_node_kernel<P><<<ng, 128, 0, c->stream>>>(g, E, x, b, wd, dt, r32, part, c->part_stride, kl);
