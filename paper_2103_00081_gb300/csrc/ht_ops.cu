@@ -496,7 +496,7 @@ struct HeatOp {
         T s1[n * n], s2[n * n];
 #pragma unroll
         for (int ba = 0; ba < n * n; ++ba) { s1[ba] = T(0); s2[ba] = T(0); }
-#pragma unroll
+#pragma unroll 1   // rolled: fewer live registers per plane thread (measured faster)
         for (int qy = 0; qy < n; ++qy) {
             T yBB[n], yDB[n], yBD[n];
             T hBB[HQ ? n : 1], hDB[HQ ? n : 1], hBD[HQ ? n : 1];
