@@ -2026,12 +2026,16 @@ int launch_heat_planes(ht_ctx* c, const Grid& g, const Op& op, const NV& nv, T* 
     constexpr int threads = 32 * (P + 1);
     dim3 grid;
     int zlen;
-    if (hq) {
-        plane_pass_dims(c, g, resident_per_sm_threads<heat_plane_kernel<P, T, Op, NV, true>>(threads), &grid, &zlen);
-        heat_plane_kernel<P, T, Op, NV, true><<<grid, dim3(32, P + 1), 0, c->stream>>>(g, op, nv, hq, E, zlen, sc);
-        ++c->n_launch;
-        HT_CUDA(c, cudaGetLastError());
-        return HT_OK;
+    if constexpr (sizeof(T) == 4) {   // the head-formed velocity is an FP32-operator feature
+        if (hq) {
+            plane_pass_dims(c, g, resident_per_sm_threads<heat_plane_kernel<P, T, Op, NV, true>>(threads), &grid,
+                            &zlen);
+            heat_plane_kernel<P, T, Op, NV, true><<<grid, dim3(32, P + 1), 0, c->stream>>>(g, op, nv, hq, E, zlen,
+                                                                                          sc);
+            ++c->n_launch;
+            HT_CUDA(c, cudaGetLastError());
+            return HT_OK;
+        }
     }
     plane_pass_dims(c, g, resident_per_sm_threads<heat_plane_kernel<P, T, Op, NV, false>>(threads), &grid, &zlen);
     heat_plane_kernel<P, T, Op, NV, false><<<grid, dim3(32, P + 1), 0, c->stream>>>(g, op, nv, hq, E, zlen, sc);
