@@ -312,6 +312,26 @@ struct HeadOp {
         fdm(res, dt * cvt<T>(ldro(K + c)));
     }
 
+    // the same in place (u becomes A_e u), adding u^T A_e u to dot: in the
+    // eigenbasis v = G^3 u the element matrix is diagonal, so the energy is
+    // sum_l (alpha + beta LS_l) v_l^2 and u need not be kept
+    __device__ __forceinline__ void compute_dot_inplace(T (&u)[NL], long long c, T& dot) const {
+        const T beta = dt * cvt<T>(ldro(K + c));
+        sweep<n, 0, false>(u, e.G[0]);
+        sweep<n, 1, false>(u, e.G[1]);
+        sweep<n, 2, false>(u, e.G[2]);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const T sl = fma(beta, e.LS[l], alpha);
+            const T v = u[l] * sl;
+            dot = fma(v, u[l], dot);
+            u[l] = v;
+        }
+        sweep<n, 2, true>(u, e.G[2]);
+        sweep<n, 1, true>(u, e.G[1]);
+        sweep<n, 0, true>(u, e.G[0]);
+    }
+
     __device__ __forceinline__ void emit(const Grid& g, int i, int j, int k, T val, T& dot) const {
         const long long id = nidx(g, i, j, k);
         const bool d = on_dir(g, i, j, k);
@@ -1193,12 +1213,15 @@ __device__ __forceinline__ T march_cells(const Grid& g, const Op& op, const NV& 
     const bool edge_xy = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1);
     int base = P * cx + NX * P * cy + NXY * P * cz0;
     int c = cx + g.ncx * cy + layer * cz0;
-    T u[NL];
+    T carry[NF];
 #pragma unroll
     for (int b = 0; b < n; ++b)
 #pragma unroll
-        for (int a = 0; a < n; ++a) u[a + n * b] = nv(base + NX * b + a);
+        for (int a = 0; a < n; ++a) carry[a + n * b] = nv(base + NX * b + a);
     for (int cz = cz0; cz < cz1; ++cz, base += NXY * P, c += layer) {
+        T u[NL];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u[f] = carry[f];
 #pragma unroll
         for (int c2 = 1; c2 < n; ++c2)
 #pragma unroll
@@ -1214,17 +1237,20 @@ __device__ __forceinline__ T march_cells(const Grid& g, const Op& op, const NV& 
                     for (int a = 0; a < n; ++a)
                         if (on_dir(g, P * cx + a, P * cy + b, P * cz + c2)) u[a + n * (b + n * c2)] = T(0);
         }
-        T res[NL];
-        op.compute(u, c, res);
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            E[l * nc + c] = res[l];
-            if (DOT) dot = fma(u[l], res[l], dot);
-        }
         // the top face becomes the next bottom face; a node zeroed as a
         // Dirichlet node is zero in the next cell too
 #pragma unroll
-        for (int f = 0; f < NF; ++f) u[f] = u[f + NF * P];
+        for (int f = 0; f < NF; ++f) carry[f] = u[f + NF * P];
+        if (DOT) {
+            op.compute_dot_inplace(u, c, dot);
+        } else {
+            T res[NL];
+            op.compute(u, c, res);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) u[l] = res[l];
+        }
+#pragma unroll
+        for (int l = 0; l < NL; ++l) E[l * nc + c] = u[l];
     }
     return dot;
 }
