@@ -423,18 +423,28 @@ def run_batch(args):
     opts = dict(tol=1e-10, precision=L.HT_MIXED, inner_tol=1e-4, krylov=L.HT_KRYLOV_BICGSTAB)
     sims = [hydro.Simulator.from_scenario(sc, **opts) for sc in scs]
     dt = scs[0].dt
-    batch = hydro.Batch(sims)
-    for _ in range(args.warmup):
-        batch.step(dt)
-    for sm in sims:
-        sm.profile(True)
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for _ in range(args.steps):
-        stats = batch.step(dt)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - w0
-    launches = sum(sm.profile_read()["launches"] for sm in sims)
+
+    def timed_batch(mode):
+        batch = hydro.Batch(sims, mode=mode)
+        for _ in range(args.warmup):
+            batch.step(dt)
+        for sm in sims:
+            sm.profile(True)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            stats = batch.step(dt)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - w0
+        launches = sum(sm.profile_read()["launches"] for sm in sims)
+        for sm in sims:
+            sm.profile(False)
+        batch.close()
+        return t, stats, launches
+
+    # concurrent per-problem steps (the default), then the shared-launch head CG
+    t_batch, stats, launches = timed_batch(L.HT_BATCH_CONCURRENT)
+    t_shared, _, _ = timed_batch(L.HT_BATCH_SHARED_LAUNCHES)
     # the same problems stepped one by one through ht_step
     w0 = time.perf_counter()
     for _ in range(args.steps):
@@ -442,7 +452,6 @@ def run_batch(args):
             sm.step(dt)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - w0
-    batch.close()
     years = args.steps * dt / YEAR * len(scs)
     nodes = sum(sc.n_nodes for sc in scs)
     print(json.dumps({
@@ -453,6 +462,7 @@ def run_batch(args):
         "config": {"workload": f"{len(scs)} Q1 problems, {nodes} nodes in total, dt=1 d, tol 1e-10",
                    "sizes": sorted(set(f"{sc.nx}x{sc.ny}x{sc.nz}" for sc in scs))[:8]},
         "sequential": {"value": years / (t_seq / 3600), "ms_per_step": t_seq / args.steps * 1e3},
+        "shared_launches": {"value": years / (t_shared / 3600), "ms_per_step": t_shared / args.steps * 1e3},
         "speedup_vs_sequential": t_seq / t_batch,
         "iters_head": [st["iters_head"] for st in stats][:8], "gpu_launches": launches,
     }))

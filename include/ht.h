@@ -226,6 +226,16 @@ int ht_batch_create(ht_batch** out, int n, ht_ctx* const* problems);
 void ht_batch_destroy(ht_batch* batch);
 int ht_batch_step(ht_batch* batch, double dt, ht_step_stats* stats);
 const char* ht_batch_last_error(const ht_batch* batch);
+/* Execution of ht_batch_step.  HT_BATCH_CONCURRENT (the default) steps the
+ * problems concurrently: host worker threads run each problem's own step
+ * (fused Krylov kernels, CUDA-graph replays) on the problem's own stream, so
+ * the small problems of a batch overlap on the GPU; problems that share a
+ * stream are stepped one after another.  HT_BATCH_SHARED_LAUNCHES runs the
+ * inner head CG of all problems in shared launches as described above.  Both
+ * give each problem the result of its own ht_step up to rounding order. */
+#define HT_BATCH_CONCURRENT 0
+#define HT_BATCH_SHARED_LAUNCHES 1
+int ht_batch_set_mode(ht_batch* batch, int mode);
 
 /* Learned warm start: a small 3D U-Net (2 levels, 16 / 32 channels) with
  * hand-written forward, backward and Adam kernels; BF16 weights in the

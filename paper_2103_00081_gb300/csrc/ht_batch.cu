@@ -13,6 +13,10 @@
 
 #include "ht_internal.cuh"
 
+#include <atomic>
+#include <string>
+#include <thread>
+
 namespace ht {
 
 namespace {
@@ -297,6 +301,7 @@ struct ht_batch {
     int n_cell = 0, n_node = 0, n_vec = 0;
     cudaGraphExec_t graph = nullptr;
     double graph_dt = -1.0;
+    int mode = HT_BATCH_CONCURRENT;
     std::string err;
 };
 
@@ -479,11 +484,56 @@ void ht_batch_destroy(ht_batch* b) {
 
 const char* ht_batch_last_error(const ht_batch* b) { return b ? b->err.c_str() : ""; }
 
+int ht_batch_set_mode(ht_batch* b, int mode) {
+    if (!b) return HT_EINVAL;
+    if (mode != HT_BATCH_CONCURRENT && mode != HT_BATCH_SHARED_LAUNCHES) return bfail(b, HT_EINVAL, "unknown mode");
+    b->mode = mode;
+    return HT_OK;
+}
+
+// concurrent mode: worker threads step the problems on their own streams
+static int batch_step_concurrent(ht_batch* b, double dt, ht_step_stats* stats) {
+    const int np = (int)b->probs.size();
+    bool shared = false;
+    for (int i = 0; i < np && !shared; ++i)
+        for (int j = 0; j < i && !shared; ++j) shared = b->probs[i]->stream == b->probs[j]->stream;
+    std::vector<int> rcs(np, HT_OK);
+    std::vector<ht_step_stats> st(np);
+    std::atomic<int> next(0);
+    auto work = [&] {
+        cudaSetDevice(b->device);
+        for (int i = next++; i < np; i = next++) rcs[i] = ht_step(b->probs[i], dt, &st[i]);
+    };
+    const int nt = shared ? 1 : std::min(np, 8);
+    if (nt <= 1) {
+        work();
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t) pool.emplace_back(work);
+        for (auto& th : pool) th.join();
+    }
+    int rc = HT_OK;
+    for (int i = 0; i < np; ++i) {
+        if (stats) stats[i] = st[i];
+        if (rcs[i] != HT_OK && rc == HT_OK) {
+            rc = rcs[i];
+            b->err = std::string("problem ") + std::to_string(i) + ": " + ht_last_error(b->probs[i]);
+        }
+    }
+    return rc;
+}
+
 int ht_batch_step(ht_batch* b, double dt, ht_step_stats* stats) {
     if (!b) return HT_EINVAL;
     if (!(dt > 0)) return bfail(b, HT_EINVAL, "dt must be positive");
     cudaSetDevice(b->device);
     const int np = (int)b->probs.size();
+    for (int i = 0; i < np; ++i) {
+        const ht_ctx* c = b->probs[i];
+        if (c->opts.precision != HT_MIXED || c->opts.precond != HT_PREC_JACOBI)
+            return bfail(b, HT_EINVAL, "batched problems need precision HT_MIXED with the Jacobi preconditioner");
+    }
+    if (b->mode == HT_BATCH_CONCURRENT) return batch_step_concurrent(b, dt, stats);
     // every problem works on the batch stream for the duration of the step
     std::vector<cudaStream_t> saved(np);
     for (int i = 0; i < np; ++i) {

@@ -214,10 +214,12 @@ class Simulator:
 
 
 class Batch:
-    """Batched steps of several Simulators (ht_batch_*): the inner FP32 head
-    CG of all problems runs in shared launches captured in a CUDA graph."""
+    """Batched steps of several Simulators (ht_batch_*).  mode
+    HT_BATCH_CONCURRENT (the library default) steps the problems concurrently
+    on their own streams; HT_BATCH_SHARED_LAUNCHES runs the inner FP32 head CG
+    of all problems in shared launches captured in a CUDA graph."""
 
-    def __init__(self, sims):
+    def __init__(self, sims, mode=None):
         self._lib = L.lib()
         self.sims = list(sims)
         arr = (c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
@@ -226,6 +228,10 @@ class Batch:
         if rc != L.HT_OK:
             raise HTError(rc, "ht_batch_create failed")
         self._h = h
+        if mode is not None:
+            rc = self._lib.ht_batch_set_mode(self._h, int(mode))
+            if rc != L.HT_OK:
+                raise HTError(rc, self._lib.ht_batch_last_error(self._h).decode())
 
     def step(self, dt, check=True):
         n = len(self.sims)
