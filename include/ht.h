@@ -100,7 +100,13 @@ typedef struct {
  * outer_fp64 != 0 computes the outer residuals b - A x of the mixed form
  * with the operator in FP64; 0 (the default) applies it in float-float
  * arithmetic on the FP32 pipes (about 48 significant bits, relative error of
- * order 1e-14 in A x), with b, x and r kept in FP64. */
+ * order 1e-14 in A x), with b, x and r kept in FP64.
+ * check_every is the first host convergence check interval of the Krylov
+ * loops (doubling to 64).  use_graphs != 0 (the default of ht_default_solver)
+ * replays the fused Krylov iterations of the two-pass variant from a CUDA
+ * graph of 8 iterations, captured on the context's stream the first time a
+ * solve runs with a given set of vectors, step size and operator scalars;
+ * a stream that the caller is capturing is launched to directly instead. */
 typedef struct {
     double tol;
     int max_iter;
