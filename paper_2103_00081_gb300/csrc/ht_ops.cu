@@ -1537,30 +1537,11 @@ __global__ void __launch_bounds__(256) fbi_update_kernel(long long n, T* __restr
 // ---------------------------------------------------------------------------
 // Right-hand sides through the element buffer.  Cells without Dirichlet nodes
 // need only the mass term (light kernel); the few cells with Dirichlet nodes
-// take the full lifted element RHS (heavy kernel, launched over the same
-// columns but doing work only on those cells).  The node pass sums the
-// contributions in a fixed order and emits through the operator (g_D on
-// Dirichlet rows, the sum plus dt F elsewhere).
+// take the full lifted element RHS (heavy kernel over an enumeration of the
+// face slabs).  The node pass sums the contributions in a fixed order and
+// emits through the operator (g_D on Dirichlet rows, the sum plus dt F
+// elsewhere).
 // ---------------------------------------------------------------------------
-template <int P, typename T, class Op>
-__global__ void __launch_bounds__(128) rhs_interior_kernel(const Grid g, const Op op, T* __restrict__ E,
-                                                           const int zlen) {
-    constexpr int n = P + 1, NL = n * n * n;
-    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (cx >= g.ncx || cy >= g.ncy) return;
-    const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
-    const int nc = (int)g.nc, layer = g.ncx * g.ncy;
-    for (int cz = cz0; cz < cz1; ++cz) {
-        if (cell_touches_dir(g, cx, cy, cz)) continue;
-        const int c = cx + g.ncx * cy + layer * cz;
-        T res[NL];
-        op.rhs_interior(g, cx, cy, cz, res);
-#pragma unroll
-        for (int l = 0; l < NL; ++l) E[l * nc + c] = res[l];
-    }
-}
-
 // Cells of the slab next to a Dirichlet face: candidate t enumerates face 0's
 // slab, then face 1's, ...; a cell in several slabs belongs to the first of
 // them whose face is Dirichlet, so each boundary cell is done exactly once.
@@ -1585,8 +1566,8 @@ __device__ __forceinline__ bool face_cell(const Grid& g, long long t, int* cx, i
     return false;
 }
 
-template <int P, typename T, class Op>
-__global__ void __launch_bounds__(128) rhs_boundary_kernel(const Grid g, const Op op, T* __restrict__ E,
+template <int P, typename T, class Op, typename ET = T>
+__global__ void __launch_bounds__(128) rhs_boundary_kernel(const Grid g, const Op op, ET* __restrict__ E,
                                                            const long long n_cand) {
     constexpr int n = P + 1, NL = n * n * n;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1597,26 +1578,69 @@ __global__ void __launch_bounds__(128) rhs_boundary_kernel(const Grid g, const O
     T res[NL];
     op.cell(g, cx, cy, cz, c, res);
 #pragma unroll
-    for (int l = 0; l < NL; ++l) E[l * nc + c] = res[l];
+    for (int l = 0; l < NL; ++l) E[l * nc + c] = cvt<ET>(res[l]);
 }
 
-template <int P, typename T, class Op>
-__global__ void __launch_bounds__(128) node_emit_kernel(const Grid g, const T* __restrict__ E, const Op op,
-                                                        const int klen) {
+// Mass-only right-hand side of the cells without Dirichlet nodes in
+// float-float arithmetic: scale (G^T)^3 G^3 u_old with u_old split from FP64
+// and scale S_s (head) or the cell's c_T (heat); cells with Dirichlet nodes
+// are left to rhs_boundary_kernel.
+template <int P>
+__global__ void __launch_bounds__(128) rhs_interior_df_kernel(const Grid g, const Elem<df64> e,
+                                                              const double* __restrict__ x,
+                                                              const double* __restrict__ scale_c, const df64 scale_u,
+                                                              df64* __restrict__ E, const int zlen) {
+    constexpr int n = P + 1, NL = n * n * n;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cx >= g.ncx || cy >= g.ncy) return;
+    const int cz0 = blockIdx.z * zlen, cz1 = min(cz0 + zlen, g.ncz);
+    const int nc = (int)g.nc, layer = g.ncx * g.ncy;
+    const int NX = g.Nx, NXY = g.Nx * g.Ny;
+    for (int cz = cz0; cz < cz1; ++cz) {
+        if (cell_touches_dir(g, cx, cy, cz)) continue;
+        const int c = cx + g.ncx * cy + layer * cz;
+        const int base = P * cx + NX * P * cy + NXY * P * cz;
+        df64 u[NL];
+#pragma unroll
+        for (int c2 = 0; c2 < n; ++c2)
+#pragma unroll
+            for (int b = 0; b < n; ++b)
+#pragma unroll
+                for (int a = 0; a < n; ++a) u[a + n * (b + n * c2)] = df_from(ldro(x + base + NX * b + NXY * c2 + a));
+        sweep<n, 0, false>(u, e.G[0]);
+        sweep<n, 1, false>(u, e.G[1]);
+        sweep<n, 2, false>(u, e.G[2]);
+        const df64 sc = scale_c ? df_from(ldro(scale_c + c)) : scale_u;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) u[l] = u[l] * sc;
+        sweep<n, 2, true>(u, e.G[2]);
+        sweep<n, 1, true>(u, e.G[1]);
+        sweep<n, 0, true>(u, e.G[0]);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) E[l * nc + c] = u[l];
+    }
+}
+
+// node pass of the right-hand side from float-float contributions
+template <int P, class Op>
+__global__ void __launch_bounds__(128) node_emit_df_kernel(const Grid g, const df64* __restrict__ E, const Op op,
+                                                           const int klen) {
     const int NXY = g.Nx * g.Ny;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= NXY) return;
     const int i = m % g.Nx, j = m / g.Nx;
     const NodeXY<P> nx(g, i, j);
     const int k0 = blockIdx.y * klen, k1 = min(k0 + klen, g.Nz);
-    T dot = T(0);
+    double dot = 0.0;
     for (int k = k0; k < k1; ++k) {
-        T v[8];
+        df64 v[8];
         nx.load(g, E, k, v);
-        const T sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-        op.emit(g, i, j, k, sum, dot);
+        const df64 sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        op.emit(g, i, j, k, df_to(sum), dot);
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // Outer residual of the mixed form in float-float arithmetic: the element pass
@@ -2278,18 +2302,28 @@ int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y, dou
 
 template <int P, class Op>
 static int launch_rhs_two_pass(ht_ctx* c, const Grid& g, const Op& op) {
-    double* E = elem_buffer<double>(c);
+    // the mass-only cells in float-float (the FP64 rate makes FP64 the slow
+    // part here), the Dirichlet cells in FP64, the sum in float-float; the
+    // element buffer holds float pairs
+    df64* E = reinterpret_cast<df64*>(elem_buffer<double>(c));
     dim3 ci, ng;
     int zi, kl;
-    cell_pass_dims(c, g, resident_per_sm<rhs_interior_kernel<P, double, Op>>(), &ci, &zi);
-    layer_node_dims(c, g, resident_per_sm<node_emit_kernel<P, double, Op>>(), &ng, &kl);
-    rhs_interior_kernel<P, double, Op><<<ci, dim3(32, 4), 0, c->stream>>>(g, op, E, zi); ++c->n_launch;
+    cell_pass_dims(c, g, resident_per_sm<rhs_interior_df_kernel<P>>(), &ci, &zi);
+    layer_node_dims(c, g, resident_per_sm<node_emit_df_kernel<P, Op>>(), &ng, &kl);
+    const double* scale_c = nullptr;
+    double scale_u = 0.0;
+    if constexpr (Op::kPlanes) { scale_c = op.cTc; scale_u = op.cT_u; }
+    else { scale_u = op.alpha; }
+    const float su_hi = (float)scale_u;
+    const df64 su(su_hi, (float)(scale_u - (double)su_hi));
+    rhs_interior_df_kernel<P><<<ci, dim3(32, 4), 0, c->stream>>>(g, c->edf, op.x, scale_c, su, E, zi); ++c->n_launch;
     if (g.dmask) {
         const long long n_cand = 2LL * ((long long)g.ncy * g.ncz + (long long)g.ncx * g.ncz + (long long)g.ncx * g.ncy);
-        rhs_boundary_kernel<P, double, Op><<<(unsigned)((n_cand + 127) / 128), 128, 0, c->stream>>>(g, op, E, n_cand);
+        rhs_boundary_kernel<P, double, Op, df64><<<(unsigned)((n_cand + 127) / 128), 128, 0, c->stream>>>(g, op, E,
+                                                                                                           n_cand);
         ++c->n_launch;
     }
-    node_emit_kernel<P, double, Op><<<ng, 128, 0, c->stream>>>(g, E, op, kl); ++c->n_launch;
+    node_emit_df_kernel<P, Op><<<ng, 128, 0, c->stream>>>(g, E, op, kl); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
 }
