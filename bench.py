@@ -165,6 +165,14 @@ def measured_traffic(workload):
     return d.get("dram_bytes_per_iteration")
 
 
+def arm_config(sc, world):
+    """The workload description shared by both arms of the benchmark."""
+    return {"workload": f"{sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{sc.order}, {sc.n_nodes} nodes/field, "
+                        f"dt={sc.dt / 86400:g} d, tol 1e-10",
+            "nodes_per_field": sc.n_nodes, "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "working set per step > L2 (no flush needed)"}
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -326,10 +334,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32-inner/f64-outer",
         "data": "synthetic (seeded lognormal K layers, well pair)",
-        "config": {"workload": f"{sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{order}, {nn} nodes/field, "
-                               f"dt={dt / 86400:g} d, tol 1e-10",
-                   "nodes_per_field": nn, "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "working set per step > L2 (no flush needed)"},
+        "config": arm_config(sc, world),
         "plain_fp64": {"value": rate_fp64, "unit": UNIT, "ms_per_step": ms_fp64 / args.steps,
                        "iters_head": [s["iters_head"] for s in st_fp64],
                        "iters_heat": [s["iters_heat"] for s in st_fp64],
@@ -400,10 +405,10 @@ def run_reference(args):
           "sample": f"{args.steps} step(s) of {sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{sc.order} "
                     f"({sc.n_nodes} nodes), scaled linearly by node count to {sc_full.n_nodes} nodes"}
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"{sc_full.name} (sampled at {sc.nx}x{sc.ny}x{sc.nz})"},
+        "data": "synthetic (seeded lognormal K layers, well pair)", "config": arm_config(sc_full, args.gpus),
         "cpu_baseline": cb,
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
