@@ -200,6 +200,10 @@ struct ht_ctx {
         double ss = 0.0;                // operator scalars baked into the captured launches
     };
     FusedGraph g_cg[2], g_bi[2];
+    // iterations of the inner solves of the last step, per field and outer
+    // pass: the next solve checks convergence first near that count
+    int iter_hint[2][8] = {};
+    int cur_hint = 0;
     std::vector<std::vector<float>> prof_ms = std::vector<std::vector<float>>(HT_PROF_KINDS);
 };
 

@@ -843,7 +843,16 @@ int drive_fused(ht_ctx* c, int slot, ht_ctx::FusedGraph& gr, const void* const* 
     }
     int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
     if (graphs) chunk = (chunk + kGraphIters - 1) / kGraphIters * kGraphIters;
+    const int base_chunk = chunk;
+    // with a count from the previous step, the first check comes a few
+    // iterations before it, then every base_chunk (doubling) iterations
+    if (c->cur_hint > 0) {
+        int h = c->cur_hint - 1 - 8;
+        if (graphs) h = h / kGraphIters * kGraphIters;
+        if (h > chunk) chunk = h;
+    }
     HT_TRY(sync_scal(c, slot));
+    bool first_chunk = true;
     while (!c->scal_host[slot].done) {
         const int before = c->scal_host[slot].iters;
         if (c->prof_on) HT_TRY(prof_begin(c, kind));
@@ -858,7 +867,9 @@ int drive_fused(ht_ctx* c, int slot, ht_ctx::FusedGraph& gr, const void* const* 
         if (c->prof_on) HT_TRY(prof_end_weighted(c, chunk));
         HT_TRY(sync_scal(c, slot));
         if (c->prof_on && c->scal_host[slot].iters - before != chunk) prof_drop_last(c);
-        if (chunk < 64) chunk *= 2;
+        if (first_chunk && chunk > base_chunk) chunk = base_chunk;
+        else if (chunk < 64) chunk *= 2;
+        first_chunk = false;
     }
     return HT_OK;
 }
@@ -1291,6 +1302,7 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
         const double need = s.rr > 0 ? 0.5 * tol * sqrt(s.bb / s.rr) : 1.0;
         const double itol = std::max(inner_tol, std::min(need, 0.5));
         int it = 0;
+        c->cur_hint = k < 8 ? c->iter_hint[field][k] : 0;
         if (field == HT_HEAD && c->opts.precond == HT_PREC_CHEBYSHEV)
             HT_TRY((run_cg_cheb<float, Vecs32>(c, dt, w, c->z32, c->zz32, c->v32, c->r32, 1, itol,
                                                max_iter - total, &it)));
@@ -1300,6 +1312,8 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
             HT_TRY((run_gmres<float, Vecs32>(c, dt, w, c->r32, 1, itol, max_iter - total, &it)));
         else
             HT_TRY((run_bicgstab<float, Vecs32>(c, dt, w, c->r32, 1, itol, max_iter - total, &it)));
+        c->cur_hint = 0;
+        if (k < 8) c->iter_hint[field][k] = it;
         total += it;
         if (c->scal_host[1].status == ST_NAN)
             return fail(c, HT_EINVAL, "%s: FP32 inner solve produced non-finite values", what);
