@@ -9,7 +9,7 @@ loads, head CG solve, heat BiCGStab solve.
 
 Printed metric: simulated years per hour of the FP32-inner / FP64-outer form
 (value), with the plain FP64 form beside it, operator GDoF/s and the roofline
-of the dominant kernel (the head operator apply).
+of the dominant kernel (the fused Jacobi-CG iteration of the head system).
 
 --impl reference times the CPU FP64 oracle (the plain assembled-matrix
 reference) on a bounded sample of the same workload.
@@ -189,6 +189,7 @@ def run_ours(args):
     B.build()
     from paper_2103_00081_gb300 import hydro
     from paper_2103_00081_gb300 import _lib as L
+    from paper_2103_00081_gb300 import replicas as R
 
     rank, world, dist = dist_init()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -264,19 +265,14 @@ def run_ours(args):
     sim64, ms_fp64, st_fp64, prof_fp64, clk64 = timed_run(L.HT_FP64)
     sim64.close()
 
-    def to_rate(ms, steps):
-        return (steps * dt / YEAR) / (ms / 1000.0 / 3600.0)
-
-    # max over ranks of the timed duration
-    if dist:
-        t = torch.tensor([ms_mixed, ms_fp64, e2e_s], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_fp64, e2e_s = t.tolist()
+    # max over ranks of the timed duration; each rank stepped its own replica
+    ms_mixed, ms_fp64, e2e_s = R.max_over_ranks([ms_mixed, ms_fp64, e2e_s], dist, f"cuda:{local}")
     if rank != 0:
         return
-    rate_mixed = to_rate(ms_mixed, args.steps) * world
-    rate_fp64 = to_rate(ms_fp64, args.steps) * world
-    rate_e2e = (args.steps * dt / YEAR) / (e2e_s / 3600.0) * world
+    years_all = args.steps * dt / YEAR * world
+    rate_mixed = R.job_rate(years_all, ms_mixed / 1000.0 / 3600.0)
+    rate_fp64 = R.job_rate(years_all, ms_fp64 / 1000.0 / 3600.0)
+    rate_e2e = R.job_rate(years_all, e2e_s / 3600.0)
 
     order = sc.order
     # dominant kernel: the fused Jacobi-CG iteration of the head system (its
@@ -417,17 +413,29 @@ def run_reference(args):
 def run_batch(args):
     """Batched workload: 64 independent Q1 problems (32x32x16 .. 96x96x48)
     advanced together by ht_batch_step, against the same problems stepped one
-    after another; value = simulated years per hour summed over problems."""
+    after another; value = simulated years per hour summed over problems.
+    With N ranks the problems are dealt round-robin over the GPUs (no
+    data-path collective) and the slowest rank's time is the job's."""
     import torch
     from paper_2103_00081_gb300 import build as B
     B.build()
     from paper_2103_00081_gb300 import hydro
     from paper_2103_00081_gb300 import _lib as L
-    torch.cuda.set_device(0)
-    scs = S.config4(n_problems=args.batch_size)
+    from paper_2103_00081_gb300 import replicas as R
+    rank, world, dist = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    scs_all = S.config4(n_problems=args.batch_size)
+    if len(scs_all) < world:
+        raise SystemExit(f"--batch-size {len(scs_all)} is smaller than the {world} ranks")
+    scs = [scs_all[i] for i in R.shard(len(scs_all), rank, world)]
     opts = dict(tol=1e-10, precision=L.HT_MIXED, inner_tol=1e-4, krylov=L.HT_KRYLOV_BICGSTAB)
-    sims = [hydro.Simulator.from_scenario(sc, **opts) for sc in scs]
+    sims = [hydro.Simulator.from_scenario(sc, device=local, **opts) for sc in scs]
     dt = scs[0].dt
+
+    def barrier():
+        if dist:
+            dist.barrier()
 
     def timed_batch(mode):
         batch = hydro.Batch(sims, mode=mode)
@@ -436,11 +444,13 @@ def run_batch(args):
         for sm in sims:
             sm.profile(True)
         torch.cuda.synchronize()
+        barrier()
         w0 = time.perf_counter()
         for _ in range(args.steps):
             stats = batch.step(dt)
         torch.cuda.synchronize()
         t = time.perf_counter() - w0
+        barrier()
         launches = sum(sm.profile_read()["launches"] for sm in sims)
         for sm in sims:
             sm.profile(False)
@@ -451,25 +461,34 @@ def run_batch(args):
     t_batch, stats, launches = timed_batch(L.HT_BATCH_CONCURRENT)
     t_shared, _, _ = timed_batch(L.HT_BATCH_SHARED_LAUNCHES)
     # the same problems stepped one by one through ht_step
+    barrier()
     w0 = time.perf_counter()
     for _ in range(args.steps):
         for sm in sims:
             sm.step(dt)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - w0
-    years = args.steps * dt / YEAR * len(scs)
-    nodes = sum(sc.n_nodes for sc in scs)
+    dev = f"cuda:{local}"
+    t_batch, t_shared, t_seq = R.max_over_ranks([t_batch, t_shared, t_seq], dist, dev)
+    (launches,) = R.sum_over_ranks([launches], dist, dev)
+    if rank != 0:
+        return
+    years = args.steps * dt / YEAR * len(scs_all)
+    nodes = sum(sc.n_nodes for sc in scs_all)
     print(json.dumps({
-        "metric": "simulated-years/hour summed over the batch at 1e-10 residual", "value": years / (t_batch / 3600),
-        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "metric": "simulated-years/hour summed over the batch at 1e-10 residual",
+        "value": R.job_rate(years, t_batch / 3600),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic (seeded GRF lnK, piles)",
-        "config": {"workload": f"{len(scs)} Q1 problems, {nodes} nodes in total, dt=1 d, tol 1e-10",
-                   "sizes": sorted(set(f"{sc.nx}x{sc.ny}x{sc.nz}" for sc in scs))[:8]},
-        "sequential": {"value": years / (t_seq / 3600), "ms_per_step": t_seq / args.steps * 1e3},
-        "shared_launches": {"value": years / (t_shared / 3600), "ms_per_step": t_shared / args.steps * 1e3},
+        "config": {"workload": f"{len(scs_all)} Q1 problems, {nodes} nodes in total, dt=1 d, tol 1e-10",
+                   "sizes": sorted(set(f"{sc.nx}x{sc.ny}x{sc.nz}" for sc in scs_all))[:8],
+                   "parallelism": "problems dealt round-robin over ranks" if world > 1 else "single GPU"},
+        "sequential": {"value": R.job_rate(years, t_seq / 3600), "ms_per_step": t_seq / args.steps * 1e3},
+        "shared_launches": {"value": R.job_rate(years, t_shared / 3600),
+                            "ms_per_step": t_shared / args.steps * 1e3},
         "speedup_vs_sequential": t_seq / t_batch,
-        "iters_head": [st["iters_head"] for st in stats][:8], "gpu_launches": launches,
+        "iters_head": [st["iters_head"] for st in stats][:8], "gpu_launches": int(launches),
     }))
 
 
