@@ -20,6 +20,9 @@ sum factorisation, no blocking, then a sparse direct solve):
   the same Gauss points (Darcy's law, Section 2, q = -k (grad p + rho_w g)).
   D_w is the lumped term of an injection well, c_w (Q/L) int N_i s dV with s
   the well's lateral profile (a line, or a normal density of width sigma).
+* Loads F_T: Neumann faces and box sources (heat flux q(t) over a horizontal
+  rectangle snapped to cell faces, the building heat of Section 1) as
+  int q N_i dS; energy piles (Section 3.2) as int q_l N_i dz.
 * Quadrature: (p+1)-point Gauss-Legendre per direction for order p.
 * Dirichlet nodes: rows replaced by the identity and the prescribed values
   moved to the right-hand side (columns eliminated, so the head operator stays
@@ -329,6 +332,48 @@ def face_load(mesh: Mesh, face: int, value: float) -> np.ndarray:
     return F
 
 
+def box_snap(mesh: Mesh, box):
+    """Cell-face indices (i0, i1, j0, j1, k) of a box source's rectangle.
+
+    Each edge x0, x1, y0, y1 moves to the nearest cell face (ties upwards)
+    and is clamped to the mesh; z moves to the nearest plane of horizontal
+    cell faces.  The rectangle covers cells i0 <= cx < i1, j0 <= cy < j1 on
+    the node plane p * k.
+    """
+    def nearest(v, d, n):
+        return int(min(max(math.floor((v - mesh.origin[d]) / mesh.H[d] + 0.5), 0), n))
+    i0, i1 = nearest(box[0], 0, mesh.nx), nearest(box[1], 0, mesh.nx)
+    j0, j1 = nearest(box[2], 1, mesh.ny), nearest(box[3], 1, mesh.ny)
+    k = nearest(box[4], 2, mesh.nz)
+    return i0, i1, j0, j1, k
+
+
+def box_weights(mesh: Mesh, box) -> Dict[int, float]:
+    """w_i = int_R N_i dS over the snapped horizontal rectangle R of a box
+    source, by (p+1) x (p+1) Gauss points on every cell face inside R."""
+    p = mesh.p
+    i0, i1, j0, j1, k = box_snap(mesh, box)
+    xg, wg = gauss01(p + 1)
+    Hx, Hy = mesh.H[0], mesh.H[1]
+    w: Dict[int, float] = {}
+    for cy in range(j0, j1):
+        for cx in range(i0, i1):
+            for gy in range(p + 1):
+                for gx in range(p + 1):
+                    dS = wg[gx] * Hx * wg[gy] * Hy
+                    for b in range(p + 1):
+                        for a in range(p + 1):
+                            node = mesh.node_index(p * cx + a, p * cy + b, p * k)
+                            w[node] = w.get(node, 0.0) + dS * lagrange_value(p, a, xg[gx]) * \
+                                lagrange_value(p, b, xg[gy])
+    return w
+
+
+def box_flux(box, t: float) -> float:
+    """q(t) = mean + amp sin(2 pi t / period + phase), W/m^2 into the domain."""
+    return box[5] + box[6] * math.sin(2.0 * math.pi * t / box[7] + box[8])
+
+
 def pile_amplitude(pile, t: float) -> float:
     """q_l(t) = mean + amp sin(2 pi t / period + phase), W/m."""
     return pile[4] + pile[5] * math.sin(2.0 * math.pi * t / pile[6] + pile[7])
@@ -428,6 +473,8 @@ class OracleSim:
                     self.Tin_well[node] += self.cw * wl[4] / L * wv * wl[5]
         self.pile_w = [line_weights(m, pl[0], pl[1], pl[2], pl[3])
                        for pl in np.asarray(sc.piles).reshape(-1, 8)]
+        self.boxes = np.asarray(getattr(sc, "boxes", np.zeros((0, 9))), dtype=np.float64).reshape(-1, 9)
+        self.box_w = [box_weights(m, bx) for bx in self.boxes]
         self.extra = {HEAD: np.zeros(m.n_nodes), TEMP: np.zeros(m.n_nodes)}
         self.h = np.array(sc.h0, dtype=np.float64)
         self.T = np.array(sc.T0, dtype=np.float64)
@@ -465,6 +512,10 @@ class OracleSim:
         F = self.F_static[TEMP] + self.extra[TEMP] + self.Tin_well
         for pl, wts in zip(np.asarray(self.sc.piles).reshape(-1, 8), self.pile_w):
             a = pile_amplitude(pl, t)
+            for node, wv in wts.items():
+                F[node] += a * wv
+        for bx, wts in zip(self.boxes, self.box_w):
+            a = box_flux(bx, t)
             for node, wv in wts.items():
                 F[node] += a * wv
         return F

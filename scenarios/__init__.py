@@ -68,6 +68,9 @@ class Scenario:
     n_steps: int
     lam_cells: Optional[np.ndarray] = None   # optional per-cell lambda
     cT_cells: Optional[np.ndarray] = None    # optional per-cell c_T
+    # horizontal heat-flux rectangles [n, 9]: x0, x1, y0, y1, z, mean, amp,
+    # period, phase (W/m^2 into the domain), edges snapped to cell faces
+    boxes: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 9)))
 
     @property
     def n_cells(self) -> int:
@@ -259,9 +262,11 @@ def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
                  n_piles: int = 3, n_wells: int = 2, sigma_lnK: float = 1.0,
                  faces_head=(0, 1), faces_temp=(0, 1, 2, 3, 5),
                  extent=(40.0, 30.0, 20.0), dt: float = 0.5 * DAY,
-                 per_cell_thermal: bool = False) -> Scenario:
+                 per_cell_thermal: bool = False, n_boxes: int = 0) -> Scenario:
     """Small random problem for parity tests: iid lognormal K, random piles
-    and wells at arbitrary (off-node) positions, random initial fields."""
+    and wells at arbitrary (off-node) positions, random initial fields, and
+    optionally box heat sources whose edges lie within 0.3 cells of a cell
+    face (so that snapping is exercised but never ambiguous)."""
     rng = np.random.default_rng(seed)
     lam, cT, cw, Ss = _sand()
     Lx, Ly, Lz = extent
@@ -291,7 +296,27 @@ def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
     if per_cell_thermal:
         sc.lam_cells = lam * np.exp(0.3 * rng.standard_normal(nc))
         sc.cT_cells = cT * np.exp(0.2 * rng.standard_normal(nc))
+    if n_boxes:
+        sc.boxes = random_boxes(rng, n_boxes, (nx, ny, nz), extent)
     return sc
+
+
+def random_boxes(rng, n: int, cells: Tuple[int, int, int], extent, period: float = 30 * DAY) -> np.ndarray:
+    """n box heat sources [n, 9]: a random non-empty run of cell faces per
+    axis, each edge (and the plane z) jittered by up to 0.3 cells, fluxes of
+    -20..20 W/m^2 with seasonal amplitude 0..15 W/m^2."""
+    nx, ny, nz = cells
+    Hx, Hy, Hz = extent[0] / nx, extent[1] / ny, extent[2] / nz
+    rows = []
+    for _ in range(n):
+        i0 = int(rng.integers(0, nx)); i1 = int(rng.integers(i0 + 1, nx + 1))
+        j0 = int(rng.integers(0, ny)); j1 = int(rng.integers(j0 + 1, ny + 1))
+        k = int(rng.integers(0, nz + 1))
+        jit = rng.uniform(-0.3, 0.3, 5)
+        z = min(max((k + jit[4]) * Hz, 0.0), extent[2])
+        rows.append([(i0 + jit[0]) * Hx, (i1 + jit[1]) * Hx, (j0 + jit[2]) * Hy, (j1 + jit[3]) * Hy, z,
+                     rng.uniform(-20, 20), rng.uniform(0, 15), period, rng.uniform(0, 2 * np.pi)])
+    return np.asarray(rows, dtype=np.float64).reshape(-1, 9)
 
 
 def config4(n_problems: int = 64, seed0: int = 1000, n_steps: int = 30,

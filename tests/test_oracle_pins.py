@@ -400,3 +400,66 @@ def test_gaussian_well_integrals_match_erf_closed_forms():
         wl = np.array([sc.extent[0] / 2, sc.extent[1] / 2, 15.0, 5.0, 1e-3, 20.0, 2.0])
         w = fem.well_weights(fem.Mesh(sc.nx, sc.ny, sc.nz, p, sc.origin, sc.extent), wl)
         assert abs(sum(w.values()) - 10.0) < 1e-9
+
+
+def test_box_source_weights_closed_forms():
+    """Box heat sources: the weights integrate 1, x, y and x*y over the snapped
+    rectangle exactly (area, first moments and the mixed moment in closed
+    form), every weight sits on the snapped node plane, and edges that lie
+    within 0.3 cells of a face snap to that face."""
+    for p in (1, 2):
+        m = fem.Mesh(7, 5, 4, p, (1.0, -2.0, 0.5), (14.0, 10.0, 8.0))
+        Hx, Hy, Hz = m.H
+        box = [1.0 + 2 * Hx + 0.29 * Hx, 1.0 + 6 * Hx - 0.21 * Hx, -2.0 + 1 * Hy - 0.3 * Hy,
+               -2.0 + 4 * Hy + 0.1 * Hy, 0.5 + 3 * Hz + 0.2 * Hz, 1.0, 0.0, 1.0, 0.0]
+        assert fem.box_snap(m, box) == (2, 6, 1, 4, 3)
+        xa, xb, ya, yb = 1.0 + 2 * Hx, 1.0 + 6 * Hx, -2.0 + Hy, -2.0 + 4 * Hy
+        w = fem.box_weights(m, box)
+        x, y, z = m.node_xyz()
+        idx = np.array(list(w.keys()))
+        val = np.array(list(w.values()))
+        assert np.allclose(z[idx], 0.5 + 3 * Hz, rtol=0, atol=1e-12)
+        area = (xb - xa) * (yb - ya)
+        assert abs(val.sum() - area) <= 1e-12 * area
+        assert abs((val * x[idx]).sum() - 0.5 * (xb ** 2 - xa ** 2) * (yb - ya)) <= 1e-11 * area * 15
+        assert abs((val * y[idx]).sum() - 0.5 * (yb ** 2 - ya ** 2) * (xb - xa)) <= 1e-11 * area * 15
+        mixed = 0.25 * (xb ** 2 - xa ** 2) * (yb ** 2 - ya ** 2)
+        assert abs((val * x[idx] * y[idx]).sum() - mixed) <= 1e-11 * abs(mixed)
+        if p == 2:   # Q2 also integrates x^2 exactly
+            sq = (xb ** 3 - xa ** 3) / 3 * (yb - ya)
+            assert abs((val * x[idx] ** 2).sum() - sq) <= 1e-11 * sq
+        # edges outside the mesh are clamped to it
+        assert fem.box_snap(m, [-50.0, 100.0, -50.0, 100.0, 99.0, 0, 0, 1, 0]) == (0, 7, 0, 5, 4)
+
+
+def test_box_source_over_the_top_face_equals_the_face_flux():
+    """A box covering the whole top face with a constant flux gives the same
+    nodal load as a Neumann flux on that face."""
+    for p in (1, 2):
+        m = fem.Mesh(4, 3, 2, p, (0.0, 0.0, 0.0), (8.0, 6.0, 4.0))
+        box = [0.0, 8.0, 0.0, 6.0, 4.0, 0.89, 0.0, 1.0, 0.0]
+        F = np.zeros(m.n_nodes)
+        for nd, wv in fem.box_weights(m, box).items():
+            F[nd] += fem.box_flux(box, 0.0) * wv
+        np.testing.assert_allclose(F, fem.face_load(m, 5, 0.89), rtol=0, atol=1e-14)
+
+
+def test_energy_balance_with_box_sources():
+    """Insulated box, still water: the stored heat of one step is dt times the
+    sum over boxes of q(t^{n+1}) times the snapped area (Eq. 4 with the
+    conduction term summing to zero over all rows)."""
+    for p in (1, 2):
+        sc = S.random_small(8, 5, 4, 3, p, n_piles=0, n_wells=0, n_boxes=3)
+        sc.bc = {S.HEAD: {}, S.TEMP: {}}
+        sc.h0 = np.zeros_like(sc.h0)
+        o = fem.OracleSim(sc)
+        T0 = o.T.copy()
+        o.step(sc.dt)
+        assert np.abs(o.h).max() == 0.0
+        stored = (o.McT @ (o.T - T0)).sum()
+        expect = 0.0
+        for bx in sc.boxes:
+            i0, i1, j0, j1, _ = fem.box_snap(o.mesh, bx)
+            expect += fem.box_flux(bx, sc.dt) * (i1 - i0) * o.mesh.H[0] * (j1 - j0) * o.mesh.H[1]
+        assert abs(expect) > 0
+        assert abs(stored - sc.dt * expect) <= 1e-10 * abs(sc.dt * expect)
