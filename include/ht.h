@@ -67,6 +67,18 @@ typedef struct {
     double x, y, z_top, z_bot, mean, amp, period, phase;
 } ht_line_src;
 
+/* Horizontal heat source over a rectangle: building heat entering the ground
+ * through a footprint or basement floor (the anthropogenic heat of Section 1),
+ * applied like the heat-flux boundary term of Eq. 4 (the bottom flux of
+ * Section 3.3).  The rectangle [x0, x1] x [y0, y1] on the plane z is snapped
+ * to cell faces: each of x0, x1, y0, y1 and z moves to the nearest face
+ * x0_mesh + i*Hx (y, z alike; ties upwards), x and y edges clamped to the
+ * mesh.  Flux q(t) = mean + amp*sin(2*pi*t/period + phase) in W/m^2 into the
+ * domain; heat load F_T,i += q(t) int_R N_i dS over the snapped rectangle R. */
+typedef struct {
+    double x0, x1, y0, y1, z, mean, amp, period, phase;
+} ht_box_src;
+
 /* Vertical well screened from z_bot to z_top at (x, y): volumetric rate Q
  * (m^3/s, > 0 injects) spread uniformly over the screen length L and
  * laterally with profile s(x, y): the axis itself (sigma = 0, a line source)
@@ -178,6 +190,12 @@ int ht_set_state(ht_ctx* ctx, const double* h, const double* T, double t, int on
  * for a source outside the box or with z_top <= z_bot. */
 int ht_add_line_sources(ht_ctx* ctx, int n, const ht_line_src* src);
 int ht_add_wells(ht_ctx* ctx, int n, const ht_well* wells);
+
+/* Append box heat sources (see ht_box_src); they take effect from the next
+ * step.  The array is copied.  Errors: HT_EINVAL for a non-finite field,
+ * x1 <= x0 or y1 <= y0, period <= 0, z outside [z0, z0 + Lz], or a
+ * rectangle that is empty once snapped (both edges on the same face). */
+int ht_add_box_sources(ht_ctx* ctx, int n, const ht_box_src* boxes);
 
 /* Extra nodal load vector added to F of `field` at every step (NULL clears).
  * A test hook for manufactured solutions. */

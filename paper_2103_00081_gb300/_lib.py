@@ -44,6 +44,10 @@ class LineSrc(ctypes.Structure):
     _fields_ = [(n, c_double) for n in ("x", "y", "z_top", "z_bot", "mean", "amp", "period", "phase")]
 
 
+class BoxSrc(ctypes.Structure):
+    _fields_ = [(n, c_double) for n in ("x0", "x1", "y0", "y1", "z", "mean", "amp", "period", "phase")]
+
+
 class Well(ctypes.Structure):
     _fields_ = [(n, c_double) for n in ("x", "y", "z_top", "z_bot", "Q", "T_in", "sigma")]
 
@@ -85,6 +89,7 @@ SIGNATURES = {
     "ht_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int]),
     "ht_add_line_sources": (c_int, [c_void_p, c_int, POINTER(LineSrc)]),
     "ht_add_wells": (c_int, [c_void_p, c_int, POINTER(Well)]),
+    "ht_add_box_sources": (c_int, [c_void_p, c_int, POINTER(BoxSrc)]),
     "ht_set_extra_rhs": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "ht_set_solver": (c_int, [c_void_p, POINTER(SolverOpts)]),
     "ht_step": (c_int, [c_void_p, c_double, POINTER(StepStats)]),

@@ -306,6 +306,38 @@ int line_weights(ht_ctx* c, double x, double y, double ztop, double zbot, std::m
     return HT_OK;
 }
 
+// Cell-face index nearest to v along axis d (ties upwards), clamped to [0, n].
+int snap_face(const ht_ctx* c, int d, double v) {
+    const double org[3] = {c->mesh.x0, c->mesh.y0, c->mesh.z0};
+    const int n[3] = {c->mesh.nx, c->mesh.ny, c->mesh.nz};
+    const double f = floor((v - org[d]) / c->H[d] + 0.5);
+    return (int)std::max(0.0, std::min(f, (double)n[d]));
+}
+
+// Box source weights w_i = int_R N_i dS over the snapped rectangle R: on each
+// cell face inside R the integral factors into Hx int phi_a * Hy int phi_b.
+int box_weights(ht_ctx* c, const ht_box_src& b, std::map<long long, double>& out) {
+    const int P = c->grid.P;
+    const int i0 = snap_face(c, 0, b.x0), i1 = snap_face(c, 0, b.x1);
+    const int j0 = snap_face(c, 1, b.y0), j1 = snap_face(c, 1, b.y1);
+    const int k = snap_face(c, 2, b.z);
+    if (i1 <= i0 || j1 <= j0) return fail(c, HT_EINVAL, "box source is empty once snapped to cell faces");
+    double ix[3], iy[3];
+    for (int a = 0; a <= P; ++a) {
+        ix[a] = c->H[0] * phi_int(P, a);
+        iy[a] = c->H[1] * phi_int(P, a);
+    }
+    const long long kk = (long long)P * k;
+    for (int cy = j0; cy < j1; ++cy)
+        for (int cx = i0; cx < i1; ++cx)
+            for (int bb = 0; bb <= P; ++bb)
+                for (int a = 0; a <= P; ++a) {
+                    const long long i = (long long)P * cx + a, j = (long long)P * cy + bb;
+                    out[i + (long long)c->grid.Nx * (j + (long long)c->grid.Ny * kk)] += ix[a] * iy[bb];
+                }
+    return HT_OK;
+}
+
 bool node_on_dirichlet(const ht_ctx* c, int field, long long id) {
     const Grid& g = c->grid;
     const int i = (int)(id % g.Nx), j = (int)((id / g.Nx) % g.Ny), k = (int)(id / ((long long)g.Nx * g.Ny));
@@ -478,13 +510,27 @@ int finalize_setup(ht_ctx* c) {
         HT_CUDA(c, cudaMemcpyAsync(c->wdn32, d32.data(), nn * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         HT_CUDA(c, cudaStreamSynchronize(c->stream));
     }
-    // pile tables: CSR over unique nodes
+    // time-varying heat sources (piles, then boxes): CSR over unique nodes of
+    // (source, weight); each source's time function q(t) = mean + amp sin(.)
+    std::vector<ht_line_src> tf(c->piles);
     std::map<long long, std::vector<std::pair<int, double>>> pm;
     for (size_t s = 0; s < c->piles.size(); ++s) {
         const ht_line_src& p = c->piles[s];
         std::map<long long, double> lw;
         HT_TRY(line_weights(c, p.x, p.y, p.z_top, p.z_bot, lw, "line source"));
         for (auto& kv : lw) pm[kv.first].push_back({(int)s, kv.second});
+    }
+    for (const ht_box_src& b : c->boxes) {
+        std::map<long long, double> bw;
+        HT_TRY(box_weights(c, b, bw));
+        const int s = (int)tf.size();
+        ht_line_src f{};
+        f.mean = b.mean;
+        f.amp = b.amp;
+        f.period = b.period;
+        f.phase = b.phase;
+        tf.push_back(f);
+        for (auto& kv : bw) pm[kv.first].push_back({s, kv.second});
     }
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->pile_w); dfree(c->d_piles);
     c->n_pile_nodes = (int)pm.size();
@@ -501,12 +547,12 @@ int finalize_setup(ht_ctx* c) {
         HT_TRY(dalloc(c, &c->pile_off, po.size()));
         HT_TRY(dalloc(c, &c->pile_src, ps.size()));
         HT_TRY(dalloc(c, &c->pile_w, pw.size()));
-        HT_TRY(dalloc(c, &c->d_piles, c->piles.size()));
+        HT_TRY(dalloc(c, &c->d_piles, tf.size()));
         HT_CUDA(c, cudaMemcpyAsync(c->pile_node, pn.data(), pn.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
         HT_CUDA(c, cudaMemcpyAsync(c->pile_off, po.data(), po.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
         HT_CUDA(c, cudaMemcpyAsync(c->pile_src, ps.data(), ps.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
         HT_CUDA(c, cudaMemcpyAsync(c->pile_w, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        HT_CUDA(c, cudaMemcpyAsync(c->d_piles, c->piles.data(), c->piles.size() * sizeof(ht_line_src),
+        HT_CUDA(c, cudaMemcpyAsync(c->d_piles, tf.data(), tf.size() * sizeof(ht_line_src),
                                    cudaMemcpyHostToDevice, c->stream));
     }
     HT_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -835,6 +881,27 @@ int ht_add_line_sources(ht_ctx* c, int n, const ht_line_src* src) {
         HT_TRY(line_weights(c, s.x, s.y, s.z_top, s.z_bot, probe, "line source"));
     }
     c->piles.insert(c->piles.end(), src, src + n);
+    c->loads_dirty = true;
+    return HT_OK;
+}
+
+int ht_add_box_sources(ht_ctx* c, int n, const ht_box_src* b) {
+    if (!c || n < 0 || (n > 0 && !b)) return HT_EINVAL;
+    const ht_mesh& m = c->mesh;
+    const double eps = 1e-9 * std::max(m.Lx, std::max(m.Ly, m.Lz));
+    for (int i = 0; i < n; ++i) {
+        const ht_box_src& s = b[i];
+        const double v[9] = {s.x0, s.x1, s.y0, s.y1, s.z, s.mean, s.amp, s.period, s.phase};
+        for (double e : v)
+            if (!isfinite(e)) return fail(c, HT_EINVAL, "box source %d: non-finite parameter", i);
+        if (!(s.x1 > s.x0) || !(s.y1 > s.y0) || !(s.period > 0))
+            return fail(c, HT_EINVAL, "box source %d: needs x1 > x0, y1 > y0 and period > 0", i);
+        if (!(s.z >= m.z0 - eps && s.z <= m.z0 + m.Lz + eps))
+            return fail(c, HT_EINVAL, "box source %d: plane z = %g lies outside the box", i, s.z);
+        std::map<long long, double> probe;
+        HT_TRY(box_weights(c, s, probe));
+    }
+    c->boxes.insert(c->boxes.end(), b, b + n);
     c->loads_dirty = true;
     return HT_OK;
 }

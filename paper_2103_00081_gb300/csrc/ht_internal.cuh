@@ -130,6 +130,7 @@ struct ht_ctx {
     double* F[2] = {nullptr, nullptr};       // loads at the current step time
     double* extra[2] = {nullptr, nullptr};
     std::vector<ht_line_src> piles;
+    std::vector<ht_box_src> boxes;
     std::vector<ht_well> wells;
     bool loads_dirty = true;
     int n_pile_nodes = 0;

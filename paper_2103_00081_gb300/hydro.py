@@ -99,6 +99,15 @@ class Simulator:
             tp = keep[1].ctypes.data_as(c_void_p) if keep[1] is not None else None
         return self._check(self._lib.ht_set_state(self._h, hp, tp, float(t), int(dev)))
 
+    def add_box_sources(self, rows):
+        """Rows of (x0, x1, y0, y1, z, mean, amp, period, phase): heat flux in
+        W/m^2 over a horizontal rectangle snapped to cell faces."""
+        rows = np.asarray(rows, dtype=np.float64).reshape(-1, 9)
+        if rows.shape[0] == 0:
+            return L.HT_OK
+        arr = (L.BoxSrc * rows.shape[0])(*[L.BoxSrc(*map(float, r)) for r in rows])
+        return self._check(self._lib.ht_add_box_sources(self._h, rows.shape[0], arr))
+
     def add_line_sources(self, rows):
         rows = np.asarray(rows, dtype=np.float64).reshape(-1, 8)
         if rows.shape[0] == 0:
@@ -207,6 +216,7 @@ class Simulator:
                 s.set_bc(field, face, typ, val)
         s.add_line_sources(sc.piles)
         s.add_wells(sc.wells)
+        s.add_box_sources(getattr(sc, "boxes", np.zeros((0, 9))))
         s.set_state(sc.h0, sc.T0, 0.0)
         if solver:
             s.set_solver(**solver)

@@ -261,6 +261,50 @@ def test_fused_two_pass_bicgstab_steps_match_oracle(Sim, case, mixed):
             assert abs(st["iters_heat"] - st_ref["iters_heat"]) <= max(2, 0.1 * st_ref["iters_heat"])
 
 
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4], CASES[5]], ids=_ids)
+def test_box_heat_sources_match_oracle(Sim, case):
+    """Box heat sources (flux over horizontal rectangles snapped to cell
+    faces, on interior planes and on the natural top and bottom faces): the
+    heat right-hand side to 1e-12 and three steps to the forward-error bound."""
+    p, nx, ny, nz, seed = case
+    sc = S.random_small(seed, nx, ny, nz, p, n_piles=2, n_wells=1, n_boxes=4, faces_temp=(0, 1, 2))
+    o = fem.OracleSim(sc)
+    tol = 1e-13
+    sim = Sim.from_scenario(sc, tol=tol, max_iter=50000)
+    _close(sim.rhs(S.TEMP, sc.dt), o.heat_rhs(sc.dt, sc.dt, o.h))
+    for _ in range(3):
+        h_prev, T_prev, t1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP), o.t + sc.dt
+        st = sim.step(sc.dt)
+        o.step(sc.dt)
+        h1, T1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP)
+        tol_h, tol_T = _fwd_tol(o, sc.dt, tol)
+        assert st["res_heat"] <= tol * 1.001
+        assert _rel(h1, o.h) <= tol_h
+        assert _rel(T1, o.T) <= tol_T
+        rh, rT = _backward(o, sc.dt, t1, h_prev, T_prev, h1, T1)
+        assert rh <= 10 * tol and rT <= 10 * tol, (rh, rT)
+
+
+def test_invalid_box_sources_are_rejected(Sim):
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(CASES[0])
+    sim = Sim.from_scenario(sc)
+    H = sc.extent[0] / sc.nx
+    good = [0.0, 3 * H, 0.0, 5.0, 0.0, 1.0, 0.5, 1e6, 0.0]
+    bad = [
+        [3 * H, 0.0] + good[2:],                                  # x1 <= x0
+        [1.1 * H, 1.3 * H] + good[2:],                            # both edges snap to face 1
+        good[:4] + [sc.extent[2] + 1.0] + good[5:],               # plane above the box
+        good[:7] + [0.0, 0.0],                                    # period 0
+        good[:5] + [float("nan")] + good[6:],                     # non-finite flux
+    ]
+    for row in bad:
+        with pytest.raises(RuntimeError) as e:
+            sim.add_box_sources([row])
+        assert e.value.code == L.HT_EINVAL
+    assert sim.add_box_sources([good]) == L.HT_OK
+
+
 @pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[5]], ids=_ids)
 def test_float_float_outer_residual_matches_fp64(Sim, case):
     """The mixed form computes its outer residuals b - A x with the operator
