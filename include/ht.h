@@ -182,6 +182,21 @@ int ht_set_cells(ht_ctx* ctx, const double* K, const double* lambda, const doubl
  * On edges shared by two Dirichlet faces the higher face index wins. */
 int ht_set_bc(ht_ctx* ctx, int field, int face, int type, double value);
 
+/* The same with one value per face node: Dirichlet values, or a normal flux
+ * interpolated by the face's shape functions (F_i += int N_i q_h dS).  Used
+ * for boundary data that vary along a face, such as the hydrostatic side
+ * pressures and the monthly surface temperature of Section 3.3 (re-set
+ * between steps for a time-varying record).  values[n] is a host array in
+ * ascending node order: of the two axes along the face, the lower one
+ * (x before y before z) runs fastest; n must equal the face's node count
+ * (ht_face_nodes).  The array is copied.  ht_set_bc on the face drops the
+ * per-node values.  Errors: HT_EINVAL for a wrong count, a non-finite value
+ * or a type other than HT_BC_DIRICHLET / HT_BC_FLUX. */
+int ht_set_bc_values(ht_ctx* ctx, int field, int face, int type, const double* values, size_t n);
+
+/* Number of nodes on `face` (0..5) of the mesh. */
+int ht_face_nodes(const ht_ctx* ctx, int face, size_t* n);
+
 /* Set the state h, T [nodes] and the time t.  Either pointer may be NULL to
  * keep that field.  on_device selects device vs host pointers. */
 int ht_set_state(ht_ctx* ctx, const double* h, const double* T, double t, int on_device);

@@ -374,6 +374,43 @@ def box_flux(box, t: float) -> float:
     return box[5] + box[6] * math.sin(2.0 * math.pi * t / box[7] + box[8])
 
 
+def face_load_nodal(mesh: Mesh, face: int, q: np.ndarray) -> np.ndarray:
+    """F_i = int_face N_i q_h dS for a normal flux given at the face nodes
+    (ascending node order) and interpolated by the face's shape functions,
+    q_h = sum_j q_j N_j, integrated by (p+1)^2 Gauss points per cell face."""
+    p = mesh.p
+    F = np.zeros(mesh.n_nodes)
+    axis = face // 2
+    t1, t2 = [d for d in range(3) if d != axis]
+    nodes = mesh.face_nodes(face)
+    q = np.asarray(q, dtype=np.float64).reshape(-1)
+    if q.size != nodes.size:
+        raise ValueError(f"face {face} has {nodes.size} nodes, got {q.size} values")
+    qn = np.zeros(mesh.n_nodes)
+    qn[nodes] = q
+    xg, wg = gauss01(p + 1)
+    ncs = (mesh.nx, mesh.ny, mesh.nz)
+    fixed = 0 if face % 2 == 0 else mesh.N[axis] - 1
+    dA = mesh.H[t1] * mesh.H[t2]
+    for c2 in range(ncs[t2]):
+        for c1 in range(ncs[t1]):
+            local = []
+            for b in range(p + 1):
+                for a in range(p + 1):
+                    ijk = [0, 0, 0]
+                    ijk[axis] = fixed
+                    ijk[t1] = p * c1 + a
+                    ijk[t2] = p * c2 + b
+                    local.append((a, b, mesh.node_index(*ijk)))
+            for g2 in range(p + 1):
+                for g1 in range(p + 1):
+                    Ng = [lagrange_value(p, a, xg[g1]) * lagrange_value(p, b, xg[g2]) for a, b, _ in local]
+                    qg = sum(n * qn[nd] for n, (_, _, nd) in zip(Ng, local))
+                    for n, (_, _, nd) in zip(Ng, local):
+                        F[nd] += wg[g1] * wg[g2] * dA * n * qg
+    return F
+
+
 def pile_amplitude(pile, t: float) -> float:
     """q_l(t) = mean + amp sin(2 pi t / period + phase), W/m."""
     return pile[4] + pile[5] * math.sin(2.0 * math.pi * t / pile[6] + pile[7])
@@ -384,7 +421,8 @@ def pile_amplitude(pile, t: float) -> float:
 # ---------------------------------------------------------------------------
 def dirichlet_data(mesh: Mesh, bc: Dict[int, Tuple[int, float]]):
     """Mask and values of Dirichlet nodes; later faces override earlier ones
-    on shared edges."""
+    on shared edges.  A face's value is a scalar or one value per face node
+    in ascending node order (the lower tangential axis fastest)."""
     mask = np.zeros(mesh.n_nodes, dtype=bool)
     g = np.zeros(mesh.n_nodes)
     for face in range(6):
@@ -455,7 +493,8 @@ class OracleSim:
         for f in (HEAD, TEMP):
             for face, (typ, val) in sc.bc.get(f, {}).items():
                 if typ == FLUX:
-                    self.F_static[f] += face_load(m, face, val)
+                    self.F_static[f] += face_load(m, face, val) if np.ndim(val) == 0 else \
+                        face_load_nodal(m, face, val)
         # wells: head source and lumped heat injection term
         self.d_well = np.zeros(m.n_nodes)
         self.Tin_well = np.zeros(m.n_nodes)       # sum d*T_in

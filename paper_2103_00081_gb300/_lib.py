@@ -86,6 +86,8 @@ SIGNATURES = {
     "ht_sizes": (c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t)]),
     "ht_set_cells": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double, c_double]),
     "ht_set_bc": (c_int, [c_void_p, c_int, c_int, c_int, c_double]),
+    "ht_set_bc_values": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_size_t]),
+    "ht_face_nodes": (c_int, [c_void_p, c_int, POINTER(c_size_t)]),
     "ht_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int]),
     "ht_add_line_sources": (c_int, [c_void_p, c_int, POINTER(LineSrc)]),
     "ht_add_wells": (c_int, [c_void_p, c_int, POINTER(Well)]),

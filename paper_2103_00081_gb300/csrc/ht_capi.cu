@@ -224,6 +224,15 @@ double phi_int(int P, int a) {
     return s;
 }
 
+// integral of phi_a phi_b over [0,1] (exact Gauss)
+double phi_phi_int(int P, int a, int b) {
+    double xq[3], wq[3];
+    gauss01(P + 1, xq, wq);
+    double s = 0;
+    for (int q = 0; q <= P; ++q) s += wq[q] * lag(P, a, xq[q]) * lag(P, b, xq[q]);
+    return s;
+}
+
 // 1D boundary integral weight of node i along a direction with nc cells of size H
 double node_int_1d(int P, int nc, double H, int i) {
     double s = 0;
@@ -445,15 +454,42 @@ int finalize_setup(ht_ctx* c) {
             const int ncs[3] = {g.ncx, g.ncy, g.ncz};
             if (c->bc_type[f][face] == HT_BC_DIRICHLET) mask |= 1 << face;
             if (c->bc_type[f][face] == HT_BC_NONE) continue;
+            const std::vector<double>& nodal = c->bc_nodal[f][face];
+            auto face_node = [&](int a, int b) {
+                int ijk[3];
+                ijk[axis] = fixed;
+                ijk[t1] = a;
+                ijk[t2] = b;
+                return ijk[0] + (long long)g.Nx * (ijk[1] + (long long)g.Ny * ijk[2]);
+            };
+            if (c->bc_type[f][face] == HT_BC_FLUX && !nodal.empty()) {
+                // flux interpolated from its face-node values: F_i += sum_j M^face_ij q_j,
+                // the face mass matrix a tensor product of 1D mass matrices per cell
+                const int P = g.P;
+                double M1[2][3][3];
+                for (int a = 0; a <= P; ++a)
+                    for (int b = 0; b <= P; ++b) {
+                        M1[0][a][b] = c->H[t1] * phi_phi_int(P, a, b);
+                        M1[1][a][b] = c->H[t2] * phi_phi_int(P, a, b);
+                    }
+                for (int c2 = 0; c2 < ncs[t2]; ++c2)
+                    for (int c1 = 0; c1 < ncs[t1]; ++c1)
+                        for (int b = 0; b <= P; ++b)
+                            for (int a = 0; a <= P; ++a) {
+                                double sum = 0.0;
+                                for (int b2 = 0; b2 <= P; ++b2)
+                                    for (int a2 = 0; a2 <= P; ++a2)
+                                        sum += M1[0][a][a2] * M1[1][b][b2] *
+                                               nodal[(P * c1 + a2) + (size_t)Nd[t1] * (P * c2 + b2)];
+                                Fs[face_node(P * c1 + a, P * c2 + b)] += sum;
+                            }
+                continue;
+            }
             for (int b = 0; b < Nd[t2]; ++b)
                 for (int a = 0; a < Nd[t1]; ++a) {
-                    int ijk[3];
-                    ijk[axis] = fixed;
-                    ijk[t1] = a;
-                    ijk[t2] = b;
-                    const long long id = ijk[0] + (long long)g.Nx * (ijk[1] + (long long)g.Ny * ijk[2]);
+                    const long long id = face_node(a, b);
                     if (c->bc_type[f][face] == HT_BC_DIRICHLET) {
-                        gv[id] = c->bc_val[f][face];
+                        gv[id] = nodal.empty() ? c->bc_val[f][face] : nodal[a + (size_t)Nd[t1] * b];
                     } else {
                         Fs[id] += c->bc_val[f][face] * node_int_1d(g.P, ncs[t1], c->H[t1], a) *
                                   node_int_1d(g.P, ncs[t2], c->H[t2], b);
@@ -855,6 +891,35 @@ int ht_set_bc(ht_ctx* c, int field, int face, int type, double value) {
     if (!isfinite(value)) return fail(c, HT_EINVAL, "boundary value must be finite");
     c->bc_type[field][face] = type;
     c->bc_val[field][face] = value;
+    c->bc_nodal[field][face].clear();
+    c->bc_dirty = true;
+    c->cheb_dt[field] = -1.0;
+    return HT_OK;
+}
+
+int ht_face_nodes(const ht_ctx* c, int face, size_t* n) {
+    if (!c || !n || face < 0 || face > 5) return HT_EINVAL;
+    const Grid& g = c->grid;
+    const size_t Nd[3] = {(size_t)g.Nx, (size_t)g.Ny, (size_t)g.Nz};
+    const int axis = face / 2;
+    *n = Nd[axis == 0 ? 1 : 0] * Nd[axis == 2 ? 1 : 2];
+    return HT_OK;
+}
+
+int ht_set_bc_values(ht_ctx* c, int field, int face, int type, const double* values, size_t n) {
+    if (!c) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    if (face < 0 || face > 5) return fail(c, HT_EINVAL, "face must be 0..5");
+    if (type != HT_BC_DIRICHLET && type != HT_BC_FLUX)
+        return fail(c, HT_EINVAL, "per-node values need HT_BC_DIRICHLET or HT_BC_FLUX, got %d", type);
+    size_t nf = 0;
+    ht_face_nodes(c, face, &nf);
+    if (!values || n != nf) return fail(c, HT_EINVAL, "face %d has %zu nodes, got %zu values", face, nf, n);
+    for (size_t i = 0; i < n; ++i)
+        if (!isfinite(values[i])) return fail(c, HT_EINVAL, "boundary value %zu is not finite", i);
+    c->bc_type[field][face] = type;
+    c->bc_val[field][face] = 0.0;
+    c->bc_nodal[field][face].assign(values, values + n);
     c->bc_dirty = true;
     c->cheb_dt[field] = -1.0;
     return HT_OK;

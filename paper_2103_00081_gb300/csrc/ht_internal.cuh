@@ -116,6 +116,7 @@ struct ht_ctx {
     // boundary conditions
     int bc_type[2][6] = {{0}};
     double bc_val[2][6] = {{0}};
+    std::vector<double> bc_nodal[2][6];     // per-face-node values (empty: bc_val everywhere)
     int dmask[2] = {0, 0};
     double* g[2] = {nullptr, nullptr};     // nodal Dirichlet values (0 off the mask)
     bool bc_dirty = true;

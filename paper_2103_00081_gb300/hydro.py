@@ -86,7 +86,18 @@ class Simulator:
             float(lam_u), float(cT_u), float(cw), float(Ss)))
 
     def set_bc(self, field, face, typ, value=0.0):
-        return self._check(self._lib.ht_set_bc(self._h, int(field), int(face), int(typ), float(value)))
+        """Boundary condition on a face: a scalar value, or one value per face
+        node in ascending node order (the lower tangential axis fastest)."""
+        if np.ndim(value) == 0:
+            return self._check(self._lib.ht_set_bc(self._h, int(field), int(face), int(typ), float(value)))
+        v = np.ascontiguousarray(value, dtype=np.float64).reshape(-1)
+        return self._check(self._lib.ht_set_bc_values(self._h, int(field), int(face), int(typ),
+                                                      v.ctypes.data, v.size))
+
+    def face_nodes(self, face):
+        n = ctypes.c_size_t()
+        self._check(self._lib.ht_face_nodes(self._h, int(face), ctypes.byref(n)))
+        return n.value
 
     def set_state(self, h=None, T=None, t=0.0):
         dev = _is_torch_cuda(h) or _is_torch_cuda(T)

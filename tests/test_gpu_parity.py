@@ -285,6 +285,70 @@ def test_box_heat_sources_match_oracle(Sim, case):
         assert rh <= 10 * tol and rT <= 10 * tol, (rh, rT)
 
 
+def _nodal_bc_scenario(case):
+    """random_small with boundary data that vary along the faces: per-node
+    Dirichlet heads on x faces and a per-node recharge flux at the bottom;
+    per-node Dirichlet temperatures on the x = x0 face and the top, and a
+    per-node heat flux at the bottom."""
+    p, nx, ny, nz, seed = case
+    sc = S.random_small(seed, nx, ny, nz, p, n_piles=2, n_wells=1)
+    m = fem.Mesh(sc.nx, sc.ny, sc.nz, p, sc.origin, sc.extent)
+    rng = np.random.default_rng(500 + seed)
+
+    def vals(face, lo, hi):
+        return rng.uniform(lo, hi, m.face_nodes(face).size)
+    sc.bc = {S.HEAD: {0: (S.DIRICHLET, vals(0, -0.3, 0.3)), 1: (S.DIRICHLET, vals(1, -0.3, 0.3)),
+                      4: (S.FLUX, vals(4, -1e-7, 1e-7))},
+             S.TEMP: {0: (S.DIRICHLET, vals(0, 14.0, 16.0)), 5: (S.DIRICHLET, vals(5, 10.0, 20.0)),
+                      4: (S.FLUX, vals(4, 0.5, 1.5))}}
+    return sc
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4]], ids=_ids)
+def test_nodal_boundary_values_match_oracle(Sim, case):
+    """Per-face-node Dirichlet values and interpolated per-node fluxes:
+    right-hand sides to 1e-12 and three steps to the forward-error bound."""
+    sc = _nodal_bc_scenario(case)
+    o = fem.OracleSim(sc)
+    tol = 1e-13
+    sim = Sim.from_scenario(sc, tol=tol, max_iter=50000)
+    _close(sim.rhs(S.HEAD, sc.dt), o.head_rhs(sc.dt, sc.dt))
+    _close(sim.rhs(S.TEMP, sc.dt), o.heat_rhs(sc.dt, sc.dt, o.h))
+    for _ in range(3):
+        h_prev, T_prev, t1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP), o.t + sc.dt
+        sim.step(sc.dt)
+        o.step(sc.dt)
+        h1, T1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP)
+        tol_h, tol_T = _fwd_tol(o, sc.dt, tol)
+        assert _rel(h1, o.h) <= tol_h
+        assert _rel(T1, o.T) <= tol_T
+        rh, rT = _backward(o, sc.dt, t1, h_prev, T_prev, h1, T1)
+        assert rh <= 10 * tol and rT <= 10 * tol, (rh, rT)
+    # ht_set_bc on a face drops its per-node values
+    sim.set_bc(S.TEMP, 5, S.DIRICHLET, 12.0)
+    T = sim.get_field(S.TEMP)
+    o.sc.bc[S.TEMP][5] = (S.DIRICHLET, 12.0)
+    o2 = fem.OracleSim(o.sc)
+    o2.h, o2.T, o2.t = sim.get_field(S.HEAD), T, sim.time
+    _close(sim.rhs(S.TEMP, sc.dt), o2.heat_rhs(sc.dt, o2.t + sc.dt, o2.h))
+
+
+def test_invalid_nodal_boundary_values_are_rejected(Sim):
+    from paper_2103_00081_gb300 import _lib as L
+    sc = _scenario(CASES[1])
+    sim = Sim.from_scenario(sc)
+    Nx, Ny, Nz = sc.node_dims
+    assert [sim.face_nodes(f) for f in range(6)] == [Ny * Nz] * 2 + [Nx * Nz] * 2 + [Nx * Ny] * 2
+    for args in [(S.HEAD, 0, S.DIRICHLET, np.zeros(Ny * Nz - 1)),        # wrong count
+                 (S.HEAD, 2, S.DIRICHLET, np.zeros(Ny * Nz)),            # count of another face
+                 (S.TEMP, 4, S.NONE, np.zeros(Nx * Ny)),                 # no values for "none"
+                 (S.TEMP, 4, S.FLUX, np.full(Nx * Ny, np.inf))]:         # non-finite
+        with pytest.raises(RuntimeError) as e:
+            sim.set_bc(*args)
+        assert e.value.code == L.HT_EINVAL
+    assert sim.set_bc(S.TEMP, 4, S.FLUX, np.ones(Nx * Ny)) == L.HT_OK
+
+
 def test_invalid_box_sources_are_rejected(Sim):
     from paper_2103_00081_gb300 import _lib as L
     sc = _scenario(CASES[0])

@@ -463,3 +463,45 @@ def test_energy_balance_with_box_sources():
             expect += fem.box_flux(bx, sc.dt) * (i1 - i0) * o.mesh.H[0] * (j1 - j0) * o.mesh.H[1]
         assert abs(expect) > 0
         assert abs(stored - sc.dt * expect) <= 1e-10 * abs(sc.dt * expect)
+
+
+def test_nodal_face_flux_closed_forms():
+    """A normal flux given per face node: a constant reduces to the uniform
+    face load, and a flux linear along the face integrates to the closed-form
+    total and first moment (the face basis reproduces linear functions)."""
+    for p in (1, 2):
+        m = fem.Mesh(4, 3, 5, p, (1.0, 2.0, -3.0), (8.0, 6.0, 5.0))
+        x, y, z = m.node_xyz()
+        for face in range(6):
+            nodes = m.face_nodes(face)
+            np.testing.assert_allclose(fem.face_load_nodal(m, face, np.full(nodes.size, 0.7)),
+                                       fem.face_load(m, face, 0.7), rtol=0, atol=1e-13)
+        face = 2                                   # y = y0; tangential axes x (fastest), z
+        nodes = m.face_nodes(face)
+        q = 0.5 + 0.25 * x[nodes] - 0.4 * z[nodes]
+        F = fem.face_load_nodal(m, face, q)
+        xa, xb, za, zb = 1.0, 9.0, -3.0, 2.0
+        total = 0.5 * (xb - xa) * (zb - za) + 0.25 * 0.5 * (xb ** 2 - xa ** 2) * (zb - za) \
+            - 0.4 * 0.5 * (zb ** 2 - za ** 2) * (xb - xa)
+        first = 0.5 * 0.5 * (xb ** 2 - xa ** 2) * (zb - za) + 0.25 * (xb ** 3 - xa ** 3) / 3 * (zb - za) \
+            - 0.4 * 0.25 * (xb ** 2 - xa ** 2) * (zb ** 2 - za ** 2)
+        assert abs(F.sum() - total) <= 1e-12 * abs(total)
+        assert abs((F * x).sum() - first) <= 1e-12 * abs(first)
+        assert np.all(F[np.setdiff1d(np.arange(m.n_nodes), nodes)] == 0.0)
+
+
+def test_linear_head_from_nodal_dirichlet_faces_is_exact():
+    """Per-node Dirichlet values on all six faces equal to a linear head,
+    uniform K and no storage: the discrete solution is that linear head at
+    every node, which fails if face values land on the wrong nodes."""
+    for p in (1, 2):
+        sc = S.random_small(9, 4, 3, 5, p, n_piles=0, n_wells=0)
+        sc.K = np.full(sc.n_cells, 2e-5)
+        sc.Ss = 0.0
+        m = fem.Mesh(sc.nx, sc.ny, sc.nz, p, sc.origin, sc.extent)
+        x, y, z = m.node_xyz()
+        h_lin = 0.3 + 0.02 * x - 0.05 * y + 0.07 * z
+        sc.bc = {S.HEAD: {f: (S.DIRICHLET, h_lin[m.face_nodes(f)]) for f in range(6)}, S.TEMP: {}}
+        o = fem.OracleSim(sc)
+        o.step(sc.dt)
+        np.testing.assert_allclose(o.h, h_lin, rtol=0, atol=1e-12)
