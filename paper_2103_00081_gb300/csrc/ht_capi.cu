@@ -505,9 +505,7 @@ int finalize_setup(ht_ctx* c) {
     for (const ht_well& w : c->wells) {
         std::map<long long, double> lw;
         HT_TRY(well_weights(c, w, lw));
-        const double L = std::min(w.z_top, c->mesh.z0 + c->mesh.Lz) - std::max(w.z_bot, c->mesh.z0);
         const double qlin = w.Q / (w.z_top - w.z_bot);
-        (void)L;
         for (auto& kv : lw) {
             Fs0[kv.first] += qlin * kv.second;
             // Dirichlet rows of the heat system stay identity rows
