@@ -124,8 +124,10 @@ class Clocks:
 
 
 def apply_flops_per_node(order):
-    """Algorithmic FLOPs of one head-operator apply per node (fast-
-    diagonalisation sum factorisation, counted in the design doc)."""
+    """Algorithmic FLOPs of one head-operator apply per node: per cell, the
+    six one-dimensional sweeps of the fast diagonalisation (12 n^4 flops,
+    n = p + 1) plus the scaling and accumulation of the n^3 local values,
+    spread over the nodes of a cell (one per Q1 cell, eight per Q2 cell)."""
     if order == 1:
         return 242.0
     return 143.0
