@@ -606,3 +606,150 @@ class OracleSim:
                     g[:, 1] += he[:, l] * vx * dy * vz / m.H[1]
                     g[:, 2] += he[:, l] * vx * vy * dz / m.H[2]
         return (-self.K[:, None] * g).T.copy()
+
+
+# ---------------------------------------------------------------------------
+# Selected rows at any mesh size
+# ---------------------------------------------------------------------------
+def cells_of_node(mesh: Mesh, node: int):
+    """(cell, local index) for every cell that holds the node."""
+    p = mesh.p
+    n1 = p + 1
+    ijk = (node % mesh.N[0], (node // mesh.N[0]) % mesh.N[1], node // (mesh.N[0] * mesh.N[1]))
+    per_axis = []
+    for d, nc in enumerate((mesh.nx, mesh.ny, mesh.nz)):
+        opts = []
+        for c in range(max(0, ijk[d] // p - 1), min(nc - 1, ijk[d] // p) + 1):
+            a = ijk[d] - p * c
+            if 0 <= a <= p:
+                opts.append((c, a))
+        per_axis.append(opts)
+    out = []
+    for cz, c3 in per_axis[2]:
+        for cy, b in per_axis[1]:
+            for cx, a in per_axis[0]:
+                out.append((cx + mesh.nx * (cy + mesh.ny * cz), a + n1 * (b + n1 * c3)))
+    return out
+
+
+class RowOracle:
+    """Rows of the constrained operators A0 and of the lifted right-hand
+    sides b of one step at selected nodes, for meshes too large to assemble.
+
+    The definitions are those of OracleSim (the same element matrices from
+    shape functions at the Gauss points, the same loads, Dirichlet rows as
+    identity rows and Dirichlet columns moved to the right-hand side), but
+    each requested row is summed cell by cell over the cells that hold its
+    node.  Every row also returns the sum of the absolute values of its
+    terms, the scale of its rounding error.
+    """
+
+    def __init__(self, sc):
+        self.sc = sc
+        m = Mesh(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent)
+        self.mesh = m
+        self.N, self.G, self.W = reference_element(sc.order, m.H)
+        self.Me = element_mass(self.N, self.W)
+        self.Ke = element_stiffness(self.G, self.W)
+        nc = m.n_cells
+        self.K = np.asarray(sc.K, dtype=np.float64)
+        self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, sc.lam))
+        self.cT_c = np.asarray(sc.cT_cells if sc.cT_cells is not None else np.full(nc, sc.cT))
+        self.cw, self.Ss = sc.cw, sc.Ss
+        self.dmask, self.gval, self.F_static = {}, {}, {}
+        for f in (HEAD, TEMP):
+            self.dmask[f], self.gval[f] = dirichlet_data(m, sc.bc.get(f, {}))
+            F = np.zeros(m.n_nodes)
+            for face, (typ, val) in sc.bc.get(f, {}).items():
+                if typ == FLUX:
+                    F += face_load(m, face, val) if np.ndim(val) == 0 else face_load_nodal(m, face, val)
+            self.F_static[f] = F
+        self.d_well = np.zeros(m.n_nodes)
+        self.Tin_well = np.zeros(m.n_nodes)
+        wells = np.asarray(sc.wells, dtype=np.float64)
+        for wl in wells.reshape(-1, wells.shape[-1] if wells.size else 7):
+            L = abs(wl[2] - wl[3])
+            if L <= 0:
+                continue
+            for node, wv in well_weights(m, wl).items():
+                self.F_static[HEAD][node] += wl[4] / L * wv
+                if wl[4] > 0:
+                    self.d_well[node] += self.cw * wl[4] / L * wv
+                    self.Tin_well[node] += self.cw * wl[4] / L * wv * wl[5]
+        self.piles = np.asarray(sc.piles, dtype=np.float64).reshape(-1, 8)
+        self.pile_w = [line_weights(m, pl[0], pl[1], pl[2], pl[3]) for pl in self.piles]
+        self.boxes = np.asarray(getattr(sc, "boxes", np.zeros((0, 9))), dtype=np.float64).reshape(-1, 9)
+        self.box_w = [box_weights(m, bx) for bx in self.boxes]
+
+    # -- element matrices of one cell ------------------------------------------
+    def _advection(self, c, h):
+        qf = -self.K[c] * np.einsum("l,qld->qd", h[self.mesh.conn[c]], self.G)
+        qg = np.einsum("qd,qmd->qm", qf, self.G)
+        return self.cw * np.einsum("q,ql,qm->lm", self.W, self.N, qg)
+
+    def _cell_matrix(self, field, c, dt, h=None, mass_only=False):
+        if field == HEAD:
+            return self.Ss * self.Me if mass_only else self.Ss * self.Me + dt * self.K[c] * self.Ke
+        if mass_only:
+            return self.cT_c[c] * self.Me
+        return self.cT_c[c] * self.Me + dt * self.lam_c[c] * self.Ke + dt * self._advection(c, h)
+
+    def _row(self, field, i, dt, x, cols, h=None, mass_only=False):
+        """sum_j A_ij x_j over the columns j selected by cols ('all', 'free'
+        or 'dirichlet'), with the sum of |A_ij x_j|."""
+        mask = self.dmask[field]
+        s = a = 0.0
+        for c, l in cells_of_node(self.mesh, i):
+            nodes = self.mesh.conn[c]
+            keep = np.ones(nodes.size, dtype=bool) if cols == "all" else \
+                (~mask[nodes] if cols == "free" else mask[nodes])
+            terms = self._cell_matrix(field, c, dt, h, mass_only)[l] * x[nodes] * keep
+            s += terms.sum()
+            a += np.abs(terms).sum()
+        if field == TEMP and not mass_only and (cols == "all" or (cols == "free") != mask[i]):
+            t = dt * self.d_well[i] * x[i]
+            s += t
+            a += abs(t)
+        return s, a
+
+    # -- rows of A0 x and of b ----------------------------------------------------
+    def apply_rows(self, field, dt, x, rows, h=None):
+        """(A0 x)_i: x_i on Dirichlet rows, the free-column sum elsewhere.
+        The heat operator takes the Darcy flux of the head h."""
+        x = np.asarray(x, dtype=np.float64)
+        y, a = np.zeros(len(rows)), np.zeros(len(rows))
+        for k, i in enumerate(rows):
+            if self.dmask[field][i]:
+                y[k], a[k] = x[i], abs(x[i])
+            else:
+                y[k], a[k] = self._row(field, i, dt, x, "free", h)
+        return y, a
+
+    def load(self, field, t, i):
+        """F_i(t): face fluxes, wells, and for heat the piles and boxes."""
+        F = self.F_static[field][i]
+        if field == TEMP:
+            F += self.Tin_well[i]
+            for pl, wts in zip(self.piles, self.pile_w):
+                F += pile_amplitude(pl, t) * wts.get(i, 0.0)
+            for bx, wts in zip(self.boxes, self.box_w):
+                F += box_flux(bx, t) * wts.get(i, 0.0)
+        return F
+
+    def rhs_rows(self, field, dt, t1, state, rows, h=None):
+        """b_i of the step from the state (h^n or T^n) to t1: g_i on
+        Dirichlet rows, else (c M state)_i + dt F_i(t1) - sum_{j in D} A_ij g_j
+        (c = S_s for head, c_T for heat; the heat operator at the head h)."""
+        state = np.asarray(state, dtype=np.float64)
+        g = self.gval[field]
+        b, a = np.zeros(len(rows)), np.zeros(len(rows))
+        for k, i in enumerate(rows):
+            if self.dmask[field][i]:
+                b[k], a[k] = g[i], abs(g[i])
+                continue
+            ms, ma = self._row(field, i, dt, state, "all", mass_only=True)
+            ls, la = self._row(field, i, dt, g, "dirichlet", h)
+            F = dt * self.load(field, t1, i)
+            b[k] = ms + F - ls
+            a[k] = ma + abs(F) + la
+        return b, a

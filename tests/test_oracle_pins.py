@@ -505,3 +505,44 @@ def test_linear_head_from_nodal_dirichlet_faces_is_exact():
         o = fem.OracleSim(sc)
         o.step(sc.dt)
         np.testing.assert_allclose(o.h, h_lin, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("case", [(1, 5, 4, 3, 11), (2, 3, 4, 2, 12)])
+@pytest.mark.parametrize("nodal", [False, True])
+def test_row_oracle_equals_the_assembled_oracle_at_every_row(case, nodal):
+    """The row-wise oracle (used to check meshes too large to assemble) gives
+    the assembled oracle's A0 x and lifted b at every row: piles, wells, box
+    sources, per-cell thermal coefficients, and optionally per-node
+    boundary data."""
+    p, nx, ny, nz, seed = case
+    sc = S.random_small(seed, nx, ny, nz, p, n_piles=2, n_wells=2, n_boxes=2, per_cell_thermal=True,
+                        faces_temp=(0, 2, 5))
+    if nodal:
+        m = fem.Mesh(nx, ny, nz, p, sc.origin, sc.extent)
+        rng = np.random.default_rng(seed)
+        sc.bc[S.HEAD][1] = (S.DIRICHLET, rng.uniform(-1, 1, m.face_nodes(1).size))
+        sc.bc[S.TEMP][4] = (S.FLUX, rng.uniform(0, 2, m.face_nodes(4).size))
+    o = fem.OracleSim(sc)
+    r = fem.RowOracle(sc)
+    rows = list(range(sc.n_nodes))
+    x = np.random.default_rng(1).standard_normal(sc.n_nodes)
+    h = np.random.default_rng(2).standard_normal(sc.n_nodes)
+    dt, t1 = sc.dt, 1.7 * sc.dt
+    for (got, scale), ref in [(r.apply_rows(S.HEAD, dt, x, rows), o.apply_head(x, dt)),
+                              (r.apply_rows(S.TEMP, dt, x, rows, h), o.apply_heat(x, h, dt)),
+                              (r.rhs_rows(S.HEAD, dt, t1, o.h, rows), o.head_rhs(dt, t1)),
+                              (r.rhs_rows(S.TEMP, dt, t1, o.T, rows, h), o.heat_rhs(dt, t1, h))]:
+        assert np.all(np.abs(got - ref) <= 1e-13 * scale + 1e-300)
+        assert np.all(scale >= np.abs(ref) * (1 - 1e-12))
+
+
+def test_cells_of_node_lists_each_holding_cell_once():
+    for p in (1, 2):
+        m = fem.Mesh(3, 2, 2, p, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+        seen = {}
+        for c in range(m.n_cells):
+            for l, nd in enumerate(m.conn[c]):
+                seen.setdefault(int(nd), set()).add((c, l))
+        for nd in range(m.n_nodes):
+            got = fem.cells_of_node(m, nd)
+            assert len(got) == len(set(got)) and set(got) == seen[nd]
