@@ -31,8 +31,12 @@ sum factorisation, no blocking, then a sparse direct solve):
 Parity pins (tests/test_oracle_pins.py) tie this code to closed forms: the 1D
 Q1/Q2 mass and stiffness matrices, exact symbolic integrals on one cell,
 discrete eigenmode decay, exactness for linear heads, energy balance, the
-erfc and Ogata-Banks 1D solutions and manufactured-solution convergence
-orders.
+erfc and Ogata-Banks 1D solutions, manufactured-solution convergence
+orders, and the moments of the box-source and per-node face loads.
+
+RowOracle evaluates the same definitions row by row (cell by cell over the
+cells holding a node) for meshes too large to assemble; it is pinned to the
+assembled form at every row of small meshes.
 """
 from __future__ import annotations
 
