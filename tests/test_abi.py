@@ -50,3 +50,31 @@ def test_invalid_mesh_is_rejected_before_touching_the_device(lib):
     assert b"order" in lib.ht_last_error(None)
     bad = _lib.Mesh(0, 4, 4, 1, 0, 0, 0, 1, 1, 1)
     assert lib.ht_create(ctypes.byref(h), ctypes.byref(bad), 0, None) == _lib.HT_EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: loading a library that is not there raises."""
+    from paper_2103_00081_gb300 import _lib
+    with pytest.raises(ImportError):
+        _lib.load(str(tmp_path / "libht.so"))
+
+
+def test_struct_layouts_match_the_header():
+    """The ctypes structures have the field counts and sizes of include/ht.h."""
+    from paper_2103_00081_gb300 import _lib
+    txt = open(os.path.join(ROOT, "include", "ht.h")).read()
+
+    def fields(name):
+        m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", txt)
+        body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+        n = 0
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if decl:
+                n += len(decl.split(None, 1)[1].split(","))
+        return n
+    for cname, cls in (("ht_mesh", _lib.Mesh), ("ht_line_src", _lib.LineSrc), ("ht_well", _lib.Well),
+                       ("ht_box_src", _lib.BoxSrc), ("ht_solver_opts", _lib.SolverOpts),
+                       ("ht_step_stats", _lib.StepStats), ("ht_profile_stats", _lib.ProfileStats)):
+        assert fields(cname) == len(cls._fields_), cname
+    assert ctypes.sizeof(_lib.BoxSrc) == 9 * 8 and ctypes.sizeof(_lib.LineSrc) == 8 * 8
