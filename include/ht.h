@@ -42,7 +42,8 @@ extern "C" {
 #define HT_ECUDA (-3)       /* a CUDA runtime call failed */
 #define HT_ENOCONV (-4)     /* Krylov solve hit max_iter before the tolerance */
 #define HT_EBREAKDOWN (-5)  /* BiCGStab breakdown that a restart did not cure */
-#define HT_ETIMEOUT (-6)    /* a bounded device wait gave up */
+#define HT_ETIMEOUT (-6)    /* reserved for a bounded device wait that gives up; no current kernel
+                               waits on another CTA or launch, so no call returns it */
 
 enum { HT_HEAD = 0, HT_TEMP = 1, HT_QX = 2, HT_QY = 3, HT_QZ = 4 };
 enum { HT_BC_NONE = 0, HT_BC_DIRICHLET = 1, HT_BC_FLUX = 2 };
