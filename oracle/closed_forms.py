@@ -13,6 +13,10 @@ paper's equations reduce to in a special case:
                         (Eq. 3 / Eq. 4 on a uniform mesh).
 * ``line_source_e1`` -- continuous infinite line source in a still medium
                         (exponential integral E1).
+* ``moving_line_source`` -- the same line source in a uniform groundwater flow
+                        (the moving infinite line source of Diao, Li and Fang,
+                        2004), and its steady limit with the modified Bessel
+                        function K0.
 """
 from __future__ import annotations
 
@@ -56,3 +60,30 @@ def line_source_e1(r, t, ql, lam, a):
     """dT = q_l / (4 pi lambda) * E1(r^2 / (4 a t)) for a continuous infinite
     line source of strength q_l (W/m) switched on at t = 0."""
     return ql / (4.0 * math.pi * lam) * special.exp1(np.asarray(r) ** 2 / (4.0 * a * t))
+
+
+def moving_line_source(x, y, t, ql, lam, a, U):
+    """dT(x, y, t) = q_l / (4 pi lambda) exp(U x / (2 a))
+    * int_{r^2/(4 a t)}^inf exp(-psi - U^2 r^2 / (16 a^2 psi)) / psi dpsi,
+    r^2 = x^2 + y^2, for a line source at the origin switched on at t = 0 in
+    a medium of diffusivity a whose heat moves at U along +x (U = c_w q / c_T
+    for a Darcy flux q).  With U = 0 it is line_source_e1."""
+    from scipy import integrate
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    y = np.atleast_1d(np.asarray(y, dtype=np.float64))
+    out = np.empty(np.broadcast(x, y).shape)
+    for k, (xx, yy) in enumerate(np.broadcast(x, y)):
+        r2 = xx * xx + yy * yy
+        c = U * U * r2 / (16.0 * a * a)
+        val, _ = integrate.quad(lambda s: math.exp(-s - c / s) / s, r2 / (4.0 * a * t), np.inf,
+                                epsabs=0.0, epsrel=1e-12, limit=200)
+        out.flat[k] = ql / (4.0 * math.pi * lam) * math.exp(U * xx / (2.0 * a)) * val
+    return out
+
+
+def moving_line_source_steady(x, y, ql, lam, a, U):
+    """t -> infinity limit: q_l / (2 pi lambda) exp(U x / (2 a)) K0(U r / (2 a))."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    r = np.sqrt(x * x + y * y)
+    return ql / (2.0 * math.pi * lam) * np.exp(U * x / (2.0 * a)) * special.k0(U * r / (2.0 * a))

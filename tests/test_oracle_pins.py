@@ -592,3 +592,54 @@ def test_response_decays_monotonically_with_distance_from_a_pile():
     r, T, _ = _line_source_run(40, 20, 30 * 86400.0)
     assert np.all(np.diff(T) < 0.0)
     assert T[0] > 0.0
+
+
+def test_moving_line_source_closed_form_limits():
+    """The moving-line-source integral reduces to E1 without flow and to the
+    steady K0 form at long times."""
+    lam, cT, U = 1.93, 2.654e6, 1.575e-6
+    a = lam / cT
+    x, y = np.array([2.0, -3.0, 0.0, 1.0]), np.array([0.5, 1.0, 2.0, -1.5])
+    t = 30 * 86400.0
+    np.testing.assert_allclose(cf.moving_line_source(x, y, t, 10.0, lam, a, 0.0),
+                               cf.line_source_e1(np.hypot(x, y), t, 10.0, lam, a), rtol=1e-10)
+    np.testing.assert_allclose(cf.moving_line_source(x, y, 1e14, 10.0, lam, a, U),
+                               cf.moving_line_source_steady(x, y, 10.0, lam, a, U), rtol=1e-8)
+
+
+def test_line_source_in_uniform_flow_converges_to_the_moving_line_source():
+    """A full-height line source of 10 W/m in a uniform Darcy flux
+    q = 1e-6 m/s along x (a linear head, which Q1 reproduces exactly), 30 d:
+    the oracle approaches the moving-line-source solution, U = c_w q / c_T,
+    downstream and to the side, with the error falling as H and dt halve;
+    the plume is carried downstream."""
+    L, Lz, grad, K = 30.0, 2.0, 0.01, 1e-4
+    t_end = 30 * 86400.0
+    pts = [(2.0, 0.0), (3.0, 0.0), (4.0, 0.0), (0.0, 2.0)]
+    errs, temps = [], []
+    for n, steps in ((30, 10), (60, 20)):
+        sc = S.config1(nx=n, ny=n, nz=1, order=1, n_steps=steps)
+        sc.extent = (L, L, Lz)
+        sc.K = np.full(sc.n_cells, K)
+        sc.h0 = np.zeros(sc.n_nodes)
+        sc.T0 = np.zeros(sc.n_nodes)
+        sc.bc = {S.HEAD: {0: (S.DIRICHLET, grad * L), 1: (S.DIRICHLET, 0.0)},
+                 S.TEMP: {f: (S.DIRICHLET, 0.0) for f in (0, 1, 2, 3)}}
+        sc.piles = np.array([[L / 2, L / 2, Lz, 0.0, 10.0, 0.0, 1e9, 0.0]])
+        sc.dt = t_end / steps
+        o = fem.OracleSim(sc)
+        for _ in range(steps):
+            o.step(sc.dt)
+        x, y, z = o.mesh.node_xyz()
+        U = sc.cw * K * grad / sc.cT
+        a = sc.lam / sc.cT
+        got = []
+        for px, py in pts + [(-2.0, 0.0)]:
+            got.append(o.T[np.nonzero((np.abs(x - L / 2 - px) < 1e-9) & (np.abs(y - L / 2 - py) < 1e-9)
+                                      & (z == 0.0))[0][0]])
+        ex = cf.moving_line_source([p[0] for p in pts], [p[1] for p in pts], t_end, 10.0, sc.lam, a, U)
+        errs.append(np.abs(np.array(got[:-1]) - ex) / ex)
+        temps.append(got)
+    assert np.all(errs[1][:3] < 0.05) and errs[1][3] < 0.15, errs[1]
+    assert np.all(errs[0] > 1.6 * errs[1]), errs
+    assert temps[1][0] > 10.0 * temps[1][-1]     # downstream of the pile >> upstream
