@@ -643,3 +643,29 @@ def test_line_source_in_uniform_flow_converges_to_the_moving_line_source():
     assert np.all(errs[1][:3] < 0.05) and errs[1][3] < 0.15, errs[1]
     assert np.all(errs[0] > 1.6 * errs[1]), errs
     assert temps[1][0] > 10.0 * temps[1][-1]     # downstream of the pile >> upstream
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_dirichlet_lift_satisfies_the_unconstrained_free_rows_and_reactions_close_the_balance(p):
+    """After a step with Dirichlet faces, the free rows of the unconstrained
+    systems hold exactly: R = A u^{n+1} - c M u^n - dt F vanishes off the
+    Dirichlet nodes (so lifting b = F - A g_D was done right), u^{n+1} = g on
+    them, and the boundary reactions R_D close the balance: with 1^T K = 0,
+    S_s 1^T M (h^{n+1} - h^n) = dt 1^T F_h + sum_D R_D for the head."""
+    sc = S.random_small(21, 4, 3, 3, p, n_piles=2, n_wells=2)
+    o = fem.OracleSim(sc)
+    h0, T0 = o.h.copy(), o.T.copy()
+    t1 = sc.dt
+    o.step(sc.dt)
+    for field, u0, u1, A, cM in ((S.HEAD, h0, o.h, o.head_matrix(sc.dt), sc.Ss * o.M),
+                                 (S.TEMP, T0, o.T, o.heat_matrix(sc.dt, o.h), o.McT)):
+        F = o.head_load(t1) if field == S.HEAD else o.heat_load(t1)
+        R = A @ u1 - cM @ u0 - sc.dt * F
+        mask = o.dmask[field]
+        scale = np.abs(A) @ np.abs(u1) + np.abs(cM) @ np.abs(u0) + sc.dt * np.abs(F)
+        assert np.all(np.abs(R[~mask]) <= 1e-12 * scale[~mask])
+        np.testing.assert_allclose(u1[mask], o.gval[field][mask], rtol=1e-14, atol=0)
+    R = o.head_matrix(sc.dt) @ o.h - sc.Ss * (o.M @ h0) - sc.dt * o.head_load(t1)
+    stored = sc.Ss * (o.M @ (o.h - h0)).sum()
+    rhs = sc.dt * o.head_load(t1).sum() + R[o.dmask[S.HEAD]].sum()
+    assert abs(stored - rhs) <= 1e-10 * (abs(stored) + abs(rhs))
