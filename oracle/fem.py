@@ -93,13 +93,32 @@ def lagrange_deriv(p: int, a: int, xi: float) -> float:
 # Mesh
 # ---------------------------------------------------------------------------
 class Mesh:
-    """Structured box of nx*ny*nz Lagrange hexahedra of order p."""
+    """Structured box of nx*ny*nz Lagrange hexahedra of order p.
 
-    def __init__(self, nx, ny, nz, p, origin, extent):
+    Cells are uniform along each axis (H = extent / n), or graded with a
+    tensor-product spacing: spacing = (widths along x, along y, along z),
+    one positive width per cell layer, summing to the extent.  A graded mesh
+    has H = None, and every geometric quantity is taken per cell.
+    """
+
+    def __init__(self, nx, ny, nz, p, origin, extent, spacing=None):
         self.nx, self.ny, self.nz, self.p = nx, ny, nz, p
         self.origin = tuple(float(v) for v in origin)
-        self.extent = tuple(float(v) for v in extent)
-        self.H = (self.extent[0] / nx, self.extent[1] / ny, self.extent[2] / nz)
+        ncs = (nx, ny, nz)
+        if spacing is None:
+            self.extent = tuple(float(v) for v in extent)
+            self.H = (self.extent[0] / nx, self.extent[1] / ny, self.extent[2] / nz)
+            self.widths = tuple(np.full(ncs[d], self.H[d]) for d in range(3))
+            self.faces = tuple(self.origin[d] + np.arange(ncs[d] + 1) * self.H[d] for d in range(3))
+        else:
+            self.widths = tuple(np.asarray(spacing[d], dtype=np.float64).reshape(-1) for d in range(3))
+            for d in range(3):
+                if self.widths[d].size != ncs[d] or not np.all(self.widths[d] > 0):
+                    raise ValueError(f"spacing along axis {d} needs {ncs[d]} positive widths")
+            self.extent = tuple(float(self.widths[d].sum()) for d in range(3))
+            self.H = None
+            self.faces = tuple(self.origin[d] + np.concatenate([[0.0], np.cumsum(self.widths[d])])
+                               for d in range(3))
         self.N = (p * nx + 1, p * ny + 1, p * nz + 1)
         self.n_nodes = self.N[0] * self.N[1] * self.N[2]
         self.n_cells = nx * ny * nz
@@ -127,8 +146,35 @@ class Mesh:
 
     def node_xyz(self):
         i, j, k = self.node_ijk()
-        hx, hy, hz = (self.H[d] / self.p for d in range(3))
-        return (self.origin[0] + i * hx, self.origin[1] + j * hy, self.origin[2] + k * hz)
+        if self.H is not None:
+            hx, hy, hz = (self.H[d] / self.p for d in range(3))
+            return (self.origin[0] + i * hx, self.origin[1] + j * hy, self.origin[2] + k * hz)
+        out = []
+        for d, idx in enumerate((i, j, k)):
+            c = np.minimum(idx // self.p, self.widths[d].size - 1)
+            out.append(self.faces[d][c] + (idx - self.p * c) * self.widths[d][c] / self.p)
+        return tuple(out)
+
+    def width(self, d: int, c: int) -> float:
+        """Width of cell layer c along axis d."""
+        return self.H[d] if self.H is not None else float(self.widths[d][c])
+
+    def locate(self, d: int, v: float):
+        """Cell layer along axis d that holds coordinate v (clamped to the
+        mesh) and the local coordinate of v in it."""
+        n = self.widths[d].size
+        if self.H is not None:
+            s = (v - self.origin[d]) / self.H[d]
+            c = int(min(max(math.floor(s), 0), n - 1))
+            return c, s - c
+        c = int(min(max(np.searchsorted(self.faces[d], v, side="right") - 1, 0), n - 1))
+        return c, (v - self.faces[d][c]) / self.widths[d][c]
+
+    def cell_widths(self):
+        """(hx, hy, hz) of every cell: [cells, 3]."""
+        cz, cy, cx = np.meshgrid(np.arange(self.nz), np.arange(self.ny), np.arange(self.nx), indexing="ij")
+        return np.stack([self.widths[0][cx.reshape(-1)], self.widths[1][cy.reshape(-1)],
+                         self.widths[2][cz.reshape(-1)]], axis=1)
 
     def face_nodes(self, face: int) -> np.ndarray:
         i, j, k = self.node_ijk()
@@ -196,16 +242,39 @@ def assemble(mesh: Mesh, coef: np.ndarray, Ke: np.ndarray) -> sp.csr_matrix:
 
 
 def darcy_at_qp(mesh: Mesh, K: np.ndarray, G: np.ndarray, h: np.ndarray) -> np.ndarray:
-    """q = -K_c grad h at every Gauss point of every cell: [cells, q, 3]."""
+    """q = -K_c grad h at every Gauss point of every cell: [cells, q, 3].
+    G is [q, l, d] (one cell size) or [cells, q, l, d] (graded)."""
     he = h[mesh.conn]                                   # [c, l]
-    gh = np.einsum("cl,qld->cqd", he, G)
+    gh = np.einsum("cl,qld->cqd", he, G) if G.ndim == 3 else np.einsum("cl,cqld->cqd", he, G)
     return -K[:, None, None] * gh
 
 
 def advection_elements(N, G, W, qf: np.ndarray, cw: float) -> np.ndarray:
-    """C_e[c, l, m] = sum_q W_q c_w N_l(q) (q_c(q) . grad N_m(q))."""
-    qg = np.einsum("cqd,qmd->cqm", qf, G)               # q . grad N_m
-    return cw * np.einsum("q,ql,cqm->clm", W, N, qg)
+    """C_e[c, l, m] = sum_q W_q c_w N_l(q) (q_c(q) . grad N_m(q)); G, W per
+    cell ([cells, q, l, d], [cells, q]) on graded meshes."""
+    if G.ndim == 3:
+        qg = np.einsum("cqd,qmd->cqm", qf, G)           # q . grad N_m
+        return cw * np.einsum("q,ql,cqm->clm", W, N, qg)
+    qg = np.einsum("cqd,cqmd->cqm", qf, G)
+    return cw * np.einsum("cq,ql,cqm->clm", W, N, qg)
+
+
+def cell_geometry(mesh: Mesh, p: int):
+    """Shape values and per-cell gradients, weights, mass and stiffness
+    element matrices: N [q, l] and G, W, Me, Ke for one cell size, or with a
+    leading cell axis on a graded mesh (reference_element of each cell)."""
+    if mesh.H is not None:
+        N, G, W = reference_element(p, mesh.H)
+        return N, G, W, element_mass(N, W), element_stiffness(G, W)
+    hw = mesh.cell_widths()
+    # reference_element of a cell of widths (hx, hy, hz): the unit cell's
+    # gradients divided by the widths and its weights times the volume
+    N, G1, W1 = reference_element(p, (1.0, 1.0, 1.0))
+    G = G1[None, :, :, :] / hw[:, None, None, :]
+    W = W1[None, :] * np.prod(hw, axis=1)[:, None]
+    Me = np.einsum("cq,ql,qm->clm", W, N, N)
+    Ke = np.einsum("cq,cqld,cqmd->clm", W, G, G)
+    return N, G, W, Me, Ke
 
 
 # ---------------------------------------------------------------------------
@@ -216,10 +285,7 @@ def _column_weights(mesh: Mesh, x: float, y: float):
     p = mesh.p
     out = []
     for d, v in ((0, x), (1, y)):
-        s = (v - mesh.origin[d]) / mesh.H[d]
-        n = (mesh.nx, mesh.ny)[d]
-        c = int(min(max(math.floor(s), 0), n - 1))
-        xi = s - c
+        c, xi = mesh.locate(d, v)
         out.append((c, [lagrange_value(p, a, xi) for a in range(p + 1)]))
     return out
 
@@ -228,14 +294,14 @@ def line_weights(mesh: Mesh, x: float, y: float, z_top: float, z_bot: float) -> 
     """w_i = int_{z_bot}^{z_top} N_i(x, y, z) dz for a vertical segment."""
     p = mesh.p
     (cx, fx), (cy, fy) = _column_weights(mesh, x, y)
-    z0, Hz = mesh.origin[2], mesh.H[2]
+    z0 = mesh.origin[2]
     lo, hi = max(min(z_bot, z_top), z0), min(max(z_bot, z_top), z0 + mesh.extent[2])
     w: Dict[int, float] = {}
     if hi <= lo:
         return w
     xg, wg = gauss01(3)
     for cz in range(mesh.nz):
-        a0, a1 = z0 + cz * Hz, z0 + (cz + 1) * Hz
+        a0, a1, Hz = mesh.faces[2][cz], mesh.faces[2][cz + 1], mesh.width(2, cz)
         s0, s1 = max(a0, lo), min(a1, hi)
         if s1 <= s0:
             continue
@@ -259,10 +325,9 @@ def gaussian_cell_integrals(mesh: Mesh, axis: int, centre: float, sigma: float, 
     p = mesh.p
     xg, wg = gauss01(nq)
     n = (mesh.nx, mesh.ny, mesh.nz)[axis]
-    H, o = mesh.H[axis], mesh.origin[axis]
     out = {}
     for c in range(n):
-        a0 = o + c * H
+        a0, H = mesh.faces[axis][c], mesh.width(axis, c)
         if a0 > centre + 10 * sigma or a0 + H < centre - 10 * sigma:
             continue
         for a in range(p + 1):
@@ -278,12 +343,12 @@ def gaussian_cell_integrals(mesh: Mesh, axis: int, centre: float, sigma: float, 
 def segment_z_integrals(mesh: Mesh, z_top: float, z_bot: float):
     """J[(cz, c)] = int over [z_bot, z_top] of phi_c on cell layer cz."""
     p = mesh.p
-    z0, Hz = mesh.origin[2], mesh.H[2]
+    z0 = mesh.origin[2]
     lo, hi = max(min(z_bot, z_top), z0), min(max(z_bot, z_top), z0 + mesh.extent[2])
     xg, wg = gauss01(3)
     out = {}
     for cz in range(mesh.nz):
-        a0, a1 = z0 + cz * Hz, z0 + (cz + 1) * Hz
+        a0, a1, Hz = mesh.faces[2][cz], mesh.faces[2][cz + 1], mesh.width(2, cz)
         s0, s1 = max(a0, lo), min(a1, hi)
         if s1 <= s0:
             continue
@@ -332,7 +397,7 @@ def face_load(mesh: Mesh, face: int, value: float) -> np.ndarray:
                     ijk[axis] = fixed
                     ijk[t1] = p * c1 + a
                     ijk[t2] = p * c2 + b
-                    F[mesh.node_index(*ijk)] += value * i1[a] * mesh.H[t1] * i1[b] * mesh.H[t2]
+                    F[mesh.node_index(*ijk)] += value * i1[a] * mesh.width(t1, c1) * i1[b] * mesh.width(t2, c2)
     return F
 
 
@@ -345,7 +410,10 @@ def box_snap(mesh: Mesh, box):
     the node plane p * k.
     """
     def nearest(v, d, n):
-        return int(min(max(math.floor((v - mesh.origin[d]) / mesh.H[d] + 0.5), 0), n))
+        if mesh.H is not None:
+            return int(min(max(math.floor((v - mesh.origin[d]) / mesh.H[d] + 0.5), 0), n))
+        dist = np.abs(mesh.faces[d] - v)
+        return int(np.nonzero(dist == dist.min())[0][-1])
     i0, i1 = nearest(box[0], 0, mesh.nx), nearest(box[1], 0, mesh.nx)
     j0, j1 = nearest(box[2], 1, mesh.ny), nearest(box[3], 1, mesh.ny)
     k = nearest(box[4], 2, mesh.nz)
@@ -358,10 +426,10 @@ def box_weights(mesh: Mesh, box) -> Dict[int, float]:
     p = mesh.p
     i0, i1, j0, j1, k = box_snap(mesh, box)
     xg, wg = gauss01(p + 1)
-    Hx, Hy = mesh.H[0], mesh.H[1]
     w: Dict[int, float] = {}
     for cy in range(j0, j1):
         for cx in range(i0, i1):
+            Hx, Hy = mesh.width(0, cx), mesh.width(1, cy)
             for gy in range(p + 1):
                 for gx in range(p + 1):
                     dS = wg[gx] * Hx * wg[gy] * Hy
@@ -395,9 +463,9 @@ def face_load_nodal(mesh: Mesh, face: int, q: np.ndarray) -> np.ndarray:
     xg, wg = gauss01(p + 1)
     ncs = (mesh.nx, mesh.ny, mesh.nz)
     fixed = 0 if face % 2 == 0 else mesh.N[axis] - 1
-    dA = mesh.H[t1] * mesh.H[t2]
     for c2 in range(ncs[t2]):
         for c1 in range(ncs[t1]):
+            dA = mesh.width(t1, c1) * mesh.width(t2, c2)
             local = []
             for b in range(p + 1):
                 for a in range(p + 1):
@@ -474,11 +542,9 @@ class OracleSim:
 
     def __init__(self, sc, solver: str = "direct", tol: float = 1e-14):
         self.sc = sc
-        self.mesh = Mesh(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent)
+        self.mesh = Mesh(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, getattr(sc, "spacing", None))
         m = self.mesh
-        self.N, self.G, self.W = reference_element(sc.order, m.H)
-        self.Me = element_mass(self.N, self.W)
-        self.Ke = element_stiffness(self.G, self.W)
+        self.N, self.G, self.W, self.Me, self.Ke = cell_geometry(m, sc.order)
         nc = m.n_cells
         self.K = np.asarray(sc.K, dtype=np.float64)
         self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, sc.lam))
@@ -597,6 +663,7 @@ class OracleSim:
         p = m.p
         n = p + 1
         he = h[m.conn]
+        hw = m.cell_widths()
         g = np.zeros((m.n_cells, 3))
         for c in range(n):
             for b in range(n):
@@ -606,9 +673,9 @@ class OracleSim:
                                   lagrange_value(p, c, 0.5))
                     dx, dy, dz = (lagrange_deriv(p, a, 0.5), lagrange_deriv(p, b, 0.5),
                                   lagrange_deriv(p, c, 0.5))
-                    g[:, 0] += he[:, l] * dx * vy * vz / m.H[0]
-                    g[:, 1] += he[:, l] * vx * dy * vz / m.H[1]
-                    g[:, 2] += he[:, l] * vx * vy * dz / m.H[2]
+                    g[:, 0] += he[:, l] * dx * vy * vz / hw[:, 0]
+                    g[:, 1] += he[:, l] * vx * dy * vz / hw[:, 1]
+                    g[:, 2] += he[:, l] * vx * vy * dz / hw[:, 2]
         return (-self.K[:, None] * g).T.copy()
 
 
@@ -650,11 +717,9 @@ class RowOracle:
 
     def __init__(self, sc):
         self.sc = sc
-        m = Mesh(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent)
+        m = Mesh(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, getattr(sc, "spacing", None))
         self.mesh = m
-        self.N, self.G, self.W = reference_element(sc.order, m.H)
-        self.Me = element_mass(self.N, self.W)
-        self.Ke = element_stiffness(self.G, self.W)
+        self.N, self.G, self.W, self.Me, self.Ke = cell_geometry(m, sc.order)
         nc = m.n_cells
         self.K = np.asarray(sc.K, dtype=np.float64)
         self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, sc.lam))
@@ -687,16 +752,20 @@ class RowOracle:
 
     # -- element matrices of one cell ------------------------------------------
     def _advection(self, c, h):
-        qf = -self.K[c] * np.einsum("l,qld->qd", h[self.mesh.conn[c]], self.G)
-        qg = np.einsum("qd,qmd->qm", qf, self.G)
-        return self.cw * np.einsum("q,ql,qm->lm", self.W, self.N, qg)
+        G = self.G if self.G.ndim == 3 else self.G[c]
+        W = self.W if self.W.ndim == 1 else self.W[c]
+        qf = -self.K[c] * np.einsum("l,qld->qd", h[self.mesh.conn[c]], G)
+        qg = np.einsum("qd,qmd->qm", qf, G)
+        return self.cw * np.einsum("q,ql,qm->lm", W, self.N, qg)
 
     def _cell_matrix(self, field, c, dt, h=None, mass_only=False):
+        Me = self.Me if self.Me.ndim == 2 else self.Me[c]
+        Ke = self.Ke if self.Ke.ndim == 2 else self.Ke[c]
         if field == HEAD:
-            return self.Ss * self.Me if mass_only else self.Ss * self.Me + dt * self.K[c] * self.Ke
+            return self.Ss * Me if mass_only else self.Ss * Me + dt * self.K[c] * Ke
         if mass_only:
-            return self.cT_c[c] * self.Me
-        return self.cT_c[c] * self.Me + dt * self.lam_c[c] * self.Ke + dt * self._advection(c, h)
+            return self.cT_c[c] * Me
+        return self.cT_c[c] * Me + dt * self.lam_c[c] * Ke + dt * self._advection(c, h)
 
     def _row(self, field, i, dt, x, cols, h=None, mass_only=False):
         """sum_j A_ij x_j over the columns j selected by cols ('all', 'free'

@@ -220,6 +220,8 @@ class Simulator:
     # -- scenario helper -----------------------------------------------------------
     @classmethod
     def from_scenario(cls, sc, device=0, stream=None, **solver):
+        if getattr(sc, "spacing", None) is not None:
+            raise ValueError("the library takes uniform cells along each axis; graded spacing is not supported")
         s = cls(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, device=device, stream=stream)
         s.set_cells(sc.K, sc.lam_cells, sc.cT_cells, sc.lam, sc.cT, sc.cw, sc.Ss)
         for field, faces in sc.bc.items():

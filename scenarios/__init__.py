@@ -71,6 +71,9 @@ class Scenario:
     # horizontal heat-flux rectangles [n, 9]: x0, x1, y0, y1, z, mean, amp,
     # period, phase (W/m^2 into the domain), edges snapped to cell faces
     boxes: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 9)))
+    # optional graded mesh: cell widths along x, y and z (tensor-product
+    # spacing summing to the extent); None for uniform cells
+    spacing: Optional[Tuple[np.ndarray, np.ndarray, np.ndarray]] = None
 
     @property
     def n_cells(self) -> int:
@@ -91,9 +94,17 @@ class Scenario:
         Nx, Ny, Nz = self.node_dims
         x0, y0, z0 = self.origin
         Lx, Ly, Lz = self.extent
-        return (x0 + Lx * np.arange(Nx) / (Nx - 1),
-                y0 + Ly * np.arange(Ny) / (Ny - 1),
-                z0 + Lz * np.arange(Nz) / (Nz - 1))
+        if self.spacing is None:
+            return (x0 + Lx * np.arange(Nx) / (Nx - 1),
+                    y0 + Ly * np.arange(Ny) / (Ny - 1),
+                    z0 + Lz * np.arange(Nz) / (Nz - 1))
+        out = []
+        for o, w in zip(self.origin, self.spacing):
+            w = np.asarray(w, dtype=np.float64)
+            faces = o + np.concatenate([[0.0], np.cumsum(w)])
+            sub = [faces[:-1, None] + w[:, None] * np.arange(self.order)[None, :] / self.order]
+            out.append(np.concatenate([np.concatenate(sub, axis=1).reshape(-1), faces[-1:]]))
+        return tuple(out)
 
     def cell_centres(self):
         x0, y0, z0 = self.origin
@@ -299,6 +310,15 @@ def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
     if n_boxes:
         sc.boxes = random_boxes(rng, n_boxes, (nx, ny, nz), extent)
     return sc
+
+
+def graded_widths(n: int, length: float, stretch: float) -> np.ndarray:
+    """n cell widths of a graded spacing along one axis: faces at
+    length * expm1(stretch * s) / expm1(stretch) for s = 0, 1/n, ..., 1, so
+    that refining n refines the same smooth map (stretch 0: uniform)."""
+    s = np.arange(n + 1, dtype=np.float64) / n
+    x = length * s if stretch == 0.0 else length * np.expm1(stretch * s) / math.expm1(stretch)
+    return np.diff(x)
 
 
 def random_boxes(rng, n: int, cells: Tuple[int, int, int], extent, period: float = 30 * DAY) -> np.ndarray:

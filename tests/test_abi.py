@@ -78,3 +78,17 @@ def test_struct_layouts_match_the_header():
                        ("ht_step_stats", _lib.StepStats), ("ht_profile_stats", _lib.ProfileStats)):
         assert fields(cname) == len(cls._fields_), cname
     assert ctypes.sizeof(_lib.BoxSrc) == 9 * 8 and ctypes.sizeof(_lib.LineSrc) == 8 * 8
+
+
+def test_graded_scenarios_are_refused_by_the_binding():
+    """The library assumes uniform cells along each axis: a scenario with a
+    graded spacing is refused before any library call."""
+    import numpy as np
+
+    import scenarios as S
+    from paper_2103_00081_gb300 import hydro
+    sc = S.random_small(1, 3, 2, 2, 1)
+    sc.spacing = tuple(S.graded_widths(n, L, 0.5) for n, L in zip((3, 2, 2), sc.extent))
+    with pytest.raises(ValueError):
+        hydro.Simulator.from_scenario(sc)
+    assert np.allclose([w.sum() for w in sc.spacing], sc.extent)
