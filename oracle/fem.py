@@ -34,6 +34,10 @@ discrete eigenmode decay, exactness for linear heads, energy balance, the
 erfc and Ogata-Banks 1D solutions, manufactured-solution convergence
 orders, and the moments of the box-source and per-node face loads.
 
+Meshes are uniform along each axis, or graded with tensor-product cell
+widths (the fine-near-the-piles meshes of Section 3.3, Fig. 10b); a graded
+mesh takes every geometric quantity per cell.
+
 RowOracle evaluates the same definitions row by row (cell by cell over the
 cells holding a node) for meshes too large to assemble; it is pinned to the
 assembled form at every row of small meshes.
