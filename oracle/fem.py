@@ -509,6 +509,37 @@ def dirichlet_data(mesh: Mesh, bc: Dict[int, Tuple[int, float]]):
     return mask, g
 
 
+def pile_surface_nodes(mesh: Mesh, row) -> np.ndarray:
+    """Nodes held at a pile's temperature: those within `radius` of the pile
+    axis (x, y) and between z_bot and z_top, or, when no node lies within the
+    radius, the node column nearest the axis (lowest index on ties).
+    row = (x, y, z_top, z_bot, radius, T_mean, T_amp, period, phase)."""
+    X, Y, Z = mesh.node_xyz()
+    eps = 1e-9 * max(mesh.extent)
+    inz = (Z >= min(row[2], row[3]) - eps) & (Z <= max(row[2], row[3]) + eps)
+    lat = (X - row[0]) ** 2 + (Y - row[1]) ** 2
+    sel = inz & (lat <= row[4] ** 2 + eps)
+    if not sel.any():
+        cand = np.nonzero(inz)[0]
+        if cand.size == 0:
+            raise ValueError("pile lies outside the mesh")
+        best = cand[np.argmin(lat[cand])]
+        sel = inz & (X == X[best]) & (Y == Y[best])
+    return np.nonzero(sel)[0]
+
+
+def pile_temperature(row, t: float) -> float:
+    """Square wave T_mean + T_amp sign(sin(2 pi t / period + phase)), with
+    sign(0) = +1: the warm half first (Section 3.3: 301.55 K for six months,
+    then 275.55 K)."""
+    return row[5] + row[6] * (1.0 if math.sin(2.0 * math.pi * t / row[7] + row[8]) >= 0.0 else -1.0)
+
+
+def seasonal_value(v, t: float) -> float:
+    """mean + amp sin(2 pi t / period + phase) for v = (mean, amp, period, phase)."""
+    return v[0] + v[1] * math.sin(2.0 * math.pi * t / v[2] + v[3])
+
+
 def constrain(A: sp.csr_matrix, mask: np.ndarray) -> sp.csr_matrix:
     """A0 = P A P + (I - P), P = projector on free nodes."""
     free = (~mask).astype(np.float64)
@@ -541,7 +572,41 @@ def solve(A0: sp.csr_matrix, b: np.ndarray, method: str = "direct", tol: float =
 # ---------------------------------------------------------------------------
 # The simulator
 # ---------------------------------------------------------------------------
-class OracleSim:
+class _TimeDirichlet:
+    """Dirichlet values that change with time: faces with a seasonal value
+    (mean, amp, period, phase), re-evaluated at each step's t^{n+1}, and pile
+    surfaces held at a square-wave temperature.  Faces keep their order on
+    shared edges (the higher face index wins); pile nodes override faces."""
+
+    def _init_time_dirichlet(self, sc):
+        m = self.mesh
+        self.seasonal = {f: dict(d) for f, d in (getattr(sc, "bc_seasonal", None) or {}).items()}
+        for f, faces in self.seasonal.items():
+            bc_mask = dict(sc.bc.get(f, {}))
+            for face in faces:
+                bc_mask[face] = (DIRICHLET, 0.0)
+            self.dmask[f], self.gval[f] = dirichlet_data(m, bc_mask)
+        self.pile_temps = np.asarray(getattr(sc, "pile_temps", np.zeros((0, 9))), dtype=np.float64).reshape(-1, 9)
+        self.pile_nodes = [pile_surface_nodes(m, row) for row in self.pile_temps]
+        for nodes in self.pile_nodes:
+            self.dmask[TEMP][nodes] = True
+
+    def g_at(self, field: int, t: float) -> np.ndarray:
+        """Dirichlet values of `field` at time t."""
+        seas = self.seasonal.get(field, {})
+        if not seas and (field != TEMP or not self.pile_nodes):
+            return self.gval[field]
+        bc_t = dict(self.sc.bc.get(field, {}))
+        for face, v in seas.items():
+            bc_t[face] = (DIRICHLET, seasonal_value(v, t))
+        _, g = dirichlet_data(self.mesh, bc_t)
+        if field == TEMP:
+            for row, nodes in zip(self.pile_temps, self.pile_nodes):
+                g[nodes] = pile_temperature(row, t)
+        return g
+
+
+class OracleSim(_TimeDirichlet):
     """Plain FP64 reference of one coupled step (head, then heat)."""
 
     def __init__(self, sc, solver: str = "direct", tol: float = 1e-14):
@@ -562,6 +627,7 @@ class OracleSim:
         self.gval = {}
         for f in (HEAD, TEMP):
             self.dmask[f], self.gval[f] = dirichlet_data(m, sc.bc.get(f, {}))
+        self._init_time_dirichlet(sc)
         # static loads: Neumann faces
         self.F_static = {HEAD: np.zeros(m.n_nodes), TEMP: np.zeros(m.n_nodes)}
         for f in (HEAD, TEMP):
@@ -636,24 +702,24 @@ class OracleSim:
     def head_rhs(self, dt, t1):
         A = self.head_matrix(dt)
         rhs = self.Ss * (self.M @ self.h) + dt * self.head_load(t1)
-        return lifted_rhs(A, rhs, self.dmask[HEAD], self.gval[HEAD])
+        return lifted_rhs(A, rhs, self.dmask[HEAD], self.g_at(HEAD, t1))
 
     def heat_rhs(self, dt, t1, h1):
         A = self.heat_matrix(dt, h1)
         rhs = self.McT @ self.T + dt * self.heat_load(t1)
-        return lifted_rhs(A, rhs, self.dmask[TEMP], self.gval[TEMP])
+        return lifted_rhs(A, rhs, self.dmask[TEMP], self.g_at(TEMP, t1))
 
     # -- one backward Euler step: head first, then heat with q(h^{n+1}) -------
     def step(self, dt):
         t1 = self.t + dt
         Ah = self.head_matrix(dt)
         bh = lifted_rhs(Ah, self.Ss * (self.M @ self.h) + dt * self.head_load(t1),
-                        self.dmask[HEAD], self.gval[HEAD])
+                        self.dmask[HEAD], self.g_at(HEAD, t1))
         h1 = solve(constrain(Ah, self.dmask[HEAD]), bh, self.solver if self.solver == "direct" else "cg",
                    self.tol, x0=self.h)
         AT = self.heat_matrix(dt, h1)
         bT = lifted_rhs(AT, self.McT @ self.T + dt * self.heat_load(t1),
-                        self.dmask[TEMP], self.gval[TEMP])
+                        self.dmask[TEMP], self.g_at(TEMP, t1))
         T1 = solve(constrain(AT, self.dmask[TEMP]), bT,
                    self.solver if self.solver == "direct" else "bicgstab", self.tol, x0=self.T)
         self.h, self.T, self.t = h1, T1, t1
@@ -707,7 +773,7 @@ def cells_of_node(mesh: Mesh, node: int):
     return out
 
 
-class RowOracle:
+class RowOracle(_TimeDirichlet):
     """Rows of the constrained operators A0 and of the lifted right-hand
     sides b of one step at selected nodes, for meshes too large to assemble.
 
@@ -737,6 +803,7 @@ class RowOracle:
                 if typ == FLUX:
                     F += face_load(m, face, val) if np.ndim(val) == 0 else face_load_nodal(m, face, val)
             self.F_static[f] = F
+        self._init_time_dirichlet(sc)
         self.d_well = np.zeros(m.n_nodes)
         self.Tin_well = np.zeros(m.n_nodes)
         wells = np.asarray(sc.wells, dtype=np.float64)
@@ -818,7 +885,7 @@ class RowOracle:
         Dirichlet rows, else (c M state)_i + dt F_i(t1) - sum_{j in D} A_ij g_j
         (c = S_s for head, c_T for heat; the heat operator at the head h)."""
         state = np.asarray(state, dtype=np.float64)
-        g = self.gval[field]
+        g = self.g_at(field, t1)
         b, a = np.zeros(len(rows)), np.zeros(len(rows))
         for k, i in enumerate(rows):
             if self.dmask[field][i]:

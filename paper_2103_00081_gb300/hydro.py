@@ -222,6 +222,9 @@ class Simulator:
     def from_scenario(cls, sc, device=0, stream=None, **solver):
         if getattr(sc, "spacing", None) is not None:
             raise ValueError("the library takes uniform cells along each axis; graded spacing is not supported")
+        if np.size(getattr(sc, "pile_temps", np.zeros(0))) or getattr(sc, "bc_seasonal", None):
+            raise ValueError("pile surface temperatures and seasonal faces are not supported by the library; "
+                             "re-set face values between steps with set_bc instead")
         s = cls(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, device=device, stream=stream)
         s.set_cells(sc.K, sc.lam_cells, sc.cT_cells, sc.lam, sc.cT, sc.cw, sc.Ss)
         for field, faces in sc.bc.items():

@@ -74,6 +74,13 @@ class Scenario:
     # optional graded mesh: cell widths along x, y and z (tensor-product
     # spacing summing to the extent); None for uniform cells
     spacing: Optional[Tuple[np.ndarray, np.ndarray, np.ndarray]] = None
+    # optional pile surfaces held at a square-wave temperature [n, 9]: x, y,
+    # z_top, z_bot, radius, T_mean, T_amp, period, phase
+    pile_temps: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 9)))
+    # optional Dirichlet faces whose value follows a seasonal sinusoid:
+    # field -> face -> (mean, amp, period, phase)
+    bc_seasonal: Dict[int, Dict[int, Tuple[float, float, float, float]]] = \
+        dataclasses.field(default_factory=dict)
 
     @property
     def n_cells(self) -> int:

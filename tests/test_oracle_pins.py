@@ -784,3 +784,86 @@ def test_graded_mesh_manufactured_solution_converges_at_order_p_plus_1(p):
     e1, e2 = _graded_mms_error(p, 3), _graded_mms_error(p, 6)
     order = math.log(e1 / e2) / math.log(2.0)
     assert order > p + 1 - 0.35, (e1, e2, order)
+
+
+def _pile_temp_scenario(p, rows, n=6, nz=3, insulated=False):
+    sc = S.config1(nx=n, ny=n, nz=nz, order=p)
+    sc.extent = (12.0, 12.0, 6.0)
+    sc.piles = np.zeros((0, 8))
+    sc.h0 = np.zeros(sc.n_nodes)
+    sc.T0 = np.full(sc.n_nodes, 15.0)
+    sc.bc = {S.HEAD: {}, S.TEMP: {} if insulated else {0: (S.DIRICHLET, 15.0), 1: (S.DIRICHLET, 15.0)}}
+    sc.pile_temps = np.asarray(rows, dtype=np.float64).reshape(-1, 9)
+    return sc
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_pile_surface_temperature_is_held_and_drives_an_insulated_box_to_it(p):
+    """Pile surfaces held at a square wave (Section 3.3: 288.55 K +- 13 K, six
+    months each way): the pile nodes take T_p(t^{n+1}) exactly at every step,
+    the wave flips after half a period, and with insulated outer faces one
+    very long step brings the whole block to the pile temperature."""
+    year = 365 * S.DAY
+    row = [6.0, 6.0, 6.0, 1.0, 0.8, 288.55, 13.0, year, 0.0]
+    sc = _pile_temp_scenario(p, [row])
+    o = fem.OracleSim(sc)
+    nodes = o.pile_nodes[0]
+    X, Y, Z = o.mesh.node_xyz()
+    assert nodes.size > 0 and np.all((X[nodes] - 6) ** 2 + (Y[nodes] - 6) ** 2 <= 0.64 + 1e-9)
+    dt = 60 * S.DAY
+    for k in range(1, 8):
+        o.step(dt)
+        expect = 301.55 if math.sin(2 * math.pi * k * dt / year) >= 0 else 275.55
+        np.testing.assert_array_equal(o.T[nodes], expect)
+    # a radius below the node spacing takes the nearest node column
+    thin = fem.pile_surface_nodes(o.mesh, [6.1, 5.9, 6.0, 1.0, 1e-3, 0, 0, 1, 0])
+    assert np.all(X[thin] == 6.0) and np.all(Y[thin] == 6.0)
+    si = _pile_temp_scenario(p, [[6.0, 6.0, 6.0, 0.0, 0.8, 290.0, 0.0, year, 0.0]], insulated=True)
+    oi = fem.OracleSim(si)
+    oi.step(1e19)       # the block's diffusion time is ~2e8 s: storage is negligible
+    np.testing.assert_allclose(oi.T, 290.0, rtol=0, atol=1e-7)
+
+
+def test_two_identical_pile_surfaces_give_a_mirror_symmetric_field():
+    year = 365 * S.DAY
+    rows = [[3.0, 6.0, 6.0, 1.0, 0.8, 288.55, 13.0, year, 0.0],
+            [9.0, 6.0, 6.0, 1.0, 0.8, 288.55, 13.0, year, 0.0]]
+    sc = _pile_temp_scenario(1, rows, n=12)
+    o = fem.OracleSim(sc)
+    for _ in range(3):
+        o.step(30 * S.DAY)
+    T = o.T.reshape(sc.node_dims[::-1])
+    np.testing.assert_allclose(T, T[:, :, ::-1], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_seasonal_surface_temperature_follows_its_record_and_the_lift_holds(p):
+    """A seasonal top-face temperature (the monthly surface record of
+    Section 3.3 as a sinusoid): the top nodes take T_s(t^{n+1}) at every
+    step, the x = x1 face (static Dirichlet, lower index) loses the shared
+    edge to it, the free rows of the unconstrained heat system hold, and the
+    row-wise oracle agrees with the assembled one."""
+    year = 365 * S.DAY
+    sc = _pile_temp_scenario(p, [[6.0, 6.0, 6.0, 3.0, 0.8, 288.55, 13.0, year, 0.0]])
+    sc.bc[S.TEMP][5] = (S.DIRICHLET, 0.0)
+    sc.bc_seasonal = {S.TEMP: {5: (287.45, 8.0, year, 0.3)}}
+    o = fem.OracleSim(sc)
+    r = fem.RowOracle(sc)
+    top = o.mesh.face_nodes(5)
+    dt = 20 * S.DAY
+    for k in range(1, 4):
+        T0 = o.T.copy()
+        t1 = k * dt
+        b_rows = r.rhs_rows(S.TEMP, dt, t1, T0, list(range(sc.n_nodes)), h=o.h)[0]
+        np.testing.assert_allclose(b_rows, o.heat_rhs(dt, t1, o.h), rtol=0,
+                                   atol=1e-12 * np.abs(o.heat_rhs(dt, t1, o.h)).max())
+        o.step(dt)
+        ts = 287.45 + 8.0 * math.sin(2 * math.pi * t1 / year + 0.3)
+        pile = set(o.pile_nodes[0].tolist())
+        top_free_of_pile = np.array([i for i in top if i not in pile])
+        np.testing.assert_allclose(o.T[top_free_of_pile], ts, rtol=0, atol=1e-9)
+        A = o.heat_matrix(dt, o.h)
+        R = A @ o.T - o.McT @ T0 - dt * o.heat_load(t1)
+        mask = o.dmask[S.TEMP]
+        scale = np.abs(A) @ np.abs(o.T) + np.abs(o.McT) @ np.abs(T0) + dt * np.abs(o.heat_load(t1))
+        assert np.all(np.abs(R[~mask]) <= 1e-12 * scale[~mask])
