@@ -867,3 +867,16 @@ def test_seasonal_surface_temperature_follows_its_record_and_the_lift_holds(p):
         mask = o.dmask[S.TEMP]
         scale = np.abs(A) @ np.abs(o.T) + np.abs(o.McT) @ np.abs(T0) + dt * np.abs(o.heat_load(t1))
         assert np.all(np.abs(R[~mask]) <= 1e-12 * scale[~mask])
+
+
+def test_iterative_oracle_solves_agree_with_the_direct_solve():
+    """The Jacobi-PCG / BiCGStab path the CPU baseline times reaches the
+    direct solution to the forward-error bound of its tolerance."""
+    sc = S.random_small(40, 8, 6, 4, 2, n_piles=2, n_wells=2)
+    od = fem.OracleSim(sc, solver="direct")
+    oi = fem.OracleSim(sc, solver="iterative", tol=1e-13)
+    for _ in range(2):
+        od.step(sc.dt)
+        oi.step(sc.dt)
+    for a, b in ((oi.h, od.h), (oi.T, od.T)):
+        assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
