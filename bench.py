@@ -380,7 +380,24 @@ def cpu_baseline(args, sc_full, steps=1, warm=0):
             "sample": f"{steps} step(s) of {sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{sc.order} "
                       f"({sc.n_nodes} nodes), Jacobi-PCG/BiCGStab to 1e-10 on assembled CSR, "
                       f"{el:.1f} s; scaled linearly by node count to {sc_full.n_nodes} nodes",
-            "sample_rate": rate_sample, "seconds": el}
+            "sample_rate": rate_sample, "seconds": el, "s_per_step_sample": el / steps,
+            "spmv": oracle_spmv_rate(o, sc)}
+
+
+def oracle_spmv_rate(o, sc, reps=5):
+    """The oracle's assembled head-operator SpMV on the sample: GB/s counted
+    as CSR values and column indices (12 B per nonzero) plus x read and y
+    written (16 B per row), best of `reps`."""
+    from oracle import fem
+    A = fem.constrain(o.head_matrix(sc.dt), o.dmask[fem.HEAD])
+    x = np.random.default_rng(0).standard_normal(A.shape[0])
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        A @ x
+        best = min(best, time.perf_counter() - t0)
+    nbytes = 12.0 * A.nnz + 16.0 * A.shape[0]
+    return {"gbs": nbytes / best / 1e9, "nnz": int(A.nnz), "rows": int(A.shape[0]), "seconds": best}
 
 
 def run_reference(args):
@@ -401,7 +418,8 @@ def run_reference(args):
     rate = rate_sample * sc.n_nodes / sc_full.n_nodes
     cb = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
           "sample": f"{args.steps} step(s) of {sc.name} {sc.nx}x{sc.ny}x{sc.nz} Q{sc.order} "
-                    f"({sc.n_nodes} nodes), scaled linearly by node count to {sc_full.n_nodes} nodes"}
+                    f"({sc.n_nodes} nodes), scaled linearly by node count to {sc_full.n_nodes} nodes",
+          "s_per_step_sample": el / args.steps, "spmv": oracle_spmv_rate(o, sc)}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,

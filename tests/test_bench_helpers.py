@@ -64,3 +64,13 @@ def test_clock_record_parser(tmp_path):
     assert s["reasons"] == ["sw_power_cap"]
     c.path = str(tmp_path / "missing.csv")
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_cpu_baseline_reports_rate_step_time_and_spmv_bandwidth():
+    import types
+    args = types.SimpleNamespace(cpu_sample_cells=6)
+    sc_full = bench.workload("ates_q2")
+    cb = bench.cpu_baseline(args, sc_full)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    assert cb["s_per_step_sample"] > 0 and cb["spmv"]["gbs"] > 0
+    assert cb["spmv"]["rows"] == (2 * 6 + 1) ** 2 * (2 * 2 + 1)
