@@ -157,7 +157,8 @@ int ht_default_solver(ht_solver_opts* opts);
 
 /* Create a context for the mesh on CUDA device `device`.  cuda_stream is a
  * cudaStream_t (NULL: the library creates a non-blocking stream it owns).
- * Errors: HT_EINVAL (order not 1/2, non-positive sizes), HT_ENOMEM, HT_ECUDA. */
+ * Errors: HT_EINVAL (order not 1/2, non-positive sizes, more than 2e9 nodes
+ * or more than INT_MAX / (3 (order+1)^3) cells), HT_ENOMEM, HT_ECUDA. */
 int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream);
 
 /* Free all device memory and the context.  NULL is ignored. */
@@ -360,9 +361,14 @@ int ht_profile_read(ht_ctx* ctx, ht_profile_stats* out);
  * Scratch: the per-tile partial sums of x^T y live in one static device
  * array of 4096 doubles (32 KiB) that every GPU loading this library keeps
  * until the process exits.  Meshes needing more than 4096 operator tiles are
- * rejected with HT_EINVAL.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share the array; every slot a call
+ * rejected with HT_EINVAL, and so are meshes of more than INT_MAX nodes or
+ * cells.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  The kept address does not survive
+ * cudaDeviceReset (or any other teardown of the device's primary context),
+ * so do not call this entry point after one.  The call makes `device`
+ * current while it queues work and restores the caller's current device
+ * before it returns, on success and on error.  All calls on a device share the array; every slot a call
  * reads is written earlier by the same call, so nothing needs clearing, but
  * calls whose kernels can run at the same time on one GPU (for example on
  * two streams) race on it and must be serialised by the caller.  The

@@ -96,6 +96,30 @@ def lagrange_deriv(p: int, a: int, xi: float) -> float:
 # ---------------------------------------------------------------------------
 # Mesh
 # ---------------------------------------------------------------------------
+def mixture(phi, lam_s, lam_w, c_s, c_w):
+    """Bulk thermal conductivity and volumetric heat capacity of the saturated
+    medium: volume-fraction averages of the solid and water values, the
+    mixture rules given with Eq. 2 (Section 2)."""
+    return (1.0 - phi) * lam_s + phi * lam_w, (1.0 - phi) * c_s + phi * c_w
+
+
+def specific_storage(B_poro, rho_w=1000.0, g=9.81):
+    """Specific storage of the head form: Eq. 1's storage coefficient 1/B_poro
+    times rho_w g, from p = rho_w g (h - z) (Section 2)."""
+    return rho_w * g / B_poro
+
+
+def bulk_properties(sc):
+    """(lambda, c_T, c_w, S_s) of a scenario: its directly given bulk values
+    where present, else the mixture rules and the storage of Eq. 1 applied to
+    its raw material properties."""
+    m = sc.material
+    lam, cT = mixture(m.phi, m.lam_s, m.lam_w, m.c_s, m.c_w)
+    Ss = specific_storage(m.B_poro, m.rho_w, m.g)
+    return (sc.lam if sc.lam is not None else lam, sc.cT if sc.cT is not None else cT, m.c_w,
+            sc.Ss if sc.Ss is not None else Ss)
+
+
 class Mesh:
     """Structured box of nx*ny*nz Lagrange hexahedra of order p.
 
@@ -616,9 +640,9 @@ class OracleSim(_TimeDirichlet):
         self.N, self.G, self.W, self.Me, self.Ke = cell_geometry(m, sc.order)
         nc = m.n_cells
         self.K = np.asarray(sc.K, dtype=np.float64)
-        self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, sc.lam))
-        self.cT_c = np.asarray(sc.cT_cells if sc.cT_cells is not None else np.full(nc, sc.cT))
-        self.cw, self.Ss = sc.cw, sc.Ss
+        lam, cT, self.cw, self.Ss = bulk_properties(sc)
+        self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, lam))
+        self.cT_c = np.asarray(sc.cT_cells if sc.cT_cells is not None else np.full(nc, cT))
         self.M = assemble(m, np.ones(nc), self.Me)
         self.KK = assemble(m, self.K, self.Ke)
         self.McT = assemble(m, self.cT_c, self.Me)
@@ -792,9 +816,9 @@ class RowOracle(_TimeDirichlet):
         self.N, self.G, self.W, self.Me, self.Ke = cell_geometry(m, sc.order)
         nc = m.n_cells
         self.K = np.asarray(sc.K, dtype=np.float64)
-        self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, sc.lam))
-        self.cT_c = np.asarray(sc.cT_cells if sc.cT_cells is not None else np.full(nc, sc.cT))
-        self.cw, self.Ss = sc.cw, sc.Ss
+        lam, cT, self.cw, self.Ss = bulk_properties(sc)
+        self.lam_c = np.asarray(sc.lam_cells if sc.lam_cells is not None else np.full(nc, lam))
+        self.cT_c = np.asarray(sc.cT_cells if sc.cT_cells is not None else np.full(nc, cT))
         self.dmask, self.gval, self.F_static = {}, {}, {}
         for f in (HEAD, TEMP):
             self.dmask[f], self.gval[f] = dirichlet_data(m, sc.bc.get(f, {}))

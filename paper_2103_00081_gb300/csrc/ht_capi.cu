@@ -1,6 +1,7 @@
 // C ABI of the hydrothermal step (include/ht.h): context set-up, host-side
 // load tables, the time stepper and parity hooks.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -737,9 +738,19 @@ int ht_create(ht_ctx** out, const ht_mesh* mesh, int device, void* cuda_stream) 
         g_create_error = "mesh sizes must be positive";
         return HT_EINVAL;
     }
+    {
+        // counts in doubles (no integer overflow): node indices and the largest
+        // per-cell table index, 3 (P+1)^3 cells (Gauss-point velocities), must fit int
+        const double Pd = mesh->order, nq = (Pd + 1) * (Pd + 1) * (Pd + 1);
+        const double nnd = (Pd * mesh->nx + 1) * (Pd * mesh->ny + 1) * (Pd * mesh->nz + 1);
+        const double ncd = (double)mesh->nx * mesh->ny * mesh->nz;
+        if (nnd > 2.0e9 || 3.0 * nq * ncd > (double)INT_MAX) {
+            g_create_error = "mesh too large for 32-bit node and cell tables";
+            return HT_EINVAL;
+        }
+    }
     const long long P = mesh->order;
     const long long nn = (P * mesh->nx + 1) * (P * mesh->ny + 1) * (P * mesh->nz + 1);
-    if (nn > 2000000000LL) { g_create_error = "mesh too large for 32-bit node tables"; return HT_EINVAL; }
     ht_ctx* c = new ht_ctx();
     c->device = device;
     cudaError_t e = cudaSetDevice(device);
@@ -1215,6 +1226,17 @@ int ht_head_apply_dot_noalloc(const ht_mesh* mesh, int dirichlet_faces, double S
         dirichlet_faces < 0 || dirichlet_faces > 63) {
         if (msg && msg_len) snprintf(msg, msg_len, "invalid mesh, coefficient or face mask");
         return HT_EINVAL;
+    }
+    {
+        // node and cell counts without integer overflow (doubles are exact far
+        // beyond the limit); the kernels index nodes and cells with int
+        const double P = mesh->order;
+        const double nn = (P * mesh->nx + 1) * (P * mesh->ny + 1) * (P * mesh->nz + 1);
+        const double nc = (double)mesh->nx * mesh->ny * mesh->nz;
+        if (nn > (double)INT_MAX || nc > (double)INT_MAX) {
+            if (msg && msg_len) snprintf(msg, msg_len, "mesh too large: %.0f nodes, %.0f cells", nn, nc);
+            return HT_EINVAL;
+        }
     }
     Grid g{};
     g.P = mesh->order;

@@ -691,12 +691,28 @@ __global__ void resid_kernel(long long n, const double* __restrict__ b, const do
 }
 
 // r = b - q with q from the FP32 operator: r32 = (float) r, partials r.r, b.b
-__global__ void resid32_kernel(long long n, const double* __restrict__ b, const float* __restrict__ q,
-                               float* __restrict__ r32, double* __restrict__ part, int stride) {
+// r32 = b - q with q = A x from the FP32 operator.  On Dirichlet rows the
+// constrained operator is the identity, so the residual there is taken as
+// b - x in FP64 (zero once x carries the Dirichlet values): the FP32 copy of
+// x_D would leave a rounding residual on rows that the fused Krylov
+// iterations keep at zero and could never reduce.
+__global__ void resid32_kernel(const Grid g, long long n, const double* __restrict__ b, const float* __restrict__ q,
+                               const double* __restrict__ x, float* __restrict__ r32, double* __restrict__ part,
+                               int stride) {
     double rr = 0, bb = 0;
+    const long long nxy = (long long)g.Nx * g.Ny;
     GRID_LOOP(i, n) {
         const double bi = b[i];
-        const double ri = bi - (double)q[i];
+        bool d = false;
+        if (g.dmask) {
+            const int k = (int)(i / nxy);
+            const int m = (int)(i - (long long)k * nxy);
+            const int jj = m / g.Nx, ii = m - jj * g.Nx;
+            const int dm = g.dmask;
+            d = ((dm & 1) && ii == 0) || ((dm & 2) && ii == g.Nx - 1) || ((dm & 4) && jj == 0) ||
+                ((dm & 8) && jj == g.Ny - 1) || ((dm & 16) && k == 0) || ((dm & 32) && k == g.Nz - 1);
+        }
+        const double ri = d ? bi - x[i] : bi - (double)q[i];
         r32[i] = (float)ri;
         rr = fma(ri, ri, rr);
         bb = fma(bi, bi, bb);
@@ -1268,7 +1284,9 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
         if (fast) {
             to_f32_kernel<<<G, kVecThreads, 0, c->stream>>>(n, x, c->x32); ++c->n_launch;
             HT_TRY(launch_apply32(c, field, (float)dt, c->x32, c->q32, nullptr, nullptr, nullptr));
-            resid32_kernel<<<G, kVecThreads, 0, c->stream>>>(n, b, c->q32, c->r32, c->part, S); ++c->n_launch;
+            Grid gf = c->grid;
+            gf.dmask = c->dmask[field];
+            resid32_kernel<<<G, kVecThreads, 0, c->stream>>>(gf, n, b, c->q32, x, c->r32, c->part, S); ++c->n_launch;
             HT_CUDA(c, cudaGetLastError());
         } else if (c->opts.outer_fp64) {
             HT_TRY(launch_apply64(c, field, dt, x, c->q, nullptr, nullptr, nullptr));

@@ -2595,7 +2595,15 @@ int noalloc_head_apply_dot(const Grid& g, const Elem<double>& e, double Ss, doub
         if (msg && msg_len) snprintf(msg, msg_len, "device %d out of range", device);
         return HT_EINVAL;
     }
-    cudaError_t err = cudaSetDevice(device);
+    // the caller's current device is restored on every return path
+    struct DeviceRestore {
+        int prev = -1;
+        ~DeviceRestore() { if (prev >= 0) cudaSetDevice(prev); }
+    } restore;
+    cudaError_t err = cudaGetDevice(&restore.prev);
+    if (err != cudaSuccess) restore.prev = -1;
+    else if (restore.prev != device) err = cudaSetDevice(device);
+    else restore.prev = -1;        // already current: nothing to restore
     double* part = nullptr;
     int num_sms = 0;
     if (err == cudaSuccess) {

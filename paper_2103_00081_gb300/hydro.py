@@ -218,6 +218,13 @@ class Simulator:
         return st.as_dict()
 
     # -- scenario helper -----------------------------------------------------------
+    def bulk_properties(self, m):
+        """(lambda, c_T, S_s) from raw material properties by the library's
+        ht_mixture and ht_specific_storage."""
+        lam, cT = c_double(), c_double()
+        self._check(self._lib.ht_mixture(m.phi, m.lam_s, m.lam_w, m.c_s, m.c_w, byref(lam), byref(cT)))
+        return lam.value, cT.value, self._lib.ht_specific_storage(m.B_poro, m.rho_w, m.g)
+
     @classmethod
     def from_scenario(cls, sc, device=0, stream=None, **solver):
         if getattr(sc, "spacing", None) is not None:
@@ -226,7 +233,9 @@ class Simulator:
             raise ValueError("pile surface temperatures and seasonal faces are not supported by the library; "
                              "re-set face values between steps with set_bc instead")
         s = cls(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, device=device, stream=stream)
-        s.set_cells(sc.K, sc.lam_cells, sc.cT_cells, sc.lam, sc.cT, sc.cw, sc.Ss)
+        lam, cT, Ss = s.bulk_properties(sc.material)
+        s.set_cells(sc.K, sc.lam_cells, sc.cT_cells, sc.lam if sc.lam is not None else lam,
+                    sc.cT if sc.cT is not None else cT, sc.material.c_w, sc.Ss if sc.Ss is not None else Ss)
         for field, faces in sc.bc.items():
             for face, (typ, val) in faces.items():
                 s.set_bc(field, face, typ, val)

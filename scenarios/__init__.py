@@ -6,10 +6,13 @@ initial fields.  It holds none of the finite element arithmetic (no shape
 functions, no quadrature, no operators, no loads), so both the CUDA path and
 the CPU oracle can consume the same inputs without sharing any method code.
 
-Physical parameters follow the paper: the mixture rules of Section 2 (below
-Eq. 2) give the bulk thermal conductivity and heat capacity, the specific
-storage S_s = rho_w g / B_poro follows from Eq. 1 rewritten for hydraulic head,
-and Table 1 / Table 3 supply the material values.  The synthetic workloads
+Material values are handed over raw: porosity, solid and water thermal
+conductivities and heat capacities, and the bulk modulus B_poro of Table 1.
+The bulk coefficients that the method derives from them (the mixture rules
+below Eq. 2 and the specific storage of Eq. 1) are computed by each consumer
+on its own side: the oracle in oracle/fem.py, the library by ht_mixture and
+ht_specific_storage.  A scenario may instead carry bulk values directly
+(lam, cT, Ss), as the Table 3 layers are given.  The synthetic workloads
 (sizes, layering, random fields, pile and well layouts) stand in for the
 paper's ATES benchmark (Section 2) and Treasure Island energy-pile case
 (Section 3), whose site data exist only in figures.
@@ -55,10 +58,7 @@ class Scenario:
     origin: Tuple[float, float, float]
     extent: Tuple[float, float, float]
     K: np.ndarray                      # [cells] hydraulic conductivity, m/s
-    lam: float                         # bulk thermal conductivity, W/(m K)
-    cT: float                          # bulk volumetric heat capacity, J/(m^3 K)
-    cw: float                          # water volumetric heat capacity, J/(m^3 K)
-    Ss: float                          # specific storage, 1/m
+    material: "Material"               # raw phase properties (bulk values derived by the consumer)
     bc: Dict[int, Dict[int, Tuple[int, float]]]   # field -> face -> (type, value)
     piles: np.ndarray                  # [n, 8]
     wells: np.ndarray                  # [n, 7]
@@ -81,6 +81,17 @@ class Scenario:
     # field -> face -> (mean, amp, period, phase)
     bc_seasonal: Dict[int, Dict[int, Tuple[float, float, float, float]]] = \
         dataclasses.field(default_factory=dict)
+    # optional bulk values given directly (None: derived from `material` by
+    # the consumer): thermal conductivity W/(m K), heat capacity J/(m^3 K),
+    # specific storage 1/m
+    lam: Optional[float] = None
+    cT: Optional[float] = None
+    Ss: Optional[float] = None
+
+    @property
+    def cw(self) -> float:
+        """Volumetric heat capacity of water, J/(m^3 K) (a raw property)."""
+        return self.material.c_w
 
     @property
     def n_cells(self) -> int:
@@ -121,25 +132,25 @@ class Scenario:
                 z0 + Lz * (np.arange(self.nz) + 0.5) / self.nz)
 
 
-def mixture(phi: float, lam_s: float, lam_w: float, c_s: float, c_w: float):
-    """Bulk conductivity and heat capacity by the volume-fraction mixture rules
-    stated beneath Eq. 2 (Section 2)."""
-    return (1.0 - phi) * lam_s + phi * lam_w, (1.0 - phi) * c_s + phi * c_w
+@dataclasses.dataclass(frozen=True)
+class Material:
+    """Raw properties of the saturated porous medium (Section 2 symbols):
+    porosity phi, solid and water thermal conductivities lam_s, lam_w
+    (W/(m K)), solid and water volumetric heat capacities c_s, c_w
+    (J/(m^3 K)), bulk modulus B_poro (Pa), water density rho_w and gravity g."""
+    phi: float
+    lam_s: float
+    lam_w: float
+    c_s: float
+    c_w: float
+    B_poro: float
+    rho_w: float = RHO_W
+    g: float = G_ACC
 
 
-def specific_storage(B_poro: float, rho_w: float = RHO_W, g: float = G_ACC) -> float:
-    """S_s = rho_w g / B_poro: Eq. 1 divided through by rho_w g with p = rho_w g (h - z)."""
-    return rho_w * g / B_poro
-
-
-# Sand / water thermal values shared by the synthetic workloads.
-SAND = dict(phi=0.3, lam_s=2.5, lam_w=0.6, c_s=2.0e6, c_w=4.18e6)
-B_PORO_TABLE1 = 1.0e5   # Table 1
-
-
-def _sand():
-    lam, cT = mixture(SAND["phi"], SAND["lam_s"], SAND["lam_w"], SAND["c_s"], SAND["c_w"])
-    return lam, cT, SAND["c_w"], specific_storage(B_PORO_TABLE1)
+# Sand / water values shared by the synthetic workloads; B_poro from Table 1.
+B_PORO_TABLE1 = 1.0e5
+SAND = Material(phi=0.3, lam_s=2.5, lam_w=0.6, c_s=2.0e6, c_w=4.18e6, B_poro=B_PORO_TABLE1)
 
 
 def _linear_x(sc_dims, origin, extent, order, a, b, nx, ny, nz):
@@ -181,7 +192,6 @@ def config1(nx: int = 16, ny: Optional[int] = None, nz: Optional[int] = None,
     backward Euler with dt = 1 day."""
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
-    lam, cT, cw, Ss = _sand()
     L = 20.0
     K = np.full(nx * ny * nz, 1.0e-4)
     h0 = _linear_x(None, (0, 0, 0), (L, L, L), order, 0.2, -0.01, nx, ny, nz)
@@ -192,7 +202,7 @@ def config1(nx: int = 16, ny: Optional[int] = None, nz: Optional[int] = None,
              {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
               3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
     return Scenario("plain_q1_cube", nx, ny, nz, order, (0.0, 0.0, 0.0), (L, L, L),
-                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 7)), h0, T0,
+                    K, SAND, bc, piles, np.zeros((0, 7)), h0, T0,
                     1.0 * DAY, n_steps)
 
 
@@ -204,7 +214,6 @@ def config2(nx: int = 128, ny: int = 128, nz: int = 32, seed: int = 2,
     0.5), an injection well (+5 L/s at T0 + 10) and an extraction well
     (-5 L/s) 60 m apart, both screened over the aquifer layer; dt = 0.5 day."""
     rng = np.random.default_rng(seed)
-    lam, cT, cw, Ss = _sand()
     Lx, Ly, Lz = 200.0, 200.0, 50.0
     nb = int(round(nz * 10 / 32))
     nt = int(round(nz * 10 / 32))
@@ -234,7 +243,7 @@ def config2(nx: int = 128, ny: int = 128, nz: int = 32, seed: int = 2,
              {0: (DIRICHLET, T_amb), 1: (DIRICHLET, T_amb), 2: (DIRICHLET, T_amb),
               3: (DIRICHLET, T_amb), 5: (DIRICHLET, T_amb)})
     return Scenario("ates_layered_q2", nx, ny, nz, order, (0.0, 0.0, 0.0), (Lx, Ly, Lz),
-                    K, lam, cT, cw, Ss, bc, np.zeros((0, 8)), wells, h0, T0,
+                    K, SAND, bc, np.zeros((0, 8)), wells, h0, T0,
                     0.5 * DAY, n_steps)
 
 
@@ -247,7 +256,6 @@ def config3(nx: int = 256, ny: int = 256, nz: int = 64, seed: int = 3,
     phase) W/m with random phases; head gradient 5.1e-4 along x (5 Pa/m,
     Section 3.3); dt = 1 day."""
     rng = np.random.default_rng(seed)
-    lam, cT, cw, Ss = _sand()
     Lx, Ly, Lz = extent
     lnK = math.log(1e-5) + gaussian_field_fft((nz, ny, nx), (Lz / nz, Ly / ny, Lx / nx),
                                               50.0, 1.0, rng)
@@ -272,8 +280,77 @@ def config3(nx: int = 256, ny: int = 256, nz: int = 64, seed: int = 3,
              {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
               3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
     return Scenario("pile_field_q1", nx, ny, nz, order, (0.0, 0.0, 0.0), extent,
-                    K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 7)), h0, T0,
+                    K, SAND, bc, piles, np.zeros((0, 7)), h0, T0,
                     1.0 * DAY, n_steps)
+
+
+# Layered profile of the city-scale workload, bottom to top: (name, thickness
+# as a fraction of the depth, geometric-mean K in m/s).  The conductivities
+# are those of Table 3 (Section 3.3); the order and proportions follow its
+# description of the profile (bedrock from about 75 % of the depth down, the
+# two bay muds above it, a thin shoal and the fill at the top), stretched to
+# the workload's depth.
+CITY_LAYERS = (("franciscan_bedrock", 0.25, 1.0e-6),
+               ("old_bay_mud", 0.35, 1.7e-9),
+               ("young_bay_mud", 0.25, 1.7e-9),
+               ("shoal", 0.05, 3.5e-5),
+               ("fill", 0.10, 1.1e-5))
+
+
+def config5(nx: int = 512, ny: int = 512, nz: int = 96, seed: int = 5,
+            n_steps: int = 365, pile_grid: Tuple[int, int] = (160, 125),
+            n_boxes: int = 50, extent=(10000.0, 10000.0, 200.0)) -> Scenario:
+    """City-scale workload: 10 km x 10 km x 200 m, Q1 cells, layered lnK
+    (the five Table 3 soils, CITY_LAYERS) plus a Gaussian random field
+    (sigma 1, correlation length 50 m), 20,000 piles (a 160 x 125 grid at
+    50 m spacing with +-10 m jitter, 30 m long from the top, q_l = 40 sin(2 pi
+    t / 1 yr + phase) W/m with random phases), and 50 basement / subway heat
+    sources: horizontal rectangles 100-600 m (and at least 1.5 cells) on a
+    side at 4-20 m below the surface, 5-20 W/m^2 into the ground with a seasonal part of up to a
+    quarter of that.  Head gradient 5.1e-4 along x (5 Pa/m, Section 3.3);
+    T = 15 on the lateral faces and the top; dt = 1 day."""
+    rng = np.random.default_rng(seed)
+    Lx, Ly, Lz = extent
+    # layer of each cell layer (by the depth of its centre)
+    zc = (np.arange(nz) + 0.5) / nz
+    bounds = np.cumsum([f for _, f, _ in CITY_LAYERS])
+    lay = np.minimum(np.searchsorted(bounds, zc, side="right"), len(CITY_LAYERS) - 1)
+    ln_mean = np.log(np.array([k for _, _, k in CITY_LAYERS]))[lay]
+    lnK = ln_mean[:, None, None] + gaussian_field_fft((nz, ny, nx), (Lz / nz, Ly / ny, Lx / nx),
+                                                      50.0, 1.0, rng)
+    K = np.exp(lnK).reshape(-1)
+    gx, gy = pile_grid
+    px = Lx / 2 - 50.0 * (gx - 1) / 2 + 50.0 * np.arange(gx)
+    py = Ly / 2 - 50.0 * (gy - 1) / 2 + 50.0 * np.arange(gy)
+    PX, PY = np.meshgrid(px, py, indexing="ij")
+    n = PX.size
+    jit = rng.uniform(-10.0, 10.0, size=(n, 2))
+    X = np.clip(PX.reshape(-1) + jit[:, 0], 0.0, Lx)
+    Y = np.clip(PY.reshape(-1) + jit[:, 1], 0.0, Ly)
+    phase = rng.uniform(0.0, 2 * np.pi, size=n)
+    piles = np.stack([X, Y, np.full(n, Lz), np.full(n, Lz - 30.0),
+                      np.zeros(n), np.full(n, 40.0), np.full(n, 365 * DAY), phase], axis=1)
+    # at least 1.5 cells on a side, so that no box snaps to an empty rectangle
+    # on the coarser meshes of the same generator
+    wx = np.maximum(rng.uniform(100.0, 600.0, n_boxes), 1.5 * Lx / nx)
+    wy = np.maximum(rng.uniform(100.0, 600.0, n_boxes), 1.5 * Ly / ny)
+    bx0 = rng.uniform(0.0, Lx - wx)
+    by0 = rng.uniform(0.0, Ly - wy)
+    bz = Lz - rng.uniform(4.0, 20.0, n_boxes)
+    flux = rng.uniform(5.0, 20.0, n_boxes)
+    boxes = np.stack([bx0, bx0 + wx, by0, by0 + wy, bz, flux,
+                      flux * rng.uniform(0.0, 0.25, n_boxes), np.full(n_boxes, 365 * DAY),
+                      rng.uniform(0.0, 2 * np.pi, n_boxes)], axis=1)
+    grad = 5.0 / (RHO_W * G_ACC)
+    h0 = _linear_x(None, (0, 0, 0), extent, 1, grad * Lx, -grad, nx, ny, nz)
+    T0 = np.full(h0.size, 15.0)
+    bc = _bc({0: (DIRICHLET, grad * Lx), 1: (DIRICHLET, 0.0)},
+             {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
+              3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
+    sc = Scenario("city_q1", nx, ny, nz, 1, (0.0, 0.0, 0.0), extent,
+                  K, SAND, bc, piles, np.zeros((0, 7)), h0, T0, 1.0 * DAY, n_steps)
+    sc.boxes = boxes
+    return sc
 
 
 def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
@@ -286,7 +363,6 @@ def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
     optionally box heat sources whose edges lie within 0.3 cells of a cell
     face (so that snapping is exercised but never ambiguous)."""
     rng = np.random.default_rng(seed)
-    lam, cT, cw, Ss = _sand()
     Lx, Ly, Lz = extent
     nc = nx * ny * nz
     K = np.exp(math.log(3e-5) + sigma_lnK * rng.standard_normal(nc))
@@ -309,11 +385,12 @@ def random_small(seed: int, nx: int, ny: int, nz: int, order: int,
     bc = {HEAD: {f: (DIRICHLET, float(rng.uniform(-0.3, 0.3))) for f in faces_head},
           TEMP: {f: (DIRICHLET, float(rng.uniform(14, 16))) for f in faces_temp}}
     sc = Scenario(f"random_q{order}_{nx}x{ny}x{nz}_s{seed}", nx, ny, nz, order,
-                  (0.0, 0.0, 0.0), extent, K, lam, cT, cw, Ss, bc, piles, wells,
+                  (0.0, 0.0, 0.0), extent, K, SAND, bc, piles, wells,
                   h0, T0, dt, 3)
     if per_cell_thermal:
-        sc.lam_cells = lam * np.exp(0.3 * rng.standard_normal(nc))
-        sc.cT_cells = cT * np.exp(0.2 * rng.standard_normal(nc))
+        # lognormal about the sand's bulk values (1.93 W/(m K), 2.654e6 J/(m^3 K))
+        sc.lam_cells = 1.93 * np.exp(0.3 * rng.standard_normal(nc))
+        sc.cT_cells = 2.654e6 * np.exp(0.2 * rng.standard_normal(nc))
     if n_boxes:
         sc.boxes = random_boxes(rng, n_boxes, (nx, ny, nz), extent)
     return sc
@@ -357,7 +434,6 @@ def config4(n_problems: int = 64, seed0: int = 1000, n_steps: int = 30,
         rng = np.random.default_rng(seed0 + i)
         nz = int(rng.integers(size_range[0], size_range[1] + 1))
         nx = ny = 2 * nz
-        lam, cT, cw, Ss = _sand()
         Lx, Ly, Lz = extent
         sig = float(rng.uniform(0.5, 1.5))
         lnK = math.log(1e-5) + gaussian_field_fft((nz, ny, nx), (Lz / nz, Ly / ny, Lx / nx), 50.0, sig, rng)
@@ -374,5 +450,5 @@ def config4(n_problems: int = 64, seed0: int = 1000, n_steps: int = 30,
                  {0: (DIRICHLET, 15.0), 1: (DIRICHLET, 15.0), 2: (DIRICHLET, 15.0),
                   3: (DIRICHLET, 15.0), 5: (DIRICHLET, 15.0)})
         out.append(Scenario(f"batch_q1_{nx}x{ny}x{nz}_s{seed0 + i}", nx, ny, nz, 1, (0.0, 0.0, 0.0), extent,
-                            K, lam, cT, cw, Ss, bc, piles, np.zeros((0, 7)), h0, T0, 1.0 * DAY, n_steps))
+                            K, SAND, bc, piles, np.zeros((0, 7)), h0, T0, 1.0 * DAY, n_steps))
     return out

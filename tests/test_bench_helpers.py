@@ -1,6 +1,7 @@
 """CPU checks of the measurement helpers in bench.py: the algorithmic bytes per
 node, the traffic record's source check, the peak fallback and the clock
 record parser."""
+import hashlib
 import json
 import os
 import shutil
@@ -33,6 +34,11 @@ def _tree(tmp_path):
 def test_traffic_record_is_used_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):
     root = _tree(tmp_path)
     rec = json.load(open(root / "profiles" / "fused_cg_traffic.json"))
+    # a record taken on the copied source
+    with open(root / "paper_2103_00081_gb300" / "csrc" / "ht_ops.cu", "rb") as f:
+        rec["source_sha256"] = hashlib.sha256(f.read()).hexdigest()
+    with open(root / "profiles" / "fused_cg_traffic.json", "w") as f:
+        json.dump(rec, f)
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.measured_traffic(rec["workload"]) == rec["dram_bytes_per_iteration"]
     assert bench.measured_traffic("another workload") is None

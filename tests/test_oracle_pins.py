@@ -17,6 +17,31 @@ from oracle import fem
 import scenarios as S
 
 
+def _lam(sc):
+    """Bulk thermal conductivity of a scenario (the oracle's mixture rule)."""
+    return fem.bulk_properties(sc)[0]
+
+
+def _cT(sc):
+    """Bulk volumetric heat capacity of a scenario (the oracle's mixture rule)."""
+    return fem.bulk_properties(sc)[1]
+
+
+def test_mixture_rules_and_storage_match_hand_values():
+    """The Section 2 mixture rules for the sand of the workloads (phi 0.3,
+    lambda_s 2.5, lambda_w 0.6, c_s 2e6, c_w 4.18e6) worked by hand:
+    0.7 * 2.5 + 0.3 * 0.6 = 1.93 and 0.7 * 2e6 + 0.3 * 4.18e6 = 2.654e6; the
+    storage of Eq. 1 with Table 1's B_poro: 1000 * 9.81 / 1e5 = 0.0981."""
+    lam, cT = fem.mixture(0.3, 2.5, 0.6, 2.0e6, 4.18e6)
+    assert abs(lam - 1.93) < 1e-14 and abs(cT - 2.654e6) < 1e-8
+    assert fem.mixture(0.0, 2.5, 0.6, 2.0e6, 4.18e6) == (2.5, 2.0e6)       # no pores: the solid
+    assert fem.mixture(1.0, 2.5, 0.6, 2.0e6, 4.18e6) == (0.6, 4.18e6)      # all water
+    assert abs(fem.specific_storage(1.0e5) - 0.0981) < 1e-16
+    sc = S.config1(nx=2)
+    assert fem.bulk_properties(sc)[:3] == (*fem.mixture(0.3, 2.5, 0.6, 2.0e6, 4.18e6), 4.18e6)
+    sc.lam, sc.cT, sc.Ss = 2.2, 2.5e6, 0.0           # bulk values given directly win
+    assert fem.bulk_properties(sc) == (2.2, 2.5e6, 4.18e6, 0.0)
+
 def _kron3(Ax, Ay, Az):
     # local node l = a + n*(b + n*c): x fastest -> kron(z, kron(y, x))
     return np.kron(Az, np.kron(Ay, Ax))
@@ -167,12 +192,13 @@ def test_discrete_sine_mode_decays_by_closed_form_factor(field):
         sc.bc = {S.HEAD: {}, S.TEMP: _all_dirichlet(0.0)}
         sc.h0 = np.zeros_like(mode)
         sc.T0 = mode.copy()
-        diff = sc.lam / sc.cT
+        lam, cT, _, _ = fem.bulk_properties(sc)
+        diff = lam / cT
     else:
         sc.bc = {S.HEAD: _all_dirichlet(0.0), S.TEMP: {}}
         sc.h0 = mode.copy()
         sc.T0 = np.zeros_like(mode)
-        diff = sc.K[0] / sc.Ss
+        diff = sc.K[0] / fem.bulk_properties(sc)[3]
     o = fem.OracleSim(sc)
     dt = 0.3 * S.DAY if field == "heat" else 20.0
     fac = cf.q1_mode_factor(dt, diff, o.mesh.H, sc.extent)
@@ -245,7 +271,7 @@ def test_erfc_conduction_converges(p):
         for _ in range(nsteps):
             o.step(sc.dt)
         x, _, _ = o.mesh.node_xyz()
-        ex = cf.erfc_1d(x, t_end, sc.lam / sc.cT, 1.0)
+        ex = cf.erfc_1d(x, t_end, _lam(sc) / _cT(sc), 1.0)
         errs.append(np.max(np.abs(o.T - ex)))
     assert errs[0] < 0.02
     assert errs[1] < errs[0] / 2.5, errs
@@ -267,8 +293,8 @@ def test_ogata_banks_advection_diffusion_converges():
         sc.h0 = grad * (L - x)
         K = 1e-4
         q = K * grad
-        v = sc.cw * q / sc.cT
-        D = sc.lam / sc.cT
+        v = sc.cw * q / _cT(sc)
+        D = _lam(sc) / _cT(sc)
         t_end = 0.4 * L / v
         sc.dt = t_end / nsteps
         o = fem.OracleSim(sc)
@@ -300,7 +326,7 @@ def _mms_error(p, n, with_advection):
     lap = (-1.0 - 0.49 + 0.09)
     dt = 1000.0
     qx = Kh * grad if with_advection else 0.0
-    lam, cT, cw = sc.lam, sc.cT, sc.cw
+    lam, cT, cw, _ = fem.bulk_properties(sc)
 
     def f(x, y, z):
         uu = u(x, y, z)
@@ -579,7 +605,7 @@ def test_infinite_line_source_converges_to_the_e1_solution():
     for n, steps in ((20, 10), (40, 20)):
         r, T, sc = _line_source_run(n, steps, t_end)
         keep = np.isin(np.round(r, 9), [2.0, 3.0, 4.0])
-        ex = cf.line_source_e1(r[keep], t_end, 10.0, sc.lam, sc.lam / sc.cT)
+        ex = cf.line_source_e1(r[keep], t_end, 10.0, _lam(sc), _lam(sc) / _cT(sc))
         errs.append(np.abs(T[keep] - ex) / ex)
     assert errs[0].size == errs[1].size == 3
     assert np.all(errs[1] < 0.05), errs[1]
@@ -631,13 +657,13 @@ def test_line_source_in_uniform_flow_converges_to_the_moving_line_source():
         for _ in range(steps):
             o.step(sc.dt)
         x, y, z = o.mesh.node_xyz()
-        U = sc.cw * K * grad / sc.cT
-        a = sc.lam / sc.cT
+        U = sc.cw * K * grad / _cT(sc)
+        a = _lam(sc) / _cT(sc)
         got = []
         for px, py in pts + [(-2.0, 0.0)]:
             got.append(o.T[np.nonzero((np.abs(x - L / 2 - px) < 1e-9) & (np.abs(y - L / 2 - py) < 1e-9)
                                       & (z == 0.0))[0][0]])
-        ex = cf.moving_line_source([p[0] for p in pts], [p[1] for p in pts], t_end, 10.0, sc.lam, a, U)
+        ex = cf.moving_line_source([p[0] for p in pts], [p[1] for p in pts], t_end, 10.0, _lam(sc), a, U)
         errs.append(np.abs(np.array(got[:-1]) - ex) / ex)
         temps.append(got)
     assert np.all(errs[1][:3] < 0.05) and errs[1][3] < 0.15, errs[1]
@@ -657,7 +683,7 @@ def test_dirichlet_lift_satisfies_the_unconstrained_free_rows_and_reactions_clos
     h0, T0 = o.h.copy(), o.T.copy()
     t1 = sc.dt
     o.step(sc.dt)
-    for field, u0, u1, A, cM in ((S.HEAD, h0, o.h, o.head_matrix(sc.dt), sc.Ss * o.M),
+    for field, u0, u1, A, cM in ((S.HEAD, h0, o.h, o.head_matrix(sc.dt), o.Ss * o.M),
                                  (S.TEMP, T0, o.T, o.heat_matrix(sc.dt, o.h), o.McT)):
         F = o.head_load(t1) if field == S.HEAD else o.heat_load(t1)
         R = A @ u1 - cM @ u0 - sc.dt * F
@@ -665,8 +691,8 @@ def test_dirichlet_lift_satisfies_the_unconstrained_free_rows_and_reactions_clos
         scale = np.abs(A) @ np.abs(u1) + np.abs(cM) @ np.abs(u0) + sc.dt * np.abs(F)
         assert np.all(np.abs(R[~mask]) <= 1e-12 * scale[~mask])
         np.testing.assert_allclose(u1[mask], o.gval[field][mask], rtol=1e-14, atol=0)
-    R = o.head_matrix(sc.dt) @ o.h - sc.Ss * (o.M @ h0) - sc.dt * o.head_load(t1)
-    stored = sc.Ss * (o.M @ (o.h - h0)).sum()
+    R = o.head_matrix(sc.dt) @ o.h - o.Ss * (o.M @ h0) - sc.dt * o.head_load(t1)
+    stored = o.Ss * (o.M @ (o.h - h0)).sum()
     rhs = sc.dt * o.head_load(t1).sum() + R[o.dmask[S.HEAD]].sum()
     assert abs(stored - rhs) <= 1e-10 * (abs(stored) + abs(rhs))
 

@@ -29,7 +29,7 @@ def _table(name):
 def test_table1_specific_storage():
     t1 = _table("table1_ates_parameters.txt")
     # S_s = rho_w g / B_poro with B_poro from Table 1
-    assert abs(S.specific_storage(t1["B_poro"]) - 0.0981) < 1e-15
+    assert abs(fem.specific_storage(t1["B_poro"]) - 0.0981) < 1e-15
 
 
 def test_table3_low_diffusivity_layer_responds_least_to_surface_forcing():

@@ -1,11 +1,14 @@
-"""The allocation-free head apply (ht_head_apply_dot_noalloc) against the
-context-based ht_apply, through the C ABI, on two calls in a row.
+"""The allocation-free head apply (ht_head_apply_dot_noalloc), through the C
+ABI, on two calls in a row: y and x^T y against the CPU oracle's constrained
+head operator and against the context-based entry point ht_apply.
 
 This entry point serves callers that cannot allocate device memory (an
 application whose own pool owns all device memory, or a latency-critical loop
 that must not call cudaMalloc); its scratch is a static device array.  The
-file is named to be collected last so a stop-at-first-failure run has already
-run every other test.
+cases include a face mask that is not the workloads' default (one Dirichlet
+face) so that the mask handling is checked against the oracle on its own.
+The file is named to be collected last so a stop-at-first-failure run has
+already run every other test.
 """
 import ctypes
 
@@ -13,21 +16,26 @@ import numpy as np
 import pytest
 
 import scenarios as S
+from oracle import fem
 
 pytestmark = pytest.mark.gpu
 
+CASES = [(1, 33, 20, 7, 31, (0, 1)), (2, 17, 9, 5, 32, (0, 1)), (1, 12, 9, 6, 33, (3,)),
+         (2, 6, 5, 4, 34, (4,))]
 
-@pytest.mark.parametrize("case", [(1, 33, 20, 7, 31), (2, 17, 9, 5, 32)])
-def test_noalloc_head_apply_matches_context_apply_twice(built_lib, case):
+
+@pytest.mark.parametrize("case", CASES)
+def test_noalloc_head_apply_matches_oracle_and_context_apply_twice(built_lib, case):
     import torch
     from paper_2103_00081_gb300 import _lib as L
     from paper_2103_00081_gb300 import hydro
 
-    p, nx, ny, nz, seed = case
-    sc = S.random_small(seed, nx, ny, nz, p)
+    p, nx, ny, nz, seed, faces = case
+    sc = S.random_small(seed, nx, ny, nz, p, faces_head=faces)
+    oracle = fem.OracleSim(sc)
     sim = hydro.Simulator.from_scenario(sc)
     lib = L.lib()
-    mask = sum(1 << f for f, (typ, _) in sc.bc[S.HEAD].items() if typ == S.DIRICHLET)
+    mask = sum(1 << f for f in faces)
     mesh = L.Mesh(nx, ny, nz, p, *sc.origin, *sc.extent)
     dev = torch.device("cuda:0")
     K = torch.tensor(sc.K, dtype=torch.float64, device=dev)
@@ -39,19 +47,22 @@ def test_noalloc_head_apply_matches_context_apply_twice(built_lib, case):
         x_host = rng.standard_normal(sc.n_nodes)
         x = torch.tensor(x_host, dtype=torch.float64, device=dev)
         y.fill_(float("nan"))
-        rc = lib.ht_head_apply_dot_noalloc(ctypes.byref(mesh), mask, sc.Ss, sc.dt,
+        dot.fill_(float("nan"))
+        rc = lib.ht_head_apply_dot_noalloc(ctypes.byref(mesh), mask, oracle.Ss, sc.dt,
                                            ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                            ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(dot.data_ptr()),
                                            0, None, msg, len(msg))
         assert rc == L.HT_OK, msg.value
         torch.cuda.synchronize()
-        ref = sim.apply(S.HEAD, sc.dt, x_host)
         got = y.cpu().numpy()
-        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        assert rel <= 1e-12, (call, rel)
-        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
-        ref_dot = float(x_host @ ref)
-        assert abs(dot.item() - ref_dot) <= 1e-12 * np.sum(np.abs(x_host * ref)), (call, dot.item(), ref_dot)
+        for name, ref in (("oracle", oracle.apply_head(x_host, sc.dt)),
+                          ("ht_apply", sim.apply(S.HEAD, sc.dt, x_host))):
+            rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert rel <= 1e-12, (name, call, rel)
+            assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (name, call)
+            ref_dot = float(x_host @ ref)
+            assert abs(dot.item() - ref_dot) <= 1e-12 * np.sum(np.abs(x_host * ref)), \
+                (name, call, dot.item(), ref_dot)
     sim.close()
 
 
@@ -65,3 +76,18 @@ def test_noalloc_rejects_meshes_beyond_the_static_scratch(built_lib):
                                        0, None, msg, len(msg))
     assert rc == L.HT_EINVAL
     assert b"static scratch" in msg.value
+
+
+def test_noalloc_rejects_meshes_whose_counts_overflow_int(built_lib):
+    """Sizes whose node count exceeds the kernels' int indexing are refused
+    before any device work (the pointers are never touched)."""
+    from paper_2103_00081_gb300 import _lib as L
+    lib = L.lib()
+    msg = ctypes.create_string_buffer(256)
+    dummy = ctypes.c_void_p(1)
+    for dims in ((2 ** 30, 2 ** 30, 2 ** 30), (70000, 70000, 1), (2 ** 31 - 1, 2, 2)):
+        huge = L.Mesh(*dims, 2, 0, 0, 0, 1, 1, 1)
+        rc = lib.ht_head_apply_dot_noalloc(ctypes.byref(huge), 0, 0.1, 1.0, dummy, dummy, dummy, dummy,
+                                           0, None, msg, len(msg))
+        assert rc == L.HT_EINVAL, dims
+        assert b"too large" in msg.value, msg.value
