@@ -50,7 +50,7 @@ enum { HT_BC_NONE = 0, HT_BC_DIRICHLET = 1, HT_BC_FLUX = 2 };
 enum { HT_FP64 = 0, HT_MIXED = 1 };
 enum { HT_KRYLOV_BICGSTAB = 0, HT_KRYLOV_GMRES = 1 };
 enum { HT_PREC_JACOBI = 0, HT_PREC_CHEBYSHEV = 1 };
-enum { HT_APPLY_AUTO = 0, HT_APPLY_TILED = 1, HT_APPLY_TWO_PASS = 2 };
+enum { HT_APPLY_AUTO = 0, HT_APPLY_TILED = 1, HT_APPLY_TWO_PASS = 2, HT_APPLY_SINGLE_PASS = 3 };
 
 typedef struct ht_ctx ht_ctx;
 
@@ -103,9 +103,12 @@ typedef struct {
  * z_chunks > 0 fixes the number of z chunks of the operator tiles (0: the
  * library picks it from the SM count).  apply_variant selects the operator
  * kernel: HT_APPLY_TILED (one fused owner-computes tile kernel),
- * HT_APPLY_TWO_PASS (cells into an element buffer, then a node gather) or
- * HT_APPLY_AUTO (two-pass in FP32, tiled in FP64).  Both change performance,
- * not results beyond rounding order.
+ * HT_APPLY_TWO_PASS (cells into an element buffer, then a node gather),
+ * HT_APPLY_SINGLE_PASS (on Q1 meshes the FP32 head CG runs one tiled kernel
+ * per iteration in the single-reduction form of CG; other operators as AUTO)
+ * or HT_APPLY_AUTO (single-pass head CG on Q1 in FP32, otherwise two-pass
+ * in FP32 and tiled in FP64).  They change performance, not results beyond
+ * rounding order.
  * inner_tol is the smallest relative residual reduction asked of one FP32
  * inner solve of the head system (the solve stops earlier when the outer
  * tolerance needs less); inner_tol_heat is the same for the heat system

@@ -18,7 +18,7 @@ HT_BC_NONE, HT_BC_DIRICHLET, HT_BC_FLUX = 0, 1, 2
 HT_FP64, HT_MIXED = 0, 1
 HT_KRYLOV_BICGSTAB, HT_KRYLOV_GMRES = 0, 1
 HT_PREC_JACOBI, HT_PREC_CHEBYSHEV = 0, 1
-HT_APPLY_AUTO, HT_APPLY_TILED, HT_APPLY_TWO_PASS = 0, 1, 2
+HT_APPLY_AUTO, HT_APPLY_TILED, HT_APPLY_TWO_PASS, HT_APPLY_SINGLE_PASS = 0, 1, 2, 3
 HT_BATCH_CONCURRENT, HT_BATCH_SHARED_LAUNCHES = 0, 1
 
 ERROR_NAMES = {0: "HT_OK", -1: "HT_EINVAL", -2: "HT_ENOMEM", -3: "HT_ECUDA", -4: "HT_ENOCONV",

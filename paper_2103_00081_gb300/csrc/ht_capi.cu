@@ -831,7 +831,7 @@ void ht_destroy(ht_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (auto* gr : {&c->g_cg[0], &c->g_cg[1], &c->g_bi[0], &c->g_bi[1]})
+    for (auto* gr : {&c->g_cg[0], &c->g_cg[1], &c->g_bi[0], &c->g_bi[1], &c->g_cg1})
         if (gr->exec) cudaGraphExecDestroy(gr->exec);
     double** v64[] = {&c->h, &c->T, &c->g[0], &c->g[1], &c->Fstat[0], &c->Fstat[1], &c->F[0], &c->F[1],
                       &c->extra[0], &c->extra[1], &c->x, &c->r, &c->z, &c->p, &c->q, &c->b, &c->D,
@@ -1020,7 +1020,7 @@ int ht_set_solver(ht_ctx* c, const ht_solver_opts* o) {
     if (o->z_chunks < 0) return fail(c, HT_EINVAL, "z_chunks must be >= 0");
     if (!(o->inner_tol >= 0 && o->inner_tol < 1) || !(o->inner_tol_heat >= 0 && o->inner_tol_heat < 1))
         return fail(c, HT_EINVAL, "inner tolerances must be in [0, 1)");
-    if (o->apply_variant < HT_APPLY_AUTO || o->apply_variant > HT_APPLY_TWO_PASS)
+    if (o->apply_variant < HT_APPLY_AUTO || o->apply_variant > HT_APPLY_SINGLE_PASS)
         return fail(c, HT_EINVAL, "unknown apply variant %d", o->apply_variant);
     c->opts = *o;
     return HT_OK;

@@ -202,6 +202,7 @@ struct ht_ctx {
         double ss = 0.0;                // operator scalars baked into the captured launches
     };
     FusedGraph g_cg[2], g_bi[2];
+    FusedGraph g_cg1;                   // single-pass Q1 CG iteration (FP32)
     // iterations of the inner solves of the last step, per field and outer
     // pass: the next solve checks convergence first near that count
     int iter_hint[2][8] = {};
@@ -273,6 +274,13 @@ int fused_cg_iteration64(ht_ctx* c, double dt, double* x, double* r, const doubl
 int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* Dinv, float* p, Scal* sc,
                          int first);
 bool fused_cg_available(const ht_ctx* c, int fp32);
+// single-pass Jacobi-CG iteration of the Q1 head system in FP32 (ht_q1.cu):
+// reads r, p (halos included) and writes r_out, p_out (the next iteration
+// swaps them); x is updated in place.  first = 1 only forms the scalars of
+// the start (x unchanged, r_out = r, p_out = D^-1 r)
+bool q1_cg_available(const ht_ctx* c, int fp32);
+int q1_cg_iteration32(ht_ctx* c, float dt, float* x, const float* r, const float* p, float* r_out, float* p_out,
+                      Scal* sc, int first);
 // fused two-pass Jacobi-BiCGStab iteration of the heat system (ht_ops.cu)
 int fused_bicgstab_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* rh, double* p, double* v,
                                double* t, const double* Dinv, Scal* sc);

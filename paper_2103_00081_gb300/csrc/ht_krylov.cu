@@ -913,6 +913,28 @@ int run_cg(ht_ctx* c, double dt, const V& w, const T* b, int slot, double tol, i
         return HT_OK;
     }
     int it_enq = 0;
+    if (sizeof(T) == 4 && q1_cg_available(c, 1)) {
+        // one launch per iteration (single-reduction CG on Q1 tiles); the
+        // first launch only forms alpha_0 = r.z / z.Az.  Launch j reads r, p
+        // from copy j % 2 and writes copy (j + 1) % 2 (copy 1 of r is s, of p
+        // is q, both free in the head CG); graphs hold an even number of
+        // launches, so every replay starts on the same copy
+        const double ss = c->Ss;
+        float* rr[2] = {(float*)w.r, (float*)w.s};
+        float* pp[2] = {(float*)w.p, (float*)w.q};
+        const void* key[6] = {w.x, w.r, w.p, w.s, w.q, sc};
+        ht_ctx::FusedGraph& gr = c->g_cg1;
+        if (gr.exec && gr.ss != ss) gr.dt = -1.0;
+        long long j = 0;
+        HT_TRY(drive_fused(c, slot, gr, key, 6, dt, HT_PROF_CG_ITER, 1, [&](int first) {
+            const int a = (int)(j & 1);
+            ++j;
+            return q1_cg_iteration32(c, (float)dt, (float*)w.x, rr[a], pp[a], rr[a ^ 1], pp[a ^ 1], sc, first);
+        }));
+        gr.ss = ss;
+        *iters = c->scal_host[slot].iters;
+        return HT_OK;
+    }
     if (fused_cg_available(c, sizeof(T) == 4)) {
         // two launches per iteration: the p update rides in the element pass,
         // the x / r update and the next dot products in the node gather

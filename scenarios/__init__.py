@@ -176,7 +176,7 @@ def gaussian_field_fft(shape, spacing, corr_len, sigma, rng):
     kx = 2 * np.pi * np.fft.rfftfreq(nx, d=hx)
     k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
     amp = np.exp(-0.25 * k2 * corr_len ** 2)          # sqrt of Gaussian spectrum
-    f = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=shape)
+    f = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=shape, axes=(0, 1, 2))
     std = f.std()
     return sigma * f / (std if std > 0 else 1.0)
 

@@ -450,3 +450,56 @@ def test_error_codes(Sim):
     sim2 = Sim.from_scenario(sc2, tol=1e-14, max_iter=1)
     st = sim2.step(sc2.dt, check=False)
     assert st["rc"] == L.HT_ENOCONV
+
+
+Q1_SINGLE = [(1, 33, 20, 7, 41), (1, 57, 44, 9, 42), (1, 1, 1, 1, 43), (1, 16, 16, 16, 44), (1, 29, 21, 5, 45)]
+
+
+@pytest.mark.parametrize("case", Q1_SINGLE, ids=_ids)
+@pytest.mark.parametrize("faces", [(0, 1), (0, 1, 2, 3, 4, 5), (4,)])
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+def test_single_pass_q1_cg_steps_match_oracle(Sim, case, faces, chunks):
+    """The single-pass Q1 head CG (one tiled launch per iteration, the
+    single-reduction form of CG with the Jacobi diagonal formed from the
+    cell conductivities): mixed-precision steps match the oracle, the GPU
+    solution solves the oracle's system of the step, and the inner iteration
+    count stays within rounding of classical PCG over the tiled apply.  The
+    tiles own at most 28 x 20 node columns, so these meshes give several
+    tiles with ragged tails; chunks 0 lets the library split the planes (one
+    plane per chunk on these small meshes), 1 and 3 force multi-plane chunks.
+    The face sets put Dirichlet rows on x, on every face, or on the bottom."""
+    from paper_2103_00081_gb300 import _lib as L
+    p, nx, ny, nz, seed = case
+    sc = S.random_small(seed, nx, ny, nz, p, n_piles=3, n_wells=2, faces_head=faces)
+    o = fem.OracleSim(sc)
+    prec = dict(tol=1e-12, precision=L.HT_MIXED, inner_tol=1e-4, max_iter=50000, z_chunks=chunks)
+    sim = Sim.from_scenario(sc, apply_variant=L.HT_APPLY_SINGLE_PASS, **prec)
+    ref = Sim.from_scenario(sc, apply_variant=L.HT_APPLY_TILED, **prec)
+    for _ in range(3):
+        h_prev, T_prev, t1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP), o.t + sc.dt
+        st = sim.step(sc.dt)
+        o.step(sc.dt)
+        h1, T1 = sim.get_field(S.HEAD), sim.get_field(S.TEMP)
+        tol_h, tol_T = _fwd_tol(o, sc.dt, prec["tol"])
+        assert st["res_head"] <= prec["tol"] * 1.001
+        assert _rel(h1, o.h) <= tol_h
+        assert _rel(T1, o.T) <= tol_T
+        rh, rT = _backward(o, sc.dt, t1, h_prev, T_prev, h1, T1)
+        assert rh <= 10 * prec["tol"] and rT <= 10 * prec["tol"], (rh, rT)
+        st_ref = ref.step(sc.dt)
+        assert abs(st["iters_head"] - st_ref["iters_head"]) <= max(3, 0.05 * st_ref["iters_head"]), \
+            (st["iters_head"], st_ref["iters_head"])
+    sim.close()
+    ref.close()
+
+
+def test_single_pass_q1_cg_reports_non_convergence(Sim):
+    """An iteration limit below what the solve needs ends the single-pass CG
+    with HT_ENOCONV, through the same device flags as the other solvers."""
+    from paper_2103_00081_gb300 import _lib as L
+    sc = S.random_small(46, 20, 18, 9, 1)
+    sim = Sim.from_scenario(sc, tol=1e-12, precision=L.HT_MIXED, inner_tol=1e-4, max_iter=3,
+                            apply_variant=L.HT_APPLY_SINGLE_PASS)
+    st = sim.step(sc.dt, check=False)
+    assert st["rc"] == L.HT_ENOCONV
+    sim.close()
