@@ -380,6 +380,15 @@ int ht_head_apply_dot_noalloc(const ht_mesh* mesh, int dirichlet_faces, double S
                               const double* K, const double* x, double* y, double* xAx,
                               int device, void* cuda_stream, char* msg, size_t msg_len);
 
+/* Measured arithmetic peak of `device` in TFLOP/s: fused multiply-add
+ * chains in every thread of a full grid (FP64 if fp64, else FP32), best of
+ * five timed launches.  The paper has no counterpart; it is the denominator
+ * of the roofline of the operator kernels bound by arithmetic (FP64 runs at
+ * a small fraction of the FP32 rate on GB300).  Allocates and frees one
+ * word of device memory; runs on the legacy default stream and restores the
+ * caller's current device.  Errors: HT_EINVAL (null tflops), HT_ECUDA. */
+int ht_fma_peak(int device, int fp64, double* tflops);
+
 /* Bulk coefficients from the mixture rules of Section 2 and the storage of
  * Eq. 1: lambda = (1-phi) lambda_s + phi lambda_w, cT = (1-phi) c_s +
  * phi c_w, Ss = rho_w g / B_poro. */

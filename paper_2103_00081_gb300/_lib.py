@@ -124,6 +124,7 @@ SIGNATURES = {
                                           c_void_p, c_void_p, c_int, c_void_p, ctypes.c_char_p, c_size_t]),
     "ht_mixture": (c_int, [c_double, c_double, c_double, c_double, c_double, POINTER(c_double), POINTER(c_double)]),
     "ht_specific_storage": (c_double, [c_double, c_double, c_double]),
+    "ht_fma_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
 }
 
 

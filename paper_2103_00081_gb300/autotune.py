@@ -25,8 +25,18 @@ def signature(nx: int, ny: int, nz: int, order: int, precision: int) -> str:
     return f"q{order}-{nx}x{ny}x{nz}-prec{precision}"
 
 
-def default_candidates(precision: int) -> List[Dict]:
+def default_candidates(precision: int, order: int = 2) -> List[Dict]:
+    """Operator-kernel and solver choices worth timing for a mesh of this
+    order: on Q1 the single-pass head CG against the two-pass and tiled
+    kernels; on Q2 the two-pass and tiled kernels, the heat Krylov method
+    and a Chebyshev preconditioner."""
     out = []
+    if order == 1:
+        for krylov in (L.HT_KRYLOV_BICGSTAB, L.HT_KRYLOV_GMRES):
+            out.append(dict(apply_variant=L.HT_APPLY_SINGLE_PASS, krylov=krylov, precond=L.HT_PREC_JACOBI))
+        out.append(dict(apply_variant=L.HT_APPLY_TWO_PASS, krylov=L.HT_KRYLOV_BICGSTAB, precond=L.HT_PREC_JACOBI))
+        out.append(dict(apply_variant=L.HT_APPLY_TILED, krylov=L.HT_KRYLOV_BICGSTAB, precond=L.HT_PREC_JACOBI))
+        return out
     variants = [L.HT_APPLY_TWO_PASS, L.HT_APPLY_TILED]
     for v in variants:
         for krylov in (L.HT_KRYLOV_BICGSTAB, L.HT_KRYLOV_GMRES):

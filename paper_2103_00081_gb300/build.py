@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libht.so")
-SOURCES = ["ht_ops.cu", "ht_krylov.cu", "ht_capi.cu", "ht_batch.cu", "ht_unet.cu", "ht_learned.cu", "ht_q1.cu"]
+SOURCES = ["ht_ops.cu", "ht_krylov.cu", "ht_capi.cu", "ht_batch.cu", "ht_unet.cu", "ht_learned.cu", "ht_q1.cu", "ht_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -12,9 +12,12 @@ import bench
 
 
 def test_algorithmic_bytes_per_node():
-    # fused CG iteration: 10 FP32 vector words per node plus K once per cell
-    assert bench.fused_cg_bytes_per_node(2, True) == 40.5      # Q2: a cell per 8 nodes
-    assert bench.fused_cg_bytes_per_node(1, True) == 44.0      # Q1: a cell per node
+    # Q1 single-pass CG: x, r, p read and written (24 B per node) and K once per cell
+    nn, nc = 1000, 729
+    assert bench.cg_bytes(1, nn, nc) == 4.0 * (6 * nn + nc)
+    # Q2 fused CG: the apply (x, y, K per cell) plus 24 B per node of CG vectors;
+    # 32.5 B per node when a cell holds eight nodes
+    assert bench.cg_bytes(2, 8000, 1000) / 8000 == 32.5
     # operator apply: x read, y written, K once per cell
     assert bench.apply_bytes_per_node(2, False) == 17.0
     assert bench.apply_bytes_per_node(1, True) == 12.0
@@ -25,26 +28,26 @@ def _tree(tmp_path):
     root = tmp_path / "repo"
     (root / "profiles").mkdir(parents=True)
     (root / "paper_2103_00081_gb300" / "csrc").mkdir(parents=True)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "fused_cg_traffic.json"), root / "profiles")
-    shutil.copy(os.path.join(bench.ROOT, "paper_2103_00081_gb300", "csrc", "ht_ops.cu"),
-                root / "paper_2103_00081_gb300" / "csrc")
+    for f in ("ht_q1.cu", "ht_ops.cu"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_2103_00081_gb300", "csrc", f),
+                    root / "paper_2103_00081_gb300" / "csrc")
     return root
 
 
 def test_traffic_record_is_used_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):
     root = _tree(tmp_path)
-    rec = json.load(open(root / "profiles" / "fused_cg_traffic.json"))
-    # a record taken on the copied source
-    with open(root / "paper_2103_00081_gb300" / "csrc" / "ht_ops.cu", "rb") as f:
-        rec["source_sha256"] = hashlib.sha256(f.read()).hexdigest()
-    with open(root / "profiles" / "fused_cg_traffic.json", "w") as f:
-        json.dump(rec, f)
+    src = root / "paper_2103_00081_gb300" / "csrc" / "ht_q1.cu"
+    recs = [{"workload": "city_q1 512x512x96 Q1", "dram_bytes_per_iteration": 7.0e8,
+             "source_sha256": hashlib.sha256(src.read_bytes()).hexdigest()},
+            {"workload": "other", "dram_bytes_per_iteration": 1.0, "source_sha256": "0"}]
+    (root / "profiles" / "cg_iteration_traffic.json").write_text(json.dumps(recs))
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.measured_traffic(rec["workload"]) == rec["dram_bytes_per_iteration"]
-    assert bench.measured_traffic("another workload") is None
-    with open(root / "paper_2103_00081_gb300" / "csrc" / "ht_ops.cu", "a") as f:
+    assert bench.measured_traffic("city_q1 512x512x96 Q1", 1) == 7.0e8
+    assert bench.measured_traffic("another workload", 1) is None
+    assert bench.measured_traffic("city_q1 512x512x96 Q1", 2) is None      # taken on the Q1 kernel only
+    with open(src, "a") as f:
         f.write("\n// changed\n")
-    assert bench.measured_traffic(rec["workload"]) is None
+    assert bench.measured_traffic("city_q1 512x512x96 Q1", 1) is None
 
 
 def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
@@ -72,11 +75,14 @@ def test_clock_record_parser(tmp_path):
     assert c.summary()["reasons"] == ["unsampled"]
 
 
-def test_cpu_baseline_reports_rate_step_time_and_spmv_bandwidth():
-    import types
-    args = types.SimpleNamespace(cpu_sample_cells=6)
-    sc_full = bench.workload("ates_q2")
-    cb = bench.cpu_baseline(args, sc_full)
+def test_cpu_baseline_reports_rate_fit_and_spmv_bandwidth():
+    sc_full = bench.workload("plain_q1")
+    cb = bench.cpu_baseline(sc_full, "plain_q1")
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
-    assert cb["s_per_step_sample"] > 0 and cb["spmv"]["gbs"] > 0
-    assert cb["spmv"]["rows"] == (2 * 6 + 1) ** 2 * (2 * 2 + 1)
+    assert len(cb["s_per_step_samples"]) == 2 and all(t > 0 for t in cb["s_per_step_samples"])
+    assert cb["exponent"] >= 1.0 and cb["host"]["nproc"] >= 1
+    assert cb["spmv"]["gbs"] > 0 and cb["spmv"]["rows"] == 17 ** 3
+    # the extrapolation follows the fitted law from the larger sample
+    n = cb["nodes_samples"]
+    assert cb["s_per_step_full_extrapolated"] == pytest.approx(
+        cb["s_per_step_samples"][1] * (sc_full.n_nodes / n[1]) ** cb["exponent"])

@@ -1,13 +1,18 @@
-"""Parity at the full size of the step benchmark: the ATES-like layered
-aquifer of 128 x 128 x 32 Q2 cells (4,293,185 nodes per field, two spread
-wells), with the solver options the benchmark times (mixed precision, the
-two-pass fused kernels, BiCGStab for heat).
+"""Parity at the full sizes of the step benchmark's workloads, with the
+solver options the benchmark times (mixed precision; on Q1 the single-pass
+head CG, on Q2 the two-pass fused kernels; BiCGStab for heat):
 
-The oracle cannot assemble this mesh, so it computes sampled rows one by one
-(``fem.RowOracle``, itself checked against the assembled oracle at every row
-of small meshes).  The samples cover random nodes, every face and the layer
-next to it (Dirichlet rows and lifted rows), the corners, the K layer
-interfaces and the well nodes.
+* city_q1: 512 x 512 x 96 Q1 (25,527,393 nodes per field), layered + GRF lnK,
+  20,000 piles and 50 box heat sources -- the benchmark's default workload;
+* pile_q1: 256 x 256 x 64 Q1 (4,293,185 nodes), GRF lnK, 1000 piles;
+* ates_q2: 128 x 128 x 32 Q2 (4,293,185 nodes), lognormal layers, two wells.
+
+The oracle cannot assemble these meshes, so it computes sampled rows one by
+one (``fem.RowOracle``, itself checked against the assembled oracle at every
+row of small meshes).  The samples cover random nodes, every face and the
+layer next to it (Dirichlet rows and lifted rows), the corners, the K layer
+interfaces, nodes carrying pile, box or well loads, and the nodes of largest
+load.
 
 * FP64 operator rows (the tiled kernels of the plain FP64 leg): |diff| <=
   1e-12 times the larger of the row's sum of absolute terms and the largest
@@ -29,17 +34,17 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
-@pytest.fixture(scope="module")
-def full(built_lib):
-    from paper_2103_00081_gb300 import _lib as L
-    from paper_2103_00081_gb300 import hydro
-    sc = S.config2()
-    ro = fem.RowOracle(sc)
-    sim = hydro.Simulator.from_scenario(
-        sc, tol=TOL, precision=L.HT_MIXED, inner_tol=1e-5, inner_tol_heat=1e-4, max_iter=200000,
-        apply_variant=L.HT_APPLY_TWO_PASS, krylov=L.HT_KRYLOV_BICGSTAB, precond=L.HT_PREC_JACOBI)
-    yield sc, ro, sim, _rows(sc, ro)
-    sim.close()
+def _layer_planes(sc):
+    """Node planes at and beside the cell-layer interfaces of the K layering."""
+    if sc.name.startswith("ates"):
+        nb = int(round(sc.nz * 10 / 32))
+        return [nb, sc.nz - nb]
+    if sc.name.startswith("city"):
+        zc = (np.arange(sc.nz) + 0.5) / sc.nz
+        bounds = np.cumsum([f for _, f, _ in S.CITY_LAYERS])
+        lay = np.searchsorted(bounds, zc, side="right")
+        return [int(k) for k in np.nonzero(np.diff(lay))[0] + 1]
+    return [sc.nz // 2]
 
 
 def _rows(sc, ro, n_random=96, seed=0):
@@ -57,15 +62,33 @@ def _rows(sc, ro, n_random=96, seed=0):
         for j in (0, Ny - 1):
             for k in (0, Nz - 1):
                 rows.add(int(m.node_index(i, j, k)))
-    # K layer interfaces (10 / 12 / 10 of 32 cell layers) and the node layers beside them
-    nb = int(round(sc.nz * 10 / 32))
-    for kc in (nb, sc.nz - nb):
+    for kc in _layer_planes(sc):
         for k in (m.p * kc - 1, m.p * kc, m.p * kc + 1):
             rows.add(int(m.node_index(Nx // 3, 2 * Ny // 3, k)))
-    # the nodes of largest injection weight and of largest head load
+    # nodes of the first piles and boxes, the wells and the largest head loads
+    for w in ro.pile_w[:4] + ro.box_w[:2]:
+        keys = sorted(w)
+        rows.update(int(keys[i]) for i in rng.integers(0, len(keys), min(6, len(keys))))
     rows.update(int(i) for i in np.argsort(ro.d_well)[-8:])
     rows.update(int(i) for i in np.argsort(np.abs(ro.F_static[fem.HEAD]))[-8:])
     return sorted(rows)
+
+
+WORKLOADS = {"city_q1": S.config5, "pile_q1": S.config3, "ates_q2": S.config2}
+
+
+@pytest.fixture(scope="module", params=list(WORKLOADS))
+def full(request, built_lib):
+    from paper_2103_00081_gb300 import _lib as L
+    from paper_2103_00081_gb300 import hydro
+    sc = WORKLOADS[request.param]()
+    ro = fem.RowOracle(sc)
+    variant = L.HT_APPLY_SINGLE_PASS if sc.order == 1 else L.HT_APPLY_TWO_PASS
+    sim = hydro.Simulator.from_scenario(
+        sc, tol=TOL, precision=L.HT_MIXED, inner_tol=1e-5, inner_tol_heat=1e-4, max_iter=200000,
+        apply_variant=variant, krylov=L.HT_KRYLOV_BICGSTAB, precond=L.HT_PREC_JACOBI)
+    yield sc, ro, sim, _rows(sc, ro)
+    sim.close()
 
 
 def _check(got, ref, scale, what, tol=1e-12):
