@@ -831,7 +831,7 @@ void ht_destroy(ht_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (auto* gr : {&c->g_cg[0], &c->g_cg[1], &c->g_bi[0], &c->g_bi[1], &c->g_cg1})
+    for (auto* gr : {&c->g_cg[0], &c->g_cg[1], &c->g_bi[0], &c->g_bi[1], &c->g_cg1, &c->g_bi1})
         if (gr->exec) cudaGraphExecDestroy(gr->exec);
     double** v64[] = {&c->h, &c->T, &c->g[0], &c->g[1], &c->Fstat[0], &c->Fstat[1], &c->F[0], &c->F[1],
                       &c->extra[0], &c->extra[1], &c->x, &c->r, &c->z, &c->p, &c->q, &c->b, &c->D,

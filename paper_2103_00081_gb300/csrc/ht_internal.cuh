@@ -203,6 +203,7 @@ struct ht_ctx {
     };
     FusedGraph g_cg[2], g_bi[2];
     FusedGraph g_cg1;                   // single-pass Q1 CG iteration (FP32)
+    FusedGraph g_bi1;                   // single-pass Q1 BiCGStab iteration (FP32)
     // iterations of the inner solves of the last step, per field and outer
     // pass: the next solve checks convergence first near that count
     int iter_hint[2][8] = {};
@@ -281,6 +282,14 @@ bool fused_cg_available(const ht_ctx* c, int fp32);
 bool q1_cg_available(const ht_ctx* c, int fp32);
 int q1_cg_iteration32(ht_ctx* c, float dt, float* x, const float* r, const float* p, float* r_out, float* p_out,
                       Scal* sc, int first);
+// single-pass heat applies of the Q1 BiCGStab iteration in FP32 (ht_q1.cu):
+// reads p_in, v_in (halos included), writes p_out, v_out, t; then x, r
+bool q1_bicgstab_available(const ht_ctx* c);
+int q1_bicgstab_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* rh, const float* p_in,
+                            const float* v_in, float* p_out, float* v_out, float* t, const float* Dinv, Scal* sc);
+// pointwise BiCGStab update of x and r with the next beta (ht_ops.cu)
+int launch_fbi_update32(ht_ctx* c, float* x, float* r, const float* p, const float* v, const float* t,
+                        const float* Dinv, const float* rh, Scal* sc);
 // fused two-pass Jacobi-BiCGStab iteration of the heat system (ht_ops.cu)
 int fused_bicgstab_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* rh, double* p, double* v,
                                double* t, const double* Dinv, Scal* sc);

@@ -986,8 +986,28 @@ int run_bicgstab(ht_ctx* c, double dt, const V& w, const T* b, int slot, double 
             break;
         }
         int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
-        const bool fused = fused_cg_available(c, sizeof(T) == 4);
-        if (fused) {
+        const bool q1 = sizeof(T) == 4 && q1_bicgstab_available(c);
+        const bool fused = q1 || fused_cg_available(c, sizeof(T) == 4);
+        if (q1) {
+            // two tiled heat applies and the update per iteration; iteration j
+            // reads p, v from copy j % 2 and writes copy (j + 1) % 2 (copy 1 is
+            // ph, sh, free in the fused iteration); graphs hold an even number
+            // of iterations, so every replay starts on the same copy
+            const double ss = c->cT_u + 3.0 * c->lam_u + 7.0 * c->cw;
+            float* pp[2] = {(float*)w.p, (float*)w.ph};
+            float* vv[2] = {(float*)w.v, (float*)w.sh};
+            const void* key[10] = {w.x, w.r, w.rh, w.p, w.v, w.ph, w.sh, w.t, w.Dinv, sc};
+            ht_ctx::FusedGraph& gr = c->g_bi1;
+            if (gr.exec && gr.ss != ss) gr.dt = -1.0;
+            long long j = 0;
+            HT_TRY(drive_fused(c, slot, gr, key, 10, dt, HT_PROF_BICGSTAB_ITER, 3, [&](int) {
+                const int a = (int)(j & 1);
+                ++j;
+                return q1_bicgstab_iteration32(c, (float)dt, (float*)w.x, (float*)w.r, (const float*)w.rh, pp[a],
+                                               vv[a], pp[a ^ 1], vv[a ^ 1], (float*)w.t, (const float*)w.Dinv, sc);
+            }));
+            gr.ss = ss;
+        } else if (fused) {
             // five launches per iteration (two element / node pass pairs and
             // the update); the first iteration needs no special form
             const double ss = c->cT_u + 3.0 * c->lam_u + 7.0 * c->cw;

@@ -2188,6 +2188,17 @@ int fused_cg_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* D
     return c->grid.P == 1 ? fused_cg_iteration_P<1, float>(c, dt, x, r, Dinv, p, sc, first)
                           : fused_cg_iteration_P<2, float>(c, dt, x, r, Dinv, p, sc, first);
 }
+int launch_fbi_update32(ht_ctx* c, float* x, float* r, const float* p, const float* v, const float* t,
+                        const float* Dinv, const float* rh, Scal* sc) {
+    const int G = vec_grid(c);
+    if (G > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
+    fbi_update_kernel<float><<<G, 256, 0, c->stream>>>(c->grid.nn, x, r, p, v, t, Dinv, rh, sc, c->part,
+                                                        c->part_stride);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
 int fused_bicgstab_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* rh, double* p, double* v,
                                double* t, const double* Dinv, Scal* sc) {
     return c->grid.P == 1 ? fused_bicgstab_iteration_P<1, double>(c, dt, x, r, rh, p, v, t, Dinv, sc)

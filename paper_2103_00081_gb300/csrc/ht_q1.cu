@@ -420,11 +420,413 @@ int q1_split_z(int Nz, int tiles, int resident) {
     return best;
 }
 
+// ---------------------------------------------------------------------------
+// Heat operator on Q1 cells, fused into the BiCGStab iteration of the FP32
+// inner heat solve (Eq. 4 in energy form):
+//     A_T u = c_T M u + dt lambda K u + dt c_w C(q) u (+ dt d_w u on injection-well nodes),
+//     C_ij = sum over Gauss points of W N_i (q . grad N_j),  q = -K_c grad h^{n+1}.
+// Mass and conduction use the h x h x h eigenbasis of the head kernel.  The
+// advection uses the structure of Q1 at the 2-point Gauss rule: du/dx is
+// constant in x and bilinear in (y, z), so at the 8 Gauss points it takes 4
+// values, the interpolation of the 4 x-edge differences of the cell by the
+// 1D Gauss-point matrix B = [[g1, g0], [g0, g1]] (g0, g1 the two Gauss
+// abscissae on [0, 1]) in y and z; the same holds for q from the x-edge
+// differences of h.  Testing with N_i and summing the two x Gauss points
+// (N_0 + N_1 = 1 there) leaves, for every node (a, b, c) of the cell,
+//     dt c_w (-K_c) W [Rx(b,c) / Hx^2 + Ry(a,c) / Hy^2 + Rz(a,b) / Hz^2],
+// Rx = B^T B^T applied to the Gauss-point products of the interpolated h and
+// u differences (W = Hx Hy Hz / 8, the Gauss weight of the cell).
+//
+// Two launches per BiCGStab iteration, each one tiled march like the head
+// kernel (halo of one node, tile of at most 30 x 22 node columns):
+//   MODE 0: p' = r + beta (p - omega v), v' = A (D^-1 p'); the last CTA
+//           forms alpha = rho / (r^.v');
+//   MODE 1: s = r - alpha v', t = A (D^-1 s); the last CTA forms
+//           omega = (t.s) / (t.t);
+// then the pointwise update of x and r (fbi_update_kernel).  p and v are read
+// on the halo and written on the tile, so they come in two copies (an
+// iteration reads one and writes the other).
+// ---------------------------------------------------------------------------
+constexpr int kHTX = 30, kHTY = 22;          // largest owned tile of the heat kernel
+constexpr int kHStages = 3;
+
+struct Q1HeatConst {
+    float MA[8], KB[8];     // mode eigenvalues: lambda_l = c_T MA_l + lambda KB_l
+    float g0, g1;           // Gauss abscissae on [0, 1]
+    float fx, fy, fz;       // dt c_w W / H_d^2 (times -K_c per cell)
+    float cT, lam;          // uniform values (per-cell arrays when present)
+    float dt;
+};
+
+struct Q1HeatSmem {
+    float ld_r[kHStages][kSY][kSX];
+    float ld_d[kHStages][kSY][kSX];
+    float ld_h[kHStages][kSY][kSX];
+    float ld_p[kHStages][kSY][kSX];
+    float ld_v[kHStages][kSY][kSX];
+    float ld_k[kHStages][kSY][kSX];
+    float ld_o[kHStages][kSY][kSX];   // r^ (MODE 0) at owned nodes
+    float ld_w[kHStages][kSY][kSX];   // injection-well coefficients at owned nodes
+    float uc[kSY][kSX];               // operator input at the plane of stage A
+    float hc[kSY][kSX];               // head at the plane of stage A
+    float sc[4][kSY][kSX];            // corner contributions of each cell
+};
+
+// 2D interpolation of a 2 x 2 array d[j][i] (i fastest) to the Gauss points:
+// o[qj][qi] = sum B[qj][j] B[qi][i] d[j][i], B[q][i] = g1 if q == i else g0
+__device__ __forceinline__ void gauss2(const float (&d)[4], float g0, float g1, float (&o)[4]) {
+    float t[4];
+    t[0] = fmaf(g1, d[0], g0 * d[1]);   // along i
+    t[1] = fmaf(g0, d[0], g1 * d[1]);
+    t[2] = fmaf(g1, d[2], g0 * d[3]);
+    t[3] = fmaf(g0, d[2], g1 * d[3]);
+    o[0] = fmaf(g1, t[0], g0 * t[2]);   // along j
+    o[1] = fmaf(g1, t[1], g0 * t[3]);
+    o[2] = fmaf(g0, t[0], g1 * t[2]);
+    o[3] = fmaf(g0, t[1], g1 * t[3]);
+}
+
+template <int MODE, bool PERCELL, bool WELLS>
+__global__ void __launch_bounds__(kBX * kBY, 2)
+q1_heat_kernel(const Grid g, const float* __restrict__ K, const float* __restrict__ cTc,
+               const float* __restrict__ lamc, const float* __restrict__ h, const float* __restrict__ r,
+               const float* __restrict__ Dinv, const float* __restrict__ p, const float* __restrict__ v,
+               const float* __restrict__ rh, const float* __restrict__ wd, float* __restrict__ p_out,
+               float* __restrict__ y_out, const Q1HeatConst cst, const int ntx, const int nty, const int nzc,
+               Scal* __restrict__ s, double* __restrict__ part, const int stride) {
+    if (s->done) return;
+    extern __shared__ __align__(16) unsigned char q1h_smem_raw[];
+    Q1HeatSmem& sm = *reinterpret_cast<Q1HeatSmem*>(q1h_smem_raw);
+    const float beta = (float)s->beta, omega = (float)s->omega, alpha = (float)s->alpha;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = (int)((long long)blockIdx.x * g.Nx / ntx), i1 = (int)((long long)(blockIdx.x + 1) * g.Nx / ntx);
+    const int j0 = (int)((long long)blockIdx.y * g.Ny / nty), j1 = (int)((long long)(blockIdx.y + 1) * g.Ny / nty);
+    const int k0 = (int)((long long)blockIdx.z * g.Nz / nzc), k1 = (int)((long long)(blockIdx.z + 1) * g.Nz / nzc);
+    const int w = i1 - i0, hh = j1 - j0;
+    const int NXY = g.Nx * g.Ny, CXY = g.ncx * g.ncy;
+    const int dm = g.dmask;
+    const int mbeg = k0 - 1, mend = k1;
+
+    // slot (R, C) = node (C - 1, R - 1) of the tile and the cell whose low corner it is
+    unsigned fl[kRows];
+    int nxy[kRows], cxy[kRows];
+#pragma unroll
+    for (int b = 0; b < kRows; ++b) {
+        const int R = ty + kBY * b, C = tx;
+        const int gi = i0 + C - 1, gj = j0 + R - 1;
+        unsigned f = 0;
+        if (R >= 1 && R <= hh && C >= 1 && C <= w) f |= F_OWN;
+        if (gi >= 0 && gi < g.Nx && gj >= 0 && gj < g.Ny) f |= F_NIN;
+        if (gi >= 0 && gi < g.ncx && gj >= 0 && gj < g.ncy) f |= F_FIN;
+        if (((dm & 1) && gi == 0) || ((dm & 2) && gi == g.Nx - 1) || ((dm & 4) && gj == 0) ||
+            ((dm & 8) && gj == g.Ny - 1))
+            f |= F_DXY;
+        fl[b] = f;
+        nxy[b] = (f & F_NIN) ? gi + g.Nx * gj : 0;
+        cxy[b] = (f & F_FIN) ? gi + g.ncx * gj : 0;
+    }
+
+    auto issue = [&](int q) {
+        if (q <= mend) {
+            const int st = (q - mbeg) % kHStages;
+            const bool plane_ok = q >= 0 && q < g.Nz;
+            const bool layer_ok = q >= 0 && q < g.ncz;
+            const int pofs = plane_ok ? NXY * q : 0, cofs = layer_ok ? CXY * q : 0;
+#pragma unroll
+            for (int b = 0; b < kRows; ++b) {
+                const int R = ty + kBY * b, C = tx;
+                const bool nok = plane_ok && (fl[b] & F_NIN);
+                const int id = nok ? nxy[b] + pofs : 0;
+                cp_async4(&sm.ld_r[st][R][C], r + id, nok);
+                cp_async4(&sm.ld_d[st][R][C], Dinv + id, nok);
+                cp_async4(&sm.ld_h[st][R][C], h + id, nok);
+                cp_async4(&sm.ld_v[st][R][C], v + id, nok);
+                if (MODE == 0) {
+                    cp_async4(&sm.ld_p[st][R][C], p + id, nok);
+                    cp_async4(&sm.ld_o[st][R][C], rh + id, nok && (fl[b] & F_OWN));
+                }
+                if (WELLS) cp_async4(&sm.ld_w[st][R][C], wd + id, nok && (fl[b] & F_OWN));
+                const bool kok = layer_ok && (fl[b] & F_FIN);
+                cp_async4(&sm.ld_k[st][R][C], K + (kok ? cxy[b] + cofs : 0), kok);
+            }
+        }
+        cp_async_commit();
+    };
+
+    // per-row state carried up the march
+    float hu[kRows], hv[kRows], hrh[kRows], hwd[kRows];   // node values of the plane of stage B
+    float Up[kRows][4], Hp[kRows][4], Fp[kRows][4], Tp[kRows][4];
+    float Kf[kRows], cTf[kRows], lamf[kRows];
+#pragma unroll
+    for (int b = 0; b < kRows; ++b) {
+        hu[b] = hv[b] = hrh[b] = hwd[b] = 0.0f;
+        Kf[b] = 0.0f;
+        cTf[b] = cst.cT;
+        lamf[b] = cst.lam;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Up[b][q] = Hp[b][q] = Fp[b][q] = Tp[b][q] = 0.0f;
+    }
+    float acc0 = 0.0f, acc1 = 0.0f;
+
+    issue(mbeg);
+    issue(mbeg + 1);
+    for (int m = mbeg; m <= mend; ++m) {
+        issue(m + 2);
+        asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+        __syncthreads();
+        const int st = (m - mbeg) % kHStages;
+        const bool plane_ok = m >= 0 && m < g.Nz;
+        const bool dirz = ((dm & 16) && m == 0) || ((dm & 32) && m == g.Nz - 1);
+        // ---- stage A: the operator input at plane m
+        float au[kRows], av[kRows], arh[kRows], awd[kRows], aK[kRows], acT[kRows], alam[kRows];
+#pragma unroll
+        for (int b = 0; b < kRows; ++b) {
+            const int R = ty + kBY * b, C = tx;
+            const float rv = sm.ld_r[st][R][C];
+            const float vv = sm.ld_v[st][R][C];
+            // MODE 0: p' = r + beta (p - omega v); MODE 1: s = r - alpha v
+            const float val = MODE == 0 ? fmaf(beta, fmaf(-omega, vv, sm.ld_p[st][R][C]), rv) : fmaf(-alpha, vv, rv);
+            const float uin = sm.ld_d[st][R][C] * val;
+            const bool free_node = plane_ok && (fl[b] & F_NIN) && !(fl[b] & F_DXY) && !dirz;
+            sm.uc[R][C] = free_node ? uin : 0.0f;
+            sm.hc[R][C] = sm.ld_h[st][R][C];
+            au[b] = uin;
+            av[b] = val;
+            arh[b] = MODE == 0 ? sm.ld_o[st][R][C] : 0.0f;
+            awd[b] = WELLS ? sm.ld_w[st][R][C] : 0.0f;
+            aK[b] = sm.ld_k[st][R][C];
+            const int cid = cxy[b] + CXY * m;
+            acT[b] = PERCELL && (fl[b] & F_FIN) && m >= 0 && m < g.ncz ? __ldg(cTc + cid) : cst.cT;
+            alam[b] = PERCELL && (fl[b] & F_FIN) && m >= 0 && m < g.ncz ? __ldg(lamc + cid) : cst.lam;
+        }
+        __syncthreads();
+        // ---- cell stage: cell layer m-1 (corners at planes m-1 and m)
+        const bool lay_ok = m - 1 >= 0 && m - 1 < g.ncz && m >= k0;
+#pragma unroll
+        for (int b = 0; b < kRows; ++b) {
+            const int R = ty + kBY * b, C = tx;
+            const int R1 = R + 1 < kSY ? R + 1 : R, C1 = C + 1 < kSX ? C + 1 : C;
+            float U[4] = {sm.uc[R][C], sm.uc[R][C1], sm.uc[R1][C], sm.uc[R1][C1]};
+            float H[4] = {sm.hc[R][C], sm.hc[R][C1], sm.hc[R1][C], sm.hc[R1][C1]};
+            float F[4];
+            face_fwd(U[0], U[1], U[2], U[3], F);
+            float bot[4] = {0.0f, 0.0f, 0.0f, 0.0f}, top[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (lay_ok && (fl[b] & F_FIN)) {
+                // mass + conduction in the eigenbasis
+                float lo[4], hi[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    lo[q] = (Fp[b][q] + F[q]) * fmaf(lamf[b], cst.KB[q], cTf[b] * cst.MA[q]);
+                    hi[q] = (Fp[b][q] - F[q]) * fmaf(lamf[b], cst.KB[q + 4], cTf[b] * cst.MA[q + 4]);
+                }
+                float bh[4], th[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { bh[q] = lo[q] + hi[q]; th[q] = lo[q] - hi[q]; }
+                face_bwd(bh, bot);
+                face_bwd(th, top);
+                // advection: edge differences of u and h (corner index a + 2 b, plane c)
+                const float* U0 = Up[b];
+                const float* H0 = Hp[b];
+                float du[4], dh[4], iu[4], ih[4], pr[4], rx[4], ry[4], rz[4];
+                // x: differences along a at (b, c): index b + 2 c
+                du[0] = U0[1] - U0[0]; du[1] = U0[3] - U0[2]; du[2] = U[1] - U[0]; du[3] = U[3] - U[2];
+                dh[0] = H0[1] - H0[0]; dh[1] = H0[3] - H0[2]; dh[2] = H[1] - H[0]; dh[3] = H[3] - H[2];
+                gauss2(du, cst.g0, cst.g1, iu);
+                gauss2(dh, cst.g0, cst.g1, ih);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pr[q] = iu[q] * ih[q];
+                gauss2(pr, cst.g0, cst.g1, rx);
+                // y: differences along b at (a, c): index a + 2 c
+                du[0] = U0[2] - U0[0]; du[1] = U0[3] - U0[1]; du[2] = U[2] - U[0]; du[3] = U[3] - U[1];
+                dh[0] = H0[2] - H0[0]; dh[1] = H0[3] - H0[1]; dh[2] = H[2] - H[0]; dh[3] = H[3] - H[1];
+                gauss2(du, cst.g0, cst.g1, iu);
+                gauss2(dh, cst.g0, cst.g1, ih);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pr[q] = iu[q] * ih[q];
+                gauss2(pr, cst.g0, cst.g1, ry);
+                // z: differences along c at (a, b): index a + 2 b
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { du[q] = U[q] - U0[q]; dh[q] = H[q] - H0[q]; }
+                gauss2(du, cst.g0, cst.g1, iu);
+                gauss2(dh, cst.g0, cst.g1, ih);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pr[q] = iu[q] * ih[q];
+                gauss2(pr, cst.g0, cst.g1, rz);
+                const float mk = -Kf[b];
+                const float fx = mk * cst.fx, fy = mk * cst.fy, fz = mk * cst.fz;
+                // node (a, b, c): fx Rx(b, c) + fy Ry(a, c) + fz Rz(a, b)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int a = q & 1, bb = q >> 1;
+                    bot[q] += fmaf(fx, rx[bb], fmaf(fy, ry[a], fz * rz[q]));
+                    top[q] += fmaf(fx, rx[bb + 2], fmaf(fy, ry[a + 2], fz * rz[q]));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                sm.sc[q][R][C] = Tp[b][q] + bot[q];
+                Tp[b][q] = top[q];
+                Fp[b][q] = F[q];
+                Up[b][q] = U[q];
+                Hp[b][q] = H[q];
+            }
+        }
+        __syncthreads();
+        // ---- stage B: owned nodes of plane m-1
+        const int kb = m - 1;
+        if (kb >= k0 && kb < k1) {
+            const bool dirb = ((dm & 16) && kb == 0) || ((dm & 32) && kb == g.Nz - 1);
+#pragma unroll
+            for (int b = 0; b < kRows; ++b) {
+                const int R = ty + kBY * b, C = tx;
+                if (fl[b] & F_OWN) {
+                    const int Rm = R > 0 ? R - 1 : 0, Cm = C > 0 ? C - 1 : 0;
+                    float yv = (sm.sc[0][R][C] + sm.sc[1][R][Cm]) + (sm.sc[2][Rm][C] + sm.sc[3][Rm][Cm]);
+                    if (WELLS) yv = fmaf(cst.dt * hwd[b], hu[b], yv);
+                    const bool dir = (fl[b] & F_DXY) || dirb;
+                    if (dir) yv = hu[b];
+                    const int id = nxy[b] + NXY * kb;
+                    y_out[id] = yv;
+                    if (MODE == 0) {
+                        p_out[id] = hv[b];
+                        acc0 = fmaf(hrh[b], yv, acc0);
+                    } else {
+                        acc0 = fmaf(yv, hv[b], acc0);
+                        acc1 = fmaf(yv, yv, acc1);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kRows; ++b) {
+            hu[b] = au[b];
+            hv[b] = av[b];
+            hrh[b] = arh[b];
+            hwd[b] = awd[b];
+            Kf[b] = aK[b];
+            cTf[b] = acT[b];
+            lamf[b] = alam[b];
+        }
+    }
+    double vals[2];
+    vals[0] = block_sum_t(acc0);
+    vals[1] = MODE == 1 ? block_sum_t(acc1) : 0.0;
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    if (MODE == 0) {
+        if (!publish_and_ticket(s, part, vals, 1, stride, nblk)) return;
+        const double a = last_cta_sum(part, (int)nblk);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            s->ticket = 0;
+            s->rv = a;
+            if (a == 0.0 || !isfinite(a)) { s->status = ST_BREAKDOWN; s->done = 1; }
+            else s->alpha = s->rho / a;
+        }
+    } else {
+        if (!publish_and_ticket(s, part + stride, vals, 2, stride, nblk)) return;
+        const double a = last_cta_sum(part + stride, (int)nblk);
+        const double b2 = last_cta_sum(part + 2 * (size_t)stride, (int)nblk);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            s->ticket = 0;
+            s->ts = a;
+            s->tt = b2;
+            s->omega = b2 == 0.0 ? 0.0 : a / b2;   // s = 0 exactly: x += alpha ph is the solution
+        }
+    }
+}
+
+Q1HeatConst q1_heat_const(const ht_ctx* c, double dt) {
+    Q1HeatConst k{};
+    const double* H = c->H;
+    double m1[3][2], k1[3][2];
+    for (int d = 0; d < 3; ++d) {
+        m1[d][0] = H[d];
+        m1[d][1] = H[d] / 3.0;
+        k1[d][0] = 0.0;
+        k1[d][1] = 4.0 / H[d];
+    }
+    for (int cz = 0; cz < 2; ++cz)
+        for (int by = 0; by < 2; ++by)
+            for (int ax = 0; ax < 2; ++ax) {
+                const int l = ax + 2 * by + 4 * cz;
+                const double M = m1[0][ax] * m1[1][by] * m1[2][cz];
+                const double Kl = k1[0][ax] * m1[1][by] * m1[2][cz] + m1[0][ax] * k1[1][by] * m1[2][cz] +
+                                  m1[0][ax] * m1[1][by] * k1[2][cz];
+                k.MA[l] = (float)(M / 64.0);
+                k.KB[l] = (float)(dt * Kl / 64.0);
+            }
+    const double d = 0.5 / sqrt(3.0);
+    k.g0 = (float)(0.5 - d);
+    k.g1 = (float)(0.5 + d);
+    const double W = H[0] * H[1] * H[2] / 8.0;
+    k.fx = (float)(dt * c->cw * W / (H[0] * H[0]));
+    k.fy = (float)(dt * c->cw * W / (H[1] * H[1]));
+    k.fz = (float)(dt * c->cw * W / (H[2] * H[2]));
+    k.cT = (float)c->cT_u;
+    k.lam = (float)c->lam_u;
+    k.dt = (float)dt;
+    return k;
+}
+
+template <int MODE, bool PERCELL, bool WELLS>
+int launch_q1_heat(ht_ctx* c, const Grid& g, const Q1HeatConst& k, const float* r, const float* Dinv, const float* p,
+                   const float* v, const float* rh, float* p_out, float* y_out, Scal* sc) {
+    auto kern = q1_heat_kernel<MODE, PERCELL, WELLS>;
+    static int resident = 0;
+    const size_t smem = sizeof(Q1HeatSmem);
+    if (resident == 0) {
+        HT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int vv = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vv, kern, kBX * kBY, smem) != cudaSuccess || vv < 1) vv = 1;
+        resident = vv;
+    }
+    const int ntx = (g.Nx + kHTX - 1) / kHTX, nty = (g.Ny + kHTY - 1) / kHTY;
+    const int sms = c->num_sms > 0 ? c->num_sms : 148;
+    int nzc = c->opts.z_chunks > 0 ? std::min(c->opts.z_chunks, g.Nz) : q1_split_z(g.Nz, ntx * nty, resident * sms);
+    while (nzc > 1 && ntx * nty * nzc > c->part_stride) --nzc;
+    if (ntx * nty * nzc > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
+    kern<<<dim3(ntx, nty, nzc), dim3(kBX, kBY), smem, c->stream>>>(
+        g, c->K32, c->cT32, c->lam32, c->h32, r, Dinv, p, v, rh, c->wdn32, p_out, y_out, k, ntx, nty, nzc, sc,
+        c->part, c->part_stride);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+template <int MODE>
+int launch_q1_heat_any(ht_ctx* c, const Grid& g, const Q1HeatConst& k, const float* r, const float* Dinv,
+                       const float* p, const float* v, const float* rh, float* p_out, float* y_out, Scal* sc) {
+    const bool percell = c->cT32 != nullptr || c->lam32 != nullptr;
+    const bool wells = c->wdn32 != nullptr;
+    if (percell && (c->cT32 == nullptr || c->lam32 == nullptr))
+        return fail(c, HT_EINVAL, "per-cell c_T and lambda must be given together for the single-pass heat kernel");
+    if (percell)
+        return wells ? launch_q1_heat<MODE, true, true>(c, g, k, r, Dinv, p, v, rh, p_out, y_out, sc)
+                     : launch_q1_heat<MODE, true, false>(c, g, k, r, Dinv, p, v, rh, p_out, y_out, sc);
+    return wells ? launch_q1_heat<MODE, false, true>(c, g, k, r, Dinv, p, v, rh, p_out, y_out, sc)
+                 : launch_q1_heat<MODE, false, false>(c, g, k, r, Dinv, p, v, rh, p_out, y_out, sc);
+}
+
 }  // namespace
 
 bool q1_cg_available(const ht_ctx* c, int fp32) {
     return fp32 && c->grid.P == 1 && c->K32 != nullptr &&
            (c->opts.apply_variant == HT_APPLY_AUTO || c->opts.apply_variant == HT_APPLY_SINGLE_PASS);
+}
+
+bool q1_bicgstab_available(const ht_ctx* c) {
+    const bool percell_ok = (c->cT32 == nullptr) == (c->lam32 == nullptr);
+    return c->grid.P == 1 && c->K32 != nullptr && c->h32 != nullptr && percell_ok &&
+           (c->opts.apply_variant == HT_APPLY_AUTO || c->opts.apply_variant == HT_APPLY_SINGLE_PASS);
+}
+
+int q1_bicgstab_iteration32(ht_ctx* c, float dt, float* x, float* r, const float* rh, const float* p_in,
+                            const float* v_in, float* p_out, float* v_out, float* t, const float* Dinv, Scal* sc) {
+    Grid g = c->grid;
+    g.dmask = c->dmask[HT_TEMP];
+    const Q1HeatConst k = q1_heat_const(c, (double)dt);
+    HT_TRY(launch_q1_heat_any<0>(c, g, k, r, Dinv, p_in, v_in, rh, p_out, v_out, sc));
+    HT_TRY(launch_q1_heat_any<1>(c, g, k, r, Dinv, nullptr, v_out, nullptr, nullptr, t, sc));
+    return launch_fbi_update32(c, x, r, p_out, v_out, t, Dinv, rh, sc);
 }
 
 int q1_cg_iteration32(ht_ctx* c, float dt, float* x, const float* r, const float* p, float* r_out, float* p_out,
