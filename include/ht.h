@@ -281,16 +281,26 @@ const char* ht_batch_last_error(const ht_batch* batch);
 #define HT_BATCH_SHARED_LAUNCHES 1
 int ht_batch_set_mode(ht_batch* batch, int mode);
 
-/* Learned warm start: a small 3D U-Net (2 levels, 16 / 32 channels) with
- * hand-written forward, backward and Adam kernels; BF16 weights in the
- * convolutions, FP32 accumulation and FP32 master weights.  The paper has no
- * learned component; the network predicts step increments that serve as
- * Krylov initial guesses (ht_step_learned_guess).
- *   e1 = relu(conv3(x; cin->16)), p1 = avgpool2(e1), e2 = relu(conv3(p1; 16->32)),
- *   d1 = relu(conv3([e1, upsample2(e2)]; 48->16)), y = conv1(d1; 16->cout)
- * Tensors are device FP32 arrays [channel][D][H][W] (W fastest) with even
- * D, H, W.  Parameters (host FP32, ht_unet_num_params values): per layer the
- * weights [co][ci][27 or 1] then the biases [co].  cout must be 2. */
+/* Learned warm start: a 3D U-Net of four levels (widths 16, 32, 48, 64) with
+ * hand-written forward, backward and Adam kernels.  The paper has no learned
+ * component; the network predicts step increments that serve as Krylov
+ * initial guesses (ht_set_learned_guess).
+ *   level 1: L0 cin -> 16, L1 16 -> 16 (e1); level 2 (pool e1): L2 16 -> 32,
+ *   L3 32 -> 32 (e2); level 3: L4 32 -> 48, L5 48 -> 48 (e3); level 4: L6
+ *   48 -> 64, L7 64 -> 64; up: L8 [up L7, e3] 112 -> 48, L9 48 -> 48, L10
+ *   [up L9, e2] 80 -> 32, L11 32 -> 32, L12 [up L11, e1] 48 -> 16, L13
+ *   16 -> 16; L14 16 -> cout (1x1).  3x3x3 convolutions with zero padding
+ *   and ReLU, 2x2x2 average pooling, nearest upsampling.
+ * The 3x3x3 convolutions, their data gradients and their weight gradients
+ * run on the tensor cores (BF16 operands, FP32 accumulation).  Weights, the
+ * input, stored activations and the gradient signals entering a
+ * convolution's backward pass are BF16; biases, the output, the loss and its
+ * gradient FP32; FP32 master weights for Adam.
+ * Tensors are device FP32 arrays [channel][D][H][W] (W fastest) with D, H, W
+ * multiples of 8 (at least 8).  Parameters (host FP32, ht_unet_num_params
+ * values): per layer in the order above the weights [taps][cout][cin] (tap
+ * 9 (dz+1) + 3 (dy+1) + (dx+1)) then the biases [cout].  1 <= cin <= 16,
+ * cout must be 2. */
 typedef struct ht_unet ht_unet;
 int ht_unet_create(ht_unet** out, int cin, int cout, int device, void* cuda_stream);
 void ht_unet_destroy(ht_unet* net);
@@ -306,18 +316,20 @@ int ht_unet_loss_grad(ht_unet* net, const float* x, const float* target, int D, 
 int ht_unet_train_step(ht_unet* net, const float* x, const float* target, int D, int H, int W,
                        float lr, double* loss);
 
-/* Attach a trained U-Net (cin 4, cout 2) as the source of Krylov initial
+/* Attach a trained U-Net (cin 8, cout 2) as the source of Krylov initial
  * guesses (NULL detaches).  Once two step increments are known, every step
- * builds the features [dT1, dT2, dh1, dh2] / (s_T, s_T, s_h, s_h) from the
- * last two increments (s = their RMS), predicts the next increments
- * (dT, dh) / (s_T, s_h), and for each field starts the Krylov solve from
- * x^n + s * prediction if its true FP64 residual is smaller than that of x^n
- * (the gate; the solver still converges to the same tolerance).  With
- * record != 0 the features and targets of every step are kept for
- * ht_learned_sample, also without a network.  Grid sizes are the node counts
- * rounded up to even. */
+ * builds the features [dT1, dT2, dh1, dh2, F_T, q_x, q_y, q_z]: the last two
+ * increments of T and h divided by s_T and s_h (the RMS of the last ones),
+ * the heat loads of the step and the nodal Darcy velocity -K grad h^n, each
+ * divided by its RMS; the network predicts the next increments
+ * (dT / s_T, dh / s_h), and for each field the Krylov solve starts from
+ * x^n + s * prediction if its residual (FP32 operator, FP64 right-hand side)
+ * is smaller than that of x^n (the gate; the solver still converges to the
+ * same tolerance).  With record != 0 the features and targets of every step
+ * are kept for ht_learned_sample, also without a network.  Grid sizes are
+ * the node counts rounded up to multiples of 8. */
 int ht_set_learned_guess(ht_ctx* ctx, ht_unet* net, int record);
-/* Copy the last step's features [4][D][H][W] and targets [2][D][H][W]
+/* Copy the last step's features [8][D][H][W] and targets [2][D][H][W]
  * (device FP32 buffers of the caller) and report D, H, W; HT_EINVAL when no
  * complete sample exists yet. */
 int ht_learned_sample(ht_ctx* ctx, float* features, float* targets, int* dims);

@@ -1038,8 +1038,8 @@ int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
     ht_step_stats s{};
     int rc = HT_OK;
     cudaEventRecord(ev[0], c->stream);
-    rc = learned_begin(c);
-    if (rc == HT_OK) rc = launch_loads(c, t1);
+    rc = launch_loads(c, t1);
+    if (rc == HT_OK) rc = learned_begin(c);     // features include the heat loads at t^{n+1}
     cudaEventRecord(ev[1], c->stream);
     // head: b = S_s M h^n + dt F_h lifted; x0 = h^n with Dirichlet values
     if (rc == HT_OK) rc = launch_rhs(c, HT_HEAD, dt, c->h, c->b);

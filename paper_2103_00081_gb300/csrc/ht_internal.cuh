@@ -310,6 +310,7 @@ int noalloc_head_apply_dot(const Grid& g, const Elem<double>& e, double Ss, doub
                            size_t msg_len);
 
 // ---- learned warm start (ht_learned.cu) --------------------------------------
+constexpr int kLearnFeatures = 8;   // input channels of the network (see ht_learned.cu)
 int learned_begin(ht_ctx* c);                                   // features + prediction
 int learned_gate(ht_ctx* c, int field, double dt, double* x, const double* b, int* used, double* res);
 int learned_end(ht_ctx* c);                                     // targets + history
@@ -319,6 +320,9 @@ void learned_free(ht_ctx* c);
 int solve_head(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);
 int solve_heat(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res);
 int true_residual(ht_ctx* c, int field, double dt, const double* x, const double* b, double* rel);
+// ||b - A x|| / ||b|| with A applied by the FP32 operator (FP64 right-hand side,
+// exact Dirichlet rows): a cheap ranking of initial guesses
+int fast_residual(ht_ctx* c, int field, double dt, const double* x, const double* b, double* rel);
 int set_dirichlet_values(ht_ctx* c, int field, double* x);
 
 }  // namespace ht

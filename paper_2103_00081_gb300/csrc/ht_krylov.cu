@@ -1400,6 +1400,26 @@ int true_residual(ht_ctx* c, int field, double dt, const double* x, const double
     return HT_OK;
 }
 
+int fast_residual(ht_ctx* c, int field, double dt, const double* x, const double* b, double* rel) {
+    const long long n = c->grid.nn;
+    const int G = vec_grid(c), S = c->part_stride;
+    if (field == HT_TEMP) {   // the FP32 heat operator forms its velocity from the FP32 head
+        to_f32_kernel<<<G, kVecThreads, 0, c->stream>>>(n, c->h, c->h32); ++c->n_launch;
+    }
+    to_f32_kernel<<<G, kVecThreads, 0, c->stream>>>(n, x, c->x32); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    HT_TRY(launch_apply32(c, field, (float)dt, c->x32, c->q32, nullptr, nullptr, nullptr));
+    Grid gf = c->grid;
+    gf.dmask = c->dmask[field];
+    resid32_kernel<<<G, kVecThreads, 0, c->stream>>>(gf, n, b, c->q32, x, c->r32, c->part, S); ++c->n_launch;
+    scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, S, G, c->scal + 3, 0.0, 0); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    HT_TRY(sync_scal(c, 3));
+    const Scal s = c->scal_host[3];
+    *rel = s.bb > 0 ? sqrt(s.rr / s.bb) : sqrt(s.rr);
+    return HT_OK;
+}
+
 // r = b - q, partial sums of r.r and b.b (slots 0 and 1); *n_part entries
 int launch_resid64(ht_ctx* c, const double* b, const double* q, double* part, int* n_part) {
     const int G = vec_grid(c);

@@ -1,8 +1,9 @@
-// Learned warm start of the per-step Krylov solves: features from the last
-// two step increments, a U-Net prediction of the next increments, and a gate
-// that keeps the previous-step initial guess whenever the learned one has the
-// larger true FP64 residual.  The solver itself is unchanged and converges to
-// the same tolerance either way.
+// Learned warm start of the per-step Krylov solves: features of the state
+// (the last two increments of T and h), the Darcy flux and the heat sources,
+// a U-Net prediction of the next increments, and a gate that keeps the
+// previous-step initial guess whenever the learned one has the larger
+// residual.  The solver itself is unchanged and converges to the same
+// tolerance either way.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -32,18 +33,46 @@ __device__ __forceinline__ double lbsum(double v) {
     return v;
 }
 
-__global__ void sumsq_kernel(long long n, const double* __restrict__ a, const double* __restrict__ b,
-                             double* __restrict__ part, int stride) {
-    double sa = 0, sb = 0;
-    LOOP(i, n) {
+// Darcy velocity at node id from the head by differences of neighbouring
+// nodes (one-sided on the faces) and the conductivity of the cell whose low
+// corner the node is (the last cell along an axis on the high faces): a
+// feature of the network, not part of the method's arithmetic
+__device__ __forceinline__ void node_flux(const Grid& g, const double* __restrict__ h, const double* __restrict__ K,
+                                          double ihx, double ihy, double ihz, long long id, double q[3]) {
+    const int i = (int)(id % g.Nx), j = (int)((id / g.Nx) % g.Ny), k = (int)(id / ((long long)g.Nx * g.Ny));
+    const int ci = min(i / g.P, g.ncx - 1), cj = min(j / g.P, g.ncy - 1), ck = min(k / g.P, g.ncz - 1);
+    const double Kc = K[ci + (long long)g.ncx * (cj + (long long)g.ncy * ck)];
+    const long long sx = 1, sy = g.Nx, sz = (long long)g.Nx * g.Ny;
+    const int ia = i > 0 ? i - 1 : i, ib = i < g.Nx - 1 ? i + 1 : i;
+    const int ja = j > 0 ? j - 1 : j, jb = j < g.Ny - 1 ? j + 1 : j;
+    const int ka = k > 0 ? k - 1 : k, kb = k < g.Nz - 1 ? k + 1 : k;
+    q[0] = -Kc * (h[id + (ib - i) * sx] - h[id + (ia - i) * sx]) * ihx / (double)max(ib - ia, 1);
+    q[1] = -Kc * (h[id + (jb - j) * sy] - h[id + (ja - j) * sy]) * ihy / (double)max(jb - ja, 1);
+    q[2] = -Kc * (h[id + (kb - k) * sz] - h[id + (ka - k) * sz]) * ihz / (double)max(kb - ka, 1);
+}
+
+// partial sums of dT1^2, dh1^2, |q|^2 and F_T^2
+__global__ void sumsq_kernel(const Grid g, const double* __restrict__ a, const double* __restrict__ b,
+                             const double* __restrict__ h, const double* __restrict__ K, const double* __restrict__ F,
+                             double ihx, double ihy, double ihz, double* __restrict__ part, int stride) {
+    double sa = 0, sb = 0, sq = 0, sf = 0;
+    LOOP(i, g.nn) {
         sa = fma(a[i], a[i], sa);
         sb = fma(b[i], b[i], sb);
+        double q[3];
+        node_flux(g, h, K, ihx, ihy, ihz, i, q);
+        sq = fma(q[0], q[0], fma(q[1], q[1], fma(q[2], q[2], sq)));
+        sf = fma(F[i], F[i], sf);
     }
     sa = lbsum(sa);
     sb = lbsum(sb);
+    sq = lbsum(sq);
+    sf = lbsum(sf);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = sa;
         part[stride + blockIdx.x] = sb;
+        part[2 * (size_t)stride + blockIdx.x] = sq;
+        part[3 * (size_t)stride + blockIdx.x] = sf;
     }
 }
 
@@ -54,22 +83,30 @@ __device__ __forceinline__ int voxel_node(const Grid& g, int Hp, int Wp, long lo
     return x + g.Nx * (y + g.Ny * z);
 }
 
+// the kLearnFeatures channels [dT1, dT2, dh1, dh2, F_T, q_x, q_y, q_z], each
+// divided by its scale (RMS over the nodes; the increments of a field share one)
 __global__ void feat_kernel(const Grid g, int Hp, int Wp, long long nv, const double* __restrict__ dT1,
                             const double* __restrict__ dT2, const double* __restrict__ dh1,
-                            const double* __restrict__ dh2, double iT, double ih, float* __restrict__ f) {
+                            const double* __restrict__ dh2, const double* __restrict__ h,
+                            const double* __restrict__ K, const double* __restrict__ F, double ihx, double ihy,
+                            double ihz, double iT, double ih, double iq, double iF, float* __restrict__ f) {
     LOOP(p, nv) {
         const int id = voxel_node(g, Hp, Wp, p);
-        float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
+        float v[kLearnFeatures] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (id >= 0) {
-            a = (float)(dT1[id] * iT);
-            b = (float)(dT2[id] * iT);
-            c = (float)(dh1[id] * ih);
-            d = (float)(dh2[id] * ih);
+            v[0] = (float)(dT1[id] * iT);
+            v[1] = (float)(dT2[id] * iT);
+            v[2] = (float)(dh1[id] * ih);
+            v[3] = (float)(dh2[id] * ih);
+            v[4] = (float)(F[id] * iF);
+            double q[3];
+            node_flux(g, h, K, ihx, ihy, ihz, id, q);
+            v[5] = (float)(q[0] * iq);
+            v[6] = (float)(q[1] * iq);
+            v[7] = (float)(q[2] * iq);
         }
-        f[p] = a;
-        f[nv + p] = b;
-        f[2 * nv + p] = c;
-        f[3 * nv + p] = d;
+#pragma unroll
+        for (int k = 0; k < kLearnFeatures; ++k) f[k * nv + p] = v[k];
     }
 }
 
@@ -117,12 +154,13 @@ int lalloc(ht_ctx* c, T** p, size_t n) {
 
 int ensure_buffers(ht_ctx* c) {
     const size_t nn = (size_t)c->grid.nn;
-    c->Dp = c->grid.Nz + (c->grid.Nz & 1);
-    c->Hp = c->grid.Ny + (c->grid.Ny & 1);
-    c->Wp = c->grid.Nx + (c->grid.Nx & 1);
+    // the network pools three times: grid sizes rounded up to multiples of 8
+    c->Dp = (c->grid.Nz + 7) / 8 * 8;
+    c->Hp = (c->grid.Ny + 7) / 8 * 8;
+    c->Wp = (c->grid.Nx + 7) / 8 * 8;
     const size_t nv = (size_t)c->Dp * c->Hp * c->Wp;
     for (double** p : {&c->hn, &c->Tn, &c->dh1, &c->dh2, &c->dT1, &c->dT2}) HT_TRY(lalloc(c, p, nn));
-    HT_TRY(lalloc(c, &c->feat, 4 * nv));
+    HT_TRY(lalloc(c, &c->feat, (size_t)kLearnFeatures * nv));
     HT_TRY(lalloc(c, &c->targ, 2 * nv));
     HT_TRY(lalloc(c, &c->pred, 2 * nv));
     return HT_OK;
@@ -139,19 +177,28 @@ int learned_begin(ht_ctx* c) {
     HT_CUDA(c, cudaMemcpyAsync(c->Tn, c->T, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     if (c->hist < 2) return HT_OK;
     const int G = vec_grid(c);
-    sumsq_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid.nn, c->dT1, c->dh1, c->part, c->part_stride); ++c->n_launch;
+    const double ihx = c->grid.P / c->H[0], ihy = c->grid.P / c->H[1], ihz = c->grid.P / c->H[2];
+    sumsq_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid, c->dT1, c->dh1, c->h, c->K64, c->F[HT_TEMP], ihx, ihy,
+                                                   ihz, c->part, c->part_stride); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
-    std::vector<double> h(2 * (size_t)c->part_stride);
-    HT_CUDA(c, cudaMemcpyAsync(h.data(), c->part, 2 * (size_t)c->part_stride * sizeof(double),
+    std::vector<double> h(4 * (size_t)c->part_stride);
+    HT_CUDA(c, cudaMemcpyAsync(h.data(), c->part, 4 * (size_t)c->part_stride * sizeof(double),
                                cudaMemcpyDeviceToHost, c->stream));
     HT_CUDA(c, cudaStreamSynchronize(c->stream));
-    double a = 0, b = 0;
-    for (int i = 0; i < G; ++i) { a += h[i]; b += h[(size_t)c->part_stride + i]; }
+    double a = 0, b = 0, q = 0, fs = 0;
+    for (int i = 0; i < G; ++i) {
+        a += h[i];
+        b += h[(size_t)c->part_stride + i];
+        q += h[2 * (size_t)c->part_stride + i];
+        fs += h[3 * (size_t)c->part_stride + i];
+    }
     c->lscale_T = a > 0 ? sqrt(a / (double)nn) : 1.0;
     c->lscale_h = b > 0 ? sqrt(b / (double)nn) : 1.0;
+    const double sq = q > 0 ? sqrt(q / (double)nn) : 1.0, sF = fs > 0 ? sqrt(fs / (double)nn) : 1.0;
     const long long nv = (long long)c->Dp * c->Hp * c->Wp;
-    feat_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid, c->Hp, c->Wp, nv, c->dT1, c->dT2, c->dh1, c->dh2,
-                                                  1.0 / c->lscale_T, 1.0 / c->lscale_h, c->feat); ++c->n_launch;
+    feat_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid, c->Hp, c->Wp, nv, c->dT1, c->dT2, c->dh1, c->dh2, c->h,
+                                                  c->K64, c->F[HT_TEMP], ihx, ihy, ihz, 1.0 / c->lscale_T,
+                                                  1.0 / c->lscale_h, 1.0 / sq, 1.0 / sF, c->feat); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     c->have_feat = 1;
     if (c->net) {
@@ -176,8 +223,11 @@ int learned_gate(ht_ctx* c, int field, double dt, double* x, const double* b, in
     *used = 0;
     *res = -1.0;
     if (!c->net || !c->have_feat) return HT_OK;
+    // the gate compares the two guesses by the residual with the FP32
+    // operator (FP64 right-hand side): enough to rank them, and a fraction of
+    // the cost of an FP64 apply
     double r0 = 0, rL = 0;
-    HT_TRY(true_residual(c, field, dt, x, b, &r0));
+    HT_TRY(fast_residual(c, field, dt, x, b, &r0));
     const size_t nn = (size_t)c->grid.nn;
     HT_CUDA(c, cudaMemcpyAsync(c->z, x, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     const long long nv = (long long)c->Dp * c->Hp * c->Wp;
@@ -186,7 +236,7 @@ int learned_gate(ht_ctx* c, int field, double dt, double* x, const double* b, in
     guess_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid, c->Hp, c->Wp, pr, s, c->z); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     HT_TRY(set_dirichlet_values(c, field, c->z));
-    HT_TRY(true_residual(c, field, dt, c->z, b, &rL));
+    HT_TRY(fast_residual(c, field, dt, c->z, b, &rL));
     if (rL < r0) {
         HT_CUDA(c, cudaMemcpyAsync(x, c->z, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         *used = 1;
@@ -238,7 +288,8 @@ int ht_learned_sample(ht_ctx* c, float* features, float* targets, int* dims) {
     if (!c->have_sample) return fail(c, HT_EINVAL, "no complete learned-guess sample yet");
     cudaSetDevice(c->device);
     const size_t nv = (size_t)c->Dp * c->Hp * c->Wp;
-    HT_CUDA(c, cudaMemcpyAsync(features, c->feat, 4 * nv * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    HT_CUDA(c, cudaMemcpyAsync(features, c->feat, (size_t)kLearnFeatures * nv * sizeof(float), cudaMemcpyDeviceToDevice,
+                               c->stream));
     HT_CUDA(c, cudaMemcpyAsync(targets, c->targ, 2 * nv * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     HT_CUDA(c, cudaStreamSynchronize(c->stream));
     dims[0] = c->Dp;

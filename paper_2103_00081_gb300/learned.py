@@ -1,8 +1,9 @@
 """Training and use of the U-Net warm start (thin driver over the C ABI).
 
 The network (include/ht.h, ht_unet_*) predicts the next step's increments of
-temperature and head from the last two increments; the solver gates the
-prediction against the previous-step initial guess (ht_set_learned_guess).
+temperature and head from the last two increments of both fields, the Darcy
+flux and the heat sources; the solver gates the prediction against the
+previous-step initial guess (ht_set_learned_guess).
 Samples come from trajectories the simulator itself generates
 (ht_learned_sample); all arithmetic runs in the library's kernels and torch
 only provides device buffers.
@@ -17,25 +18,39 @@ import numpy as np
 from . import _lib as L
 
 
+FEATURES = 8      # [dT1, dT2, dh1, dh2, F_T, q_x, q_y, q_z] (see include/ht.h)
+
+
+def layer_shapes(cin: int = FEATURES, cout: int = 2):
+    """(Cin, Cout, taps) of the 15 convolutions of the library's U-Net, in the
+    order of its parameter vector (widths 16-32-48-64)."""
+    c1, c2, c3, c4 = 16, 32, 48, 64
+    return [(cin, c1, 27), (c1, c1, 27), (c1, c2, 27), (c2, c2, 27), (c2, c3, 27), (c3, c3, 27),
+            (c3, c4, 27), (c4, c4, 27), (c4 + c3, c3, 27), (c3, c3, 27), (c3 + c2, c2, 27), (c2, c2, 27),
+            (c2 + c1, c1, 27), (c1, c1, 27), (c1, cout, 1)]
+
+
 class UNet:
-    def __init__(self, device: int = 0, seed: int = 0):
+    def __init__(self, device: int = 0, seed: int = 0, cin: int = FEATURES):
         self._lib = L.lib()
         h = c_void_p()
-        rc = self._lib.ht_unet_create(byref(h), 4, 2, int(device), None)
+        rc = self._lib.ht_unet_create(byref(h), int(cin), 2, int(device), None)
         if rc != L.HT_OK:
             raise RuntimeError(f"ht_unet_create failed ({rc})")
         self._h = h
+        self.cin = cin
         self.n_params = self._lib.ht_unet_num_params(h)
         self.set_params(self.initial_params(seed))
 
     def initial_params(self, seed: int) -> np.ndarray:
-        """He-uniform weights scaled by 1/2 (the last layer by 1/10), zero biases."""
+        """He-uniform weights (the last layer scaled by 1/10), zero biases; the
+        layout is per layer weights [taps][Cout][Cin] then biases [Cout]."""
         rng = np.random.default_rng(seed)
-        shapes = [(16, 4, 27), (32, 16, 27), (16, 48, 27), (2, 16, 1)]
+        shapes = layer_shapes(self.cin)
         out = []
-        for li, (co, ci, k) in enumerate(shapes):
-            bound = np.sqrt(6.0 / (ci * k)) * (0.1 if li == 3 else 0.5)
-            out.append(rng.uniform(-bound, bound, co * ci * k))
+        for li, (ci, co, k) in enumerate(shapes):
+            bound = np.sqrt(6.0 / (ci * k)) * (0.1 if li == len(shapes) - 1 else 1.0)
+            out.append(rng.uniform(-bound, bound, k * co * ci))
             out.append(np.zeros(co))
         theta = np.concatenate(out).astype(np.float32)
         assert theta.size == self.n_params
@@ -95,8 +110,8 @@ def collect_samples(sim, dt: float, n_steps: int):
     dims = (c_int * 3)()
     for _ in range(n_steps):
         sim.step(dt)
-        Dp, Hp, Wp = (sim.dims[2] + sim.dims[2] % 2, sim.dims[1] + sim.dims[1] % 2, sim.dims[0] + sim.dims[0] % 2)
-        f = torch.empty((4, Dp, Hp, Wp), dtype=torch.float32, device="cuda")
+        Dp, Hp, Wp = ((sim.dims[2] + 7) // 8 * 8, (sim.dims[1] + 7) // 8 * 8, (sim.dims[0] + 7) // 8 * 8)
+        f = torch.empty((FEATURES, Dp, Hp, Wp), dtype=torch.float32, device="cuda")
         t = torch.empty((2, Dp, Hp, Wp), dtype=torch.float32, device="cuda")
         rc = sim._lib.ht_learned_sample(sim._h, c_void_p(f.data_ptr()), c_void_p(t.data_ptr()), dims)
         if rc == L.HT_OK:

@@ -1,6 +1,19 @@
-"""The CUDA U-Net (forward, loss gradient, Adam) against the FP64 oracle with
-the same BF16-rounded weights.  Tolerances: FP32 accumulation over at most a
-few thousand terms, relative 1e-4 (forward) and 2e-3 (gradients)."""
+"""The CUDA U-Net (tensor-core convolutions, loss gradient, Adam) against the
+FP64 oracle of the same mixed-precision network (oracle/unet.py with
+bf16=True: the same BF16 rounding points, exact sums).
+
+What separates the two is the GPU's FP32 accumulation: it moves an
+occasional BF16 rounding to the neighbouring value, and through 15 layers of
+BF16 activations such differences spread until the two networks differ by
+about one BF16 unit (0.4%) in most elements.  The bound is therefore taken
+from the network itself: the oracle's own distance between its BF16 network
+and the exact one (same BF16 weights and input, no activation rounding),
+which measures how far one rounding more or less moves this network.  The
+GPU must stay within that distance (at least 2e-3) of the oracle's BF16
+network on the output and the loss, and within twice it on the gradient; a
+wrong index, sign or operand in any layer moves the result by O(1).  The
+volumes span several CTAs of the convolution (128 voxels) and several K
+splits of the weight gradient (64-voxel blocks)."""
 import ctypes
 
 import numpy as np
@@ -9,68 +22,92 @@ import pytest
 from oracle import unet as U
 
 pytestmark = pytest.mark.gpu
-DIMS = (4, 16, 32, 2)
+CIN, COUT = 8, 2
 
 
-def _net(torch):
+def _net():
     from paper_2103_00081_gb300 import _lib as L
     lib = L.lib()
     h = ctypes.c_void_p()
-    assert lib.ht_unet_create(ctypes.byref(h), 4, 2, 0, None) == 0
+    assert lib.ht_unet_create(ctypes.byref(h), CIN, COUT, 0, None) == 0
     return lib, h
 
 
-def test_forward_and_gradient_match_oracle(built_lib):
+@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 8, 24), (8, 16, 16)])
+def test_forward_and_gradient_match_oracle(built_lib, dims):
     torch = pytest.importorskip("torch")
-    lib, h = _net(torch)
+    lib, h = _net()
     n = lib.ht_unet_num_params(h)
-    assert n == U.n_params(*DIMS)
-    rng = np.random.default_rng(4)
-    theta = (0.2 * rng.standard_normal(n)).astype(np.float32)
-    assert lib.ht_unet_set_params(h, theta.ctypes.data_as(ctypes.c_void_p)) == 0
-    # the oracle sees the BF16-rounded weights and the FP32 biases
-    th = theta.astype(np.float64)
+    assert n == U.n_params(CIN, COUT)
+    rng = np.random.default_rng(4 + dims[0] + dims[2])
+    # He-like scales so that activations stay O(1) through the 15 layers
+    theta = np.empty(n, dtype=np.float32)
     o = 0
-    for co, ci, k in U.layer_shapes(*DIMS):
-        th[o:o + co * ci * k] = U.bf16_round(th[o:o + co * ci * k])
-        o += co * ci * k + co
-    D, H, W = 6, 8, 10
-    x = rng.standard_normal((4, D, H, W)).astype(np.float32)
-    t = rng.standard_normal((2, D, H, W)).astype(np.float32)
+    for ci, co, k in U.layer_shapes(CIN, COUT):
+        theta[o:o + k * co * ci] = rng.standard_normal(k * co * ci) * np.sqrt(2.0 / (ci * k))
+        o += k * co * ci
+        theta[o:o + co] = 0.1 * rng.standard_normal(co)
+        o += co
+    assert lib.ht_unet_set_params(h, theta.ctypes.data_as(ctypes.c_void_p)) == 0
+    D, H, W = dims
+    x = rng.standard_normal((CIN, D, H, W)).astype(np.float32)
+    t = rng.standard_normal((COUT, D, H, W)).astype(np.float32)
     xd = torch.tensor(x, device="cuda")
     td = torch.tensor(t, device="cuda")
-    yd = torch.empty((2, D, H, W), device="cuda")
+    yd = torch.empty((COUT, D, H, W), device="cuda")
     assert lib.ht_unet_forward(h, ctypes.c_void_p(xd.data_ptr()), D, H, W, ctypes.c_void_p(yd.data_ptr())) == 0
     torch.cuda.synchronize()
-    yref, _ = U.forward(th, x.astype(np.float64), DIMS)
+    th = theta.astype(np.float64)
+    x64, t64 = x.astype(np.float64), t.astype(np.float64)
+    yref, _ = U.forward(th, x64, CIN, COUT, bf16=True)
+    rel = lambda a, b: np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)   # noqa: E731
+    # the network's own sensitivity to its BF16 activation roundings
+    th_w = th.copy()
+    o = 0
+    for ci, co, k in U.layer_shapes(CIN, COUT):
+        th_w[o:o + k * co * ci] = U.bf16_round(th_w[o:o + k * co * ci])
+        o += k * co * ci + co
+    yexact, _ = U.forward(th_w, U.bf16_round(x64), CIN, COUT, bf16=False)
+    tol_y = max(2e-3, rel(yref, yexact))
     got = yd.cpu().numpy()
-    assert np.linalg.norm(got - yref) / np.linalg.norm(yref) <= 1e-4
+    assert rel(got, yref) <= tol_y, (rel(got, yref), tol_y)
     loss = ctypes.c_double()
     g = np.empty(n, dtype=np.float32)
     assert lib.ht_unet_loss_grad(h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(td.data_ptr()), D, H, W,
                                  ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p)) == 0
-    lref, gref = U.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64), DIMS)
-    assert abs(loss.value - lref) <= 1e-4 * abs(lref)
-    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 2e-3
+    lref, gref = U.loss_and_grad(th, x64, t64, CIN, COUT, bf16=True)
+    lexact, gexact = U.loss_and_grad(th_w, U.bf16_round(x64), t64, CIN, COUT, bf16=False)
+    assert abs(loss.value - lref) <= max(2e-3, 2 * abs(lref - lexact) / abs(lref)) * abs(lref)
+    tol_g = max(2e-3, rel(gref, gexact))
+    assert rel(g, gref) <= 2 * tol_g, (rel(g, gref), tol_g)
+    # every layer's weight gradient, not only the largest ones
+    o = 0
+    for li, (ci, co, k) in enumerate(U.layer_shapes(CIN, COUT)):
+        sl = slice(o, o + k * co * ci + co)
+        lt = max(2e-3, rel(gref[sl], gexact[sl]))
+        assert rel(g[sl], gref[sl]) <= 3 * lt, (li, rel(g[sl], gref[sl]), lt)
+        o += k * co * ci + co
+    lib.ht_unet_destroy(h)
+
+
+def test_rejects_grids_that_do_not_pool_three_times(built_lib):
+    from paper_2103_00081_gb300 import _lib as L
+    lib, h = _net()
+    dummy = ctypes.c_void_p(1)
+    assert lib.ht_unet_forward(h, dummy, 12, 8, 8, dummy) == L.HT_EINVAL
+    assert lib.ht_unet_forward(h, dummy, 4, 8, 8, dummy) == L.HT_EINVAL
     lib.ht_unet_destroy(h)
 
 
 def test_adam_training_reduces_the_loss(built_lib):
     torch = pytest.importorskip("torch")
-    lib, h = _net(torch)
-    n = lib.ht_unet_num_params(h)
+    from paper_2103_00081_gb300 import learned
+    net = learned.UNet(seed=5)
     rng = np.random.default_rng(5)
-    theta = (0.1 * rng.standard_normal(n)).astype(np.float32)
-    lib.ht_unet_set_params(h, theta.ctypes.data_as(ctypes.c_void_p))
-    D, H, W = 8, 8, 8
-    x = rng.standard_normal((4, D, H, W)).astype(np.float32)
+    D, H, W = 8, 16, 16
+    x = rng.standard_normal((CIN, D, H, W)).astype(np.float32)
     t = np.stack([x[0] + 0.5 * x[1], x[2] - x[3]]).astype(np.float32)   # a learnable local map
     xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
-    loss = ctypes.c_double()
-    losses = []
-    for it in range(300):
-        assert lib.ht_unet_train_step(h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(td.data_ptr()), D, H, W,
-                                      ctypes.c_float(3e-3), ctypes.byref(loss)) == 0
-        losses.append(loss.value)
+    losses = [net.train_step(xd, td, 2e-3) for _ in range(300)]
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
-    lib.ht_unet_destroy(h)
+    net.close()
