@@ -295,6 +295,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
     sim.close()
+    # --- mixed precision with the learned initial guess ---------------------
+    learned = None
+    if not args.no_learned and sc.order == 1:
+        learned = learned_leg(args, sc, tuned, stream, local, st_mixed)
     # --- plain FP64 over the same steps --------------------------------------
     ms_fp64 = None
     if not args.no_fp64:
@@ -392,9 +396,92 @@ def run_ours(args):
                                         "temperature": rel_l2(f_mixed[1], f_fp64[1]),
                                         "temperature_change": rel_l2(f_mixed[1] - sc.T0, f_fp64[1] - sc.T0)}
         line["operator_gdofs"]["fp64_head_apply"] = nn / (avg64 / 1e3) / 1e9
+    if learned is not None:
+        line["learned"] = learned
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, args.workload)
     print(json.dumps(line))
+
+
+def learned_leg(args, sc, tuned, stream, local, st_plain):
+    """The learned initial guess (spec addition): the U-Net is trained
+    with the library's kernels on trajectories of the pile-field workload
+    (256 x 256 x 64 Q1, a different generator and mesh), then attached to the
+    workload being measured; the same timed steps as the mixed leg, with the
+    gate choosing per field and step between the prediction and the
+    previous-step guess.  Training is not part of the timed region."""
+    import torch
+    from paper_2103_00081_gb300 import hydro, learned as LG
+    from paper_2103_00081_gb300 import _lib as L
+    opts = dict(tol=1e-10, precision=L.HT_MIXED, inner_tol=args.inner_tol, inner_tol_heat=args.inner_tol_heat,
+                max_iter=200000, **tuned)
+    t0 = time.perf_counter()
+    train_sc = S.config3()
+    tsim = hydro.Simulator.from_scenario(train_sc, device=local, stream=stream.cuda_stream, **opts)
+    samples = LG.collect_samples(tsim, train_sc.dt, args.learn_steps)
+    tsim.close()
+    t1 = time.perf_counter()
+    net = LG.UNet(device=local, seed=0)
+    losses = LG.train(net, samples, epochs=args.learn_epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del samples
+    sim = hydro.Simulator.from_scenario(sc, device=local, stream=stream.cuda_stream, **opts)
+    LG.attach(sim, net)
+    for _ in range(max(args.warmup, 3)):
+        sim.step(sc.dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [sim.step(sc.dt) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # the network's forward pass alone, on this workload's padded grid
+    D, H, W = ((sim.dims[2] + 7) // 8 * 8, (sim.dims[1] + 7) // 8 * 8, (sim.dims[0] + 7) // 8 * 8)
+    x = torch.zeros((LG.FEATURES, D, H, W), dtype=torch.float32, device=f"cuda:{local}")
+    y = torch.empty((2, D, H, W), dtype=torch.float32, device=f"cuda:{local}")
+    import ctypes
+    lib = L.lib()
+    ustream = torch.cuda.current_stream(local)
+    for _ in range(2):
+        lib.ht_unet_forward(net._h, ctypes.c_void_p(x.data_ptr()), D, H, W, ctypes.c_void_p(y.data_ptr()))
+    torch.cuda.synchronize()
+    f0 = time.perf_counter()
+    for _ in range(3):
+        lib.ht_unet_forward(net._h, ctypes.c_void_p(x.data_ptr()), D, H, W, ctypes.c_void_p(y.data_ptr()))
+    torch.cuda.synchronize()
+    fwd_ms = (time.perf_counter() - f0) / 3 * 1e3
+    del ustream
+    sim.close()
+    net.close()
+    flops = unet_forward_flops(D * H * W)
+    return {"value": (args.steps * sc.dt / YEAR) / (ms / 1000.0 / 3600.0), "unit": UNIT,
+            "ms_per_step": ms / args.steps,
+            "iters_head": [s["iters_head"] for s in stats], "iters_heat": [s["iters_heat"] for s in stats],
+            "iters_head_without": [s["iters_head"] for s in st_plain],
+            "iters_heat_without": [s["iters_heat"] for s in st_plain],
+            "gate_wins": {"head": sum(s["guess_head"] for s in stats), "heat": sum(s["guess_heat"] for s in stats)},
+            "unet_forward_ms": fwd_ms, "unet_forward_tflops": flops / (fwd_ms * 1e-3) / 1e12,
+            "unet_grid": [D, H, W],
+            "training": {"workload": f"{train_sc.name} {train_sc.nx}x{train_sc.ny}x{train_sc.nz} Q1",
+                         "samples": args.learn_steps - 2, "epochs": args.learn_epochs,
+                         "loss_first_last": [losses[0], losses[-1]], "sampling_s": t1 - t0, "training_s": t2 - t1}}
+
+
+def unet_forward_flops(voxels):
+    """Multiply-add FLOPs (2 per MAC) of one forward pass of the library's
+    U-Net on a grid of `voxels` voxels: the 3x3x3 layers at their levels plus
+    the 1x1 output layer."""
+    c1, c2, c3, c4 = 16, 32, 48, 64
+    lv = [(16, c1), (c1, c1), (c2 + c1, c1), (c1, c1)]                  # level 1 (input padded to 16)
+    l2 = [(c1, c2), (c2, c2), (c3 + c2, c2), (c2, c2)]
+    l3 = [(c2, c3), (c3, c3), (c4 + c3, c3), (c3, c3)]
+    l4 = [(c3, c4), (c4, c4)]
+    f = 0.0
+    for lay, div in ((lv, 1), (l2, 8), (l3, 64), (l4, 512)):
+        f += sum(2.0 * 27 * ci * co for ci, co in lay) * voxels / div
+    return f + 2.0 * c1 * 2 * voxels
 
 
 def ctypes_peak(lib, device, fp64):
@@ -616,6 +703,10 @@ def main():
     ap.add_argument("--inner-tol-heat", dest="inner_tol_heat", type=float, default=1e-4,
                     help="FP32 inner-solve reduction floor, heat system")
     ap.add_argument("--no-fp64", dest="no_fp64", action="store_true", help="skip the plain FP64 leg")
+    ap.add_argument("--no-learned", dest="no_learned", action="store_true", help="skip the learned-guess leg")
+    ap.add_argument("--learn-steps", dest="learn_steps", type=int, default=14,
+                    help="steps of the pile-field trajectory that give training samples (two fewer samples)")
+    ap.add_argument("--learn-epochs", dest="learn_epochs", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuning cache")
