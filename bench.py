@@ -657,8 +657,9 @@ def run_batch(args):
         return t, stats, launches
 
     # concurrent per-problem steps (the default), then the shared-launch head CG
-    t_batch, stats, launches = timed_batch(L.HT_BATCH_CONCURRENT)
+    t_batch, stats, _ = timed_batch(L.HT_BATCH_CONCURRENT)
     t_shared, _, _ = timed_batch(L.HT_BATCH_SHARED_LAUNCHES)
+    t_pers, stats_p, launches = timed_batch(L.HT_BATCH_PERSISTENT)
     # the same problems stepped one by one through ht_step
     barrier()
     w0 = time.perf_counter()
@@ -668,17 +669,19 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - w0
     dev = f"cuda:{local}"
-    t_batch, t_shared, t_seq = R.max_over_ranks([t_batch, t_shared, t_seq], dist, dev)
+    t_batch, t_shared, t_pers, t_seq = R.max_over_ranks([t_batch, t_shared, t_pers, t_seq], dist, dev)
     (launches,) = R.sum_over_ranks([launches], dist, dev)
     if rank != 0:
         return
     years = args.steps * dt / YEAR * len(scs_all)
     nodes = sum(sc.n_nodes for sc in scs_all)
+    # the headline is the persistent mode (one cooperative launch per outer
+    # pass for the inner head CG of all problems); the other modes beside it
     print(json.dumps({
         "metric": "simulated-years/hour summed over the batch at 1e-10 residual",
-        "value": R.job_rate(years, t_batch / 3600),
+        "value": R.job_rate(years, t_pers / 3600), "mode": "persistent",
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "scaling": "strong",
+        "ms_per_step": t_pers / args.steps * 1e3, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic (seeded GRF lnK, piles)",
         "config": {"workload": f"{len(scs_all)} Q1 problems, {nodes} nodes in total, dt=1 d, tol 1e-10",
                    "sizes": sorted(set(f"{sc.nx}x{sc.ny}x{sc.nz}" for sc in scs_all))[:8],
@@ -686,8 +689,10 @@ def run_batch(args):
         "sequential": {"value": R.job_rate(years, t_seq / 3600), "ms_per_step": t_seq / args.steps * 1e3},
         "shared_launches": {"value": R.job_rate(years, t_shared / 3600),
                             "ms_per_step": t_shared / args.steps * 1e3},
-        "speedup_vs_sequential": t_seq / t_batch,
-        "iters_head": [st["iters_head"] for st in stats][:8], "gpu_launches": int(launches),
+        "concurrent": {"value": R.job_rate(years, t_batch / 3600), "ms_per_step": t_batch / args.steps * 1e3,
+                       "iters_head": [st["iters_head"] for st in stats][:8]},
+        "speedup_vs_sequential": t_seq / t_pers,
+        "iters_head": [st["iters_head"] for st in stats_p][:8], "gpu_launches": int(launches),
     }))
 
 

@@ -42,8 +42,8 @@ extern "C" {
 #define HT_ECUDA (-3)       /* a CUDA runtime call failed */
 #define HT_ENOCONV (-4)     /* Krylov solve hit max_iter before the tolerance */
 #define HT_EBREAKDOWN (-5)  /* BiCGStab breakdown that a restart did not cure */
-#define HT_ETIMEOUT (-6)    /* reserved for a bounded device wait that gives up; no current kernel
-                               waits on another CTA or launch, so no call returns it */
+#define HT_ETIMEOUT (-6)    /* a bounded device wait gave up (the grid barrier of the persistent
+                               batched CG, ht_batch_set_persistent) */
 
 enum { HT_HEAD = 0, HT_TEMP = 1, HT_QX = 2, HT_QY = 3, HT_QZ = 4 };
 enum { HT_BC_NONE = 0, HT_BC_DIRICHLET = 1, HT_BC_FLUX = 2 };
@@ -279,7 +279,34 @@ const char* ht_batch_last_error(const ht_batch* batch);
  * give each problem the result of its own ht_step up to rounding order. */
 #define HT_BATCH_CONCURRENT 0
 #define HT_BATCH_SHARED_LAUNCHES 1
+/* HT_BATCH_PERSISTENT (Q1 problems whose options allow the single-pass
+ * kernels, HT_APPLY_AUTO or HT_APPLY_SINGLE_PASS): the set-up and the heat
+ * solves run concurrently as in HT_BATCH_CONCURRENT; the head solves of all
+ * problems run together, their inner FP32 CG (the single-reduction Jacobi
+ * CG of the single-pass kernels) as ONE cooperative launch per outer pass.
+ * The launch's CTAs take the (problem, tile, z chunk) work items of every
+ * unconverged problem round-robin and meet at a grid barrier twice per
+ * iteration (partial sums, then per-problem scalars); a problem drops out of
+ * the work list when it converges and the launch ends when all have.  Errors
+ * as above, plus HT_EINVAL from ht_batch_set_mode when a problem cannot use
+ * the single-pass kernels and HT_ETIMEOUT (below). */
+#define HT_BATCH_PERSISTENT 2
 int ht_batch_set_mode(ht_batch* batch, int mode);
+/* Options of HT_BATCH_PERSISTENT.  planes: node planes per z chunk of a work
+ * item (0, the default: chosen from the batch's total work and the number of
+ * co-resident CTAs).  wait_ms (0 < wait_ms <= 60000, default 2000): bound of
+ * every grid-barrier wait, in milliseconds at the device's maximum SM clock
+ * (counted in SM clock cycles); a wait that runs out makes every CTA of the
+ * launch return, and ht_batch_step returns HT_ETIMEOUT with the problems'
+ * times and fields unchanged (the step can be repeated).  drop_cta: -1 (the
+ * default) for normal operation; k >= 0 is a failure injection for tests:
+ * CTA k of the first launch of each step leaves at its first barrier without
+ * arriving, so that the other CTAs' waits run out.  Errors: HT_EINVAL. */
+int ht_batch_set_persistent(ht_batch* batch, int planes, double wait_ms, int drop_cta);
+/* The work list of the last persistent step: node planes per z chunk, work
+ * items, CTAs of the cooperative launch, and the CTA whose barrier wait ran
+ * out (-1 when none did).  Any pointer may be NULL. */
+int ht_batch_persistent_info(const ht_batch* batch, int* planes, int* items, int* grid, int* err_cta);
 
 /* Learned warm start: a 3D U-Net of four levels (widths 16, 32, 48, 64) with
  * hand-written forward, backward and Adam kernels.  The paper has no learned

@@ -19,7 +19,7 @@ HT_FP64, HT_MIXED = 0, 1
 HT_KRYLOV_BICGSTAB, HT_KRYLOV_GMRES = 0, 1
 HT_PREC_JACOBI, HT_PREC_CHEBYSHEV = 0, 1
 HT_APPLY_AUTO, HT_APPLY_TILED, HT_APPLY_TWO_PASS, HT_APPLY_SINGLE_PASS = 0, 1, 2, 3
-HT_BATCH_CONCURRENT, HT_BATCH_SHARED_LAUNCHES = 0, 1
+HT_BATCH_CONCURRENT, HT_BATCH_SHARED_LAUNCHES, HT_BATCH_PERSISTENT = 0, 1, 2
 
 ERROR_NAMES = {0: "HT_OK", -1: "HT_EINVAL", -2: "HT_ENOMEM", -3: "HT_ECUDA", -4: "HT_ENOCONV",
                -5: "HT_EBREAKDOWN", -6: "HT_ETIMEOUT"}
@@ -105,6 +105,8 @@ SIGNATURES = {
     "ht_batch_destroy": (None, [c_void_p]),
     "ht_batch_step": (c_int, [c_void_p, c_double, c_void_p]),
     "ht_batch_set_mode": (c_int, [c_void_p, c_int]),
+    "ht_batch_set_persistent": (c_int, [c_void_p, c_int, c_double, c_int]),
+    "ht_batch_persistent_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ht_batch_last_error": (ctypes.c_char_p, [c_void_p]),
     "ht_unet_create": (c_int, [POINTER(c_void_p), c_int, c_int, c_int, c_void_p]),
     "ht_unet_destroy": (None, [c_void_p]),

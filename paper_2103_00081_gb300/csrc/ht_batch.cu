@@ -14,6 +14,7 @@
 #include "ht_internal.cuh"
 
 #include <atomic>
+#include <functional>
 #include <string>
 #include <thread>
 
@@ -303,6 +304,12 @@ struct ht_batch {
     double graph_dt = -1.0;
     int mode = HT_BATCH_CONCURRENT;
     std::string err;
+    // persistent mode
+    ht::Q1Batch q1;
+    int planes = 0;            // node planes per z chunk (0: automatic)
+    double wait_ms = 2000.0;   // bound of each grid-barrier wait
+    int drop_cta = -1;         // failure injection (tests): CTA that skips its first arrival
+    int last_err_cta = -1;
 };
 
 namespace ht {
@@ -435,6 +442,9 @@ int batch_head_begin(ht_ctx* c, double dt);
 int batch_outer_residual(ht_ctx* c, double dt, double tol, int* converged, double* res);
 int batch_inner_init(ht_ctx* c, double dt, double inner_tol, int max_iter);
 int batch_outer_update(ht_ctx* c);
+int batch_outer_residual_enqueue(ht_ctx* c, double dt);
+int batch_outer_residual_read(ht_ctx* c, double tol, int* converged, double* res);
+int batch_outer_update_enqueue(ht_ctx* c);
 int batch_head_end_and_heat(ht_ctx* c, double dt, ht_step_stats* st);
 
 }  // namespace ht
@@ -474,6 +484,7 @@ void ht_batch_destroy(ht_batch* b) {
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    q1_batch_free(b->q1);
     for (int* p : {b->d_cell_item, b->d_node_item, b->d_vec_item, b->d_done})
         if (p) cudaFree(p);
     if (b->d_probs) cudaFree(b->d_probs);
@@ -486,23 +497,46 @@ const char* ht_batch_last_error(const ht_batch* b) { return b ? b->err.c_str() :
 
 int ht_batch_set_mode(ht_batch* b, int mode) {
     if (!b) return HT_EINVAL;
-    if (mode != HT_BATCH_CONCURRENT && mode != HT_BATCH_SHARED_LAUNCHES) return bfail(b, HT_EINVAL, "unknown mode");
+    if (mode != HT_BATCH_CONCURRENT && mode != HT_BATCH_SHARED_LAUNCHES && mode != HT_BATCH_PERSISTENT)
+        return bfail(b, HT_EINVAL, "unknown mode");
+    if (mode == HT_BATCH_PERSISTENT)
+        for (const ht_ctx* c : b->probs)
+            if (!q1_cg_available(c, 1))
+                return bfail(b, HT_EINVAL, "the persistent mode needs Q1 problems that use the single-pass kernels");
     b->mode = mode;
     return HT_OK;
 }
 
-// concurrent mode: worker threads step the problems on their own streams
-static int batch_step_concurrent(ht_batch* b, double dt, ht_step_stats* stats) {
+int ht_batch_set_persistent(ht_batch* b, int planes, double wait_ms, int drop_cta) {
+    if (!b) return HT_EINVAL;
+    if (planes < 0 || !(wait_ms > 0.0) || !(wait_ms <= 6.0e4) || drop_cta < -1)
+        return bfail(b, HT_EINVAL, "planes >= 0, 0 < wait_ms <= 60000 and drop_cta >= -1 are required");
+    b->planes = planes;
+    b->wait_ms = wait_ms;
+    b->drop_cta = drop_cta;
+    return HT_OK;
+}
+
+int ht_batch_persistent_info(const ht_batch* b, int* planes, int* items, int* grid, int* err_cta) {
+    if (!b) return HT_EINVAL;
+    if (planes) *planes = b->q1.planes;
+    if (items) *items = b->q1.nitems;
+    if (grid) *grid = b->q1.grid;
+    if (err_cta) *err_cta = b->last_err_cta;
+    return HT_OK;
+}
+
+// fn(i) for every problem, on worker threads when the problems have
+// streams of their own (one thread otherwise)
+static void for_each_problem(ht_batch* b, const std::function<void(int)>& fn) {
     const int np = (int)b->probs.size();
     bool shared = false;
     for (int i = 0; i < np && !shared; ++i)
         for (int j = 0; j < i && !shared; ++j) shared = b->probs[i]->stream == b->probs[j]->stream;
-    std::vector<int> rcs(np, HT_OK);
-    std::vector<ht_step_stats> st(np);
     std::atomic<int> next(0);
     auto work = [&] {
         cudaSetDevice(b->device);
-        for (int i = next++; i < np; i = next++) rcs[i] = ht_step(b->probs[i], dt, &st[i]);
+        for (int i = next++; i < np; i = next++) fn(i);
     };
     const int nt = shared ? 1 : std::min(np, 8);
     if (nt <= 1) {
@@ -512,6 +546,14 @@ static int batch_step_concurrent(ht_batch* b, double dt, ht_step_stats* stats) {
         for (int t = 0; t < nt; ++t) pool.emplace_back(work);
         for (auto& th : pool) th.join();
     }
+}
+
+// concurrent mode: worker threads step the problems on their own streams
+static int batch_step_concurrent(ht_batch* b, double dt, ht_step_stats* stats) {
+    const int np = (int)b->probs.size();
+    std::vector<int> rcs(np, HT_OK);
+    std::vector<ht_step_stats> st(np);
+    for_each_problem(b, [&](int i) { rcs[i] = ht_step(b->probs[i], dt, &st[i]); });
     int rc = HT_OK;
     for (int i = 0; i < np; ++i) {
         if (stats) stats[i] = st[i];
@@ -520,6 +562,115 @@ static int batch_step_concurrent(ht_batch* b, double dt, ht_step_stats* stats) {
             b->err = std::string("problem ") + std::to_string(i) + ": " + ht_last_error(b->probs[i]);
         }
     }
+    return rc;
+}
+
+// persistent mode: the per-problem set-up and the heat solves run on the
+// problems' own streams (worker threads); the head solves of all problems
+// run on the batch stream, their inner FP32 CG as one cooperative launch per
+// outer pass (q1_cg_batch_kernel), their outer residuals and updates
+// enqueued for all problems before a single host wait
+static int batch_step_persistent(ht_batch* b, double dt, ht_step_stats* stats) {
+    const int np = (int)b->probs.size();
+    std::vector<int> rcs(np, HT_OK);
+    for_each_problem(b, [&](int i) {
+        ht_ctx* c = b->probs[i];
+        rcs[i] = batch_head_begin(c, dt);
+        if (rcs[i] == HT_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rcs[i] = HT_ECUDA;
+    });
+    for (int i = 0; i < np; ++i)
+        if (rcs[i] != HT_OK) {
+            b->err = std::string("problem ") + std::to_string(i) + ": " + ht_last_error(b->probs[i]);
+            return rcs[i];
+        }
+    std::vector<cudaStream_t> saved(np);
+    for (int i = 0; i < np; ++i) {
+        saved[i] = b->probs[i]->stream;
+        b->probs[i]->stream = b->stream;
+    }
+    auto restore = [&] {
+        cudaStreamSynchronize(b->stream);
+        for (int i = 0; i < np; ++i) b->probs[i]->stream = saved[i];
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, b->stream);
+    int rc = HT_OK;
+    rc = q1_batch_prepare(b->q1, b->probs.data(), np, dt, b->planes, b->stream, &b->err);
+    std::vector<int> conv(np, 0), outer(np, 0), inner(np, 0);
+    std::vector<double> res(np, 0.0);
+    const ht_ctx* c0 = b->probs[0];
+    const double tol = c0->opts.tol;
+    const int max_outer = c0->opts.max_outer > 0 ? c0->opts.max_outer : 30;
+    const double base = c0->opts.inner_tol > 0 ? c0->opts.inner_tol : 1e-4;
+    int clock_khz = 0;
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, b->device);
+    const long long budget = (long long)(b->wait_ms * (clock_khz > 0 ? clock_khz : 2000000));
+    b->last_err_cta = -1;
+    for (int k = 0; k <= max_outer && rc == HT_OK; ++k) {
+        for (int i = 0; i < np && rc == HT_OK; ++i)
+            if (!conv[i]) rc = batch_outer_residual_enqueue(b->probs[i], dt);
+        if (rc == HT_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = bfail(b, HT_ECUDA, "sync failed");
+        bool all = true;
+        for (int i = 0; i < np && rc == HT_OK; ++i) {
+            if (conv[i]) continue;
+            rc = batch_outer_residual_read(b->probs[i], tol, &conv[i], &res[i]);
+            if (rc != HT_OK) b->err = b->probs[i]->err;
+            outer[i] = k;
+            all = all && conv[i];
+        }
+        if (rc != HT_OK || all) break;
+        if (k == max_outer) { rc = bfail(b, HT_ENOCONV, "batched head solve did not converge"); break; }
+        for (int i = 0; i < np && rc == HT_OK; ++i) {
+            ht_ctx* c = b->probs[i];
+            // no inner reduction beyond what the outer tolerance needs; a
+            // converged problem gets tolerance 1 and is done at once
+            const double need = res[i] > 0 ? 0.5 * tol / res[i] : 1.0;
+            const double itol = std::max(base, std::min(need, 0.5));
+            rc = batch_inner_init(c, dt, conv[i] ? 1.0 : itol, c->opts.max_iter);
+        }
+        int running = 0, err_cta = -1;
+        if (rc == HT_OK) {
+            rc = q1_batch_run(b->q1, b->stream, c0->opts.max_iter, budget, k == 0 ? b->drop_cta : -1, &running,
+                              &err_cta, &b->err);
+            for (ht_ctx* c : b->probs) c->n_launch += 1;
+            b->last_err_cta = err_cta;
+        }
+        for (int i = 0; i < np && rc == HT_OK; ++i)
+            if (!conv[i]) rc = batch_outer_update_enqueue(b->probs[i]);
+        if (rc == HT_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = bfail(b, HT_ECUDA, "sync failed");
+        for (int i = 0; i < np && rc == HT_OK; ++i) {
+            if (conv[i]) continue;
+            const Scal& s1 = b->probs[i]->scal_host[1];
+            if (s1.status == ST_NAN) rc = bfail(b, HT_EINVAL, "batched head solve: FP32 inner solve produced non-finite values");
+            inner[i] += s1.iters;
+        }
+    }
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    restore();
+    std::vector<ht_step_stats> st(np);
+    if (rc == HT_OK) {
+        for_each_problem(b, [&](int i) { rcs[i] = batch_head_end_and_heat(b->probs[i], dt, &st[i]); });
+        for (int i = 0; i < np && rc == HT_OK; ++i)
+            if (rcs[i] != HT_OK) {
+                rc = rcs[i];
+                b->err = std::string("problem ") + std::to_string(i) + ": " + ht_last_error(b->probs[i]);
+            }
+    }
+    if (stats)
+        for (int i = 0; i < np; ++i) {
+            stats[i] = st[i];
+            stats[i].iters_head = inner[i];
+            stats[i].outer_head = outer[i];
+            stats[i].res_head = res[i];
+            stats[i].ms_head = ms;
+        }
     return rc;
 }
 
@@ -534,6 +685,7 @@ int ht_batch_step(ht_batch* b, double dt, ht_step_stats* stats) {
             return bfail(b, HT_EINVAL, "batched problems need precision HT_MIXED with the Jacobi preconditioner");
     }
     if (b->mode == HT_BATCH_CONCURRENT) return batch_step_concurrent(b, dt, stats);
+    if (b->mode == HT_BATCH_PERSISTENT) return batch_step_persistent(b, dt, stats);
     // every problem works on the batch stream for the duration of the step
     std::vector<cudaStream_t> saved(np);
     for (int i = 0; i < np; ++i) {

@@ -282,6 +282,32 @@ bool fused_cg_available(const ht_ctx* c, int fp32);
 bool q1_cg_available(const ht_ctx* c, int fp32);
 int q1_cg_iteration32(ht_ctx* c, float dt, float* x, const float* r, const float* p, float* r_out, float* p_out,
                       Scal* sc, int first);
+// Persistent single-pass CG of the inner FP32 head solves of many Q1
+// problems (ht_q1.cu; used by the batched step).  prepare builds the work
+// list of (problem, tile, z chunk) items and the per-problem descriptors for
+// step size dt; planes > 0 fixes the node planes per z chunk (0: chosen from
+// the batch's total work and the co-resident CTAs).  run makes one
+// cooperative launch that performs the first pass and up to max_iter
+// iterations of every problem whose inner scalars (slot 1) are not done,
+// with grid-barrier waits bounded by budget clock cycles; *running receives
+// the problems still running at the end and *err_cta the CTA whose wait ran
+// out (-1 when none did; then the call returns HT_ETIMEOUT).  drop_cta >= 0
+// makes that CTA leave at its first barrier without arriving (a failure
+// injection for tests).
+struct Q1Batch {
+    void* d_probs = nullptr;
+    int* d_items = nullptr;
+    void* d_sync = nullptr;
+    void* h_sync = nullptr;
+    int nprob = 0, nitems = 0, grid = 0, planes = 0;
+    int cap_probs = 0, cap_items = 0;
+    double dt = -1.0;
+};
+int q1_batch_prepare(Q1Batch& q, ht_ctx* const* probs, int n, double dt, int planes, cudaStream_t st,
+                     std::string* err);
+int q1_batch_run(Q1Batch& q, cudaStream_t st, int max_iter, long long budget, int drop_cta, int* running,
+                 int* err_cta, std::string* err);
+void q1_batch_free(Q1Batch& q);
 // single-pass heat applies of the Q1 BiCGStab iteration in FP32 (ht_q1.cu):
 // reads p_in, v_in (halos included), writes p_out, v_out, t; then x, r
 bool q1_bicgstab_available(const ht_ctx* c);

@@ -1474,6 +1474,35 @@ int batch_outer_residual(ht_ctx* c, double dt, double tol, int* converged, doubl
     return HT_OK;
 }
 
+// the same residual without the host wait: the norms land in scal_host[2]
+// once the stream reaches the copy (batch_outer_residual_read after a sync)
+int batch_outer_residual_enqueue(ht_ctx* c, double dt) {
+    const int G = vec_grid(c);
+    HT_TRY(launch_apply64(c, HT_HEAD, dt, c->x, c->q, nullptr, nullptr, nullptr));
+    resid_kernel<<<G, kVecThreads, 0, c->stream>>>(c->grid.nn, c->b, c->q, nullptr, c->r32, c->part, c->part_stride); ++c->n_launch;
+    scalar_kernel<<<1, 256, 0, c->stream>>>(SC_NORMS, c->part, c->part_stride, G, c->scal + 2, 0.0, 0); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    HT_CUDA(c, cudaMemcpyAsync(c->scal_host + 2, c->scal + 2, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+    return HT_OK;
+}
+
+int batch_outer_residual_read(ht_ctx* c, double tol, int* converged, double* res) {
+    const Scal s = c->scal_host[2];
+    if (!isfinite(s.rr)) return fail(c, HT_EINVAL, "head solve: non-finite residual");
+    *res = s.bb > 0 ? sqrt(s.rr / s.bb) : 0.0;
+    *converged = (s.rr <= tol * tol * s.bb) ? 1 : 0;
+    return HT_OK;
+}
+
+// x += d and the inner scalars to scal_host[1], without the host wait (the
+// caller checks scal_host[1].status after a sync)
+int batch_outer_update_enqueue(ht_ctx* c) {
+    HT_CUDA(c, cudaMemcpyAsync(c->scal_host + 1, c->scal + 1, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+    add_f32_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, c->x, c->d32); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
 // start the inner FP32 CG on A32 d = r32 (d = 0); scalars in slot 1
 int batch_inner_init(ht_ctx* c, double dt, double inner_tol, int max_iter) {
     const long long n = c->grid.nn;

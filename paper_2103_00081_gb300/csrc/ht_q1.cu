@@ -43,6 +43,7 @@
 // the last CTA in a fixed order, so the iteration is deterministic.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -72,6 +73,31 @@ struct Q1Smem {
     float pc[kSY][kSX];        // p_i at the plane of stage A
     float sc[4][kSY][kSX];     // corner contributions of each face to s
     float us[kSY][kSX];        // u_{i+1} at the plane of stage B
+};
+
+// grid-barrier state of the persistent batched CG (zeroed before each launch)
+struct Q1BatchSync {
+    unsigned count;     // arrivals at the running barrier
+    unsigned gen;       // barrier generation
+    int active[2];      // problems still running, by iteration parity
+    int running;        // problems still running when the launch ended
+    int err;            // 1: a barrier wait ran out of its budget
+    int err_cta;        // the CTA whose wait ran out first
+    int pad;
+};
+
+// one problem of the persistent batched CG
+struct Q1BatchProb {
+    Grid g;                      // dmask of the head field
+    const float* K;
+    float* x;
+    float* r[2];                 // the two copies of r and p (iteration parity)
+    float* p[2];
+    Q1HeadConst cst;
+    int ntx, nty, nzc, item0, nitems;
+    double* part;                // partial sums [3][stride]
+    int stride;
+    Scal* s;
 };
 
 __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc, bool valid) {
@@ -113,21 +139,20 @@ enum : unsigned {
     F_DXY = 32u,       // node on a Dirichlet face of x or y
 };
 
-__global__ void __launch_bounds__(kBX * kBY, 2)
-q1_cg_kernel(const Grid g, const float* __restrict__ K, float* __restrict__ x, const float* __restrict__ r,
-             const float* __restrict__ p, float* __restrict__ r_out, float* __restrict__ p_out,
-             const Q1HeadConst cst, const int ntx, const int nty, const int nzc, Scal* __restrict__ s,
-             double* __restrict__ part, const int stride, const int first) {
-    if (s->done) return;
-    extern __shared__ __align__(16) unsigned char q1_smem_raw[];
-    Q1Smem& sm = *reinterpret_cast<Q1Smem*>(q1_smem_raw);
-    const float alpha = first ? 0.0f : (float)s->alpha;
-    const float beta = first ? 0.0f : (float)s->beta;
+// One CTA's share of a CG iteration: the owned tile (bx, by) of node
+// columns and chunk bz of node planes, marched upward; returns the CTA's
+// partial sums of gamma, delta and rho in thread (0, 0).
+__device__ __forceinline__ void q1_cg_tile(const Grid& g, const float* __restrict__ K, float* __restrict__ x,
+                                           const float* __restrict__ r, const float* __restrict__ p,
+                                           float* __restrict__ r_out, float* __restrict__ p_out,
+                                           const Q1HeadConst& cst, const int bx, const int by, const int bz,
+                                           const int ntx, const int nty, const int nzc, const float alpha,
+                                           const float beta, const int first, Q1Smem& sm, double (&v)[3]) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     // owned tile and chunk (balanced splits)
-    const int i0 = (int)((long long)blockIdx.x * g.Nx / ntx), i1 = (int)((long long)(blockIdx.x + 1) * g.Nx / ntx);
-    const int j0 = (int)((long long)blockIdx.y * g.Ny / nty), j1 = (int)((long long)(blockIdx.y + 1) * g.Ny / nty);
-    const int k0 = (int)((long long)blockIdx.z * g.Nz / nzc), k1 = (int)((long long)(blockIdx.z + 1) * g.Nz / nzc);
+    const int i0 = (int)((long long)bx * g.Nx / ntx), i1 = (int)((long long)(bx + 1) * g.Nx / ntx);
+    const int j0 = (int)((long long)by * g.Ny / nty), j1 = (int)((long long)(by + 1) * g.Ny / nty);
+    const int k0 = (int)((long long)bz * g.Nz / nzc), k1 = (int)((long long)(bz + 1) * g.Nz / nzc);
     const int w = i1 - i0, h = j1 - j0;
     const int NXY = g.Nx * g.Ny, CXY = g.ncx * g.ncy;
     const int dm = g.dmask;
@@ -341,10 +366,52 @@ q1_cg_kernel(const Grid g, const float* __restrict__ K, float* __restrict__ x, c
             }
         }
     }
-    double v[3];
     v[0] = block_sum_t(gam);
     v[1] = block_sum_t(del);
     v[2] = block_sum_t(rho);
+}
+
+// the scalars of the next iteration from the reduced gamma, delta and rho
+// (one thread): convergence, breakdown and non-finite checks
+__device__ __forceinline__ void q1_cg_scalars(Scal* s, double gt, double dt_, double rt, int first) {
+    s->rr = rt;
+    if (!first) s->iters += 1;
+    if (!isfinite(gt) || !isfinite(dt_) || !isfinite(rt)) {
+        s->status = ST_NAN;
+        s->done = 1;
+    } else if (rt <= s->tol2 * s->bb || s->iters >= s->max_iter) {
+        s->done = 1;
+    } else {
+        double a = 0.0, bta = 0.0;
+        if (first) {
+            a = gt / dt_;
+        } else {
+            bta = gt / s->rz;
+            const double den = dt_ - bta * gt / s->alpha;
+            a = gt / den;
+            if (!(den > 0.0)) { s->status = ST_BREAKDOWN; s->done = 1; }
+        }
+        if (!(gt > 0.0) || !(dt_ > 0.0)) { s->status = ST_BREAKDOWN; s->done = 1; }
+        s->alpha = a;
+        s->beta = bta;
+    }
+    s->pq = dt_;
+    s->rz = gt;
+}
+
+__global__ void __launch_bounds__(kBX * kBY, 2)
+q1_cg_kernel(const Grid g, const float* __restrict__ K, float* __restrict__ x, const float* __restrict__ r,
+             const float* __restrict__ p, float* __restrict__ r_out, float* __restrict__ p_out,
+             const Q1HeadConst cst, const int ntx, const int nty, const int nzc, Scal* __restrict__ s,
+             double* __restrict__ part, const int stride, const int first) {
+    if (s->done) return;
+    extern __shared__ __align__(16) unsigned char q1_smem_raw[];
+    Q1Smem& sm = *reinterpret_cast<Q1Smem*>(q1_smem_raw);
+    const float alpha = first ? 0.0f : (float)s->alpha;
+    const float beta = first ? 0.0f : (float)s->beta;
+    double v[3];
+    q1_cg_tile(g, K, x, r, p, r_out, p_out, cst, blockIdx.x, blockIdx.y, blockIdx.z, ntx, nty, nzc, alpha, beta,
+               first, sm, v);
     const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     if (!publish_and_ticket(s, part, v, 3, stride, nblk)) return;
     const double gt = last_cta_sum(part, (int)nblk);
@@ -352,30 +419,129 @@ q1_cg_kernel(const Grid g, const float* __restrict__ K, float* __restrict__ x, c
     const double rt = last_cta_sum(part + 2 * (size_t)stride, (int)nblk);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         s->ticket = 0;
-        s->rr = rt;
-        if (!first) s->iters += 1;
-        if (!isfinite(gt) || !isfinite(dt_) || !isfinite(rt)) {
-            s->status = ST_NAN;
-            s->done = 1;
-        } else if (rt <= s->tol2 * s->bb || s->iters >= s->max_iter) {
-            s->done = 1;
-        } else {
-            double a = 0.0, bta = 0.0;
-            if (first) {
-                a = gt / dt_;
-            } else {
-                bta = gt / s->rz;
-                const double den = dt_ - bta * gt / s->alpha;
-                a = gt / den;
-                if (!(den > 0.0)) { s->status = ST_BREAKDOWN; s->done = 1; }
-            }
-            if (!(gt > 0.0) || !(dt_ > 0.0)) { s->status = ST_BREAKDOWN; s->done = 1; }
-            s->alpha = a;
-            s->beta = bta;
-        }
-        s->pq = dt_;
-        s->rz = gt;
+        q1_cg_scalars(s, gt, dt_, rt, first);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent CG over many Q1 problems (the batched inner head solves): one
+// cooperative launch runs the first pass and up to `iters` iterations of
+// every problem that has not converged.  Per iteration:
+//   phase 1: the CTAs take the (problem, tile, z chunk) work items
+//            round-robin, march each tile as the single-problem kernel does
+//            and write the item's partial sums to its problem's slots;
+//   barrier;
+//   phase 2: CTA b forms the scalars of problems b, b + grid, ... (fixed
+//            summation order, so the result is deterministic) and counts the
+//            problems still running;
+//   barrier; the launch ends once no problem is running.
+// Converged problems drop out of the work list (their items are skipped).
+// Every barrier wait is bounded: a wait that is not complete within `budget`
+// clock cycles sets sync->err and the kernel returns; a CTA that sees
+// sync->err set stops waiting at once.  The host turns sync->err into
+// HT_ETIMEOUT.  drop_cta >= 0 makes that CTA leave at its first barrier
+// without arriving, which lets a test make the other CTAs' waits run out.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool batch_barrier(Q1BatchSync* sync, unsigned nblk, long long budget, bool drop) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        int ok = 1;
+        volatile unsigned* vgen = &sync->gen;
+        volatile int* verr = &sync->err;
+        const unsigned g0 = *vgen;
+        __threadfence();   // release: this CTA's writes before its arrival
+        if (drop) {
+            ok = 0;
+        } else if (atomicAdd(&sync->count, 1u) + 1u == nblk) {
+            sync->count = 0;
+            __threadfence();
+            atomicAdd(&sync->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g0) {
+                if (*verr) { ok = 0; break; }
+                if (clock64() - t0 > budget) {
+                    if (atomicExch(&sync->err, 1) == 0) sync->err_cta = (int)blockIdx.x;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    __threadfence();   // acquire: later loads see what the other CTAs wrote before arriving
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(kBX * kBY, 2)
+q1_cg_batch_kernel(const Q1BatchProb* __restrict__ probs, const int nprob, const int* __restrict__ item_prob,
+                   const int nitems, const int iters, const long long budget, Q1BatchSync* __restrict__ sync,
+                   const int drop_cta) {
+    extern __shared__ __align__(16) unsigned char q1b_smem_raw[];
+    Q1Smem& sm = *reinterpret_cast<Q1Smem*>(q1b_smem_raw);
+    __shared__ Q1BatchProb P;
+    __shared__ int skip_s, par_s;
+    __shared__ float alpha_s, beta_s;
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    const unsigned nblk = gridDim.x;
+    if (((volatile Q1BatchSync*)sync)->err) return;
+    int running = 0;
+    for (int it = 0; it <= iters; ++it) {
+        const int first = it == 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            __syncthreads();   // the previous item is finished with P and the shared planes
+            if (lead) {
+                P = probs[item_prob[item]];
+                const volatile Scal* vs = P.s;
+                skip_s = vs->done;
+                // pass j of a solve reads copy j % 2 of r and p (the first pass is pass 0)
+                par_s = first ? 0 : ((vs->iters + 1) & 1);
+                alpha_s = first ? 0.0f : (float)vs->alpha;
+                beta_s = first ? 0.0f : (float)vs->beta;
+            }
+            __syncthreads();
+            if (skip_s) continue;
+            const int local = item - P.item0;
+            const int bx = local % P.ntx, by = (local / P.ntx) % P.nty, bz = local / (P.ntx * P.nty);
+            const int a = par_s;
+            double v[3];
+            q1_cg_tile(P.g, P.K, P.x, P.r[a], P.p[a], P.r[a ^ 1], P.p[a ^ 1], P.cst, bx, by, bz, P.ntx, P.nty,
+                       P.nzc, alpha_s, beta_s, first, sm, v);
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            if (lead) {
+                P.part[local] = v[0];
+                P.part[(size_t)P.stride + local] = v[1];
+                P.part[2 * (size_t)P.stride + local] = v[2];
+            }
+        }
+        if (!batch_barrier(sync, nblk, budget, first && (int)blockIdx.x == drop_cta)) return;
+        int cnt = 0;
+        for (int pi = blockIdx.x; pi < nprob; pi += gridDim.x) {
+            __syncthreads();
+            if (lead) {
+                P = probs[pi];
+                skip_s = ((volatile Scal*)P.s)->done;
+            }
+            __syncthreads();
+            if (skip_s) continue;
+            const double gt = last_cta_sum(P.part, P.nitems);
+            const double dt_ = last_cta_sum(P.part + P.stride, P.nitems);
+            const double rt = last_cta_sum(P.part + 2 * (size_t)P.stride, P.nitems);
+            if (lead) {
+                q1_cg_scalars(P.s, gt, dt_, rt, first);
+                cnt += P.s->done ? 0 : 1;
+            }
+        }
+        if (lead) atomicAdd(&sync->active[it & 1], cnt);
+        if (!batch_barrier(sync, nblk, budget, false)) return;
+        running = ((volatile int*)sync->active)[it & 1];
+        if (blockIdx.x == 0 && lead) sync->active[(it + 1) & 1] = 0;
+        if (running == 0) break;
+    }
+    if (blockIdx.x == 0 && lead) sync->running = running;
 }
 
 // Eigenvalue parts of the Q1 cell operator in the h x h x h basis (see the
@@ -827,6 +993,161 @@ int q1_bicgstab_iteration32(ht_ctx* c, float dt, float* x, float* r, const float
     HT_TRY(launch_q1_heat_any<0>(c, g, k, r, Dinv, p_in, v_in, rh, p_out, v_out, sc));
     HT_TRY(launch_q1_heat_any<1>(c, g, k, r, Dinv, nullptr, v_out, nullptr, nullptr, t, sc));
     return launch_fbi_update32(c, x, r, p_out, v_out, t, Dinv, rh, sc);
+}
+
+int q1_batch_prepare(Q1Batch& q, ht_ctx* const* probs, int n, double dt, int planes, cudaStream_t st,
+                     std::string* err) {
+    auto bad = [&](int code, const char* msg) {
+        if (err) *err = msg;
+        return code;
+    };
+    int dev = 0, sms = 0, resident = 0;
+    const size_t smem = sizeof(Q1Smem);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(q1_cg_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, q1_cg_batch_kernel, kBX * kBY, smem) != cudaSuccess ||
+        resident < 1)
+        return bad(HT_ECUDA, "persistent batch kernel: occupancy query failed");
+    const int slots = resident * sms;
+    // tiles of every problem, then the z chunking: the same number of node
+    // planes per chunk for all problems, chosen to minimise (waves of items
+    // over the co-resident CTAs) x (planes per chunk + 3 planes of start-up)
+    std::vector<int> ntx(n), nty(n), Nz(n);
+    for (int i = 0; i < n; ++i) {
+        const ht_ctx* c = probs[i];
+        if (!q1_cg_available(c, 1)) return bad(HT_EINVAL, "persistent batch needs Q1 problems with the single-pass kernels");
+        ntx[i] = (c->grid.Nx + kTX - 1) / kTX;
+        nty[i] = (c->grid.Ny + kTY - 1) / kTY;
+        Nz[i] = c->grid.Nz;
+    }
+    auto count_items = [&](int L, std::vector<int>* nzc) {
+        long long items = 0;
+        for (int i = 0; i < n; ++i) {
+            const int z = std::max(1, (Nz[i] + L - 1) / L);
+            if (nzc) (*nzc)[i] = z;
+            items += (long long)ntx[i] * nty[i] * z;
+        }
+        return items;
+    };
+    int best = planes;
+    if (best <= 0) {
+        long long best_cost = -1;
+        int maxNz = *std::max_element(Nz.begin(), Nz.end());
+        for (int L = 2; L <= maxNz; ++L) {
+            const long long waves = (count_items(L, nullptr) + slots - 1) / slots;
+            const long long cost = waves * (L + 3);
+            if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = L; }
+        }
+        if (best_cost < 0) best = std::max(1, maxNz);
+    }
+    std::vector<int> nzc(n);
+    const long long total = count_items(best, &nzc);
+    if (total > (1LL << 30)) return bad(HT_EINVAL, "persistent batch: too many work items");
+    std::vector<Q1BatchProb> h(n);
+    std::vector<int> items;
+    items.reserve((size_t)total);
+    for (int i = 0; i < n; ++i) {
+        ht_ctx* c = probs[i];
+        Q1BatchProb& P = h[i];
+        memset(&P, 0, sizeof(P));
+        P.g = c->grid;
+        P.g.dmask = c->dmask[HT_HEAD];
+        P.K = c->K32;
+        P.x = c->d32;
+        P.r[0] = c->r32;
+        P.r[1] = c->s32;
+        P.p[0] = c->p32;
+        P.p[1] = c->q32;
+        P.cst = q1_head_const(c->H, c->Ss, dt);
+        P.ntx = ntx[i];
+        P.nty = nty[i];
+        P.nzc = nzc[i];
+        P.item0 = (int)items.size();
+        P.nitems = ntx[i] * nty[i] * nzc[i];
+        if (P.nitems > c->part_stride) return bad(HT_EINVAL, "persistent batch: too many partial sums for a problem");
+        P.part = c->part;
+        P.stride = c->part_stride;
+        P.s = c->scal + 1;
+        for (int k = 0; k < P.nitems; ++k) items.push_back(i);
+    }
+    // buffers grow only; descriptors are uploaded on every call (the
+    // operator scalars and vectors of a problem may change between steps)
+    if (n > q.cap_probs || (int)items.size() > q.cap_items || !q.d_sync) {
+        q1_batch_free(q);
+        if (cudaMalloc(&q.d_probs, n * sizeof(Q1BatchProb)) != cudaSuccess ||
+            cudaMalloc(&q.d_items, items.size() * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&q.d_sync, sizeof(Q1BatchSync)) != cudaSuccess ||
+            cudaMallocHost(&q.h_sync, sizeof(Q1BatchSync)) != cudaSuccess) {
+            q1_batch_free(q);
+            return bad(HT_ENOMEM, "persistent batch: allocation failed");
+        }
+        q.cap_probs = n;
+        q.cap_items = (int)items.size();
+    }
+    if (cudaMemcpyAsync(q.d_probs, h.data(), n * sizeof(Q1BatchProb), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(q.d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        q1_batch_free(q);
+        return bad(HT_ECUDA, "persistent batch: descriptor upload failed");
+    }
+    q.nprob = n;
+    q.nitems = (int)items.size();
+    q.grid = (int)std::min<long long>(slots, q.nitems);
+    q.planes = best;
+    q.dt = dt;
+    return HT_OK;
+}
+
+int q1_batch_run(Q1Batch& q, cudaStream_t st, int max_iter, long long budget, int drop_cta, int* running,
+                 int* err_cta, std::string* err) {
+    auto bad = [&](int code, const char* msg) {
+        if (err) *err = msg;
+        return code;
+    };
+    *running = 0;
+    *err_cta = -1;
+    if (!q.d_probs || q.nitems < 1) return bad(HT_EINVAL, "persistent batch: not prepared");
+    if (cudaMemsetAsync(q.d_sync, 0, sizeof(Q1BatchSync), st) != cudaSuccess)
+        return bad(HT_ECUDA, "persistent batch: barrier reset failed");
+    const Q1BatchProb* probs = (const Q1BatchProb*)q.d_probs;
+    const int* items = q.d_items;
+    int nprob = q.nprob, nitems = q.nitems, iters = std::max(0, max_iter);
+    long long bud = budget;
+    Q1BatchSync* sync = (Q1BatchSync*)q.d_sync;
+    int drop = drop_cta;
+    void* args[] = {(void*)&probs, (void*)&nprob, (void*)&items, (void*)&nitems, (void*)&iters,
+                    (void*)&bud, (void*)&sync, (void*)&drop};
+    // cooperative: every CTA of the grid is resident at once, which the
+    // grid barrier needs
+    if (cudaLaunchCooperativeKernel((const void*)q1_cg_batch_kernel, dim3(q.grid), dim3(kBX, kBY), args,
+                                    sizeof(Q1Smem), st) != cudaSuccess)
+        return bad(HT_ECUDA, "persistent batch: cooperative launch failed");
+    if (cudaMemcpyAsync(q.h_sync, q.d_sync, sizeof(Q1BatchSync), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return bad(HT_ECUDA, "persistent batch: status readback failed");
+    const Q1BatchSync* hs = (const Q1BatchSync*)q.h_sync;
+    if (hs->err) {
+        *err_cta = hs->err_cta;
+        return bad(HT_ETIMEOUT, "persistent batch: a grid-barrier wait ran out of its budget");
+    }
+    *running = hs->running;
+    return HT_OK;
+}
+
+void q1_batch_free(Q1Batch& q) {
+    if (q.d_probs) cudaFree(q.d_probs);
+    if (q.d_items) cudaFree(q.d_items);
+    if (q.d_sync) cudaFree(q.d_sync);
+    if (q.h_sync) cudaFreeHost(q.h_sync);
+    q.d_probs = nullptr;
+    q.d_items = nullptr;
+    q.d_sync = nullptr;
+    q.h_sync = nullptr;
+    q.nprob = q.nitems = q.grid = q.cap_probs = q.cap_items = 0;
+    q.dt = -1.0;
 }
 
 int q1_cg_iteration32(ht_ctx* c, float dt, float* x, const float* r, const float* p, float* r_out, float* p_out,

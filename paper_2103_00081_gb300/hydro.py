@@ -7,7 +7,7 @@ torch CUDA float64 tensors (passed by data pointer with on_device=1).
 from __future__ import annotations
 
 import ctypes
-from ctypes import byref, c_double, c_size_t, c_void_p
+from ctypes import byref, c_double, c_int, c_size_t, c_void_p
 
 import numpy as np
 
@@ -267,6 +267,17 @@ class Batch:
             rc = self._lib.ht_batch_set_mode(self._h, int(mode))
             if rc != L.HT_OK:
                 raise HTError(rc, self._lib.ht_batch_last_error(self._h).decode())
+
+    def set_persistent(self, planes: int = 0, wait_ms: float = 2000.0, drop_cta: int = -1):
+        """Options of the persistent mode (see ht_batch_set_persistent)."""
+        rc = self._lib.ht_batch_set_persistent(self._h, int(planes), float(wait_ms), int(drop_cta))
+        if rc != L.HT_OK:
+            raise HTError(rc, self._lib.ht_batch_last_error(self._h).decode())
+
+    def persistent_info(self) -> dict:
+        v = [c_int() for _ in range(4)]
+        self._lib.ht_batch_persistent_info(self._h, *[byref(x) for x in v])
+        return dict(zip(("planes", "items", "grid", "err_cta"), (x.value for x in v)))
 
     def step(self, dt, check=True):
         n = len(self.sims)
