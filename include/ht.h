@@ -199,6 +199,34 @@ int ht_set_bc(ht_ctx* ctx, int field, int face, int type, double value);
  * or a type other than HT_BC_DIRICHLET / HT_BC_FLUX. */
 int ht_set_bc_values(ht_ctx* ctx, int field, int face, int type, const double* values, size_t n);
 
+/* Seasonal Dirichlet face (Section 3.3: the surface and sea temperatures
+ * over the year): the face becomes a Dirichlet face of `field` whose value
+ * at each step's t^{n+1} is mean + amp sin(2 pi t / period + phase).  On an
+ * edge shared with another Dirichlet face the face of higher index wins (as
+ * for static faces); pile surfaces (below) win over faces.  ht_set_bc or
+ * ht_set_bc_values on the face ends the seasonal value.  Errors: HT_EINVAL
+ * for a bad field or face, non-finite values or period <= 0. */
+int ht_set_seasonal_face(ht_ctx* ctx, int field, int face, double mean, double amp, double period, double phase);
+
+/* Pile surfaces held at a prescribed temperature (Section 3.3: energy piles
+ * at 288.55 K +- 13 K switched every six months).  rows[n][9] (host) =
+ * x, y, z_top, z_bot, radius, T_mean, T_amp, period, phase; the pile's nodes
+ * are Dirichlet rows of the heat system with the square-wave value
+ *   T(t) = T_mean + T_amp sign(sin(2 pi t / period + phase)),  sign(0) = +1,
+ * at each step's t^{n+1}.  A pile holds the nodes whose lateral distance to
+ * (x, y) is at most `radius` (tolerance 1e-9 of the largest extent) and whose
+ * z lies in [z_bot, z_top]; when no node is that close, the node column
+ * nearest the axis (ties to the lower y index, then the lower x index) over
+ * that depth range.  A node held by several piles takes the last one's
+ * value.  Nodes off the Dirichlet faces are handled by wrapping the heat
+ * operator (columns removed, identity rows), so the heat solves of such a
+ * context use the unfused Krylov kernels and FP64 outer residuals, and
+ * ht_residual(..., emulated = 1) of the heat field is formed in FP64.
+ * n = 0 removes all pile surfaces.  The array is copied.  Errors: HT_EINVAL
+ * for non-finite entries, a negative radius, period <= 0 or a depth range
+ * outside the mesh. */
+int ht_set_pile_temperatures(ht_ctx* ctx, int n, const double* rows);
+
 /* Number of nodes on `face` (0..5) of the mesh. */
 int ht_face_nodes(const ht_ctx* ctx, int face, size_t* n);
 

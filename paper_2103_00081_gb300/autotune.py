@@ -106,3 +106,41 @@ def tune(factory: Callable[[Dict], object], dt: float, sig: str, candidates: Opt
         data[sig] = {"opts": best, "ms": best_ms, "table": table}
         _store(cache, data)
     return best, table
+
+
+def default_batch_candidates() -> List[Dict]:
+    """Batched-step choices worth timing: the persistent mode with the
+    automatic z chunking and with fixed node planes per work item (the tile
+    shape of the persistent launch along z), and the concurrent mode."""
+    out = [dict(mode=L.HT_BATCH_PERSISTENT, planes=p) for p in (0, 4, 8, 12, 16, 24, 32)]
+    out.append(dict(mode=L.HT_BATCH_CONCURRENT))
+    return out
+
+
+class _TimedBatch:
+    """Adapter that gives a batch the step() of a simulator for tune(): the
+    batched step returns only after its work on the device is complete, so
+    the host clock around it is the step's time."""
+
+    def __init__(self, batch):
+        self.batch = batch
+
+    def step(self, dt, check=True):
+        import time
+        t0 = time.perf_counter()
+        stats = self.batch.step(dt, check=False)
+        ms = (time.perf_counter() - t0) * 1e3
+        rc = next((st["rc"] for st in stats if st["rc"] != L.HT_OK), L.HT_OK)
+        return {"rc": rc, "ms_total": ms}
+
+    def close(self):
+        self.batch.close()
+
+
+def tune_batch(factory: Callable[[Dict], object], dt: float, sig: str,
+               candidates: Optional[Iterable[Dict]] = None, steps: int = 2,
+               cache: Optional[str] = DEFAULT_CACHE, force: bool = False) -> Tuple[Dict, List]:
+    """tune() for batched steps: factory(opts) must build a fresh batch (over
+    fresh simulators) configured with ``opts`` (mode, planes)."""
+    cands = list(candidates) if candidates is not None else default_batch_candidates()
+    return tune(lambda o: _TimedBatch(factory(o)), dt, sig, cands, steps=steps, cache=cache, force=force)

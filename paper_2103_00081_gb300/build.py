@@ -31,7 +31,9 @@ def nvcc_path() -> str:
 
 
 def common_flags(extra=()):
-    return ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+    # host code without contracted multiply-adds: the host-side geometry
+    # (source weights, pile-surface nodes) rounds the same way on every CPU
+    return ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
             "-I", INCLUDE, "-I", CSRC, *extra]
 
 

@@ -348,12 +348,117 @@ int box_weights(ht_ctx* c, const ht_box_src& b, std::map<long long, double>& out
     return HT_OK;
 }
 
-bool node_on_dirichlet(const ht_ctx* c, int field, long long id) {
+bool node_on_dirichlet_face(const ht_ctx* c, int field, long long id) {
     const Grid& g = c->grid;
     const int i = (int)(id % g.Nx), j = (int)((id / g.Nx) % g.Ny), k = (int)(id / ((long long)g.Nx * g.Ny));
     const int m = c->dmask[field];
     return ((m & 1) && i == 0) || ((m & 2) && i == g.Nx - 1) || ((m & 4) && j == 0) ||
            ((m & 8) && j == g.Ny - 1) || ((m & 16) && k == 0) || ((m & 32) && k == g.Nz - 1);
+}
+
+bool node_on_dirichlet(const ht_ctx* c, int field, long long id) {
+    if (node_on_dirichlet_face(c, field, id)) return true;
+    return field == HT_TEMP && std::binary_search(c->dint_host.begin(), c->dint_host.end(), id);
+}
+
+// Nodes held at a pile's temperature (Section 3.3): the nodes within the
+// radius of the pile axis (lateral distance) whose z lies in the pile's
+// depth range, or, when no node is that close, the node column nearest the
+// axis (ties to the lower j, then the lower i) over the same depth range.
+// Node coordinates are origin + index * H / P, compared with a tolerance of
+// 1e-9 of the largest extent.  row = x, y, z_top, z_bot, radius, ...
+int pile_surface_nodes(ht_ctx* c, const double* row, std::vector<long long>& out) {
+    const Grid& g = c->grid;
+    const ht_mesh& m = c->mesh;
+    const double hx = c->H[0] / g.P, hy = c->H[1] / g.P, hz = c->H[2] / g.P;
+    const double eps = 1e-9 * std::max(m.Lx, std::max(m.Ly, m.Lz));
+    const double zlo = std::min(row[2], row[3]) - eps, zhi = std::max(row[2], row[3]) + eps;
+    std::vector<int> ks;
+    for (int k = 0; k < g.Nz; ++k) {
+        const double z = m.z0 + k * hz;
+        if (z >= zlo && z <= zhi) ks.push_back(k);
+    }
+    out.clear();
+    if (ks.empty()) return fail(c, HT_EINVAL, "pile surface (%g, %g) lies outside the mesh", row[0], row[1]);
+    auto lat = [&](int i, int j) {
+        const double dx = (m.x0 + i * hx) - row[0], dy = (m.y0 + j * hy) - row[1];
+        return dx * dx + dy * dy;
+    };
+    const double r2 = row[4] * row[4] + eps;
+    const double R = sqrt(r2);
+    const int i0 = std::max(0, (int)floor((row[0] - R - m.x0) / hx) - 1);
+    const int i1 = std::min(g.Nx - 1, (int)ceil((row[0] + R - m.x0) / hx) + 1);
+    const int j0 = std::max(0, (int)floor((row[1] - R - m.y0) / hy) - 1);
+    const int j1 = std::min(g.Ny - 1, (int)ceil((row[1] + R - m.y0) / hy) + 1);
+    std::vector<std::pair<int, int>> cols;
+    for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i)
+            if (lat(i, j) <= r2) cols.push_back({i, j});
+    if (cols.empty()) {
+        int bi = 0, bj = 0;
+        double best = -1.0;
+        for (int j = 0; j < g.Ny; ++j)
+            for (int i = 0; i < g.Nx; ++i) {
+                const double d = lat(i, j);
+                if (best < 0.0 || d < best) { best = d; bi = i; bj = j; }
+            }
+        cols.push_back({bi, bj});
+    }
+    for (int k : ks)
+        for (auto& ij : cols) out.push_back(ij.first + (long long)g.Nx * (ij.second + (long long)g.Ny * k));
+    std::sort(out.begin(), out.end());
+    return HT_OK;
+}
+
+// device tables of the pile-surface nodes and the heat Dirichlet rows off
+// the faces (after the face masks are known)
+int setup_pile_temperatures(ht_ctx* c) {
+    dfree(c->ptemp_node); dfree(c->ptemp_pile); dfree(c->d_ptemp); dfree(c->dint);
+    dfree(c->dint_a64); dfree(c->dint_b64); dfree(c->dint_a32);
+    c->n_ptemp_nodes = 0;
+    c->n_dint = 0;
+    c->dint_host.clear();
+    const int np = (int)(c->ptemp_rows.size() / 9);
+    if (np == 0) return HT_OK;
+    std::map<long long, int> owner;   // node -> the last pile that holds it
+    std::vector<long long> nodes;
+    for (int p = 0; p < np; ++p) {
+        HT_TRY(pile_surface_nodes(c, &c->ptemp_rows[9 * (size_t)p], nodes));
+        for (long long id : nodes) owner[id] = p;
+    }
+    std::vector<long long> nd;
+    std::vector<int> pl;
+    std::vector<double> prm(4 * (size_t)np);
+    for (int p = 0; p < np; ++p)
+        for (int q = 0; q < 4; ++q) prm[4 * (size_t)p + q] = c->ptemp_rows[9 * (size_t)p + 5 + q];
+    for (auto& kv : owner) {
+        nd.push_back(kv.first);
+        pl.push_back(kv.second);
+        if (!node_on_dirichlet_face(c, HT_TEMP, kv.first)) c->dint_host.push_back(kv.first);
+    }
+    const size_t nn = (size_t)c->grid.nn;
+    c->n_ptemp_nodes = (int)nd.size();
+    c->n_dint = (int)c->dint_host.size();
+    if (cudaMalloc(&c->ptemp_node, nd.size() * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&c->ptemp_pile, pl.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_ptemp, prm.size() * sizeof(double)) != cudaSuccess ||
+        (c->n_dint > 0 && (cudaMalloc(&c->dint, c->dint_host.size() * sizeof(long long)) != cudaSuccess ||
+                           cudaMalloc(&c->dint_a64, nn * sizeof(double)) != cudaSuccess ||
+                           cudaMalloc(&c->dint_b64, nn * sizeof(double)) != cudaSuccess ||
+                           cudaMalloc(&c->dint_a32, nn * sizeof(float)) != cudaSuccess))) {
+        c->n_ptemp_nodes = c->n_dint = 0;
+        return fail(c, HT_ENOMEM, "pile-surface tables: allocation failed");
+    }
+    HT_CUDA(c, cudaMemcpyAsync(c->ptemp_node, nd.data(), nd.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                               c->stream));
+    HT_CUDA(c, cudaMemcpyAsync(c->ptemp_pile, pl.data(), pl.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    HT_CUDA(c, cudaMemcpyAsync(c->d_ptemp, prm.data(), prm.size() * sizeof(double), cudaMemcpyHostToDevice,
+                               c->stream));
+    if (c->n_dint > 0)
+        HT_CUDA(c, cudaMemcpyAsync(c->dint, c->dint_host.data(), c->dint_host.size() * sizeof(long long),
+                                   cudaMemcpyHostToDevice, c->stream));
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HT_OK;
 }
 
 // n-point Gauss-Legendre rule on [0, 1]: Newton iteration on the Legendre
@@ -501,6 +606,8 @@ int finalize_setup(ht_ctx* c) {
         HT_CUDA(c, cudaMemcpyAsync(c->g[f], gv.data(), nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         HT_CUDA(c, cudaStreamSynchronize(c->stream));
     }
+    // pile surfaces at a prescribed temperature (heat Dirichlet rows)
+    if (c->bc_dirty) HT_TRY(setup_pile_temperatures(c));
     // wells: head line source and (injection) lumped heat term
     std::map<long long, double> wd;
     for (const ht_well& w : c->wells) {
@@ -843,6 +950,8 @@ void ht_destroy(ht_ctx* c) {
                      &c->E32, &c->wdn32, &c->h32};
     for (float** pp : v32) dfree(*pp);
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
+    dfree(c->ptemp_node); dfree(c->ptemp_pile); dfree(c->d_ptemp); dfree(c->dint);
+    dfree(c->dint_a64); dfree(c->dint_b64); dfree(c->dint_a32);
     dfree(c->scal);
     dfree(c->gm);
     dfree(c->V64);
@@ -901,8 +1010,41 @@ int ht_set_bc(ht_ctx* c, int field, int face, int type, double value) {
     c->bc_type[field][face] = type;
     c->bc_val[field][face] = value;
     c->bc_nodal[field][face].clear();
+    c->seasonal[field][face].on = 0;
     c->bc_dirty = true;
     c->cheb_dt[field] = -1.0;
+    return HT_OK;
+}
+
+int ht_set_seasonal_face(ht_ctx* c, int field, int face, double mean, double amp, double period, double phase) {
+    if (!c) return HT_EINVAL;
+    if (field != HT_HEAD && field != HT_TEMP) return fail(c, HT_EINVAL, "field must be HT_HEAD or HT_TEMP");
+    if (face < 0 || face > 5) return fail(c, HT_EINVAL, "face must be 0..5");
+    if (!isfinite(mean) || !isfinite(amp) || !isfinite(phase) || !(period > 0) || !isfinite(period))
+        return fail(c, HT_EINVAL, "seasonal face needs finite mean, amplitude and phase and a positive period");
+    c->bc_type[field][face] = HT_BC_DIRICHLET;
+    c->bc_val[field][face] = mean;
+    c->bc_nodal[field][face].clear();
+    c->seasonal[field][face] = ht_ctx::Seasonal{1, mean, amp, period, phase};
+    c->bc_dirty = true;
+    c->cheb_dt[field] = -1.0;
+    return HT_OK;
+}
+
+int ht_set_pile_temperatures(ht_ctx* c, int n, const double* rows) {
+    if (!c || n < 0 || (n > 0 && !rows)) return HT_EINVAL;
+    for (int p = 0; p < n; ++p) {
+        const double* r = rows + 9 * (size_t)p;
+        for (int q = 0; q < 9; ++q)
+            if (!isfinite(r[q])) return fail(c, HT_EINVAL, "pile temperature row %d has a non-finite entry", p);
+        if (r[4] < 0 || !(r[7] > 0))
+            return fail(c, HT_EINVAL, "pile temperature row %d: radius >= 0 and period > 0 are required", p);
+        const ht_mesh& m = c->mesh;
+        if (std::max(r[2], r[3]) < m.z0 || std::min(r[2], r[3]) > m.z0 + m.Lz)
+            return fail(c, HT_EINVAL, "pile temperature row %d lies outside the mesh in z", p);
+    }
+    c->ptemp_rows.assign(rows, rows + 9 * (size_t)n);
+    c->bc_dirty = true;
     return HT_OK;
 }
 
@@ -1145,7 +1287,7 @@ int ht_residual(ht_ctx* c, int field, double dt, const double* x, const double* 
     HT_TRY(copy_in(c, c->v, b, n, on_device));
     if (field == HT_TEMP) HT_TRY(launch_darcy_qp(c, c->h));
     int np = 0;
-    if (emulated) {
+    if (emulated && !(field == HT_TEMP && !heat_fused_ok(c))) {
         HT_TRY(launch_resid_df(c, field, dt, c->z, c->v, c->r32, c->part, &np));
     } else {
         HT_TRY(launch_apply64(c, field, dt, c->z, c->q, nullptr, nullptr, nullptr));

@@ -120,6 +120,26 @@ struct ht_ctx {
     int dmask[2] = {0, 0};
     double* g[2] = {nullptr, nullptr};     // nodal Dirichlet values (0 off the mask)
     bool bc_dirty = true;
+    // Dirichlet faces whose value follows mean + amp sin(2 pi t / period + phase)
+    struct Seasonal {
+        int on = 0;
+        double mean = 0, amp = 0, period = 1, phase = 0;
+    };
+    Seasonal seasonal[2][6];
+    // pile surfaces held at a square-wave temperature (heat Dirichlet rows):
+    // host rows [n][9] = x, y, z_top, z_bot, radius, T_mean, T_amp, period, phase
+    std::vector<double> ptemp_rows;
+    int n_ptemp_nodes = 0;                  // nodes held (the last pile listed wins a shared node)
+    long long* ptemp_node = nullptr;
+    int* ptemp_pile = nullptr;
+    double* d_ptemp = nullptr;              // [n][4] T_mean, T_amp, period, phase
+    // heat Dirichlet rows off the Dirichlet faces (pile surfaces), sorted
+    int n_dint = 0;
+    long long* dint = nullptr;
+    std::vector<long long> dint_host;
+    double* dint_a64 = nullptr;             // scratch of the wrapped operators
+    double* dint_b64 = nullptr;
+    float* dint_a32 = nullptr;
 
     // state
     double* h = nullptr;
@@ -197,7 +217,7 @@ struct ht_ctx {
     // pointers or dt they were captured with change ([0] FP64, [1] FP32)
     struct FusedGraph {
         cudaGraphExec_t exec = nullptr;
-        const void* key[8] = {};
+        const void* key[12] = {};
         double dt = 0.0;
         double ss = 0.0;                // operator scalars baked into the captured launches
     };
@@ -268,6 +288,13 @@ int launch_well_apply32(ht_ctx* c, float dt, const float* x, float* y, const Sca
 int launch_well_diag(ht_ctx* c, double dt, double* D);
 // F[field] = Fstat + extra + pile loads at time t
 int launch_loads(ht_ctx* c, double t);
+// Dirichlet values at time t of the seasonal faces and the pile surfaces
+// (called by launch_loads with the step's t^{n+1}); ht_ops.cu
+int launch_time_dirichlet(ht_ctx* c, double t);
+// heat Dirichlet rows off the faces: the raw operator launches treat only
+// the six faces; these wrap them (ht_ops.cu)
+int dint_scatter(ht_ctx* c, double* dst, const double* src);   // dst[i] = src[i] on the rows
+bool heat_fused_ok(const ht_ctx* c);    // no interior rows: the fused heat kernels apply
 int apply_tiles(const ht_ctx* c);
 // fused two-pass Jacobi-CG iteration of the head system (ht_ops.cu)
 int fused_cg_iteration64(ht_ctx* c, double dt, double* x, double* r, const double* Dinv, double* p, Scal* sc,

@@ -986,8 +986,9 @@ int run_bicgstab(ht_ctx* c, double dt, const V& w, const T* b, int slot, double 
             break;
         }
         int chunk = c->opts.check_every > 0 ? c->opts.check_every : 8;
-        const bool q1 = sizeof(T) == 4 && q1_bicgstab_available(c);
-        const bool fused = q1 || fused_cg_available(c, sizeof(T) == 4);
+        // the fused heat kernels treat the face Dirichlet rows only
+        const bool q1 = sizeof(T) == 4 && q1_bicgstab_available(c) && heat_fused_ok(c);
+        const bool fused = q1 || (fused_cg_available(c, sizeof(T) == 4) && heat_fused_ok(c));
         if (q1) {
             // two tiled heat applies and the update per iteration; iteration j
             // reads p, v from copy j % 2 and writes copy (j + 1) % 2 (copy 1 is
@@ -1330,7 +1331,7 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
             gf.dmask = c->dmask[field];
             resid32_kernel<<<G, kVecThreads, 0, c->stream>>>(gf, n, b, c->q32, x, c->r32, c->part, S); ++c->n_launch;
             HT_CUDA(c, cudaGetLastError());
-        } else if (c->opts.outer_fp64) {
+        } else if (c->opts.outer_fp64 || (field == HT_TEMP && !heat_fused_ok(c))) {
             HT_TRY(launch_apply64(c, field, dt, x, c->q, nullptr, nullptr, nullptr));
             resid_kernel<<<G, kVecThreads, 0, c->stream>>>(n, b, c->q, nullptr, c->r32, c->part, S); ++c->n_launch;
             HT_CUDA(c, cudaGetLastError());
@@ -1441,6 +1442,7 @@ int launch_norms(ht_ctx* c, int n_part, int slot) {
 int set_dirichlet_values(ht_ctx* c, int field, double* x) {
     Grid g = c->grid;
     g.dmask = c->dmask[field];
+    if (field == HT_TEMP) HT_TRY(dint_scatter(c, x, c->g[HT_TEMP]));   // pile surfaces off the faces
     if (!g.dmask) return HT_OK;
     dirichlet_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(g, c->g[field], x); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());

@@ -2221,8 +2221,86 @@ int apply_tiles(const ht_ctx* c) {
     return (int)(grid.x * grid.y * grid.z);
 }
 
-int launch_apply64(ht_ctx* c, int field, double dt, const double* x, double* y, double* dot_part,
-                   int* n_part, const Scal* sc) {
+// ---- Dirichlet rows that change with time or lie inside the mesh ------------
+// Seasonal faces and pile surfaces (Section 3.3) take their values at each
+// step's t^{n+1}.  A pile-surface node off the Dirichlet faces is a Dirichlet
+// row of the heat system like a face node: its row of A0 is the identity row
+// and its column is removed (A0 = P A P + (I - P), P the projector on the
+// free nodes).  The raw operator kernels treat the six faces only, so the
+// heat operator launches below wrap them: the input with the interior rows
+// zeroed (the columns removed), then those rows of the output set to the
+// input (the identity rows); the diagonal is 1 there, and the lifted
+// right-hand side takes A0 g of the interior values off the free rows.
+namespace {
+
+// face `face` at value v, except nodes on a Dirichlet face of higher index
+// (on a shared edge the higher face wins)
+__global__ void face_value_kernel(Grid g, int face, double v, double* __restrict__ gval) {
+    const int axis = face / 2, side = face % 2;
+    const int Nd[3] = {g.Nx, g.Ny, g.Nz};
+    const int t1 = axis == 0 ? 1 : 0, t2 = axis == 2 ? 1 : 2;
+    const long long n = (long long)Nd[t1] * Nd[t2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        int ijk[3];
+        ijk[axis] = side ? Nd[axis] - 1 : 0;
+        ijk[t1] = (int)(q % Nd[t1]);
+        ijk[t2] = (int)(q / Nd[t1]);
+        bool higher = false;
+        for (int f2 = face + 1; f2 < 6; ++f2) {
+            const int a2 = f2 / 2;
+            if (((g.dmask >> f2) & 1) && ijk[a2] == ((f2 & 1) ? Nd[a2] - 1 : 0)) higher = true;
+        }
+        if (!higher) gval[ijk[0] + (long long)g.Nx * (ijk[1] + (long long)g.Ny * ijk[2])] = v;
+    }
+}
+
+// pile surfaces: T_mean + T_amp sign(sin(2 pi t / period + phase)), sign(0) = +1
+__global__ void pile_temp_kernel(int n, const long long* __restrict__ node, const int* __restrict__ pile,
+                                 const double* __restrict__ prm, double t, double* __restrict__ gval) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* pr = prm + 4 * pile[i];
+    const double sn = sin(2.0 * M_PI * t / pr[2] + pr[3]);
+    gval[node[i]] = pr[0] + pr[1] * (sn >= 0.0 ? 1.0 : -1.0);
+}
+
+template <typename T>
+__global__ void rows_copy_kernel(int n, const long long* __restrict__ idx, const T* __restrict__ src,
+                                 T* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[idx[i]] = src[idx[i]];
+}
+
+template <typename T>
+__global__ void rows_fill_kernel(int n, const long long* __restrict__ idx, T v, T* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[idx[i]] = v;
+}
+
+__global__ void sub64_kernel(long long n, const double* __restrict__ a, double* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] -= a[i];
+}
+
+template <typename T>
+int rows_copy(ht_ctx* c, T* dst, const T* src) {
+    const int n = c->n_dint;
+    rows_copy_kernel<T><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->dint, src, dst); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+template <typename T>
+int rows_fill(ht_ctx* c, T* dst, T v) {
+    const int n = c->n_dint;
+    rows_fill_kernel<T><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->dint, v, dst); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
+int apply64_raw(ht_ctx* c, int field, double dt, const double* x, double* y, double* dot_part, int* n_part,
+                const Scal* sc) {
     HT_TRY(prof_begin(c, field));
     int rc = c->grid.P == 1 ? apply_P<1, double>(c, field, dt, x, y, dot_part, n_part, sc)
                             : apply_P<2, double>(c, field, dt, x, y, dot_part, n_part, sc);
@@ -2232,8 +2310,8 @@ int launch_apply64(ht_ctx* c, int field, double dt, const double* x, double* y, 
     return HT_OK;
 }
 
-int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y, double* dot_part,
-                   int* n_part, const Scal* sc) {
+int apply32_raw(ht_ctx* c, int field, float dt, const float* x, float* y, double* dot_part, int* n_part,
+                const Scal* sc) {
     HT_TRY(prof_begin(c, field + 2));
     int rc = c->grid.P == 1 ? apply_P<1, float>(c, field, dt, x, y, dot_part, n_part, sc)
                             : apply_P<2, float>(c, field, dt, x, y, dot_part, n_part, sc);
@@ -2241,6 +2319,62 @@ int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y, dou
     HT_TRY(prof_end(c));
     if (field == HT_TEMP && c->n_well_nodes > 0) return launch_well_apply32(c, dt, x, y, sc);
     return HT_OK;
+}
+
+}  // namespace
+
+bool heat_fused_ok(const ht_ctx* c) { return c->n_dint == 0; }
+
+int dint_scatter(ht_ctx* c, double* dst, const double* src) {
+    if (c->n_dint == 0) return HT_OK;
+    return rows_copy<double>(c, dst, src);
+}
+
+int launch_time_dirichlet(ht_ctx* c, double t) {
+    for (int f = 0; f < 2; ++f) {
+        Grid g = c->grid;
+        g.dmask = c->dmask[f];
+        for (int face = 0; face < 6; ++face) {
+            const ht_ctx::Seasonal& sn = c->seasonal[f][face];
+            if (!sn.on) continue;
+            const double v = sn.mean + sn.amp * sin(2.0 * M_PI * t / sn.period + sn.phase);
+            face_value_kernel<<<64, 256, 0, c->stream>>>(g, face, v, c->g[f]); ++c->n_launch;
+            HT_CUDA(c, cudaGetLastError());
+        }
+    }
+    if (c->n_ptemp_nodes > 0) {
+        const int n = c->n_ptemp_nodes;
+        pile_temp_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->ptemp_node, c->ptemp_pile, c->d_ptemp, t,
+                                                                 c->g[HT_TEMP]); ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+    }
+    return HT_OK;
+}
+
+int launch_apply64(ht_ctx* c, int field, double dt, const double* x, double* y, double* dot_part,
+                   int* n_part, const Scal* sc) {
+    if (field == HT_TEMP && c->n_dint > 0) {
+        if (dot_part) return fail(c, HT_EINVAL, "heat apply with interior Dirichlet rows forms no dot products");
+        HT_CUDA(c, cudaMemcpyAsync(c->dint_a64, x, (size_t)c->grid.nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        HT_TRY(rows_fill<double>(c, c->dint_a64, 0.0));
+        HT_TRY(apply64_raw(c, field, dt, c->dint_a64, y, nullptr, nullptr, sc));
+        return rows_copy<double>(c, y, x);
+    }
+    return apply64_raw(c, field, dt, x, y, dot_part, n_part, sc);
+}
+
+int launch_apply32(ht_ctx* c, int field, float dt, const float* x, float* y, double* dot_part,
+                   int* n_part, const Scal* sc) {
+    if (field == HT_TEMP && c->n_dint > 0) {
+        if (dot_part) return fail(c, HT_EINVAL, "heat apply with interior Dirichlet rows forms no dot products");
+        HT_CUDA(c, cudaMemcpyAsync(c->dint_a32, x, (size_t)c->grid.nn * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        HT_TRY(rows_fill<float>(c, c->dint_a32, 0.0f));
+        HT_TRY(apply32_raw(c, field, dt, c->dint_a32, y, nullptr, nullptr, sc));
+        return rows_copy<float>(c, y, x);
+    }
+    return apply32_raw(c, field, dt, x, y, dot_part, n_part, sc);
 }
 
 template <int P, class Op>
@@ -2291,7 +2425,19 @@ static int rhs_P(ht_ctx* c, int field, double dt, const double* u_old, double* b
 }
 
 int launch_rhs(ht_ctx* c, int field, double dt, const double* u_old, double* b) {
-    return c->grid.P == 1 ? rhs_P<1>(c, field, dt, u_old, b) : rhs_P<2>(c, field, dt, u_old, b);
+    HT_TRY(c->grid.P == 1 ? rhs_P<1>(c, field, dt, u_old, b) : rhs_P<2>(c, field, dt, u_old, b));
+    if (field == HT_TEMP && c->n_dint > 0) {
+        // lift of the interior rows: b -= A0 g_I on every row (A0 g_I is 0 on
+        // the face rows, whose columns it never reaches), then b = g on them
+        const size_t nn = (size_t)c->grid.nn;
+        HT_CUDA(c, cudaMemsetAsync(c->dint_a64, 0, nn * sizeof(double), c->stream));
+        HT_TRY(rows_copy<double>(c, c->dint_a64, c->g[HT_TEMP]));
+        HT_TRY(apply64_raw(c, HT_TEMP, dt, c->dint_a64, c->dint_b64, nullptr, nullptr, nullptr));
+        sub64_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, c->dint_b64, b); ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+        HT_TRY(rows_copy<double>(c, b, c->g[HT_TEMP]));
+    }
+    return HT_OK;
 }
 
 template <int P>
@@ -2331,6 +2477,7 @@ int launch_diag32(ht_ctx* c, int field, double dt, float* D) {
         ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
     }
+    if (field == HT_TEMP && c->n_dint > 0) return rows_fill<float>(c, D, 1.0f);
     return HT_OK;
 }
 
@@ -2389,7 +2536,8 @@ int launch_resid_df(ht_ctx* c, int field, double dt, const double* x, const doub
 int launch_diag(ht_ctx* c, int field, double dt, double* D) {
     int rc = c->grid.P == 1 ? diag_P<1>(c, field, dt, D) : diag_P<2>(c, field, dt, D);
     if (rc != HT_OK) return rc;
-    if (field == HT_TEMP && c->n_well_nodes > 0) return launch_well_diag(c, dt, D);
+    if (field == HT_TEMP && c->n_well_nodes > 0) HT_TRY(launch_well_diag(c, dt, D));
+    if (field == HT_TEMP && c->n_dint > 0) return rows_fill<double>(c, D, 1.0);
     return HT_OK;
 }
 
@@ -2468,7 +2616,7 @@ int launch_loads(ht_ctx* c, double t) {
                                                                  c->F[HT_TEMP]); ++c->n_launch;
         HT_CUDA(c, cudaGetLastError());
     }
-    return HT_OK;
+    return launch_time_dirichlet(c, t);
 }
 
 // ---------------------------------------------------------------------------

@@ -981,7 +981,7 @@ bool q1_cg_available(const ht_ctx* c, int fp32) {
 
 bool q1_bicgstab_available(const ht_ctx* c) {
     const bool percell_ok = (c->cT32 == nullptr) == (c->lam32 == nullptr);
-    return c->grid.P == 1 && c->K32 != nullptr && c->h32 != nullptr && percell_ok &&
+    return c->grid.P == 1 && c->K32 != nullptr && c->h32 != nullptr && percell_ok && c->n_dint == 0 &&
            (c->opts.apply_variant == HT_APPLY_AUTO || c->opts.apply_variant == HT_APPLY_SINGLE_PASS);
 }
 

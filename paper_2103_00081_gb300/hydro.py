@@ -94,6 +94,18 @@ class Simulator:
         return self._check(self._lib.ht_set_bc_values(self._h, int(field), int(face), int(typ),
                                                       v.ctypes.data, v.size))
 
+    def set_seasonal_face(self, field, face, mean, amp, period, phase=0.0):
+        """Dirichlet face whose value is mean + amp sin(2 pi t / period + phase)
+        at each step's end time."""
+        return self._check(self._lib.ht_set_seasonal_face(self._h, int(field), int(face), float(mean), float(amp),
+                                                          float(period), float(phase)))
+
+    def set_pile_temperatures(self, rows):
+        """Pile surfaces held at a square-wave temperature; rows [n][9] =
+        (x, y, z_top, z_bot, radius, T_mean, T_amp, period, phase)."""
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.float64).reshape(-1, 9))
+        return self._check(self._lib.ht_set_pile_temperatures(self._h, r.shape[0], r.ctypes.data if r.size else None))
+
     def face_nodes(self, face):
         n = ctypes.c_size_t()
         self._check(self._lib.ht_face_nodes(self._h, int(face), ctypes.byref(n)))
@@ -229,9 +241,6 @@ class Simulator:
     def from_scenario(cls, sc, device=0, stream=None, **solver):
         if getattr(sc, "spacing", None) is not None:
             raise ValueError("the library takes uniform cells along each axis; graded spacing is not supported")
-        if np.size(getattr(sc, "pile_temps", np.zeros(0))) or getattr(sc, "bc_seasonal", None):
-            raise ValueError("pile surface temperatures and seasonal faces are not supported by the library; "
-                             "re-set face values between steps with set_bc instead")
         s = cls(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, device=device, stream=stream)
         lam, cT, Ss = s.bulk_properties(sc.material)
         s.set_cells(sc.K, sc.lam_cells, sc.cT_cells, sc.lam if sc.lam is not None else lam,
@@ -239,6 +248,10 @@ class Simulator:
         for field, faces in sc.bc.items():
             for face, (typ, val) in faces.items():
                 s.set_bc(field, face, typ, val)
+        for field, faces in (getattr(sc, "bc_seasonal", None) or {}).items():
+            for face, (mean, amp, period, phase) in faces.items():
+                s.set_seasonal_face(field, face, mean, amp, period, phase)
+        s.set_pile_temperatures(getattr(sc, "pile_temps", np.zeros((0, 9))))
         s.add_line_sources(sc.piles)
         s.add_wells(sc.wells)
         s.add_box_sources(getattr(sc, "boxes", np.zeros((0, 9))))

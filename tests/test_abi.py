@@ -81,9 +81,8 @@ def test_struct_layouts_match_the_header():
 
 
 def test_oracle_only_scenarios_are_refused_by_the_binding():
-    """Graded spacing, pile surfaces at a prescribed temperature and seasonal
-    faces exist only in the oracle so far: the binding refuses such a
-    scenario before any library call instead of ignoring the feature."""
+    """Graded spacing exists only in the oracle so far: the binding refuses
+    such a scenario before any library call instead of ignoring it."""
     import numpy as np
 
     import scenarios as S
@@ -93,10 +92,3 @@ def test_oracle_only_scenarios_are_refused_by_the_binding():
     with pytest.raises(ValueError):
         hydro.Simulator.from_scenario(sc)
     assert np.allclose([w.sum() for w in sc.spacing], sc.extent)
-    # likewise pile surfaces at a prescribed temperature and seasonal faces
-    for field, value in (("pile_temps", np.array([[1.0, 1.0, 2.0, 0.0, 0.5, 288.55, 13.0, 3.15e7, 0.0]])),
-                         ("bc_seasonal", {S.TEMP: {5: (287.45, 8.0, 3.15e7, 0.0)}})):
-        sc = S.random_small(1, 3, 2, 2, 1)
-        setattr(sc, field, value)
-        with pytest.raises(ValueError):
-            hydro.Simulator.from_scenario(sc)

@@ -42,3 +42,29 @@ def test_tune_picks_fastest_and_caches(tmp_path):
 def test_tune_raises_when_everything_fails(tmp_path):
     with pytest.raises(RuntimeError):
         AT.tune(lambda o: FakeSim(o, {}), 1.0, "s", [{"broken": True}], cache=None)
+
+
+class FakeBatch:
+    def __init__(self, opts, delay):
+        self.opts = opts
+        self.delay = delay
+
+    def step(self, dt, check=True):
+        import time
+        time.sleep(self.delay[self.opts["planes"]])
+        rc = -6 if self.opts["planes"] == 99 else 0
+        return [{"rc": rc}, {"rc": 0}]
+
+    def close(self):
+        pass
+
+
+def test_tune_batch_times_whole_batched_steps(tmp_path):
+    delay = {0: 0.03, 8: 0.005, 16: 0.02, 99: 0.0}
+    cands = [{"mode": 2, "planes": p} for p in (0, 8, 16, 99)]
+    best, table = AT.tune_batch(lambda o: FakeBatch(o, delay), 1.0, "b", cands, steps=1,
+                                cache=str(tmp_path / "c.json"))
+    assert best == {"mode": 2, "planes": 8}
+    assert table[3][2].startswith("failed")       # a step that returned an error
+    assert table[0][1] > table[1][1]
+    assert all(c["mode"] in (0, 2) for c in AT.default_batch_candidates())
