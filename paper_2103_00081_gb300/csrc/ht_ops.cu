@@ -2541,6 +2541,65 @@ int launch_diag(ht_ctx* c, int field, double dt, double* D) {
     return HT_OK;
 }
 
+// Q1: the derivative along an axis is the same at both Gauss points of that
+// axis, the edge difference (u1 - u0) / H interpolated in the other two
+// directions, so the 24 values of a cell come from 12 edge differences and
+// three bilinear interpolations
+__global__ void __launch_bounds__(128) darcy_qp_q1_kernel(const Grid g, const double* __restrict__ h,
+                                                          const double* __restrict__ K, const Elem<double> e,
+                                                          double* __restrict__ qs64, float* __restrict__ qs32) {
+    constexpr int NQ = 8;
+    const double B[2][2] = {{e.B[0][0], e.B[0][1]}, {e.B[1][0], e.B[1][1]}};
+    // out[i][j] = sum_a sum_b B[i][a] B[j][b] d[a][b]
+    auto interp = [&](const double (&d)[2][2], double (&out)[2][2]) {
+        double t[2][2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) t[a][j] = fma(B[j][1], d[a][1], B[j][0] * d[a][0]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) out[i][j] = fma(B[i][1], t[1][j], B[i][0] * t[0][j]);
+    };
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % g.ncx), cy = (int)((c / g.ncx) % g.ncy), cz = (int)(c / ((long long)g.ncx * g.ncy));
+        double u[8];
+        gather<1, double>(g, h, cx, cy, cz, false, u);   // u[a + 2 (b + 2 c)]
+        const double Kc = K[c];
+        double dx[2][2], dy[2][2], dz[2][2];   // dx[b][c], dy[a][c], dz[a][b]
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                dx[i][j] = u[1 + 2 * (i + 2 * j)] - u[0 + 2 * (i + 2 * j)];
+                dy[i][j] = u[i + 2 * (1 + 2 * j)] - u[i + 2 * (0 + 2 * j)];
+                dz[i][j] = u[i + 2 * (j + 2)] - u[i + 2 * j];
+            }
+        double gx[2][2], gy[2][2], gz[2][2];   // gx[qy][qz], gy[qx][qz], gz[qx][qy]
+        interp(dx, gx);
+        interp(dy, gy);
+        interp(dz, gz);
+        const double sx = -Kc * e.invH[0], sy = -Kc * e.invH[1], sz = -Kc * e.invH[2];
+#pragma unroll
+        for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+            for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+                for (int qx = 0; qx < 2; ++qx) {
+                    const int qi = qx + 2 * (qy + 2 * qz);
+                    const double q0 = sx * gx[qy][qz], q1 = sy * gy[qx][qz], q2 = sz * gz[qx][qy];
+                    qs64[(0 * NQ + qi) * g.nc + c] = q0;
+                    qs64[(1 * NQ + qi) * g.nc + c] = q1;
+                    qs64[(2 * NQ + qi) * g.nc + c] = q2;
+                    qs32[(0 * NQ + qi) * g.nc + c] = (float)q0;
+                    qs32[(1 * NQ + qi) * g.nc + c] = (float)q1;
+                    qs32[(2 * NQ + qi) * g.nc + c] = (float)q2;
+                }
+    }
+}
+
 int launch_darcy_qp(ht_ctx* c, const double* h) {
     const Grid g = field_grid(c, HT_HEAD);
     const int threads = 128;
@@ -2548,7 +2607,7 @@ int launch_darcy_qp(ht_ctx* c, const double* h) {
     const long long cap = (long long)c->num_sms * 16;
     if (blocks > cap) blocks = cap;
     if (c->grid.P == 1)
-        darcy_qp_kernel<1><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, c->e64, c->qs64, c->qs32);
+        darcy_qp_q1_kernel<<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, c->e64, c->qs64, c->qs32);
     else
         darcy_qp_kernel<2><<<(int)blocks, threads, 0, c->stream>>>(g, h, c->K64, c->e64, c->qs64, c->qs32);
     ++c->n_launch;

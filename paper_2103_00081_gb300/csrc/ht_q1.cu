@@ -53,27 +53,17 @@
 namespace ht {
 namespace {
 
-constexpr int kTX = 28, kTY = 20;   // largest owned tile (node columns)
-constexpr int kBX = 32, kBY = 8;    // threads: lanes along x, warps along y
-constexpr int kRows = 3;            // rows of a thread: (kTY + 4) / kBY
+constexpr int kBX = 32, kBY = 8;    // threads of the heat kernel: lanes along x, warps along y
+constexpr int kRows = 3;            // rows of a thread of the heat kernel
 constexpr int kSX = 32, kSY = 24;   // shared plane: kRows * kBY rows of 32
-constexpr int kStages = 6;          // load ring (five planes in flight)
 
 struct Q1HeadConst {
     float A[8], B[8];   // lambda_l = A_l + (dt K_c) B_l, mode l = a + 2 b + 4 c
     float am3;          // alpha * diag(M_e)
     float dk3;          // dt * diag(K_e)
+    float2 A2[8], B2[8];   // the same, each value twice (operands of the packed FP32 form)
 };
 
-struct Q1Smem {
-    float ld_r[kStages][kSY][kSX];
-    float ld_p[kStages][kSY][kSX];
-    float ld_x[kStages][kSY][kSX];
-    float ld_k[kStages][kSY][kSX];
-    float pc[kSY][kSX];        // p_i at the plane of stage A
-    float sc[4][kSY][kSX];     // corner contributions of each face to s
-    float us[kSY][kSX];        // u_{i+1} at the plane of stage B
-};
 
 // grid-barrier state of the persistent batched CG (zeroed before each launch)
 struct Q1BatchSync {
@@ -106,9 +96,6 @@ __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc, bool v
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_ring() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 1) : "memory");
-}
 
 // h x h on the four corners u(a, b), corner index a + 2 b
 __device__ __forceinline__ void face_fwd(float u0, float u1, float u2, float u3, float (&F)[4]) {
@@ -139,236 +126,298 @@ enum : unsigned {
     F_DXY = 32u,       // node on a Dirichlet face of x or y
 };
 
-// One CTA's share of a CG iteration: the owned tile (bx, by) of node
-// columns and chunk bz of node planes, marched upward; returns the CTA's
-// partial sums of gamma, delta and rho in thread (0, 0).
-__device__ __forceinline__ void q1_cg_tile(const Grid& g, const float* __restrict__ K, float* __restrict__ x,
-                                           const float* __restrict__ r, const float* __restrict__ p,
-                                           float* __restrict__ r_out, float* __restrict__ p_out,
-                                           const Q1HeadConst& cst, const int bx, const int by, const int bz,
-                                           const int ntx, const int nty, const int nzc, const float alpha,
-                                           const float beta, const int first, Q1Smem& sm, double (&v)[3]) {
+// ---------------------------------------------------------------------------
+// CG tile: two consecutive node rows per thread, 16 warps, 32 x 32 slots
+// (owned tiles of up to 29 x 29 node columns).  A thread's rows R = 2 ty and
+// 2 ty + 1 are processed together in packed FP32 (the x and y halves of
+// each float2); the row above the pair and the row below it belong to the
+// neighbouring warps and cross through small per-warp rows in shared
+// memory; horizontal neighbours move by warp shuffles.
+// ---------------------------------------------------------------------------
+constexpr int kCgBY = 16;                       // warps (two rows each)
+constexpr int kCgThreads = 32 * kCgBY;
+constexpr int k4SX = 32, k4SY = 2 * kCgBY, k4St = 6;
+constexpr int k4TX = k4SX - 3, k4TY = k4SY - 3;   // largest owned tile (node columns)
+constexpr int k4BY = kCgBY;
+
+struct Q1Smem4 {
+    float ld_r[k4St][k4SY][k4SX];
+    float ld_p[k4St][k4SY][k4SX];
+    float ld_x[k4St][k4SY][k4SX];
+    float ld_k[k4St][k4SY][k4SX];
+    float pc0[k4BY][k4SX];   // p at the plane of stage A, first row of each warp
+    float us0[k4BY][k4SX];   // u at the plane of stage B, first row of each warp
+    float sc2[k4BY][k4SX];   // corner-2 / corner-3 contributions of each warp's last row
+    float sc3[k4BY][k4SX];
+};
+
+__device__ __forceinline__ void cp_async_wait_ring4() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(k4St - 1) : "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Packed FP32 helpers (two values per instruction: the x component is row
+// 2 ty, the y component row 2 ty + 1).  Masks multiply instead of selecting,
+// and the per-step energy of a row pair is added to delta once per plane.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b with one rounding
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+__device__ __forceinline__ void face_fwd2(float2 u0, float2 u1, float2 u2, float2 u3, float2 (&F)[4]) {
+    const float2 s0 = add2(u0, u1), d0 = sub2(u0, u1), s1 = add2(u2, u3), d1 = sub2(u2, u3);
+    F[0] = add2(s0, s1);
+    F[1] = add2(d0, d1);
+    F[2] = sub2(s0, s1);
+    F[3] = sub2(d0, d1);
+}
+__device__ __forceinline__ void face_bwd2(const float2 (&G)[4], float2 (&u)[4]) {
+    const float2 t0 = add2(G[0], G[2]), t1 = add2(G[1], G[3]), w0 = sub2(G[0], G[2]), w1 = sub2(G[1], G[3]);
+    u[0] = add2(t0, t1);
+    u[1] = sub2(t0, t1);
+    u[2] = add2(w0, w1);
+    u[3] = sub2(w0, w1);
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v) {
+    return f2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ void cp_async4n(float* sdst, const float* gsrc, int nbytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(nbytes) : "memory");
+}
+
+// One CTA's share of a CG iteration: node planes [k0, k1) of the owned tile
+// (bx, by) of node columns, marched upward; adds the share's gamma, delta and
+// rho to the thread's accumulators.
+template <bool FIRST>
+__device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restrict__ K, float* __restrict__ x,
+                                             const float* __restrict__ r, const float* __restrict__ p,
+                                             float* __restrict__ r_out, float* __restrict__ p_out,
+                                             const Q1HeadConst& cst, const int bx, const int by, const int ntx,
+                                             const int nty, const int k0, const int k1, const float alpha,
+                                             const float beta, Q1Smem4& sm, float2& gam, float2& del,
+                                             float2& rho) {
     const int tx = threadIdx.x, ty = threadIdx.y;
-    // owned tile and chunk (balanced splits)
     const int i0 = (int)((long long)bx * g.Nx / ntx), i1 = (int)((long long)(bx + 1) * g.Nx / ntx);
     const int j0 = (int)((long long)by * g.Ny / nty), j1 = (int)((long long)(by + 1) * g.Ny / nty);
-    const int k0 = (int)((long long)bz * g.Nz / nzc), k1 = (int)((long long)(bz + 1) * g.Nz / nzc);
     const int w = i1 - i0, h = j1 - j0;
+    __syncthreads();   // the previous share is done with the shared planes
     const int NXY = g.Nx * g.Ny, CXY = g.ncx * g.ncy;
     const int dm = g.dmask;
     const int mbeg = k0 - 2, mend = k1 + 1;
+    const int R0 = 2 * ty;
+    const int tyn = ty + 1 < k4BY ? ty + 1 : ty;
+    const int typ = ty > 0 ? ty - 1 : 0;
+    const int Rext = R0 + 2 < k4SY ? R0 + 2 : k4SY - 1;
 
-    // slot (R, C) = (ty + 8 b, tx) holds node (C - 1, R - 1) of the tile, the
-    // face (cell column) whose low corner that node is, and the cell column
-    // (C - 2, R - 2) of the K plane
-    unsigned fl[kRows];
-    int nxy[kRows], cxy[kRows];
-    float ncxy[kRows];
+    // per row: node and cell offsets in a plane (0 where outside: the copy
+    // size is then 0), load sizes and masks
+    int nofs[2], kofs[2], nsz[2], xsz[2], ksz[2];
+    bool own[2];
+    float lmv[2], amv[2], omv[2], fmv[2], emv[2];
 #pragma unroll
-    for (int b = 0; b < kRows; ++b) {
-        const int R = ty + kBY * b, C = tx;
+    for (int b = 0; b < 2; ++b) {
+        const int R = R0 + b, C = tx;
         const int gi = i0 + C - 1, gj = j0 + R - 1;
-        unsigned f = 0;
-        if (R >= 1 && R <= h && C >= 1 && C <= w) f |= F_OWN;
-        if (R >= 1 && R < h + 2 && C >= 1 && C < w + 2) f |= F_R1;
-        if (gi >= 0 && gi < g.Nx && gj >= 0 && gj < g.Ny) f |= F_NIN;
-        if (gi >= 0 && gi < g.ncx && gj >= 0 && gj < g.ncy) f |= F_FIN;
-        if (gi - 1 >= 0 && gi - 1 < g.ncx && gj - 1 >= 0 && gj - 1 < g.ncy) f |= F_KIN;
-        if (((dm & 1) && gi == 0) || ((dm & 2) && gi == g.Nx - 1) || ((dm & 4) && gj == 0) ||
-            ((dm & 8) && gj == g.Ny - 1))
-            f |= F_DXY;
-        fl[b] = f;
-        nxy[b] = (f & F_NIN) ? gi + g.Nx * gj : 0;
-        cxy[b] = (f & F_KIN) ? (gi - 1) + g.ncx * (gj - 1) : 0;
-        ncxy[b] = (float)(cells_along(gi, g.Nx) * cells_along(gj, g.Ny));
+        const bool o = R >= 1 && R <= h && C >= 1 && C <= w;
+        const bool nin = gi >= 0 && gi < g.Nx && gj >= 0 && gj < g.Ny;
+        const bool fin = gi >= 0 && gi < g.ncx && gj >= 0 && gj < g.ncy;
+        const bool kin = gi - 1 >= 0 && gi - 1 < g.ncx && gj - 1 >= 0 && gj - 1 < g.ncy;
+        const bool dxy = ((dm & 1) && gi == 0) || ((dm & 2) && gi == g.Nx - 1) || ((dm & 4) && gj == 0) ||
+                         ((dm & 8) && gj == g.Ny - 1);
+        own[b] = o;
+        nofs[b] = nin ? gi + g.Nx * gj : 0;
+        kofs[b] = kin ? (gi - 1) + g.ncx * (gj - 1) : 0;
+        nsz[b] = nin ? 4 : 0;
+        xsz[b] = nin && o ? 4 : 0;
+        ksz[b] = kin ? 4 : 0;
+        lmv[b] = nin && !dxy ? 1.0f : 0.0f;
+        amv[b] = nin ? cst.am3 * (float)(cells_along(gi, g.Nx) * cells_along(gj, g.Ny)) : 1.0f;
+        omv[b] = o ? 1.0f : 0.0f;
+        fmv[b] = fin ? 1.0f : 0.0f;
+        emv[b] = o && fin ? 1.0f : 0.0f;
     }
+    const float2 lm = f2(lmv[0], lmv[1]), amn = f2(amv[0], amv[1]), om = f2(omv[0], omv[1]);
+    const float2 fm = f2(fmv[0], fmv[1]), em = f2(emv[0], emv[1]);
+    const float2 alpha2 = f2(alpha, alpha), beta2 = f2(beta, beta), nalpha2 = f2(-alpha, -alpha);
+    const float2 dk2 = f2(cst.dk3, cst.dk3);
 
-    // loads of plane / cell layer q into ring slot (q - mbeg) % kStages; every
-    // slot of the 32 x 24 planes is written (zero where outside the mesh)
-    auto issue = [&](int q) {
+    auto issue = [&](int q, int st) {
         if (q <= mend) {
-            const int st = (q - mbeg) % kStages;
             const bool plane_ok = q >= 0 && q < g.Nz;
             const bool layer_ok = q >= 0 && q < g.ncz;
             const int pofs = plane_ok ? NXY * q : 0, cofs = layer_ok ? CXY * q : 0;
 #pragma unroll
-            for (int b = 0; b < kRows; ++b) {
-                const int R = ty + kBY * b, C = tx;
-                const bool nok = plane_ok && (fl[b] & F_NIN);
-                const int id = nok ? nxy[b] + pofs : 0;
-                cp_async4(&sm.ld_r[st][R][C], r + id, nok);
-                if (!first) cp_async4(&sm.ld_p[st][R][C], p + id, nok);
-                cp_async4(&sm.ld_x[st][R][C], x + id, nok && (fl[b] & F_OWN));
-                const bool kok = layer_ok && (fl[b] & F_KIN);
-                cp_async4(&sm.ld_k[st][R][C], K + (kok ? cxy[b] + cofs : 0), kok);
+            for (int b = 0; b < 2; ++b) {
+                const int R = R0 + b;
+                const int id = nofs[b] + pofs, kid = kofs[b] + cofs;
+                const int n1 = plane_ok ? nsz[b] : 0;
+                cp_async4n(&sm.ld_r[st][R][tx], r + id, n1);
+                if (!FIRST) cp_async4n(&sm.ld_p[st][R][tx], p + id, n1);
+                cp_async4n(&sm.ld_x[st][R][tx], x + id, plane_ok ? xsz[b] : 0);
+                cp_async4n(&sm.ld_k[st][R][tx], K + kid, layer_ok ? ksz[b] : 0);
             }
         }
         cp_async_commit();
     };
 
-    // per-row state carried up the march
-    float S_prev[kRows];                                 // sum of the node's 4 cell K, layer below
-    float hr[kRows], hp[kRows], hdi[kRows], hx[kRows];   // node values of the plane of stage B
-    float Fp[kRows][4], Tp[kRows][4], Gp[kRows][4];      // face transforms of p and u, top parts
-    float Kf1[kRows], Kf2[kRows], Kf3[kRows];            // the face's K one, two, three layers down
+    const float2 z2 = f2(0.0f, 0.0f);
+    float2 S_prev = z2, hr = z2, hp = z2, hdi = z2, hm = z2, hx = z2, us = z2;
+    float2 Fp[4], Tp[4], Gp[4];
+    float2 Kf1 = z2, Kf2 = z2, Kf3 = z2;
 #pragma unroll
-    for (int b = 0; b < kRows; ++b) {
-        S_prev[b] = 0.0f;
-        hr[b] = hp[b] = hdi[b] = hx[b] = 0.0f;
-        Kf1[b] = Kf2[b] = Kf3[b] = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Fp[b][q] = Tp[b][q] = Gp[b][q] = 0.0f;
-    }
-    float gam = 0.0f, rho = 0.0f, del = 0.0f;
+    for (int q = 0; q < 4; ++q) Fp[q] = Tp[q] = Gp[q] = z2;
 
-    for (int q = mbeg; q < mbeg + kStages - 1; ++q) issue(q);
-    // Step m: stage A forms u_i, p_i at plane m; the face stage applies cell
-    // layer m-1 to p (completing s at plane m-1) and adds the energies of
-    // layer m-3 from u at planes m-3 and m-2; stage B forms r_{i+1}, u_{i+1}
-    // at plane m-1 and writes the owned outputs.
-    for (int m = mbeg; m <= mend; ++m) {
-        issue(m + kStages - 1);
-        cp_async_wait_ring();
-        __syncthreads();
-        const int st = (m - mbeg) % kStages;
-        const bool stageA = m >= k0 - 1;
-        const bool plane_ok = m >= 0 && m < g.Nz;
-        const bool dirz = ((dm & 16) && m == 0) || ((dm & 32) && m == g.Nz - 1);
-        const float nz_cells = (float)cells_along(m, g.Nz);
-        // ---- stage A
-        float ar[kRows], ap[kRows], adi[kRows], ax[kRows], Kc[kRows];
-#pragma unroll
-        for (int b = 0; b < kRows; ++b) {
-            const int R = ty + kBY * b, C = tx;
-            const int R1 = R + 1 < kSY ? R + 1 : R, C1 = C + 1 < kSX ? C + 1 : C;
-            const float Sc = (sm.ld_k[st][R][C] + sm.ld_k[st][R][C1]) + (sm.ld_k[st][R1][C] + sm.ld_k[st][R1][C1]);
-            Kc[b] = sm.ld_k[st][R1][C1];
-            const bool live = plane_ok && (fl[b] & F_NIN) && !(fl[b] & F_DXY) && !dirz;
-            const float di = live ? __frcp_rn(fmaf(cst.dk3, S_prev[b] + Sc, cst.am3 * ncxy[b] * nz_cells)) : 0.0f;
-            const float rv = sm.ld_r[st][R][C];
-            const float pv = first ? 0.0f : sm.ld_p[st][R][C];
-            const float pn = fmaf(beta, pv, di * rv);
-            sm.pc[R][C] = pn;
-            ar[b] = rv;
-            ap[b] = pn;
-            adi[b] = di;
-            ax[b] = sm.ld_x[st][R][C];
-            S_prev[b] = Sc;
-        }
-        __syncthreads();
-        // ---- face stage
-        const bool apply_on = m >= k0;
-        const bool lay_ok = m - 1 >= 0 && m - 1 < g.ncz;
-        const int lc = m - 3;                 // layer of the energies
-        const bool energy_on = lc >= k0 && lc < k1 && lc < g.ncz;
-#pragma unroll
-        for (int b = 0; b < kRows; ++b) {
-            const int R = ty + kBY * b, C = tx;
-            const int R1 = R + 1 < kSY ? R + 1 : R, C1 = C + 1 < kSX ? C + 1 : C;
-            const bool cell = apply_on && lay_ok && (fl[b] & F_FIN);
-            float F[4];
-            face_fwd(sm.pc[R][C], sm.pc[R][C1], sm.pc[R1][C], sm.pc[R1][C1], F);
-            float G[4], u[4], top[4];
-            const float bk = Kf1[b];
+    // energies of cell layer lc of the owned faces: u at planes lc (its
+    // transforms in Gp) and lc + 1 (us, the row above from us0)
+    auto energies = [&](bool add, float2 Kl) {
+        const float ue = sm.us0[tyn][tx];
+        const float2 ur = shfl_down2(us);
+        const float uer = __shfl_down_sync(0xffffffffu, ue, 1);
+        float2 Gu[4];
+        face_fwd2(us, ur, f2(us.y, ue), f2(ur.y, uer), Gu);
+        if (add) {
+            float2 e = z2;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float lo = (Fp[b][q] + F[q]) * fmaf(bk, cst.B[q], cst.A[q]);
-                const float hi = (Fp[b][q] - F[q]) * fmaf(bk, cst.B[q + 4], cst.A[q + 4]);
-                G[q] = cell ? Tp[b][q] + (lo + hi) : Tp[b][q];
-                top[q] = cell ? lo - hi : 0.0f;
+                const float2 lo = add2(Gp[q], Gu[q]), hi = sub2(Gp[q], Gu[q]);
+                e = fma2(mul2(fma2(Kl, cst.B2[q], cst.A2[q]), lo), lo, e);
+                e = fma2(mul2(fma2(Kl, cst.B2[q + 4], cst.A2[q + 4]), hi), hi, e);
             }
-            face_bwd(G, u);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                sm.sc[q][R][C] = u[q];
-                if (stageA) {
-                    Tp[b][q] = top[q];
-                    Fp[b][q] = F[q];
-                }
-            }
-            // energies of layer m-3: u at plane m-2 is still in us (stage B of
-            // the previous step), its transform at plane m-3 in Gp
-            if (m - 2 >= k0 && m - 2 <= k1 && m - 2 < g.Nz) {
-                float Gu[4];
-                face_fwd(sm.us[R][C], sm.us[R][C1], sm.us[R1][C], sm.us[R1][C1], Gu);
-                if (energy_on && (fl[b] & F_OWN) && (fl[b] & F_FIN)) {
-                    const float ek = Kf3[b];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float lo = Gp[b][q] + Gu[q], hi = Gp[b][q] - Gu[q];
-                        del = fmaf(fmaf(ek, cst.B[q], cst.A[q]) * lo, lo, del);
-                        del = fmaf(fmaf(ek, cst.B[q + 4], cst.A[q + 4]) * hi, hi, del);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) Gp[b][q] = Gu[q];
-            }
+            del = fma2(e, em, del);
         }
-        __syncthreads();
-        // ---- stage B
-        const int kb = m - 1;
-        const bool stageB = kb >= k0 && kb <= k1 && kb < g.Nz;
-        const bool owned_plane = kb < k1;
-        if (stageB) {
 #pragma unroll
-            for (int b = 0; b < kRows; ++b) {
-                const int R = ty + kBY * b, C = tx;
-                const int Rm = R > 0 ? R - 1 : 0, Cm = C > 0 ? C - 1 : 0;
-                const float sv = (sm.sc[0][R][C] + sm.sc[1][R][Cm]) + (sm.sc[2][Rm][C] + sm.sc[3][Rm][Cm]);
-                const float rn = hdi[b] != 0.0f ? fmaf(-alpha, sv, hr[b]) : hr[b];
-                const float un = hdi[b] * rn;
-                sm.us[R][C] = un;
-                if (owned_plane && (fl[b] & F_OWN)) {
-                    const int id = nxy[b] + NXY * kb;
-                    x[id] = fmaf(alpha, hp[b], hx[b]);
-                    r_out[id] = rn;
-                    p_out[id] = hp[b];
-                    gam = fmaf(rn, un, gam);
-                    rho = fmaf(rn, rn, rho);
-                }
-            }
-        }
-        // histories move up one plane
-#pragma unroll
-        for (int b = 0; b < kRows; ++b) {
-            if (stageA) {
-                hr[b] = ar[b];
-                hp[b] = ap[b];
-                hdi[b] = adi[b];
-                hx[b] = ax[b];
-            }
-            Kf3[b] = Kf2[b];
-            Kf2[b] = Kf1[b];
-            Kf1[b] = Kc[b];
-        }
+        for (int q = 0; q < 4; ++q) Gp[q] = Gu[q];
+    };
+
+    int st_issue = 0;
+    for (int q = mbeg; q < mbeg + k4St - 1; ++q) {
+        issue(q, st_issue);
+        st_issue = st_issue + 1 == k4St ? 0 : st_issue + 1;
     }
-    // the march ends with stage B at plane k1; the energies of layer k1 - 1
-    // need u at planes k1 - 1 and k1, both in hand after the last step
+    int st = 0;
+    for (int m = mbeg; m <= mend; ++m) {
+        issue(m + k4St - 1, st_issue);
+        st_issue = st_issue + 1 == k4St ? 0 : st_issue + 1;
+        cp_async_wait_ring4();
+        __syncthreads();
+        const bool stageA = m >= k0 - 1;
+        const bool plane_live = m >= 0 && m < g.Nz && !(((dm & 16) && m == 0) || ((dm & 32) && m == g.Nz - 1));
+        // ---- stage A: u_i and p_i at plane m
+        const float kk0 = sm.ld_k[st][R0][tx], kk1 = sm.ld_k[st][R0 + 1][tx], kk2 = sm.ld_k[st][Rext][tx];
+        const float kd0 = __shfl_down_sync(0xffffffffu, kk0, 1);
+        const float kd1 = __shfl_down_sync(0xffffffffu, kk1, 1);
+        const float kd2 = __shfl_down_sync(0xffffffffu, kk2, 1);
+        const float2 kA = add2(f2(kk0, kk1), f2(kd0, kd1));
+        const float2 Sc = add2(kA, f2(kA.y, kk2 + kd2));
+        const float2 Kc = f2(kd1, kd2);
+        float2 di = z2, mk = z2;
+        if (plane_live) {
+            const float nzc = (float)cells_along(m, g.Nz);
+            const float2 den = fma2(dk2, add2(S_prev, Sc), mul2(amn, f2(nzc, nzc)));
+            di = mul2(lm, f2(rcp_approx(den.x), rcp_approx(den.y)));
+            mk = lm;
+        }
+        const float2 rv = f2(sm.ld_r[st][R0][tx], sm.ld_r[st][R0 + 1][tx]);
+        const float2 u = mul2(di, rv);
+        const float2 pn = FIRST ? u : fma2(beta2, f2(sm.ld_p[st][R0][tx], sm.ld_p[st][R0 + 1][tx]), u);
+        const float2 ax = f2(sm.ld_x[st][R0][tx], sm.ld_x[st][R0 + 1][tx]);
+        S_prev = Sc;
+        sm.pc0[ty][tx] = pn.x;
+        __syncthreads();
+        // ---- face stage: cell layer m-1 applied to p
+        float2 u4[4];
+        {
+            const float pe = sm.pc0[tyn][tx];
+            const float2 pr = shfl_down2(pn);
+            const float per = __shfl_down_sync(0xffffffffu, pe, 1);
+            float2 F[4], G[4];
+            face_fwd2(pn, pr, f2(pn.y, pe), f2(pr.y, per), F);
+            if (m >= k0 && m - 1 >= 0 && m - 1 < g.ncz) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 lo = mul2(add2(Fp[q], F[q]), fma2(Kf1, cst.B2[q], cst.A2[q]));
+                    const float2 hi = mul2(sub2(Fp[q], F[q]), fma2(Kf1, cst.B2[q + 4], cst.A2[q + 4]));
+                    G[q] = fma2(add2(lo, hi), fm, Tp[q]);
+                    if (stageA) Tp[q] = mul2(sub2(lo, hi), fm);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    G[q] = Tp[q];
+                    if (stageA) Tp[q] = z2;
+                }
+            }
+            face_bwd2(G, u4);
+            if (stageA) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Fp[q] = F[q];
+            }
+        }
+        // energies of layer m-3 (u at plane m-2 from the previous stage B)
+        if (m - 2 >= k0 && m - 2 <= k1 && m - 2 < g.Nz) {
+            const int lc = m - 3;
+            energies(lc >= k0 && lc < k1 && lc < g.ncz, Kf3);
+        }
+        sm.sc2[ty][tx] = u4[2].y;
+        sm.sc3[ty][tx] = u4[3].y;
+        __syncthreads();
+        // ---- stage B: r_{i+1}, u_{i+1} at plane m-1; owned outputs
+        const int kb = m - 1;
+        if (kb >= k0 && kb <= k1 && kb < g.Nz) {
+            const float2 d2 = f2(sm.sc2[typ][tx], u4[2].x);
+            const float2 d3 = f2(sm.sc3[typ][tx], u4[3].x);
+            const float2 t = add2(u4[1], d3);
+            const float2 sh = f2(__shfl_up_sync(0xffffffffu, t.x, 1), __shfl_up_sync(0xffffffffu, t.y, 1));
+            const float2 sv = add2(add2(u4[0], d2), sh);
+            const float2 rn = fma2(mul2(nalpha2, hm), sv, hr);
+            const float2 un = mul2(hdi, rn);
+            us = un;
+            if (kb < k1) {
+                const float2 ro = mul2(rn, om);
+                gam = fma2(ro, un, gam);
+                rho = fma2(ro, rn, rho);
+                const float2 xn = fma2(alpha2, hp, hx);
+                if (own[0]) {
+                    const int id = nofs[0] + NXY * kb;
+                    x[id] = xn.x;
+                    r_out[id] = rn.x;
+                    p_out[id] = hp.x;
+                }
+                if (own[1]) {
+                    const int id = nofs[1] + NXY * kb;
+                    x[id] = xn.y;
+                    r_out[id] = rn.y;
+                    p_out[id] = hp.y;
+                }
+            }
+            sm.us0[ty][tx] = us.x;
+        }
+        if (stageA) {
+            hr = rv;
+            hp = pn;
+            hdi = di;
+            hm = mk;
+            hx = ax;
+        }
+        Kf3 = Kf2;
+        Kf2 = Kf1;
+        Kf1 = Kc;
+        st = st + 1 == k4St ? 0 : st + 1;
+    }
     {
         const int lc = k1 - 1;
-        if (lc >= k0 && lc < g.ncz) {
-            __syncthreads();
-#pragma unroll
-            for (int b = 0; b < kRows; ++b) {
-                const int R = ty + kBY * b, C = tx;
-                const int R1 = R + 1 < kSY ? R + 1 : R, C1 = C + 1 < kSX ? C + 1 : C;
-                float Gu[4];
-                face_fwd(sm.us[R][C], sm.us[R][C1], sm.us[R1][C], sm.us[R1][C1], Gu);
-                if ((fl[b] & F_OWN) && (fl[b] & F_FIN)) {
-                    const float ek = Kf3[b];   // K of layer k1 - 1 after the last shift
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float lo = Gp[b][q] + Gu[q], hi = Gp[b][q] - Gu[q];
-                        del = fmaf(fmaf(ek, cst.B[q], cst.A[q]) * lo, lo, del);
-                        del = fmaf(fmaf(ek, cst.B[q + 4], cst.A[q + 4]) * hi, hi, del);
-                    }
-                }
-            }
-        }
+        __syncthreads();
+        if (lc >= k0 && lc < g.ncz) energies(true, Kf3);
     }
-    v[0] = block_sum_t(gam);
-    v[1] = block_sum_t(del);
-    v[2] = block_sum_t(rho);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // the scalars of the next iteration from the reduced gamma, delta and rho
@@ -399,27 +448,46 @@ __device__ __forceinline__ void q1_cg_scalars(Scal* s, double gt, double dt_, do
     s->rz = gt;
 }
 
-__global__ void __launch_bounds__(kBX * kBY, 2)
+// One CG iteration over the whole mesh.  The tile columns, each Nz node
+// planes long, are laid end to end; CTA b takes planes [b T / G, (b + 1) T / G)
+// of that sequence (T = tiles x Nz, G CTAs): z segments of one or more tile
+// columns, so every CTA has the same number of planes to march whatever the
+// mesh.  The last CTA to finish reduces the partial sums.
+template <bool FIRST>
+__global__ void __launch_bounds__(kCgThreads, 1)
 q1_cg_kernel(const Grid g, const float* __restrict__ K, float* __restrict__ x, const float* __restrict__ r,
              const float* __restrict__ p, float* __restrict__ r_out, float* __restrict__ p_out,
-             const Q1HeadConst cst, const int ntx, const int nty, const int nzc, Scal* __restrict__ s,
-             double* __restrict__ part, const int stride, const int first) {
+             const Q1HeadConst cst, const int ntx, const int nty, Scal* __restrict__ s, double* __restrict__ part,
+             const int stride) {
     if (s->done) return;
     extern __shared__ __align__(16) unsigned char q1_smem_raw[];
-    Q1Smem& sm = *reinterpret_cast<Q1Smem*>(q1_smem_raw);
-    const float alpha = first ? 0.0f : (float)s->alpha;
-    const float beta = first ? 0.0f : (float)s->beta;
+    Q1Smem4& sm = *reinterpret_cast<Q1Smem4*>(q1_smem_raw);
+    const float alpha = FIRST ? 0.0f : (float)s->alpha;
+    const float beta = FIRST ? 0.0f : (float)s->beta;
+    const long long T = (long long)ntx * nty * g.Nz;
+    const long long f0 = T * blockIdx.x / gridDim.x, f1 = T * (blockIdx.x + 1) / gridDim.x;
+    float2 gam = f2(0.0f, 0.0f), del = gam, rho = gam;
+    for (long long f = f0; f < f1;) {
+        const long long tile = f / g.Nz;
+        const int k0 = (int)(f - tile * g.Nz);
+        const long long rest = f1 - f;
+        const int k1 = rest < (long long)(g.Nz - k0) ? k0 + (int)rest : g.Nz;
+        q1_cg_tile2p<FIRST>(g, K, x, r, p, r_out, p_out, cst, (int)(tile % ntx), (int)(tile / ntx), ntx, nty, k0,
+                            k1, alpha, beta, sm, gam, del, rho);
+        f += k1 - k0;
+    }
     double v[3];
-    q1_cg_tile(g, K, x, r, p, r_out, p_out, cst, blockIdx.x, blockIdx.y, blockIdx.z, ntx, nty, nzc, alpha, beta,
-               first, sm, v);
-    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    v[0] = block_sum_t(gam.x + gam.y);
+    v[1] = block_sum_t(del.x + del.y);
+    v[2] = block_sum_t(rho.x + rho.y);
+    const unsigned nblk = gridDim.x;
     if (!publish_and_ticket(s, part, v, 3, stride, nblk)) return;
     const double gt = last_cta_sum(part, (int)nblk);
     const double dt_ = last_cta_sum(part + stride, (int)nblk);
     const double rt = last_cta_sum(part + 2 * (size_t)stride, (int)nblk);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         s->ticket = 0;
-        q1_cg_scalars(s, gt, dt_, rt, first);
+        q1_cg_scalars(s, gt, dt_, rt, FIRST);
     }
 }
 
@@ -476,12 +544,12 @@ __device__ __forceinline__ bool batch_barrier(Q1BatchSync* sync, unsigned nblk, 
     return ok_s != 0;
 }
 
-__global__ void __launch_bounds__(kBX * kBY, 2)
+__global__ void __launch_bounds__(kCgThreads, 1)
 q1_cg_batch_kernel(const Q1BatchProb* __restrict__ probs, const int nprob, const int* __restrict__ item_prob,
                    const int nitems, const int iters, const long long budget, Q1BatchSync* __restrict__ sync,
                    const int drop_cta) {
     extern __shared__ __align__(16) unsigned char q1b_smem_raw[];
-    Q1Smem& sm = *reinterpret_cast<Q1Smem*>(q1b_smem_raw);
+    Q1Smem4& sm = *reinterpret_cast<Q1Smem4*>(q1b_smem_raw);
     __shared__ Q1BatchProb P;
     __shared__ int skip_s, par_s;
     __shared__ float alpha_s, beta_s;
@@ -507,10 +575,18 @@ q1_cg_batch_kernel(const Q1BatchProb* __restrict__ probs, const int nprob, const
             const int local = item - P.item0;
             const int bx = local % P.ntx, by = (local / P.ntx) % P.nty, bz = local / (P.ntx * P.nty);
             const int a = par_s;
+            const int k0 = (int)((long long)bz * P.g.Nz / P.nzc), k1 = (int)((long long)(bz + 1) * P.g.Nz / P.nzc);
+            float2 gam = f2(0.0f, 0.0f), del = gam, rho = gam;
+            if (first)
+                q1_cg_tile2p<true>(P.g, P.K, P.x, P.r[a], P.p[a], P.r[a ^ 1], P.p[a ^ 1], P.cst, bx, by, P.ntx,
+                                   P.nty, k0, k1, alpha_s, beta_s, sm, gam, del, rho);
+            else
+                q1_cg_tile2p<false>(P.g, P.K, P.x, P.r[a], P.p[a], P.r[a ^ 1], P.p[a ^ 1], P.cst, bx, by, P.ntx,
+                                    P.nty, k0, k1, alpha_s, beta_s, sm, gam, del, rho);
             double v[3];
-            q1_cg_tile(P.g, P.K, P.x, P.r[a], P.p[a], P.r[a ^ 1], P.p[a ^ 1], P.cst, bx, by, bz, P.ntx, P.nty,
-                       P.nzc, alpha_s, beta_s, first, sm, v);
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            v[0] = block_sum_t(gam.x + gam.y);
+            v[1] = block_sum_t(del.x + del.y);
+            v[2] = block_sum_t(rho.x + rho.y);
             if (lead) {
                 P.part[local] = v[0];
                 P.part[(size_t)P.stride + local] = v[1];
@@ -565,6 +641,8 @@ Q1HeadConst q1_head_const(const double H[3], double alpha, double dt) {
                                   m1[0][ax] * m1[1][by] * k1[2][cz];
                 c.A[l] = (float)(alpha * M / 64.0);
                 c.B[l] = (float)(dt * Kl / 64.0);
+                c.A2[l] = make_float2(c.A[l], c.A[l]);
+                c.B2[l] = make_float2(c.B[l], c.B[l]);
             }
     const double dM = H[0] * H[1] * H[2] / 27.0;
     const double dK = H[1] * H[2] / (9.0 * H[0]) + H[0] * H[2] / (9.0 * H[1]) + H[0] * H[1] / (9.0 * H[2]);
@@ -1002,12 +1080,12 @@ int q1_batch_prepare(Q1Batch& q, ht_ctx* const* probs, int n, double dt, int pla
         return code;
     };
     int dev = 0, sms = 0, resident = 0;
-    const size_t smem = sizeof(Q1Smem);
+    const size_t smem = sizeof(Q1Smem4);
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(q1_cg_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, q1_cg_batch_kernel, kBX * kBY, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, q1_cg_batch_kernel, kCgThreads, smem) != cudaSuccess ||
         resident < 1)
         return bad(HT_ECUDA, "persistent batch kernel: occupancy query failed");
     const int slots = resident * sms;
@@ -1018,8 +1096,8 @@ int q1_batch_prepare(Q1Batch& q, ht_ctx* const* probs, int n, double dt, int pla
     for (int i = 0; i < n; ++i) {
         const ht_ctx* c = probs[i];
         if (!q1_cg_available(c, 1)) return bad(HT_EINVAL, "persistent batch needs Q1 problems with the single-pass kernels");
-        ntx[i] = (c->grid.Nx + kTX - 1) / kTX;
-        nty[i] = (c->grid.Ny + kTY - 1) / kTY;
+        ntx[i] = (c->grid.Nx + k4TX - 1) / k4TX;
+        nty[i] = (c->grid.Ny + k4TY - 1) / k4TY;
         Nz[i] = c->grid.Nz;
     }
     auto count_items = [&](int L, std::vector<int>* nzc) {
@@ -1122,8 +1200,8 @@ int q1_batch_run(Q1Batch& q, cudaStream_t st, int max_iter, long long budget, in
                     (void*)&bud, (void*)&sync, (void*)&drop};
     // cooperative: every CTA of the grid is resident at once, which the
     // grid barrier needs
-    if (cudaLaunchCooperativeKernel((const void*)q1_cg_batch_kernel, dim3(q.grid), dim3(kBX, kBY), args,
-                                    sizeof(Q1Smem), st) != cudaSuccess)
+    if (cudaLaunchCooperativeKernel((const void*)q1_cg_batch_kernel, dim3(q.grid), dim3(32, kCgBY), args,
+                                    sizeof(Q1Smem4), st) != cudaSuccess)
         return bad(HT_ECUDA, "persistent batch: cooperative launch failed");
     if (cudaMemcpyAsync(q.h_sync, q.d_sync, sizeof(Q1BatchSync), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -1155,22 +1233,33 @@ int q1_cg_iteration32(ht_ctx* c, float dt, float* x, const float* r, const float
     Grid g = c->grid;
     g.dmask = c->dmask[HT_HEAD];
     const Q1HeadConst cst = q1_head_const(c->H, c->Ss, (double)dt);
-    const int ntx = (g.Nx + kTX - 1) / kTX, nty = (g.Ny + kTY - 1) / kTY;
+    const int ntx = (g.Nx + k4TX - 1) / k4TX, nty = (g.Ny + k4TY - 1) / k4TY;
     static int resident = 0;
-    const size_t smem = sizeof(Q1Smem);
+    const size_t smem = sizeof(Q1Smem4);
     if (resident == 0) {
-        HT_CUDA(c, cudaFuncSetAttribute(q1_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HT_CUDA(c, cudaFuncSetAttribute(q1_cg_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HT_CUDA(c, cudaFuncSetAttribute(q1_cg_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, q1_cg_kernel, kBX * kBY, smem) != cudaSuccess || v < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, q1_cg_kernel<false>, kCgThreads, smem) != cudaSuccess ||
+            v < 1)
             v = 1;
         resident = v;
     }
     const int sms = c->num_sms > 0 ? c->num_sms : 148;
-    int nzc = c->opts.z_chunks > 0 ? std::min(c->opts.z_chunks, g.Nz) : q1_split_z(g.Nz, ntx * nty, resident * sms);
-    while (nzc > 1 && ntx * nty * nzc > c->part_stride) --nzc;
-    if (ntx * nty * nzc > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
-    q1_cg_kernel<<<dim3(ntx, nty, nzc), dim3(kBX, kBY), smem, c->stream>>>(
-        g, c->K32, x, r, p, r_out, p_out, cst, ntx, nty, nzc, sc, c->part, c->part_stride, first);
+    // one CTA per co-resident slot, at least 8 node planes each (each z
+    // segment repeats 3 planes of pipeline start-up); z_chunks > 0 asks for
+    // about that many segments per tile column instead
+    const long long T = (long long)ntx * nty * g.Nz;
+    long long G = c->opts.z_chunks > 0 ? (long long)ntx * nty * std::min(c->opts.z_chunks, g.Nz)
+                                       : std::min<long long>((long long)resident * sms, (T + 7) / 8);
+    G = std::max(1LL, std::min({G, T, (long long)c->part_stride}));
+    const dim3 grid((unsigned)G), block(32, kCgBY);
+    if (first)
+        q1_cg_kernel<true><<<grid, block, smem, c->stream>>>(g, c->K32, x, r, p, r_out, p_out, cst, ntx, nty, sc,
+                                                             c->part, c->part_stride);
+    else
+        q1_cg_kernel<false><<<grid, block, smem, c->stream>>>(g, c->K32, x, r, p, r_out, p_out, cst, ntx, nty, sc,
+                                                              c->part, c->part_stride);
     ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
