@@ -46,6 +46,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "ht_device.cuh"
 #include "ht_internal.cuh"
@@ -297,19 +298,50 @@ __device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restr
         for (int q = 0; q < 4; ++q) Gp[q] = Gu[q];
     };
 
+    // stores of the owned outputs, predicated per row (no divergent branch)
+    auto store_row = [&](bool on, int id, float xv, float rv, float pv) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+            "@p st.global.f32 [%1], %4;\n\t@p st.global.f32 [%2], %5;\n\t@p st.global.f32 [%3], %6;\n\t}"
+            ::"r"((int)on), "l"(x + id), "l"(r_out + id), "l"(p_out + id), "f"(xv), "f"(rv), "f"(pv)
+            : "memory");
+    };
+
     int st_issue = 0;
     for (int q = mbeg; q < mbeg + k4St - 1; ++q) {
         issue(q, st_issue);
         st_issue = st_issue + 1 == k4St ? 0 : st_issue + 1;
     }
     int st = 0;
-    for (int m = mbeg; m <= mend; ++m) {
-        issue(m + k4St - 1, st_issue);
+    // Step m: stage A forms u_i, p_i at plane m; the face stage applies cell
+    // layer m-1 to p (completing s at plane m-1) and adds the energies of
+    // layer m-3 from u at planes m-3 and m-2; stage B forms r_{i+1}, u_{i+1}
+    // at plane m-1 and writes the owned outputs.  In the steady part of the
+    // march (STEADY) every stage is active, the planes are interior and the
+    // loads are in range, so none of these conditions is evaluated.
+    auto step = [&](const int m, auto steady_tag) {
+        constexpr bool STEADY = decltype(steady_tag)::value;
+        if (STEADY) {
+            const int q = m + k4St - 1, pofs = NXY * q, cofs = CXY * q;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int R = R0 + b;
+                const int id = nofs[b] + pofs, kid = kofs[b] + cofs;
+                cp_async4n(&sm.ld_r[st_issue][R][tx], r + id, nsz[b]);
+                if (!FIRST) cp_async4n(&sm.ld_p[st_issue][R][tx], p + id, nsz[b]);
+                cp_async4n(&sm.ld_x[st_issue][R][tx], x + id, xsz[b]);
+                cp_async4n(&sm.ld_k[st_issue][R][tx], K + kid, ksz[b]);
+            }
+            cp_async_commit();
+        } else {
+            issue(m + k4St - 1, st_issue);
+        }
         st_issue = st_issue + 1 == k4St ? 0 : st_issue + 1;
         cp_async_wait_ring4();
         __syncthreads();
-        const bool stageA = m >= k0 - 1;
-        const bool plane_live = m >= 0 && m < g.Nz && !(((dm & 16) && m == 0) || ((dm & 32) && m == g.Nz - 1));
+        const bool stageA = STEADY || m >= k0 - 1;
+        const bool plane_live =
+            STEADY || (m >= 0 && m < g.Nz && !(((dm & 16) && m == 0) || ((dm & 32) && m == g.Nz - 1)));
         // ---- stage A: u_i and p_i at plane m
         const float kk0 = sm.ld_k[st][R0][tx], kk1 = sm.ld_k[st][R0 + 1][tx], kk2 = sm.ld_k[st][Rext][tx];
         const float kd0 = __shfl_down_sync(0xffffffffu, kk0, 1);
@@ -320,7 +352,7 @@ __device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restr
         const float2 Kc = f2(kd1, kd2);
         float2 di = z2, mk = z2;
         if (plane_live) {
-            const float nzc = (float)cells_along(m, g.Nz);
+            const float nzc = STEADY ? 2.0f : (float)cells_along(m, g.Nz);
             const float2 den = fma2(dk2, add2(S_prev, Sc), mul2(amn, f2(nzc, nzc)));
             di = mul2(lm, f2(rcp_approx(den.x), rcp_approx(den.y)));
             mk = lm;
@@ -340,7 +372,7 @@ __device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restr
             const float per = __shfl_down_sync(0xffffffffu, pe, 1);
             float2 F[4], G[4];
             face_fwd2(pn, pr, f2(pn.y, pe), f2(pr.y, per), F);
-            if (m >= k0 && m - 1 >= 0 && m - 1 < g.ncz) {
+            if (STEADY || (m >= k0 && m - 1 >= 0 && m - 1 < g.ncz)) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float2 lo = mul2(add2(Fp[q], F[q]), fma2(Kf1, cst.B2[q], cst.A2[q]));
@@ -362,7 +394,9 @@ __device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restr
             }
         }
         // energies of layer m-3 (u at plane m-2 from the previous stage B)
-        if (m - 2 >= k0 && m - 2 <= k1 && m - 2 < g.Nz) {
+        if (STEADY) {
+            energies(true, Kf3);
+        } else if (m - 2 >= k0 && m - 2 <= k1 && m - 2 < g.Nz) {
             const int lc = m - 3;
             energies(lc >= k0 && lc < k1 && lc < g.ncz, Kf3);
         }
@@ -371,7 +405,7 @@ __device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restr
         __syncthreads();
         // ---- stage B: r_{i+1}, u_{i+1} at plane m-1; owned outputs
         const int kb = m - 1;
-        if (kb >= k0 && kb <= k1 && kb < g.Nz) {
+        if (STEADY || (kb >= k0 && kb <= k1 && kb < g.Nz)) {
             const float2 d2 = f2(sm.sc2[typ][tx], u4[2].x);
             const float2 d3 = f2(sm.sc3[typ][tx], u4[3].x);
             const float2 t = add2(u4[1], d3);
@@ -380,23 +414,14 @@ __device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restr
             const float2 rn = fma2(mul2(nalpha2, hm), sv, hr);
             const float2 un = mul2(hdi, rn);
             us = un;
-            if (kb < k1) {
+            if (STEADY || kb < k1) {
                 const float2 ro = mul2(rn, om);
                 gam = fma2(ro, un, gam);
                 rho = fma2(ro, rn, rho);
                 const float2 xn = fma2(alpha2, hp, hx);
-                if (own[0]) {
-                    const int id = nofs[0] + NXY * kb;
-                    x[id] = xn.x;
-                    r_out[id] = rn.x;
-                    p_out[id] = hp.x;
-                }
-                if (own[1]) {
-                    const int id = nofs[1] + NXY * kb;
-                    x[id] = xn.y;
-                    r_out[id] = rn.y;
-                    p_out[id] = hp.y;
-                }
+                const int ofs = NXY * kb;
+                store_row(own[0], nofs[0] + ofs, xn.x, rn.x, hp.x);
+                store_row(own[1], nofs[1] + ofs, xn.y, rn.y, hp.y);
             }
             sm.us0[ty][tx] = us.x;
         }
@@ -411,7 +436,14 @@ __device__ __forceinline__ void q1_cg_tile2p(const Grid& g, const float* __restr
         Kf2 = Kf1;
         Kf1 = Kc;
         st = st + 1 == k4St ? 0 : st + 1;
-    }
+    };
+    // steady steps: every stage active (m - 3 >= k0, m - 1 < k1), interior
+    // planes, and the issued plane m + 5 inside both the mesh and the march
+    const int ms0 = max(k0 + 3, mbeg), ms1 = min(k1 - 4, g.Nz - 7);
+    int m = mbeg;
+    for (; m < ms0 && m <= mend; ++m) step(m, std::false_type{});
+    for (; m <= ms1; ++m) step(m, std::true_type{});
+    for (; m <= mend; ++m) step(m, std::false_type{});
     {
         const int lc = k1 - 1;
         __syncthreads();
