@@ -480,11 +480,15 @@ __device__ __forceinline__ void q1_cg_scalars(Scal* s, double gt, double dt_, do
     s->rz = gt;
 }
 
-// One CG iteration over the whole mesh.  The tile columns, each Nz node
-// planes long, are laid end to end; CTA b takes planes [b T / G, (b + 1) T / G)
-// of that sequence (T = tiles x Nz, G CTAs): z segments of one or more tile
-// columns, so every CTA has the same number of planes to march whatever the
-// mesh.  The last CTA to finish reduces the partial sums.
+// One CG iteration over the whole mesh.  The CTAs form groups of ntx, one
+// CTA per tile column of a tile row (bx = CTA % ntx), and the members of a
+// group march the same node planes of the same tile row side by side, so
+// that x-neighbouring tiles read their shared halos and write the sectors
+// they share at about the same time (both stay in L2).  The tile rows, each
+// Nz planes long, are laid end to end and group q takes planes
+// [q R / Q, (q + 1) R / Q) of that sequence (R = nty x Nz, Q groups): every
+// CTA has the same number of planes to march whatever the mesh.  The last
+// CTA to finish reduces the partial sums.
 template <bool FIRST>
 __global__ void __launch_bounds__(kCgThreads, 1)
 q1_cg_kernel(const Grid g, const float* __restrict__ K, float* __restrict__ x, const float* __restrict__ r,
@@ -496,16 +500,18 @@ q1_cg_kernel(const Grid g, const float* __restrict__ K, float* __restrict__ x, c
     Q1Smem4& sm = *reinterpret_cast<Q1Smem4*>(q1_smem_raw);
     const float alpha = FIRST ? 0.0f : (float)s->alpha;
     const float beta = FIRST ? 0.0f : (float)s->beta;
-    const long long T = (long long)ntx * nty * g.Nz;
-    const long long f0 = T * blockIdx.x / gridDim.x, f1 = T * (blockIdx.x + 1) / gridDim.x;
+    const int groups = gridDim.x / ntx;
+    const int grp = blockIdx.x / ntx, bx = blockIdx.x % ntx;
+    const long long R = (long long)nty * g.Nz;
+    const long long f0 = R * grp / groups, f1 = R * (grp + 1) / groups;
     float2 gam = f2(0.0f, 0.0f), del = gam, rho = gam;
     for (long long f = f0; f < f1;) {
-        const long long tile = f / g.Nz;
-        const int k0 = (int)(f - tile * g.Nz);
+        const long long by = f / g.Nz;
+        const int k0 = (int)(f - by * g.Nz);
         const long long rest = f1 - f;
         const int k1 = rest < (long long)(g.Nz - k0) ? k0 + (int)rest : g.Nz;
-        q1_cg_tile2p<FIRST>(g, K, x, r, p, r_out, p_out, cst, (int)(tile % ntx), (int)(tile / ntx), ntx, nty, k0,
-                            k1, alpha, beta, sm, gam, del, rho);
+        q1_cg_tile2p<FIRST>(g, K, x, r, p, r_out, p_out, cst, bx, (int)by, ntx, nty, k0, k1, alpha, beta, sm, gam,
+                            del, rho);
         f += k1 - k0;
     }
     double v[3];
@@ -1278,14 +1284,16 @@ int q1_cg_iteration32(ht_ctx* c, float dt, float* x, const float* r, const float
         resident = v;
     }
     const int sms = c->num_sms > 0 ? c->num_sms : 148;
-    // one CTA per co-resident slot, at least 8 node planes each (each z
-    // segment repeats 3 planes of pipeline start-up); z_chunks > 0 asks for
-    // about that many segments per tile column instead
-    const long long T = (long long)ntx * nty * g.Nz;
-    long long G = c->opts.z_chunks > 0 ? (long long)ntx * nty * std::min(c->opts.z_chunks, g.Nz)
-                                       : std::min<long long>((long long)resident * sms, (T + 7) / 8);
-    G = std::max(1LL, std::min({G, T, (long long)c->part_stride}));
-    const dim3 grid((unsigned)G), block(32, kCgBY);
+    // groups of ntx CTAs (one per tile column of a tile row), as many groups
+    // as fit in the co-resident slots, at least 8 node planes per group (each
+    // z segment repeats 3 planes of pipeline start-up); z_chunks > 0 asks
+    // for about that many segments per tile row instead
+    const long long R = (long long)nty * g.Nz;
+    long long Q = c->opts.z_chunks > 0 ? (long long)nty * std::min(c->opts.z_chunks, g.Nz)
+                                       : std::min<long long>(std::max(1, resident * sms / ntx), (R + 7) / 8);
+    Q = std::max(1LL, std::min({Q, R, (long long)(c->part_stride / ntx)}));
+    if (Q * ntx > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
+    const dim3 grid((unsigned)(Q * ntx)), block(32, kCgBY);
     if (first)
         q1_cg_kernel<true><<<grid, block, smem, c->stream>>>(g, c->K32, x, r, p, r_out, p_out, cst, ntx, nty, sc,
                                                              c->part, c->part_stride);
