@@ -2509,10 +2509,198 @@ static df64 df_split(double d) {
     return df64(hi, (float)(d - (double)hi));
 }
 
+// ---------------------------------------------------------------------------
+// Q1 heat operator of one cell in float-float for the outer residual of the
+// mixed heat solve (Eq. 4: c_T M + dt lambda K + dt c_w C(q), q = -K_c grad h
+// at the 2 x 2 x 2 Gauss points).  Mass and conduction in the element
+// eigenbasis of h = [[1, 1], [1, -1]] per axis (the cell matrix is
+// (h x h x h)^T diag(c_T MA_l + dt lambda KB_l) (h x h x h)); advection from
+// the edge differences of u and of h interpolated to the Gauss points: on a
+// Q1 cell the derivative along an axis is the edge difference interpolated
+// in the other two directions, and the Gauss weight times N_i sums back the
+// same way.  The head gradient is formed from h here, so the stored Gauss
+// point velocities are not read.
+// ---------------------------------------------------------------------------
+struct Q1HeatDf {
+    df64 MA[8], KB[8];      // mode eigenvalues: c_T MA_l + (dt lambda) KB_l (KB without dt)
+    df64 g0, g1;            // Gauss abscissae on [0, 1]
+    df64 fx, fy, fz;        // dt c_w W / H_d^2 (times -K_c per cell)
+    df64 cT, dtlam;         // uniform c_T and dt lambda (per-cell arrays when present)
+    double dt;
+};
+
+__device__ __forceinline__ void gauss2_df(const df64 (&d)[4], df64 g0, df64 g1, df64 (&o)[4]) {
+    df64 t[4];
+    t[0] = g1 * d[0] + g0 * d[1];   // along i
+    t[1] = g0 * d[0] + g1 * d[1];
+    t[2] = g1 * d[2] + g0 * d[3];
+    t[3] = g0 * d[2] + g1 * d[3];
+    o[0] = g1 * t[0] + g0 * t[2];   // along j
+    o[1] = g1 * t[1] + g0 * t[3];
+    o[2] = g0 * t[0] + g1 * t[2];
+    o[3] = g0 * t[1] + g1 * t[3];
+}
+__device__ __forceinline__ void face_fwd_df(df64 u0, df64 u1, df64 u2, df64 u3, df64 (&F)[4]) {
+    const df64 s0 = u0 + u1, d0 = u0 - u1, s1 = u2 + u3, d1 = u2 - u3;
+    F[0] = s0 + s1;
+    F[1] = d0 + d1;
+    F[2] = s0 - s1;
+    F[3] = d0 - d1;
+}
+__device__ __forceinline__ void face_bwd_df(const df64 (&G)[4], df64 (&u)[4]) {
+    const df64 t0 = G[0] + G[2], t1 = G[1] + G[3], w0 = G[0] - G[2], w1 = G[1] - G[3];
+    u[0] = t0 + t1;
+    u[1] = t0 - t1;
+    u[2] = w0 + w1;
+    u[3] = w0 - w1;
+}
+
+__global__ void __launch_bounds__(128) q1_heat_df_cell_kernel(const Grid g, const double* __restrict__ x,
+                                                              const double* __restrict__ h,
+                                                              const double* __restrict__ K,
+                                                              const double* __restrict__ cTc,
+                                                              const double* __restrict__ lamc, const Q1HeatDf k,
+                                                              df64* __restrict__ E) {
+    const long long nc = g.nc;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % g.ncx), cy = (int)((c / g.ncx) % g.ncy), cz = (int)(c / ((long long)g.ncx * g.ncy));
+        const long long base = cx + (long long)g.Nx * (cy + (long long)g.Ny * cz);
+        const long long NX = g.Nx, NXY = (long long)g.Nx * g.Ny;
+        const bool chk = g.dmask != 0 && (cx == 0 || cx == g.ncx - 1 || cy == 0 || cy == g.ncy - 1 || cz == 0 ||
+                                          cz == g.ncz - 1);
+        df64 U[2][4], H[2][4];   // [plane c][corner a + 2 b]
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = q & 1, b = q >> 1;
+                const long long id = base + a + NX * b + NXY * pc;
+                df64 uv = df_from(ldro(x + id));
+                if (chk && on_dir(g, cx + a, cy + b, cz + pc)) uv = df64(0);
+                U[pc][q] = uv;
+                H[pc][q] = df_from(ldro(h + id));
+            }
+        // mass + conduction in the eigenbasis
+        const df64 cT = cTc ? df_from(ldro(cTc + c)) : k.cT;
+        const df64 dtlam = lamc ? df_from(k.dt * ldro(lamc + c)) : k.dtlam;
+        df64 F0[4], F1[4], bot[4], top[4];
+        face_fwd_df(U[0][0], U[0][1], U[0][2], U[0][3], F0);
+        face_fwd_df(U[1][0], U[1][1], U[1][2], U[1][3], F1);
+        {
+            df64 bh[4], th[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const df64 lo = (F0[q] + F1[q]) * (cT * k.MA[q] + dtlam * k.KB[q]);
+                const df64 hi = (F0[q] - F1[q]) * (cT * k.MA[q + 4] + dtlam * k.KB[q + 4]);
+                bh[q] = lo + hi;
+                th[q] = lo - hi;
+            }
+            face_bwd_df(bh, bot);
+            face_bwd_df(th, top);
+        }
+        // advection: edge differences of u and h (corner index a + 2 b, plane c)
+        df64 du[4], dh[4], iu[4], ih[4], pr[4], rx[4], ry[4], rz[4];
+        du[0] = U[0][1] - U[0][0]; du[1] = U[0][3] - U[0][2]; du[2] = U[1][1] - U[1][0]; du[3] = U[1][3] - U[1][2];
+        dh[0] = H[0][1] - H[0][0]; dh[1] = H[0][3] - H[0][2]; dh[2] = H[1][1] - H[1][0]; dh[3] = H[1][3] - H[1][2];
+        gauss2_df(du, k.g0, k.g1, iu);
+        gauss2_df(dh, k.g0, k.g1, ih);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pr[q] = iu[q] * ih[q];
+        gauss2_df(pr, k.g0, k.g1, rx);
+        du[0] = U[0][2] - U[0][0]; du[1] = U[0][3] - U[0][1]; du[2] = U[1][2] - U[1][0]; du[3] = U[1][3] - U[1][1];
+        dh[0] = H[0][2] - H[0][0]; dh[1] = H[0][3] - H[0][1]; dh[2] = H[1][2] - H[1][0]; dh[3] = H[1][3] - H[1][1];
+        gauss2_df(du, k.g0, k.g1, iu);
+        gauss2_df(dh, k.g0, k.g1, ih);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pr[q] = iu[q] * ih[q];
+        gauss2_df(pr, k.g0, k.g1, ry);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            du[q] = U[1][q] - U[0][q];
+            dh[q] = H[1][q] - H[0][q];
+        }
+        gauss2_df(du, k.g0, k.g1, iu);
+        gauss2_df(dh, k.g0, k.g1, ih);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pr[q] = iu[q] * ih[q];
+        gauss2_df(pr, k.g0, k.g1, rz);
+        const df64 mk = -df_from(ldro(K + c));
+        const df64 fx = mk * k.fx, fy = mk * k.fy, fz = mk * k.fz;
+        const int ncl = (int)nc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int a = q & 1, bb = q >> 1;
+            const df64 zq = fz * rz[q];
+            const df64 b0 = bot[q] + (fx * rx[bb] + (fy * ry[a] + zq));
+            const df64 t0 = top[q] + (fx * rx[bb + 2] + (fy * ry[a + 2] + zq));
+            E[(size_t)q * ncl + c] = b0;
+            E[(size_t)(q + 4) * ncl + c] = t0;
+        }
+    }
+}
+
+static Q1HeatDf q1_heat_df_const(const ht_ctx* c, double dt) {
+    Q1HeatDf k{};
+    const double* H = c->H;
+    double m1[3][2], k1[3][2];
+    for (int d = 0; d < 3; ++d) {
+        m1[d][0] = H[d];
+        m1[d][1] = H[d] / 3.0;
+        k1[d][0] = 0.0;
+        k1[d][1] = 4.0 / H[d];
+    }
+    auto split = [](double v) {
+        const float hi = (float)v;
+        return df64(hi, (float)(v - (double)hi));
+    };
+    for (int cz = 0; cz < 2; ++cz)
+        for (int by = 0; by < 2; ++by)
+            for (int ax = 0; ax < 2; ++ax) {
+                const int l = ax + 2 * by + 4 * cz;
+                const double M = m1[0][ax] * m1[1][by] * m1[2][cz];
+                const double Kl = k1[0][ax] * m1[1][by] * m1[2][cz] + m1[0][ax] * k1[1][by] * m1[2][cz] +
+                                  m1[0][ax] * m1[1][by] * k1[2][cz];
+                k.MA[l] = split(M / 64.0);
+                k.KB[l] = split(Kl / 64.0);
+            }
+    const double d = 0.5 / sqrt(3.0);
+    k.g0 = split(0.5 - d);
+    k.g1 = split(0.5 + d);
+    const double W = H[0] * H[1] * H[2] / 8.0;
+    k.fx = split(dt * c->cw * W / (H[0] * H[0]));
+    k.fy = split(dt * c->cw * W / (H[1] * H[1]));
+    k.fz = split(dt * c->cw * W / (H[2] * H[2]));
+    k.cT = split(c->cT_u);
+    k.dtlam = split(dt * c->lam_u);
+    k.dt = dt;
+    return k;
+}
+
 template <int P>
 static int resid_df_field(ht_ctx* c, int field, double dt, const double* x, const double* b, float* r32,
                           double* part, int* n_part) {
     const Grid g = field_grid(c, field);
+    if (P == 1 && field == HT_TEMP) {
+        // Q1 heat: the cell kernel above, then the node gather of the
+        // residual (wells and Dirichlet rows there)
+        df64* E = reinterpret_cast<df64*>(elem_buffer<double>(c));
+        dim3 ng;
+        int kl;
+        layer_node_dims(c, g, resident_per_sm<df_resid_node_kernel<P>>(), &ng, &kl);
+        if ((int)(ng.x * ng.y) > c->part_stride) return fail(c, HT_EINVAL, "too many partial sums");
+        long long blocks = (g.nc + 127) / 128;
+        const long long cap = (long long)(c->num_sms > 0 ? c->num_sms : 148) * 16;
+        if (blocks > cap) blocks = cap;
+        q1_heat_df_cell_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>(g, x, c->h, c->K64, c->cT64, c->lam64,
+                                                                         q1_heat_df_const(c, dt), E);
+        ++c->n_launch;
+        df_resid_node_kernel<P><<<ng, 128, 0, c->stream>>>(g, E, x, b, c->wdn64, dt, r32, part, c->part_stride, kl);
+        ++c->n_launch;
+        HT_CUDA(c, cudaGetLastError());
+        *n_part = (int)(ng.x * ng.y);
+        return HT_OK;
+    }
     if (field == HT_HEAD) {
         HeadOp<P, df64, MODE_APPLY, double> op{};
         op.K = c->K64; op.alpha = df_split(c->Ss); op.dt = df_split(dt); op.e = c->edf;
