@@ -952,6 +952,7 @@ void ht_destroy(ht_ctx* c) {
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
     dfree(c->ptemp_node); dfree(c->ptemp_pile); dfree(c->d_ptemp); dfree(c->dint);
     dfree(c->dint_a64); dfree(c->dint_b64); dfree(c->dint_a32);
+    dfree(c->xdf); dfree(c->hdf);
     dfree(c->scal);
     dfree(c->gm);
     dfree(c->V64);

@@ -170,6 +170,8 @@ struct ht_ctx {
     double* qs64 = nullptr;
     float* qs32 = nullptr;
     // element-result buffers of the two-pass apply [(p+1)^3][cells]
+    ht::df64* xdf = nullptr;                // float-float copies of the operand and the head for the
+    ht::df64* hdf = nullptr;                // emulated-FP64 residuals (allocated on first use)
     double* E64 = nullptr;                  // element buffers: kElemPad zeros, then (P+1)^3 nc entries
     float* E32 = nullptr;
 

@@ -1583,7 +1583,7 @@ __global__ void __launch_bounds__(128) node_emit_df_kernel(const Grid g, const d
 // b.b.  The element buffer is the FP64 one, read as float pairs.
 // ---------------------------------------------------------------------------
 template <int P, class Op>
-__global__ void __launch_bounds__(128) df_cell_kernel(const Grid g, const Op op, const double* __restrict__ x,
+__global__ void __launch_bounds__(128) df_cell_kernel(const Grid g, const Op op, const df64* __restrict__ x,
                                                       df64* __restrict__ E, const int zlen) {
     constexpr int n = P + 1, NL = n * n * n;
     const int cx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1602,7 +1602,7 @@ __global__ void __launch_bounds__(128) df_cell_kernel(const Grid g, const Op op,
 #pragma unroll
             for (int b = 0; b < n; ++b)
 #pragma unroll
-                for (int a = 0; a < n; ++a) u[a + n * (b + n * c2)] = df_from(ldro(x + base + NX * b + NXY * c2 + a));
+                for (int a = 0; a < n; ++a) u[a + n * (b + n * c2)] = ldg_any<df64>(x + base + NX * b + NXY * c2 + a);
         if (edge_xy || (g.dmask & 48 && (cz == 0 || cz == g.ncz - 1))) {
 #pragma unroll
             for (int c2 = 0; c2 < n; ++c2)
@@ -2481,6 +2481,21 @@ int launch_diag32(ht_ctx* c, int field, double dt, float* D) {
     return HT_OK;
 }
 
+// FP64 vector to float pairs, once per residual (the cell kernels read every
+// node eight times; the conversion runs on the slow FP64 pipe)
+__global__ void split_df_kernel(long long n, const double* __restrict__ a, df64* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = df_from(a[i]);
+}
+
+static int split_df(ht_ctx* c, const double* a, df64** buf) {
+    if (!*buf && cudaMalloc(buf, (size_t)c->grid.nn * sizeof(df64)) != cudaSuccess)
+        return fail(c, HT_ENOMEM, "float-float operand buffer: allocation failed");
+    split_df_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(c->grid.nn, a, *buf); ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    return HT_OK;
+}
+
 template <int P, class Op>
 static int resid_df_P(ht_ctx* c, const Grid& g, const Op& op, const double* x, const double* b, float* r32,
                       double* part, int* n_part, double dt, const double* wd) {
@@ -2495,7 +2510,8 @@ static int resid_df_P(ht_ctx* c, const Grid& g, const Op& op, const double* x, c
         dim3 cg;
         int zl;
         cell_pass_dims(c, g, resident_per_sm<df_cell_kernel<P, Op>>(), &cg, &zl);
-        df_cell_kernel<P, Op><<<cg, dim3(32, 4), 0, c->stream>>>(g, op, x, E, zl); ++c->n_launch;
+        HT_TRY(split_df(c, x, &c->xdf));
+        df_cell_kernel<P, Op><<<cg, dim3(32, 4), 0, c->stream>>>(g, op, c->xdf, E, zl); ++c->n_launch;
     }
     df_resid_node_kernel<P><<<ng, 128, 0, c->stream>>>(g, E, x, b, wd, dt, r32, part, c->part_stride, kl);
     ++c->n_launch;
@@ -2555,8 +2571,8 @@ __device__ __forceinline__ void face_bwd_df(const df64 (&G)[4], df64 (&u)[4]) {
     u[3] = w0 - w1;
 }
 
-__global__ void __launch_bounds__(128) q1_heat_df_cell_kernel(const Grid g, const double* __restrict__ x,
-                                                              const double* __restrict__ h,
+__global__ void __launch_bounds__(128) q1_heat_df_cell_kernel(const Grid g, const df64* __restrict__ x,
+                                                              const df64* __restrict__ h,
                                                               const double* __restrict__ K,
                                                               const double* __restrict__ cTc,
                                                               const double* __restrict__ lamc, const Q1HeatDf k,
@@ -2576,10 +2592,10 @@ __global__ void __launch_bounds__(128) q1_heat_df_cell_kernel(const Grid g, cons
             for (int q = 0; q < 4; ++q) {
                 const int a = q & 1, b = q >> 1;
                 const long long id = base + a + NX * b + NXY * pc;
-                df64 uv = df_from(ldro(x + id));
+                df64 uv = ldg_any<df64>(x + id);
                 if (chk && on_dir(g, cx + a, cy + b, cz + pc)) uv = df64(0);
                 U[pc][q] = uv;
-                H[pc][q] = df_from(ldro(h + id));
+                H[pc][q] = ldg_any<df64>(h + id);
             }
         // mass + conduction in the eigenbasis
         const df64 cT = cTc ? df_from(ldro(cTc + c)) : k.cT;
@@ -2692,8 +2708,10 @@ static int resid_df_field(ht_ctx* c, int field, double dt, const double* x, cons
         long long blocks = (g.nc + 127) / 128;
         const long long cap = (long long)(c->num_sms > 0 ? c->num_sms : 148) * 16;
         if (blocks > cap) blocks = cap;
-        q1_heat_df_cell_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>(g, x, c->h, c->K64, c->cT64, c->lam64,
-                                                                         q1_heat_df_const(c, dt), E);
+        HT_TRY(split_df(c, x, &c->xdf));
+        HT_TRY(split_df(c, c->h, &c->hdf));
+        q1_heat_df_cell_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>(g, c->xdf, c->hdf, c->K64, c->cT64,
+                                                                         c->lam64, q1_heat_df_const(c, dt), E);
         ++c->n_launch;
         df_resid_node_kernel<P><<<ng, 128, 0, c->stream>>>(g, E, x, b, c->wdn64, dt, r32, part, c->part_stride, kl);
         ++c->n_launch;
