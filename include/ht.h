@@ -199,6 +199,21 @@ int ht_set_bc(ht_ctx* ctx, int field, int face, int type, double value);
  * or a type other than HT_BC_DIRICHLET / HT_BC_FLUX. */
 int ht_set_bc_values(ht_ctx* ctx, int field, int face, int type, const double* values, size_t n);
 
+/* Graded tensor-product mesh (Fig. 10b: cells refined towards the piles):
+ * the cell widths along `axis` (0 x, 1 y, 2 z), widths[n] on the host with n
+ * the cells along that axis; the axis then spans [origin, origin + sum of
+ * the widths] (the other axes keep their widths: the mesh's uniform ones
+ * until set).  Every geometric quantity is taken per cell: the element
+ * matrices (the unit-cell constants scaled by the cell's volume and
+ * 1/h_d per derivative), the Gauss-point gradients and Darcy velocities, and
+ * the line, well, box, face and pile-surface geometry of the loads.  A graded
+ * context uses the generic kernels (two-pass or tiled operator, fused or
+ * unfused Krylov); the single-pass Q1 kernels, the persistent and shared-
+ * launch batch modes and ht_head_apply_dot_noalloc need uniform cells.  Set
+ * the spacing before stepping.  Errors: HT_EINVAL for a bad axis, a wrong
+ * count or a width that is not positive. */
+int ht_set_spacing(ht_ctx* ctx, int axis, const double* widths, int n);
+
 /* Seasonal Dirichlet face (Section 3.3: the surface and sea temperatures
  * over the year): the face becomes a Dirichlet face of `field` whose value
  * at each step's t^{n+1} is mean + amp sin(2 pi t / period + phase).  On an

@@ -101,6 +101,7 @@ SIGNATURES = {
     "ht_residual": (c_int, [c_void_p, c_int, c_double, c_void_p, c_void_p, c_int, c_int, POINTER(c_double)]),
     "ht_diag": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
     "ht_rhs": (c_int, [c_void_p, c_int, c_double, c_void_p, c_int]),
+    "ht_set_spacing": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "ht_set_seasonal_face": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_double]),
     "ht_set_pile_temperatures": (c_int, [c_void_p, c_int, c_void_p]),
     "ht_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),

@@ -685,6 +685,9 @@ int ht_batch_step(ht_batch* b, double dt, ht_step_stats* stats) {
             return bfail(b, HT_EINVAL, "batched problems need precision HT_MIXED with the Jacobi preconditioner");
     }
     if (b->mode == HT_BATCH_CONCURRENT) return batch_step_concurrent(b, dt, stats);
+    for (const ht_ctx* c : b->probs)
+        if (c->graded)
+            return bfail(b, HT_EINVAL, "graded meshes are batched in the concurrent mode only");
     if (b->mode == HT_BATCH_PERSISTENT) return batch_step_persistent(b, dt, stats);
     // every problem works on the batch stream for the duration of the step
     std::vector<cudaStream_t> saved(np);

@@ -158,8 +158,12 @@ void build_elem(ht_ctx* c) {
     const int P = c->grid.P, n = P + 1;
     ht::Elem<double>& e = c->e64;
     memset(&e, 0, sizeof(e));
+    // a graded mesh takes the constants of the unit cube; its kernels scale
+    // them per cell (volume, 1/h per axis)
+    const double unit[3] = {1.0, 1.0, 1.0};
+    const double* H = c->graded ? unit : c->H;
     double m[3][3][3], k[3][3][3];
-    for (int d = 0; d < 3; ++d) element_1d(P, c->H[d], m[d], k[d], e.G[d], e.Lam[d]);
+    for (int d = 0; d < 3; ++d) element_1d(P, H[d], m[d], k[d], e.G[d], e.Lam[d]);
     double xq[3], wq[3];
     gauss01(n, xq, wq);
     for (int q = 0; q < n; ++q)
@@ -167,11 +171,15 @@ void build_elem(ht_ctx* c) {
             e.B[q][a] = lag(P, a, xq[q]);
             e.D[q][a] = dlag(P, a, xq[q]);
         }
-    const double vol = c->H[0] * c->H[1] * c->H[2];
+    const double vol = H[0] * H[1] * H[2];
     for (int qz = 0; qz < n; ++qz)
         for (int qy = 0; qy < n; ++qy)
             for (int qx = 0; qx < n; ++qx) e.W[qx + n * (qy + n * qz)] = wq[qx] * wq[qy] * wq[qz] * vol;
-    for (int d = 0; d < 3; ++d) e.invH[d] = 1.0 / c->H[d];
+    for (int d = 0; d < 3; ++d) e.invH[d] = 1.0 / H[d];
+    for (int a = 0; a < n; ++a) {
+        e.dm1[a] = m[0][a][a];
+        e.dk1[a] = k[0][a][a];
+    }
     for (int cc = 0; cc < n; ++cc)
         for (int b = 0; b < n; ++b)
             for (int a = 0; a < n; ++a) {
@@ -247,6 +255,22 @@ double node_int_1d(int P, int nc, double H, int i) {
     return s;
 }
 
+int axis_cells(const ht_ctx* c, int d);
+// the same along axis d of the context (per-cell widths on a graded mesh)
+double node_int_axis(const ht_ctx* c, int d, int i) {
+    const int P = c->grid.P, nc = axis_cells(c, d);
+    if (!c->graded) return node_int_1d(P, nc, c->H[d], i);
+    double s = 0;
+    if (i % P == 0) {
+        const int cl = i / P - 1, cr = i / P;
+        if (cl >= 0) s += c->widths[d][cl] * phi_int(P, P);
+        if (cr < nc) s += c->widths[d][cr] * phi_int(P, 0);
+    } else {
+        s += c->widths[d][i / P] * phi_int(P, i % P);
+    }
+    return s;
+}
+
 template <typename T>
 int dalloc(ht_ctx* c, T** p, size_t count) {
     void* q = nullptr;
@@ -265,6 +289,41 @@ void dfree(T*& p) {
     p = nullptr;
 }
 
+// ---- geometry along an axis (uniform cells of size H, or the tensor-product
+// widths of a graded mesh, Fig. 10b) ----------------------------------------
+double axis_origin(const ht_ctx* c, int d) { return d == 0 ? c->mesh.x0 : (d == 1 ? c->mesh.y0 : c->mesh.z0); }
+int axis_cells(const ht_ctx* c, int d) { return d == 0 ? c->mesh.nx : (d == 1 ? c->mesh.ny : c->mesh.nz); }
+// low face of cell layer k along d, and its width
+double face_at(const ht_ctx* c, int d, int k) {
+    return c->graded ? c->faces[d][k] : axis_origin(c, d) + k * c->H[d];
+}
+double width_at(const ht_ctx* c, int d, int k) { return c->graded ? c->widths[d][k] : c->H[d]; }
+// cell layer along d holding coordinate v (clamped to the mesh) and the local
+// coordinate of v in it
+void locate(const ht_ctx* c, int d, double v, int* ci, double* xi) {
+    const int n = axis_cells(c, d);
+    if (!c->graded) {
+        const double s = (v - axis_origin(c, d)) / c->H[d];
+        int k = (int)floor(s);
+        k = std::max(0, std::min(k, n - 1));
+        *ci = k;
+        *xi = s - k;
+        return;
+    }
+    const std::vector<double>& f = c->faces[d];
+    int k = (int)(std::upper_bound(f.begin(), f.end(), v) - f.begin()) - 1;
+    k = std::max(0, std::min(k, n - 1));
+    *ci = k;
+    *xi = (v - f[k]) / c->widths[d][k];
+}
+// coordinate of node i along d
+double node_coord(const ht_ctx* c, int d, int i) {
+    const int P = c->grid.P;
+    if (!c->graded) return axis_origin(c, d) + i * (c->H[d] / P);
+    const int k = std::min(i / P, axis_cells(c, d) - 1);
+    return c->faces[d][k] + (i - P * k) * c->widths[d][k] / P;
+}
+
 // Vertical segment weights w_i = int_{z_bot}^{z_top} N_i(x, y, z) dz
 int line_weights(ht_ctx* c, double x, double y, double ztop, double zbot, std::map<long long, double>& out,
                  const char* what) {
@@ -280,21 +339,25 @@ int line_weights(ht_ctx* c, double x, double y, double ztop, double zbot, std::m
     double fx[2][3];
     const double pos[2] = {x, y}, org[2] = {m.x0, m.y0};
     const int ncs[2] = {m.nx, m.ny};
+    (void)org;
+    (void)ncs;
     for (int d = 0; d < 2; ++d) {
-        const double s = (pos[d] - org[d]) / c->H[d];
-        int ci = (int)floor(s);
-        ci = std::max(0, std::min(ci, ncs[d] - 1));
-        const double xi = s - ci;
+        int ci = 0;
+        double xi = 0.0;
+        locate(c, d, pos[d], &ci, &xi);
         cxy[d] = ci;
         for (int a = 0; a <= P; ++a) fx[d][a] = lag(P, a, xi);
     }
-    const double Hz = c->H[2];
     double xq[3], wq[3];
     gauss01(3, xq, wq);
-    int cz0 = (int)floor((lo - m.z0) / Hz);
-    cz0 = std::max(0, std::min(cz0, m.nz - 1));
+    int cz0 = 0;
+    if (!c->graded) {
+        cz0 = (int)floor((lo - m.z0) / c->H[2]);
+        cz0 = std::max(0, std::min(cz0, m.nz - 1));
+    }
     for (int cz = cz0; cz < m.nz; ++cz) {
-        const double a0 = m.z0 + cz * Hz, a1 = a0 + Hz;
+        const double Hz = width_at(c, 2, cz);
+        const double a0 = face_at(c, 2, cz), a1 = c->graded ? c->faces[2][cz + 1] : a0 + Hz;
         if (a0 >= hi) break;
         const double s0 = std::max(a0, lo), s1 = std::min(a1, hi);
         if (s1 <= s0) continue;
@@ -320,6 +383,13 @@ int line_weights(ht_ctx* c, double x, double y, double ztop, double zbot, std::m
 int snap_face(const ht_ctx* c, int d, double v) {
     const double org[3] = {c->mesh.x0, c->mesh.y0, c->mesh.z0};
     const int n[3] = {c->mesh.nx, c->mesh.ny, c->mesh.nz};
+    if (c->graded) {   // the nearest face; of equally near faces the higher one
+        const std::vector<double>& f = c->faces[d];
+        int best = 0;
+        for (int k = 1; k <= n[d]; ++k)
+            if (fabs(f[k] - v) <= fabs(f[best] - v)) best = k;
+        return best;
+    }
     const double f = floor((v - org[d]) / c->H[d] + 0.5);
     return (int)std::max(0.0, std::min(f, (double)n[d]));
 }
@@ -333,18 +403,19 @@ int box_weights(ht_ctx* c, const ht_box_src& b, std::map<long long, double>& out
     const int k = snap_face(c, 2, b.z);
     if (i1 <= i0 || j1 <= j0) return fail(c, HT_EINVAL, "box source is empty once snapped to cell faces");
     double ix[3], iy[3];
-    for (int a = 0; a <= P; ++a) {
-        ix[a] = c->H[0] * phi_int(P, a);
-        iy[a] = c->H[1] * phi_int(P, a);
-    }
     const long long kk = (long long)P * k;
     for (int cy = j0; cy < j1; ++cy)
-        for (int cx = i0; cx < i1; ++cx)
+        for (int cx = i0; cx < i1; ++cx) {
+            for (int a = 0; a <= P; ++a) {
+                ix[a] = width_at(c, 0, cx) * phi_int(P, a);
+                iy[a] = width_at(c, 1, cy) * phi_int(P, a);
+            }
             for (int bb = 0; bb <= P; ++bb)
                 for (int a = 0; a <= P; ++a) {
                     const long long i = (long long)P * cx + a, j = (long long)P * cy + bb;
                     out[i + (long long)c->grid.Nx * (j + (long long)c->grid.Ny * kk)] += ix[a] * iy[bb];
                 }
+        }
     return HT_OK;
 }
 
@@ -370,26 +441,29 @@ bool node_on_dirichlet(const ht_ctx* c, int field, long long id) {
 int pile_surface_nodes(ht_ctx* c, const double* row, std::vector<long long>& out) {
     const Grid& g = c->grid;
     const ht_mesh& m = c->mesh;
-    const double hx = c->H[0] / g.P, hy = c->H[1] / g.P, hz = c->H[2] / g.P;
+    const double hx = c->H[0] / g.P, hy = c->H[1] / g.P;
     const double eps = 1e-9 * std::max(m.Lx, std::max(m.Ly, m.Lz));
     const double zlo = std::min(row[2], row[3]) - eps, zhi = std::max(row[2], row[3]) + eps;
     std::vector<int> ks;
     for (int k = 0; k < g.Nz; ++k) {
-        const double z = m.z0 + k * hz;
+        const double z = node_coord(c, 2, k);
         if (z >= zlo && z <= zhi) ks.push_back(k);
     }
     out.clear();
     if (ks.empty()) return fail(c, HT_EINVAL, "pile surface (%g, %g) lies outside the mesh", row[0], row[1]);
     auto lat = [&](int i, int j) {
-        const double dx = (m.x0 + i * hx) - row[0], dy = (m.y0 + j * hy) - row[1];
+        const double dx = node_coord(c, 0, i) - row[0], dy = node_coord(c, 1, j) - row[1];
         return dx * dx + dy * dy;
     };
     const double r2 = row[4] * row[4] + eps;
     const double R = sqrt(r2);
-    const int i0 = std::max(0, (int)floor((row[0] - R - m.x0) / hx) - 1);
-    const int i1 = std::min(g.Nx - 1, (int)ceil((row[0] + R - m.x0) / hx) + 1);
-    const int j0 = std::max(0, (int)floor((row[1] - R - m.y0) / hy) - 1);
-    const int j1 = std::min(g.Ny - 1, (int)ceil((row[1] + R - m.y0) / hy) + 1);
+    int i0 = 0, i1 = g.Nx - 1, j0 = 0, j1 = g.Ny - 1;   // a graded mesh scans every column
+    if (!c->graded) {
+        i0 = std::max(0, (int)floor((row[0] - R - m.x0) / hx) - 1);
+        i1 = std::min(g.Nx - 1, (int)ceil((row[0] + R - m.x0) / hx) + 1);
+        j0 = std::max(0, (int)floor((row[1] - R - m.y0) / hy) - 1);
+        j1 = std::min(g.Ny - 1, (int)ceil((row[1] + R - m.y0) / hy) + 1);
+    }
     std::vector<std::pair<int, int>> cols;
     for (int j = j0; j <= j1; ++j)
         for (int i = i0; i <= i1; ++i)
@@ -502,9 +576,10 @@ int well_weights(ht_ctx* c, const ht_well& wl, std::map<long long, double>& out)
     const int ncs[2] = {m.nx, m.ny};
     const double sg = wl.sigma;
     for (int d = 0; d < 2; ++d) {
-        const double H = c->H[d];
+        (void)org;
         for (int ci = 0; ci < ncs[d]; ++ci) {
-            const double a0 = org[d] + ci * H;
+            const double H = width_at(c, d, ci);
+            const double a0 = face_at(c, d, ci);
             if (a0 > centre[d] + 10 * sg || a0 + H < centre[d] - 10 * sg) continue;
             for (int a = 0; a <= P; ++a) {
                 double sum = 0.0;
@@ -519,11 +594,11 @@ int well_weights(ht_ctx* c, const ht_well& wl, std::map<long long, double>& out)
     }
     // z integrals over the screen
     const double lo = std::max(wl.z_bot, m.z0), hi = std::min(wl.z_top, m.z0 + m.Lz);
-    const double Hz = c->H[2];
     double xq[3], wq[3];
     gauss01(3, xq, wq);
     for (int cz = 0; cz < m.nz; ++cz) {
-        const double a0 = m.z0 + cz * Hz, a1 = a0 + Hz;
+        const double Hz = width_at(c, 2, cz);
+        const double a0 = face_at(c, 2, cz), a1 = c->graded ? c->faces[2][cz + 1] : a0 + Hz;
         const double s0 = std::max(a0, lo), s1 = std::min(a1, hi);
         if (s1 <= s0) continue;
         for (int cc = 0; cc <= P; ++cc) {
@@ -542,8 +617,41 @@ int well_weights(ht_ctx* c, const ht_well& wl, std::map<long long, double>& out)
 }
 
 // Rebuild Dirichlet values, static loads and source tables after changes.
+// per-cell geometry of a graded mesh on the device: [4][nc] = volume, 1/hx,
+// 1/hy, 1/hz (FP64 and FP32 copies)
+int upload_geometry(ht_ctx* c) {
+    if (!c->graded || !c->geo_dirty) return HT_OK;
+    const Grid& g = c->grid;
+    const size_t nc = (size_t)g.nc;
+    std::vector<double> h(4 * nc);
+    std::vector<float> f(4 * nc);
+    for (int cz = 0; cz < g.ncz; ++cz)
+        for (int cy = 0; cy < g.ncy; ++cy)
+            for (int cx = 0; cx < g.ncx; ++cx) {
+                const size_t id = cx + (size_t)g.ncx * (cy + (size_t)g.ncy * cz);
+                const double hx = c->widths[0][cx], hy = c->widths[1][cy], hz = c->widths[2][cz];
+                h[id] = hx * hy * hz;
+                h[nc + id] = 1.0 / hx;
+                h[2 * nc + id] = 1.0 / hy;
+                h[3 * nc + id] = 1.0 / hz;
+            }
+    for (size_t i = 0; i < 4 * nc; ++i) f[i] = (float)h[i];
+    if (!c->geo64 && cudaMalloc(&c->geo64, 4 * nc * sizeof(double)) != cudaSuccess)
+        return fail(c, HT_ENOMEM, "graded-mesh geometry: allocation failed");
+    if (!c->geo32 && cudaMalloc(&c->geo32, 4 * nc * sizeof(float)) != cudaSuccess)
+        return fail(c, HT_ENOMEM, "graded-mesh geometry: allocation failed");
+    HT_CUDA(c, cudaMemcpyAsync(c->geo64, h.data(), 4 * nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    HT_CUDA(c, cudaMemcpyAsync(c->geo32, f.data(), 4 * nc * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->grid.geo64 = c->geo64;
+    c->grid.geo32 = c->geo32;
+    c->geo_dirty = false;
+    return HT_OK;
+}
+
 int finalize_setup(ht_ctx* c) {
     if (!c->cells_set) return fail(c, HT_EINVAL, "ht_set_cells must be called before stepping");
+    HT_TRY(upload_geometry(c));
     if (!c->bc_dirty && !c->loads_dirty) return HT_OK;
     const Grid& g = c->grid;
     const long long nn = g.nn;
@@ -573,13 +681,13 @@ int finalize_setup(ht_ctx* c) {
                 // the face mass matrix a tensor product of 1D mass matrices per cell
                 const int P = g.P;
                 double M1[2][3][3];
-                for (int a = 0; a <= P; ++a)
-                    for (int b = 0; b <= P; ++b) {
-                        M1[0][a][b] = c->H[t1] * phi_phi_int(P, a, b);
-                        M1[1][a][b] = c->H[t2] * phi_phi_int(P, a, b);
-                    }
                 for (int c2 = 0; c2 < ncs[t2]; ++c2)
-                    for (int c1 = 0; c1 < ncs[t1]; ++c1)
+                    for (int c1 = 0; c1 < ncs[t1]; ++c1) {
+                        for (int a = 0; a <= P; ++a)
+                            for (int b = 0; b <= P; ++b) {
+                                M1[0][a][b] = width_at(c, t1, c1) * phi_phi_int(P, a, b);
+                                M1[1][a][b] = width_at(c, t2, c2) * phi_phi_int(P, a, b);
+                            }
                         for (int b = 0; b <= P; ++b)
                             for (int a = 0; a <= P; ++a) {
                                 double sum = 0.0;
@@ -589,6 +697,7 @@ int finalize_setup(ht_ctx* c) {
                                                nodal[(P * c1 + a2) + (size_t)Nd[t1] * (P * c2 + b2)];
                                 Fs[face_node(P * c1 + a, P * c2 + b)] += sum;
                             }
+                    }
                 continue;
             }
             for (int b = 0; b < Nd[t2]; ++b)
@@ -597,8 +706,7 @@ int finalize_setup(ht_ctx* c) {
                     if (c->bc_type[f][face] == HT_BC_DIRICHLET) {
                         gv[id] = nodal.empty() ? c->bc_val[f][face] : nodal[a + (size_t)Nd[t1] * b];
                     } else {
-                        Fs[id] += c->bc_val[f][face] * node_int_1d(g.P, ncs[t1], c->H[t1], a) *
-                                  node_int_1d(g.P, ncs[t2], c->H[t2], b);
+                        Fs[id] += c->bc_val[f][face] * node_int_axis(c, t1, a) * node_int_axis(c, t2, b);
                     }
                 }
         }
@@ -952,7 +1060,7 @@ void ht_destroy(ht_ctx* c) {
     dfree(c->pile_node); dfree(c->pile_off); dfree(c->pile_src); dfree(c->d_piles); dfree(c->well_node);
     dfree(c->ptemp_node); dfree(c->ptemp_pile); dfree(c->d_ptemp); dfree(c->dint);
     dfree(c->dint_a64); dfree(c->dint_b64); dfree(c->dint_a32);
-    dfree(c->xdf); dfree(c->hdf);
+    dfree(c->xdf); dfree(c->hdf); dfree(c->geo64); dfree(c->geo32);
     dfree(c->scal);
     dfree(c->gm);
     dfree(c->V64);
@@ -1014,6 +1122,45 @@ int ht_set_bc(ht_ctx* c, int field, int face, int type, double value) {
     c->seasonal[field][face].on = 0;
     c->bc_dirty = true;
     c->cheb_dt[field] = -1.0;
+    return HT_OK;
+}
+
+int ht_set_spacing(ht_ctx* c, int axis, const double* widths, int n) {
+    if (!c) return HT_EINVAL;
+    if (axis < 0 || axis > 2) return fail(c, HT_EINVAL, "axis must be 0, 1 or 2");
+    if (!widths || n != axis_cells(c, axis))
+        return fail(c, HT_EINVAL, "axis %d has %d cells, got %d widths", axis, axis_cells(c, axis), n);
+    for (int k = 0; k < n; ++k)
+        if (!(widths[k] > 0) || !isfinite(widths[k])) return fail(c, HT_EINVAL, "width %d must be positive", k);
+    if (!c->graded) {   // the other axes keep their uniform widths
+        for (int d = 0; d < 3; ++d) {
+            const int nd = axis_cells(c, d);
+            c->widths[d].assign(nd, c->H[d]);
+        }
+    }
+    c->widths[axis].assign(widths, widths + n);
+    for (int d = 0; d < 3; ++d) {
+        const int nd = axis_cells(c, d);
+        c->faces[d].resize(nd + 1);
+        const double org = axis_origin(c, d);
+        double cum = 0.0;
+        for (int k = 0; k <= nd; ++k) {
+            c->faces[d][k] = org + cum;
+            if (k < nd) cum += c->widths[d][k];
+        }
+        if (d == 0) c->mesh.Lx = cum;
+        if (d == 1) c->mesh.Ly = cum;
+        if (d == 2) c->mesh.Lz = cum;
+        c->H[d] = cum / nd;   // mean width (nominal cell size)
+    }
+    for (auto* gr : {&c->g_cg[0], &c->g_cg[1], &c->g_bi[0], &c->g_bi[1], &c->g_cg1, &c->g_bi1})
+        gr->dt = -1.0;   // captured launches hold the element constants: recapture
+    c->graded = true;
+    c->geo_dirty = true;
+    c->bc_dirty = true;
+    c->loads_dirty = true;
+    c->cheb_dt[0] = c->cheb_dt[1] = -1.0;
+    build_elem(c);
     return HT_OK;
 }
 

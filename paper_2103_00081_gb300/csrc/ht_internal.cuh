@@ -20,6 +20,9 @@ struct Grid {
     int Nx, Ny, Nz;             // nodes per direction (P*nc + 1)
     long long nn, nc;           // node and cell counts
     int dmask;                  // Dirichlet faces of the field (bit f = face f)
+    // graded mesh: per-cell volume, 1/hx, 1/hy, 1/hz as [4][nc] (null: uniform)
+    const double* geo64;
+    const float* geo32;
 };
 
 // Reference-element constants for a uniform axis-aligned cell.
@@ -42,6 +45,7 @@ struct Elem {
     T dM[27];
     T dK[27];
     T LS[27];      // Lx[a] + Ly[b] + Lz[c] per mode l = a + n(b + n c)
+    T dm1[3], dk1[3];   // diagonals of the 1D mass and stiffness of the unit cell (graded meshes)
 };
 
 // A float-float value hi + lo (|lo| <= ulp(hi)/2, about 48 significant bits),
@@ -170,6 +174,15 @@ struct ht_ctx {
     double* qs64 = nullptr;
     float* qs32 = nullptr;
     // element-result buffers of the two-pass apply [(p+1)^3][cells]
+    // graded mesh (tensor-product cell widths): face coordinates per axis
+    // (empty: uniform cells of size H) and the per-cell geometry [4][nc]
+    // (volume, 1/hx, 1/hy, 1/hz) on the device
+    std::vector<double> faces[3];
+    std::vector<double> widths[3];
+    bool graded = false;
+    bool geo_dirty = false;
+    double* geo64 = nullptr;
+    float* geo32 = nullptr;
     ht::df64* xdf = nullptr;                // float-float copies of the operand and the head for the
     ht::df64* hdf = nullptr;                // emulated-FP64 residuals (allocated on first use)
     double* E64 = nullptr;                  // element buffers: kElemPad zeros, then (P+1)^3 nc entries

@@ -26,6 +26,7 @@
 #include <stdio.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "ht_device.cuh"
 #include "ht_internal.cuh"
@@ -169,8 +170,27 @@ __device__ __forceinline__ void sweep(T (&u)[n * n * n], const T (&M)[3][3]) {
 // ---------------------------------------------------------------------------
 // Operators (cell computation + node emission)
 // ---------------------------------------------------------------------------
+// Per-cell geometry of a graded mesh (Fig. 10b: tensor-product cell widths):
+// geo[k * nc + c] = volume, 1/hx, 1/hy, 1/hz of cell c in storage type S;
+// null on a uniform mesh, whose element constants carry the cell size.  On a
+// graded mesh the element constants are those of the unit cube and each
+// cell scales them: the volume scales mass and Gauss weights, 1/h_d each
+// derivative along d (for the fast diagonalisation: G = sqrt(h) G_1 per
+// axis, so the cell matrix is vol (G_1^T)^3 diag(alpha + beta sum_d
+// Lam_1,d / h_d^2) G_1^3).
+template <typename T, typename S>
+struct CellGeo {
+    const S* geo;
+    long long gnc;
+    __device__ __forceinline__ void geom(long long c, T& vol, T (&ih)[3]) const {
+        vol = cvt<T>(ldro(geo + c));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ih[d] = cvt<T>(ldro(geo + (d + 1) * gnc + c));
+    }
+};
+
 template <int P, typename T, int MODE, typename S = T>
-struct HeadOp {
+struct HeadOp : CellGeo<T, S> {
     static constexpr int n = P + 1, NL = n * n * n;
     static constexpr bool kPlanes = false;
     const T* x;        // APPLY: input; RHS: u_old
@@ -185,13 +205,30 @@ struct HeadOp {
                                          T (&res)[NL]) const {
         const T beta = dt * cvt<T>(ldro(K + c));
         if (MODE == MODE_DIAG) {
+            if (this->geo) {
+                T vol, ih[3];
+                this->geom(c, vol, ih);
+                const T i0 = ih[0] * ih[0], i1 = ih[1] * ih[1], i2 = ih[2] * ih[2];
+#pragma unroll
+                for (int cc = 0; cc < n; ++cc)
+#pragma unroll
+                    for (int b = 0; b < n; ++b)
+#pragma unroll
+                        for (int a = 0; a < n; ++a) {
+                            const T dm = e.dm1[a] * e.dm1[b] * e.dm1[cc];
+                            const T dk = e.dk1[a] * i0 * e.dm1[b] * e.dm1[cc] + e.dm1[a] * e.dk1[b] * i1 * e.dm1[cc] +
+                                         e.dm1[a] * e.dm1[b] * e.dk1[cc] * i2;
+                            res[a + n * (b + n * cc)] = vol * fma(beta, dk, alpha * dm);
+                        }
+                return;
+            }
 #pragma unroll
             for (int l = 0; l < NL; ++l) res[l] = fma(beta, e.dK[l], alpha * e.dM[l]);
             return;
         }
         if (MODE == MODE_APPLY) {
             gather<P, T>(g, x, cx, cy, cz, true, res);
-            fdm(res, beta);
+            fdm(res, beta, c);
             return;
         } else if (!cell_touches_dir(g, cx, cy, cz)) {
             rhs_interior(g, cx, cy, cz, res);
@@ -218,6 +255,12 @@ struct HeadOp {
             sweep<n, 0, false>(us, e.G[0]);
             sweep<n, 1, false>(us, e.G[1]);
             sweep<n, 2, false>(us, e.G[2]);
+            T vol = T(1), i2[3] = {T(1), T(1), T(1)};
+            if (this->geo) {
+                this->geom(c, vol, i2);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) i2[d] = i2[d] * i2[d];
+            }
 #pragma unroll
             for (int c2 = 0; c2 < n; ++c2)
 #pragma unroll
@@ -225,8 +268,9 @@ struct HeadOp {
 #pragma unroll
                     for (int a = 0; a < n; ++a) {
                         const int l = a + n * (b + n * c2);
-                        res[l] = alpha * res[l] -
-                                 beta * (e.Lam[0][a] + e.Lam[1][b] + e.Lam[2][c2]) * us[l];
+                        res[l] = vol * (alpha * res[l] -
+                                        beta * (e.Lam[0][a] * i2[0] + e.Lam[1][b] * i2[1] + e.Lam[2][c2] * i2[2]) *
+                                            us[l]);
                     }
         }
         sweep<n, 2, true>(res, e.G[2]);
@@ -241,20 +285,49 @@ struct HeadOp {
         sweep<n, 0, false>(res, e.G[0]);
         sweep<n, 1, false>(res, e.G[1]);
         sweep<n, 2, false>(res, e.G[2]);
+        T sa = alpha;
+        if (this->geo) {
+            T vol, ih[3];
+            this->geom((long long)cx + (long long)g.ncx * ((long long)cy + (long long)g.ncy * cz), vol, ih);
+            sa = alpha * vol;
+        }
 #pragma unroll
-        for (int l = 0; l < NL; ++l) res[l] *= alpha;
+        for (int l = 0; l < NL; ++l) res[l] *= sa;
         sweep<n, 2, true>(res, e.G[2]);
         sweep<n, 1, true>(res, e.G[1]);
         sweep<n, 0, true>(res, e.G[0]);
     }
 
+    // the scale of mode l of cell c: alpha + beta LS_l (uniform mesh) or
+    // vol (alpha + beta sum_d Lam_d / h_d^2) (graded mesh, unit constants)
+    __device__ __forceinline__ void mode_scales(long long c, const T beta, T (&sl)[NL]) const {
+        if (this->geo) {
+            T vol, ih[3];
+            this->geom(c, vol, ih);
+            const T i0 = ih[0] * ih[0], i1 = ih[1] * ih[1], i2 = ih[2] * ih[2];
+#pragma unroll
+            for (int cc = 0; cc < n; ++cc)
+#pragma unroll
+                for (int b = 0; b < n; ++b)
+#pragma unroll
+                    for (int a = 0; a < n; ++a)
+                        sl[a + n * (b + n * cc)] =
+                            vol * fma(beta, e.Lam[0][a] * i0 + e.Lam[1][b] * i1 + e.Lam[2][cc] * i2, alpha);
+        } else {
+#pragma unroll
+            for (int l = 0; l < NL; ++l) sl[l] = fma(beta, e.LS[l], alpha);
+        }
+    }
+
     // res <- (G^T)^3 diag(alpha + beta (Lx+Ly+Lz)) G^3 res, in place
-    __device__ __forceinline__ void fdm(T (&res)[NL], const T beta) const {
+    __device__ __forceinline__ void fdm(T (&res)[NL], const T beta, long long c) const {
         sweep<n, 0, false>(res, e.G[0]);
         sweep<n, 1, false>(res, e.G[1]);
         sweep<n, 2, false>(res, e.G[2]);
+        T sl[NL];
+        mode_scales(c, beta, sl);
 #pragma unroll
-        for (int l = 0; l < NL; ++l) res[l] *= fma(beta, e.LS[l], alpha);
+        for (int l = 0; l < NL; ++l) res[l] *= sl[l];
         sweep<n, 2, true>(res, e.G[2]);
         sweep<n, 1, true>(res, e.G[1]);
         sweep<n, 0, true>(res, e.G[0]);
@@ -264,7 +337,7 @@ struct HeadOp {
     __device__ __forceinline__ void compute(const T (&u)[NL], long long c, T (&res)[NL]) const {
 #pragma unroll
         for (int l = 0; l < NL; ++l) res[l] = u[l];
-        fdm(res, dt * cvt<T>(ldro(K + c)));
+        fdm(res, dt * cvt<T>(ldro(K + c)), c);
     }
 
     // the same in place (u becomes A_e u), adding u^T A_e u to dot: in the
@@ -275,9 +348,11 @@ struct HeadOp {
         sweep<n, 0, false>(u, e.G[0]);
         sweep<n, 1, false>(u, e.G[1]);
         sweep<n, 2, false>(u, e.G[2]);
+        T sls[NL];
+        mode_scales(c, beta, sls);
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-            const T sl = fma(beta, e.LS[l], alpha);
+            const T sl = sls[l];
             const T v = u[l] * sl;
             dot = fma(v, u[l], dot);
             u[l] = v;
@@ -304,7 +379,7 @@ struct HeadOp {
 };
 
 template <int P, typename T, int MODE, typename S = T>
-struct HeatOp {
+struct HeatOp : CellGeo<T, S> {
     static constexpr int n = P + 1, NL = n * n * n, NQ = n * n * n;
     static constexpr bool kPlanes = true;   // element pass: one thread per Gauss plane
     const T* x;        // APPLY: input; RHS: T_old
@@ -337,13 +412,31 @@ struct HeatOp {
             //   sum_q W c_w N_l (q . grad N_l) = sum_d sum_q f_d(q) M^x_a M^y_b M^z_c
             // with f_d = W q_d / H_d and 1D factors B*D (direction d) or B*B,
             // contracted direction by direction (sum factorisation)
+            T vol = T(1), ih[3] = {e.invH[0], e.invH[1], e.invH[2]};
+            if (this->geo) {
+                this->geom(c, vol, ih);
+                const T i0 = ih[0] * ih[0], i1 = ih[1] * ih[1], i2 = ih[2] * ih[2];
 #pragma unroll
-            for (int l = 0; l < NL; ++l) res[l] = fma(dtlam, e.dK[l], cT * e.dM[l]);
+                for (int cc = 0; cc < n; ++cc)
+#pragma unroll
+                    for (int b = 0; b < n; ++b)
+#pragma unroll
+                        for (int a = 0; a < n; ++a) {
+                            const T dm = e.dm1[a] * e.dm1[b] * e.dm1[cc];
+                            const T dk = e.dk1[a] * i0 * e.dm1[b] * e.dm1[cc] + e.dm1[a] * e.dk1[b] * i1 * e.dm1[cc] +
+                                         e.dm1[a] * e.dm1[b] * e.dk1[cc] * i2;
+                            res[a + n * (b + n * cc)] = vol * fma(dtlam, dk, cT * dm);
+                        }
+            } else {
+#pragma unroll
+                for (int l = 0; l < NL; ++l) res[l] = fma(dtlam, e.dK[l], cT * e.dM[l]);
+            }
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 T f[NQ];
 #pragma unroll
-                for (int qi = 0; qi < NQ; ++qi) f[qi] = dtcw * e.W[qi] * e.invH[d] * cvt<T>(ldro(qs + (d * NQ + qi) * nc + c));
+                for (int qi = 0; qi < NQ; ++qi)
+                    f[qi] = dtcw * (e.W[qi] * vol) * ih[d] * cvt<T>(ldro(qs + (d * NQ + qi) * nc + c));
                 // x: f1[qz][qy][a] = sum_qx Mx[qx][a] f[qz][qy][qx]
                 T f1[NQ];
 #pragma unroll
@@ -421,8 +514,14 @@ struct HeatOp {
         sweep<n, 0, false>(res, e.G[0]);
         sweep<n, 1, false>(res, e.G[1]);
         sweep<n, 2, false>(res, e.G[2]);
+        T sc = cT;
+        if (this->geo) {
+            T vol, ih[3];
+            this->geom(c, vol, ih);
+            sc = cT * vol;
+        }
 #pragma unroll
-        for (int l = 0; l < NL; ++l) res[l] *= cT;
+        for (int l = 0; l < NL; ++l) res[l] *= sc;
         sweep<n, 2, true>(res, e.G[2]);
         sweep<n, 1, true>(res, e.G[1]);
         sweep<n, 0, true>(res, e.G[0]);
@@ -439,6 +538,8 @@ struct HeatOp {
     template <bool HQ = false>
     __device__ __forceinline__ void plane(const T* u, const T* hv, const long long c, const long long nc,
                                           const int qz, T* out) const {
+        T vol = T(1), ih[3] = {e.invH[0], e.invH[1], e.invH[2]};
+        if (this->geo) this->geom(c, vol, ih);
         const T cT = cTc ? cvt<T>(ldro(cTc + c)) : cT_u;
         const T dtlam = dt * (lamc ? cvt<T>(ldro(lamc + c)) : lam_u);
         const T dtcw = dt * cw;
@@ -509,9 +610,9 @@ struct HeatOp {
                     gy = fma(e.B[qx][a], yDB[a], gy);
                     gz = fma(e.B[qx][a], yBD[a], gz);
                 }
-                gx *= e.invH[0];
-                gy *= e.invH[1];
-                gz *= e.invH[2];
+                gx *= ih[0];
+                gy *= ih[1];
+                gz *= ih[2];
                 const int qi = qx + n * (qy + n * qz);
                 T q0, q1, q2;
                 if (HQ) {
@@ -522,20 +623,20 @@ struct HeatOp {
                         hy = fma(e.B[qx][a], hDB[a], hy);
                         hz = fma(e.B[qx][a], hBD[a], hz);
                     }
-                    q0 = mK * (hx * e.invH[0]);
-                    q1 = mK * (hy * e.invH[1]);
-                    q2 = mK * (hz * e.invH[2]);
+                    q0 = mK * (hx * ih[0]);
+                    q1 = mK * (hy * ih[1]);
+                    q2 = mK * (hz * ih[2]);
                 } else {
                     q0 = cvt<T>(ldro(qs + (0 * NQ + qi) * nc + c));
                     q1 = cvt<T>(ldro(qs + (1 * NQ + qi) * nc + c));
                     q2 = cvt<T>(ldro(qs + (2 * NQ + qi) * nc + c));
                 }
-                const T W = e.W[qi];
+                const T W = (e.W[qi] * vol);
                 const T v = W * fma(cT, val, dtcw * (q0 * gx + q1 * gy + q2 * gz));
                 const T f = W * dtlam;
-                const T gxs = f * gx * e.invH[0];
-                const T gys = f * gy * e.invH[1];
-                const T gzs = f * gz * e.invH[2];
+                const T gxs = f * gx * ih[0];
+                const T gys = f * gy * ih[1];
+                const T gzs = f * gz * ih[2];
 #pragma unroll
                 for (int a = 0; a < n; ++a) {
                     t1[a] = fma(e.B[qx][a], v, fma(e.D[qx][a], gxs, t1[a]));
@@ -562,6 +663,8 @@ struct HeatOp {
     __device__ __forceinline__ void core(const T (&um)[NL], const T (&us)[NL], const T sgn,
                                          const T cT, const T dtlam, const T dtcw, const long long c,
                                          const long long nc, T (&res)[NL]) const {
+        T vol = T(1), ih[3] = {e.invH[0], e.invH[1], e.invH[2]};
+        if (this->geo) this->geom(c, vol, ih);
 #pragma unroll
         for (int l = 0; l < NL; ++l) res[l] = T(0);
 #pragma unroll
@@ -612,19 +715,19 @@ struct HeatOp {
                         gy = fma(e.B[qx][a], yDBs[a], gy);
                         gz = fma(e.B[qx][a], yBDs[a], gz);
                     }
-                    gx *= e.invH[0];
-                    gy *= e.invH[1];
-                    gz *= e.invH[2];
+                    gx *= ih[0];
+                    gy *= ih[1];
+                    gz *= ih[2];
                     const int qi = qx + n * (qy + n * qz);
                     const T q0 = cvt<T>(ldro(qs + (0 * NQ + qi) * nc + c));
                     const T q1 = cvt<T>(ldro(qs + (1 * NQ + qi) * nc + c));
                     const T q2 = cvt<T>(ldro(qs + (2 * NQ + qi) * nc + c));
-                    const T W = e.W[qi];
+                    const T W = (e.W[qi] * vol);
                     const T v = W * fma(cT, val, sgn * dtcw * (q0 * gx + q1 * gy + q2 * gz));
                     const T f = sgn * W * dtlam;
-                    const T gxs = f * gx * e.invH[0];
-                    const T gys = f * gy * e.invH[1];
-                    const T gzs = f * gz * e.invH[2];
+                    const T gxs = f * gx * ih[0];
+                    const T gys = f * gy * ih[1];
+                    const T gzs = f * gz * ih[2];
 #pragma unroll
                     for (int a = 0; a < n; ++a) {
                         t1[a] = fma(e.B[qx][a], v, fma(e.D[qx][a], gxs, t1[a]));
@@ -1543,7 +1646,8 @@ __global__ void __launch_bounds__(128) rhs_interior_df_kernel(const Grid g, cons
         sweep<n, 0, false>(u, e.G[0]);
         sweep<n, 1, false>(u, e.G[1]);
         sweep<n, 2, false>(u, e.G[2]);
-        const df64 sc = scale_c ? df_from(ldro(scale_c + c)) : scale_u;
+        df64 sc = scale_c ? df_from(ldro(scale_c + c)) : scale_u;
+        if (g.geo64) sc = sc * df_from(ldro(g.geo64 + c));   // graded mesh: times the cell volume
 #pragma unroll
         for (int l = 0; l < NL; ++l) u[l] = u[l] * sc;
         sweep<n, 2, true>(u, e.G[2]);
@@ -1753,6 +1857,9 @@ __global__ void darcy_qp_kernel(const Grid g, const double* __restrict__ h,
         double u[NL];
         gather<P, double>(g, h, cx, cy, cz, false, u);
         const double Kc = K[c];
+        double ih[3] = {e.invH[0], e.invH[1], e.invH[2]};
+        if (g.geo64)
+            for (int d = 0; d < 3; ++d) ih[d] = g.geo64[(d + 1) * g.nc + c];
         // gradient at the Gauss points by sum factorisation: z, then y, then x
         double zB[NQ], zD[NQ];   // [qz][b][a]
 #pragma unroll
@@ -1794,9 +1901,9 @@ __global__ void darcy_qp_kernel(const Grid g, const double* __restrict__ h,
                         gz = fma(e.B[qx][a], yBD[a], gz);
                     }
                     const int qi = qx + n * (qy + n * qz);
-                    const double q0 = -Kc * gx * e.invH[0];
-                    const double q1 = -Kc * gy * e.invH[1];
-                    const double q2 = -Kc * gz * e.invH[2];
+                    const double q0 = -Kc * gx * ih[0];
+                    const double q1 = -Kc * gy * ih[1];
+                    const double q2 = -Kc * gz * ih[2];
                     qs64[(0 * NQ + qi) * g.nc + c] = q0;
                     qs64[(1 * NQ + qi) * g.nc + c] = q1;
                     qs64[(2 * NQ + qi) * g.nc + c] = q2;
@@ -1832,7 +1939,7 @@ __global__ void cell_flux_kernel(const Grid g, const double* __restrict__ h,
                     const double fc = comp == 2 ? cb.d[c2] : cb.v[c2];
                     s += fa * fb * fc * u[a + n * (b + n * c2)];
                 }
-        out[c] = -K[c] * s * invH;
+        out[c] = -K[c] * s * (g.geo64 ? g.geo64[(comp + 1) * g.nc + c] : invH);
     }
 }
 
@@ -2081,6 +2188,15 @@ const Elem<double>& elem_of<double>(const ht_ctx* c) { return c->e64; }
 template <>
 const Elem<float>& elem_of<float>(const ht_ctx* c) { return c->e32; }
 
+// the per-cell geometry of a graded mesh in the operator's storage type
+template <class Op>
+void set_geo(Op& op, const ht_ctx* c) {
+    using S = std::remove_const_t<std::remove_pointer_t<decltype(op.geo)>>;
+    if constexpr (std::is_same<S, float>::value) op.geo = c->geo32;
+    else op.geo = c->geo64;
+    op.gnc = c->grid.nc;
+}
+
 template <int P, typename T>
 int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal* sc, int first) {
     using Op = HeadOp<P, T, MODE_APPLY>;
@@ -2090,6 +2206,7 @@ int fused_cg_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* Dinv, T* p, Scal*
     op.alpha = (T)c->Ss;
     op.dt = dt;
     op.e = elem_of<T>(c);
+    set_geo(op, c);
     T* E = elem_buffer<T>(c);
     dim3 cgrid, ngrid;
     int zlen, klen;
@@ -2126,6 +2243,7 @@ int fused_bicgstab_iteration_P(ht_ctx* c, T dt, T* x, T* r, const T* rh, T* p, T
     op.lamc = f64 ? (const T*)c->lam64 : (const T*)c->lam32;
     op.cT_u = (T)c->cT_u; op.lam_u = (T)c->lam_u; op.dt = dt; op.cw = (T)c->cw;
     op.e = elem_of<T>(c);
+    set_geo(op, c);
     op.g_nc = g.nc;
     T* E = elem_buffer<T>(c);
     const T* wd = well_dense<T>(c);
@@ -2160,6 +2278,7 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
         op.x = x; op.y = y;
         op.K = f64 ? (const T*)c->K64 : (const T*)c->K32;
         op.alpha = (T)c->Ss; op.dt = dt; op.e = elem_of<T>(c);
+        set_geo(op, c);
         if (use_two_pass<T>(c)) return launch_apply_two_pass<P, T>(c, g, op, x, y, dot_part, n_part, sc);
         return launch_apply_staged<P, T>(c, g, op, x, y, dot_part, n_part, sc);
     }
@@ -2170,6 +2289,7 @@ int apply_P(ht_ctx* c, int field, T dt, const T* x, T* y, double* dot_part, int*
     op.lamc = f64 ? (const T*)c->lam64 : (const T*)c->lam32;
     op.cT_u = (T)c->cT_u; op.lam_u = (T)c->lam_u; op.dt = dt; op.cw = (T)c->cw;
     op.e = elem_of<T>(c);
+    set_geo(op, c);
     op.g_nc = g.nc;
     if (use_two_pass<T>(c)) return launch_apply_two_pass<P, T>(c, g, op, x, y, dot_part, n_part, sc);
     return launch_apply_staged<P, T>(c, g, op, x, y, dot_part, n_part, sc);
@@ -2413,6 +2533,7 @@ static int rhs_P(ht_ctx* c, int field, double dt, const double* u_old, double* b
         HeadOp<P, double, MODE_RHS> op{};
         op.x = u_old; op.gD = c->g[field]; op.F = c->F[field]; op.y = b;
         op.K = c->K64; op.alpha = c->Ss; op.dt = dt; op.e = c->e64;
+        set_geo(op, c);
         if (two_pass) return launch_rhs_two_pass<P>(c, g, op);
         return launch_tile<P, double>(c, g, op, nullptr, nullptr);
     }
@@ -2420,6 +2541,7 @@ static int rhs_P(ht_ctx* c, int field, double dt, const double* u_old, double* b
     op.x = u_old; op.gD = c->g[field]; op.F = c->F[field]; op.y = b;
     op.qs = c->qs64; op.cTc = c->cT64; op.lamc = c->lam64;
     op.cT_u = c->cT_u; op.lam_u = c->lam_u; op.dt = dt; op.cw = c->cw; op.e = c->e64;
+    set_geo(op, c);
     if (two_pass) return launch_rhs_two_pass<P>(c, g, op);
     return launch_tile<P, double>(c, g, op, nullptr, nullptr);
 }
@@ -2446,11 +2568,13 @@ static int diag_P(ht_ctx* c, int field, double dt, double* D) {
     if (field == HT_HEAD) {
         HeadOp<P, double, MODE_DIAG> op{};
         op.y = D; op.K = c->K64; op.alpha = c->Ss; op.dt = dt; op.e = c->e64;
+        set_geo(op, c);
         return launch_tile<P, double>(c, g, op, nullptr, nullptr);
     }
     HeatOp<P, double, MODE_DIAG> op{};
     op.y = D; op.qs = c->qs64; op.cTc = c->cT64; op.lamc = c->lam64;
     op.cT_u = c->cT_u; op.lam_u = c->lam_u; op.dt = dt; op.cw = c->cw; op.e = c->e64;
+    set_geo(op, c);
     return launch_tile<P, double>(c, g, op, nullptr, nullptr);
 }
 
@@ -2460,11 +2584,13 @@ static int diag32_P(ht_ctx* c, int field, float dt, float* D) {
     if (field == HT_HEAD) {
         HeadOp<P, float, MODE_DIAG> op{};
         op.y = D; op.K = c->K32; op.alpha = (float)c->Ss; op.dt = dt; op.e = c->e32;
+        set_geo(op, c);
         return launch_tile<P, float>(c, g, op, nullptr, nullptr);
     }
     HeatOp<P, float, MODE_DIAG> op{};
     op.y = D; op.qs = c->qs32; op.cTc = c->cT32; op.lamc = c->lam32;
     op.cT_u = (float)c->cT_u; op.lam_u = (float)c->lam_u; op.dt = dt; op.cw = (float)c->cw; op.e = c->e32;
+    set_geo(op, c);
     return launch_tile<P, float>(c, g, op, nullptr, nullptr);
 }
 
@@ -2697,7 +2823,7 @@ template <int P>
 static int resid_df_field(ht_ctx* c, int field, double dt, const double* x, const double* b, float* r32,
                           double* part, int* n_part) {
     const Grid g = field_grid(c, field);
-    if (P == 1 && field == HT_TEMP) {
+    if (P == 1 && field == HT_TEMP && !c->graded) {
         // Q1 heat: the cell kernel above, then the node gather of the
         // residual (wells and Dirichlet rows there)
         df64* E = reinterpret_cast<df64*>(elem_buffer<double>(c));
@@ -2722,12 +2848,14 @@ static int resid_df_field(ht_ctx* c, int field, double dt, const double* x, cons
     if (field == HT_HEAD) {
         HeadOp<P, df64, MODE_APPLY, double> op{};
         op.K = c->K64; op.alpha = df_split(c->Ss); op.dt = df_split(dt); op.e = c->edf;
+        set_geo(op, c);
         return resid_df_P<P>(c, g, op, x, b, r32, part, n_part, dt, nullptr);
     }
     HeatOp<P, df64, MODE_APPLY, double> op{};
     op.qs = c->qs64; op.cTc = c->cT64; op.lamc = c->lam64;
     op.cT_u = df_split(c->cT_u); op.lam_u = df_split(c->lam_u); op.dt = df_split(dt); op.cw = df_split(c->cw);
     op.e = c->edf;
+    set_geo(op, c);
     op.g_nc = g.nc;
     return resid_df_P<P>(c, g, op, x, b, r32, part, n_part, dt, c->wdn64);
 }
@@ -2787,7 +2915,10 @@ __global__ void __launch_bounds__(128) darcy_qp_q1_kernel(const Grid g, const do
         interp(dx, gx);
         interp(dy, gy);
         interp(dz, gz);
-        const double sx = -Kc * e.invH[0], sy = -Kc * e.invH[1], sz = -Kc * e.invH[2];
+        double ih[3] = {e.invH[0], e.invH[1], e.invH[2]};
+        if (g.geo64)
+            for (int d = 0; d < 3; ++d) ih[d] = g.geo64[(d + 1) * g.nc + c];
+        const double sx = -Kc * ih[0], sy = -Kc * ih[1], sz = -Kc * ih[2];
 #pragma unroll
         for (int qz = 0; qz < 2; ++qz)
 #pragma unroll

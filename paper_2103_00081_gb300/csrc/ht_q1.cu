@@ -1091,13 +1091,13 @@ int launch_q1_heat_any(ht_ctx* c, const Grid& g, const Q1HeatConst& k, const flo
 }  // namespace
 
 bool q1_cg_available(const ht_ctx* c, int fp32) {
-    return fp32 && c->grid.P == 1 && c->K32 != nullptr &&
+    return fp32 && c->grid.P == 1 && c->K32 != nullptr && !c->graded &&
            (c->opts.apply_variant == HT_APPLY_AUTO || c->opts.apply_variant == HT_APPLY_SINGLE_PASS);
 }
 
 bool q1_bicgstab_available(const ht_ctx* c) {
     const bool percell_ok = (c->cT32 == nullptr) == (c->lam32 == nullptr);
-    return c->grid.P == 1 && c->K32 != nullptr && c->h32 != nullptr && percell_ok && c->n_dint == 0 &&
+    return c->grid.P == 1 && c->K32 != nullptr && c->h32 != nullptr && percell_ok && c->n_dint == 0 && !c->graded &&
            (c->opts.apply_variant == HT_APPLY_AUTO || c->opts.apply_variant == HT_APPLY_SINGLE_PASS);
 }
 

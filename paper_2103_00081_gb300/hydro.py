@@ -94,6 +94,11 @@ class Simulator:
         return self._check(self._lib.ht_set_bc_values(self._h, int(field), int(face), int(typ),
                                                       v.ctypes.data, v.size))
 
+    def set_spacing(self, axis, widths):
+        """Cell widths along one axis of a graded tensor-product mesh."""
+        w = np.ascontiguousarray(widths, dtype=np.float64).reshape(-1)
+        return self._check(self._lib.ht_set_spacing(self._h, int(axis), w.ctypes.data, int(w.size)))
+
     def set_seasonal_face(self, field, face, mean, amp, period, phase=0.0):
         """Dirichlet face whose value is mean + amp sin(2 pi t / period + phase)
         at each step's end time."""
@@ -239,9 +244,10 @@ class Simulator:
 
     @classmethod
     def from_scenario(cls, sc, device=0, stream=None, **solver):
-        if getattr(sc, "spacing", None) is not None:
-            raise ValueError("the library takes uniform cells along each axis; graded spacing is not supported")
         s = cls(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, device=device, stream=stream)
+        if getattr(sc, "spacing", None) is not None:
+            for axis, w in enumerate(sc.spacing):
+                s.set_spacing(axis, w)
         lam, cT, Ss = s.bulk_properties(sc.material)
         s.set_cells(sc.K, sc.lam_cells, sc.cT_cells, sc.lam if sc.lam is not None else lam,
                     sc.cT if sc.cT is not None else cT, sc.material.c_w, sc.Ss if sc.Ss is not None else Ss)

@@ -79,16 +79,3 @@ def test_struct_layouts_match_the_header():
         assert fields(cname) == len(cls._fields_), cname
     assert ctypes.sizeof(_lib.BoxSrc) == 9 * 8 and ctypes.sizeof(_lib.LineSrc) == 8 * 8
 
-
-def test_oracle_only_scenarios_are_refused_by_the_binding():
-    """Graded spacing exists only in the oracle so far: the binding refuses
-    such a scenario before any library call instead of ignoring it."""
-    import numpy as np
-
-    import scenarios as S
-    from paper_2103_00081_gb300 import hydro
-    sc = S.random_small(1, 3, 2, 2, 1)
-    sc.spacing = tuple(S.graded_widths(n, L, 0.5) for n, L in zip((3, 2, 2), sc.extent))
-    with pytest.raises(ValueError):
-        hydro.Simulator.from_scenario(sc)
-    assert np.allclose([w.sum() for w in sc.spacing], sc.extent)
