@@ -287,14 +287,17 @@ def advection_elements(N, G, W, qf: np.ndarray, cw: float) -> np.ndarray:
     return cw * np.einsum("cq,ql,cqm->clm", W, N, qg)
 
 
-def cell_geometry(mesh: Mesh, p: int):
+def cell_geometry(mesh: Mesh, p: int, cells=None):
     """Shape values and per-cell gradients, weights, mass and stiffness
     element matrices: N [q, l] and G, W, Me, Ke for one cell size, or with a
-    leading cell axis on a graded mesh (reference_element of each cell)."""
+    leading cell axis on a graded mesh (reference_element of each cell; of
+    the cells listed in `cells` only, when given)."""
     if mesh.H is not None:
         N, G, W = reference_element(p, mesh.H)
         return N, G, W, element_mass(N, W), element_stiffness(G, W)
     hw = mesh.cell_widths()
+    if cells is not None:
+        hw = hw[np.asarray(cells, dtype=np.int64)]
     # reference_element of a cell of widths (hx, hy, hz): the unit cell's
     # gradients divided by the widths and its weights times the volume
     N, G1, W1 = reference_element(p, (1.0, 1.0, 1.0))
@@ -813,7 +816,14 @@ class RowOracle(_TimeDirichlet):
         self.sc = sc
         m = Mesh(sc.nx, sc.ny, sc.nz, sc.order, sc.origin, sc.extent, getattr(sc, "spacing", None))
         self.mesh = m
-        self.N, self.G, self.W, self.Me, self.Ke = cell_geometry(m, sc.order)
+        # on a graded mesh the element matrices of a cell are formed when a
+        # row first needs them (the same cell_geometry, one cell at a time)
+        self.graded = m.H is None
+        self._geo_cache = {}
+        if self.graded:
+            self.N = cell_geometry(m, sc.order, cells=[0])[0]
+        else:
+            self.N, self.G, self.W, self.Me, self.Ke = cell_geometry(m, sc.order)
         nc = m.n_cells
         self.K = np.asarray(sc.K, dtype=np.float64)
         lam, cT, self.cw, self.Ss = bulk_properties(sc)
@@ -846,16 +856,23 @@ class RowOracle(_TimeDirichlet):
         self.box_w = [box_weights(m, bx) for bx in self.boxes]
 
     # -- element matrices of one cell ------------------------------------------
+    def _geo(self, c):
+        """G, W, Me, Ke of cell c."""
+        if not self.graded:
+            return self.G, self.W, self.Me, self.Ke
+        if c not in self._geo_cache:
+            _, G, W, Me, Ke = cell_geometry(self.mesh, self.mesh.p, cells=[c])
+            self._geo_cache[c] = (G[0], W[0], Me[0], Ke[0])
+        return self._geo_cache[c]
+
     def _advection(self, c, h):
-        G = self.G if self.G.ndim == 3 else self.G[c]
-        W = self.W if self.W.ndim == 1 else self.W[c]
+        G, W, _, _ = self._geo(c)
         qf = -self.K[c] * np.einsum("l,qld->qd", h[self.mesh.conn[c]], G)
         qg = np.einsum("qd,qmd->qm", qf, G)
         return self.cw * np.einsum("q,ql,qm->lm", W, self.N, qg)
 
     def _cell_matrix(self, field, c, dt, h=None, mass_only=False):
-        Me = self.Me if self.Me.ndim == 2 else self.Me[c]
-        Ke = self.Ke if self.Ke.ndim == 2 else self.Ke[c]
+        _, _, Me, Ke = self._geo(c)
         if field == HEAD:
             return self.Ss * Me if mass_only else self.Ss * Me + dt * self.K[c] * Ke
         if mass_only:

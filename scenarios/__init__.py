@@ -452,3 +452,101 @@ def config4(n_problems: int = 64, seed0: int = 1000, n_steps: int = 30,
         out.append(Scenario(f"batch_q1_{nx}x{ny}x{nz}_s{seed0 + i}", nx, ny, nz, 1, (0.0, 0.0, 0.0), extent,
                             K, SAND, bc, piles, np.zeros((0, 7)), h0, T0, 1.0 * DAY, n_steps))
     return out
+
+
+def geometric_widths(first: float, n: int, length: float) -> np.ndarray:
+    """n cell widths growing by a constant ratio from `first`, summing to
+    `length` (the ratio is found by bisection; n * first = length gives
+    uniform cells, and a larger n * first shrinks the cells instead)."""
+    if n == 1:
+        return np.array([float(length)])
+    def total(r):
+        return first * n if abs(r - 1.0) < 1e-14 else first * (r ** n - 1.0) / (r - 1.0)
+    lo, hi = (1.0, 2.0) if first * n <= length else (1e-6, 1.0)
+    while total(hi) < length:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if total(mid) < length:
+            lo = mid
+        else:
+            hi = mid
+    w = first * (0.5 * (lo + hi)) ** np.arange(n)
+    return w * (length / w.sum())
+
+
+# Table 1 (Section 2): the ATES benchmark's material values, shared by all
+# three formations, and its boundary data.
+ATES_TABLE1 = dict(cT=1.2e6, lam=1.2, B_poro=1.0e5, T_top=278.15, T_b=288.15, P0=1.0e5,
+                   Q_b=1.0e-3, c_w=1.0e6, dTdz=0.05)
+
+
+def ates_table1(n_bore: int = 42, n_out: int = 224, nz_aquifer: int = 50, nz_confining: int = 20,
+                radius: float = 20.0, depth: float = 300.0, r_w: float = 0.1,
+                layers=(100.0, 100.0, 100.0), K_aquifer: float = 1.0e-6,
+                K_confining: float = 1.0e-10, n_steps: int = 180, dt: float = DAY,
+                first_dz: float = 1.0) -> Scenario:
+    """Hot-water injection benchmark of Section 2 (Fig. 2, Table 1) on a box
+    mesh: one quarter of the 20 m x 300 m cylinder around the wellbore, cut
+    by its two symmetry planes x = 0 and y = 0 (no-flow, insulated), the
+    wellbore axis on their common edge.
+
+    Formations, bottom to top: basement rock, aquifer, caprock (`layers`, m;
+    the thicknesses are not printed, equal thirds are taken), K = 1e-6 m/s in
+    the aquifer and 1e-10 m/s in the confining layers.  Table 1 gives c_T,
+    lambda, B_poro (S_s = rho_w g / B_poro), c_w, T_top, the geothermal
+    gradient dT, the initial pressure P0 and the wellbore data Q_b and T_b.
+
+    * Wellbore (radius r_w, not printed; 0.1 m taken), over the aquifer:
+      injection flux Q_b through its surface, i.e. Q = Q_b 2 pi r_w b for the
+      whole well and a quarter of it here, as a line source on the axis
+      (`wells`), and temperature T_b on every node within r_w of the axis
+      (`pile_temps`, constant).
+    * Head: hydrostatic initial state from P0 at the top, h = P0/(rho_w g) +
+      z_top everywhere, held on the outer faces x = R and y = R.
+    * Temperature: the geotherm T_top + dT (z_top - z) initially, T_top on
+      the top face, the geothermal flux lambda dT into the bottom face,
+      natural (outflow) conditions on the outer faces.
+    * Cells: n_bore equal cells across [0, r_w] and n_out cells growing
+      geometrically from the same width to R; in z, nz_aquifer equal cells in
+      the aquifer and nz_confining cells in each confining layer growing from
+      `first_dz` at the aquifer.  The defaults keep the cell Peclet number
+      c_w |q| H / lambda at or below 2 everywhere outside the wellbore (|q|
+      <= Q_b r_w / r), so that the plain Galerkin heat operator of Eq. 4 needs
+      no stabilisation.
+
+    180 daily steps give the six months of Section 2."""
+    t = ATES_TABLE1
+    h_b = r_w / n_bore
+    wx = np.concatenate([np.full(n_bore, h_b), geometric_widths(h_b, n_out, radius - r_w)])
+    d_bas, d_aq, d_cap = layers
+    assert abs(d_bas + d_aq + d_cap - depth) < 1e-9 * depth
+    wz = np.concatenate([geometric_widths(first_dz, nz_confining, d_bas)[::-1],
+                         np.full(nz_aquifer, d_aq / nz_aquifer),
+                         geometric_widths(first_dz, nz_confining, d_cap)])
+    nx = ny = wx.size
+    nz = wz.size
+    z_lo, z_hi = d_bas, d_bas + d_aq
+    zc = np.concatenate([[0.0], np.cumsum(wz)])
+    zc = 0.5 * (zc[:-1] + zc[1:])
+    in_aq = (zc > z_lo) & (zc < z_hi)
+    K = np.where(in_aq, K_aquifer, K_confining)[:, None, None] * np.ones((1, ny, nx))
+    K = K.reshape(-1)
+    mat = Material(phi=0.0, lam_s=t["lam"], lam_w=t["lam"], c_s=t["cT"], c_w=t["c_w"],
+                   B_poro=t["B_poro"])
+    Q = t["Q_b"] * 2.0 * math.pi * r_w * d_aq
+    wells = np.array([[0.0, 0.0, z_hi, z_lo, Q / 4.0, t["T_b"], 0.0]])
+    bore = np.array([[0.0, 0.0, z_hi, z_lo, r_w, t["T_b"], 0.0, 365 * DAY, 0.0]])
+    h_top = t["P0"] / (RHO_W * G_ACC) + depth
+    sc = Scenario("ates_table1_q1", nx, ny, nz, 1, (0.0, 0.0, 0.0), (radius, radius, depth),
+                  K, mat, {}, np.zeros((0, 8)), wells, np.zeros(1), np.zeros(1), dt, n_steps)
+    sc.spacing = (wx, wx.copy(), wz)
+    _, _, zn = sc.node_coords()
+    Nx, Ny, Nz = sc.node_dims
+    sc.h0 = np.full(sc.n_nodes, h_top)
+    sc.T0 = np.repeat(t["T_top"] + t["dTdz"] * (depth - zn), Nx * Ny)
+    sc.bc = _bc({1: (DIRICHLET, h_top), 3: (DIRICHLET, h_top)},
+                {5: (DIRICHLET, t["T_top"]), 4: (FLUX, t["lam"] * t["dTdz"])})
+    sc.pile_temps = bore
+    sc.lam, sc.cT = t["lam"], t["cT"]
+    return sc
