@@ -51,6 +51,7 @@ enum { HT_FP64 = 0, HT_MIXED = 1 };
 enum { HT_KRYLOV_BICGSTAB = 0, HT_KRYLOV_GMRES = 1 };
 enum { HT_PREC_JACOBI = 0, HT_PREC_CHEBYSHEV = 1 };
 enum { HT_APPLY_AUTO = 0, HT_APPLY_TILED = 1, HT_APPLY_TWO_PASS = 2, HT_APPLY_SINGLE_PASS = 3 };
+enum { HT_GUESS_PREVIOUS = 0, HT_GUESS_EXTRAPOLATE = 1 };
 
 typedef struct ht_ctx ht_ctx;
 
@@ -122,7 +123,18 @@ typedef struct {
  * replays the fused Krylov iterations of the two-pass variant from a CUDA
  * graph of 8 iterations, captured on the context's stream the first time a
  * solve runs with a given set of vectors, step size and operator scalars;
- * a stream that the caller is capturing is launched to directly instead. */
+ * a stream that the caller is capturing is launched to directly instead.
+ * guess selects the initial guess of each step's two solves (the paper does
+ * not state one; the solution is the same to the tolerance either way):
+ * HT_GUESS_PREVIOUS starts from the field at t^n; HT_GUESS_EXTRAPOLATE (the
+ * default) also forms the Lagrange extrapolation to t^{n+1} through the
+ * fields of the last two or three completed steps (linear after two,
+ * quadratic after three; the step sizes may differ) and starts from
+ * whichever of the two has the smaller relative residual b - A x under the
+ * FP32 operator.  The extrapolation keeps two past fields of each system
+ * (4 vectors of FP64 node values, allocated on the first step that needs
+ * them), also across ht_batch_step; ht_set_state, a failed step and a switch
+ * to HT_GUESS_PREVIOUS forget them. */
 typedef struct {
     double tol;
     int max_iter;
@@ -139,6 +151,7 @@ typedef struct {
     int apply_variant;
     double inner_tol_heat;
     int outer_fp64;
+    int guess;
 } ht_solver_opts;
 
 /* Per-step statistics: Krylov iterations (inner iterations in mixed mode),
@@ -151,8 +164,10 @@ typedef struct {
     double t;
     double ms_loads, ms_head, ms_heat, ms_total;
     int status;
-    int guess_head, guess_heat;          /* 1: the learned initial guess won the gate */
-    double guess_res_head, guess_res_heat; /* relative residual of the chosen guess */
+    int guess_head, guess_heat;          /* initial guess of the solve: 0 the field at t^n,
+                                            1 the learned guess, 2 the extrapolated one */
+    double guess_res_head, guess_res_heat; /* relative residual of the chosen guess (FP32
+                                              operator), -1 when no gate ran */
 } ht_step_stats;
 
 /* Fill *opts with the defaults (tol 1e-10, max_iter 20000, Jacobi, FP64). */
@@ -394,8 +409,9 @@ int ht_unet_train_step(ht_unet* net, const float* x, const float* target, int D,
  * divided by its RMS; the network predicts the next increments
  * (dT / s_T, dh / s_h), and for each field the Krylov solve starts from
  * x^n + s * prediction if its residual (FP32 operator, FP64 right-hand side)
- * is smaller than that of x^n (the gate; the solver still converges to the
- * same tolerance).  With record != 0 the features and targets of every step
+ * is smaller than that of the guess chosen without it (x^n, or the
+ * extrapolated field under HT_GUESS_EXTRAPOLATE) (the gate; the solver still
+ * converges to the same tolerance).  With record != 0 the features and targets of every step
  * are kept for ht_learned_sample, also without a network.  Grid sizes are
  * the node counts rounded up to multiples of 8. */
 int ht_set_learned_guess(ht_ctx* ctx, ht_unet* net, int record);

@@ -20,6 +20,7 @@ HT_KRYLOV_BICGSTAB, HT_KRYLOV_GMRES = 0, 1
 HT_PREC_JACOBI, HT_PREC_CHEBYSHEV = 0, 1
 HT_APPLY_AUTO, HT_APPLY_TILED, HT_APPLY_TWO_PASS, HT_APPLY_SINGLE_PASS = 0, 1, 2, 3
 HT_BATCH_CONCURRENT, HT_BATCH_SHARED_LAUNCHES, HT_BATCH_PERSISTENT = 0, 1, 2
+HT_GUESS_PREVIOUS, HT_GUESS_EXTRAPOLATE = 0, 1
 
 ERROR_NAMES = {0: "HT_OK", -1: "HT_EINVAL", -2: "HT_ENOMEM", -3: "HT_ECUDA", -4: "HT_ENOCONV",
                -5: "HT_EBREAKDOWN", -6: "HT_ETIMEOUT"}
@@ -37,7 +38,7 @@ class SolverOpts(ctypes.Structure):
                 ("cheb_degree", c_int), ("precision", c_int), ("inner_tol", c_double),
                 ("max_outer", c_int), ("check_every", c_int), ("use_graphs", c_int),
                 ("z_chunks", c_int), ("apply_variant", c_int), ("inner_tol_heat", c_double),
-                ("outer_fp64", c_int)]
+                ("outer_fp64", c_int), ("guess", c_int)]
 
 
 class LineSrc(ctypes.Structure):

@@ -846,14 +846,57 @@ int upload_cells(ht_ctx* c, double** d64, float** d32, const double* h, size_t n
 
 int batch_prepare_diag(ht_ctx* c, double dt);
 
+// Initial guess of one system of the step to t1, in c->x on entry (the field
+// at t^n with its Dirichlet values): the extrapolation through the past
+// fields replaces it when its residual under the FP32 operator is smaller.
+// *used becomes 2 and *res that residual when it does; *res is the residual
+// of the previous-step guess otherwise (-1 when no extrapolation was formed).
+static int gate_extrapolated(ht_ctx* c, int field, double dt, double t1, int* used, double* res) {
+    int deg = 0;
+    HT_TRY(guess_extrapolate(c, field, t1, c->z, &deg));
+    if (deg == 0) return HT_OK;
+    double r0 = 0.0, r1 = 0.0;
+    HT_TRY(fast_residual(c, field, dt, c->x, c->b, &r0));
+    HT_TRY(fast_residual(c, field, dt, c->z, c->b, &r1));
+    *res = r0;
+    if (r1 < r0) {
+        HT_CUDA(c, cudaMemcpyAsync(c->x, c->z, (size_t)c->grid.nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        *used = 2;
+        *res = r1;
+    }
+    c->guess_fast[field] = *res;   // the solve's first residual need not be formed in FP32 again
+    return HT_OK;
+}
+
+// the learned guess against whatever c->x holds (ht_set_learned_guess)
+static int gate_learned(ht_ctx* c, int field, double dt, int* used, double* res) {
+    int won = 0;
+    double r = -1.0;
+    HT_TRY(learned_gate(c, field, dt, c->x, c->b, &won, &r));
+    if (won) *used = 1;
+    if (won || *res < 0) *res = r;
+    if (r >= 0) c->guess_fast[field] = *res;
+    return HT_OK;
+}
+
 // first part of a batched step: loads at t + dt, head right-hand side,
 // initial iterate with Dirichlet values, diagonal
 int batch_head_begin(ht_ctx* c, double dt) {
+    // a batched step that ended early left the past fields half rotated
+    if (c->guess_open) c->ghist = 0;
+    c->guess_open = false;
     HT_TRY(finalize_setup(c));
     HT_TRY(launch_loads(c, c->t + dt));
     HT_TRY(launch_rhs(c, HT_HEAD, dt, c->h, c->b));
     HT_CUDA(c, cudaMemcpyAsync(c->x, c->h, (size_t)c->grid.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     HT_TRY(set_dirichlet_values(c, HT_HEAD, c->x));
+    if (c->opts.guess == HT_GUESS_EXTRAPOLATE) {
+        c->guess_open = true;
+        int used = 0;
+        double res = -1.0;
+        HT_TRY(gate_extrapolated(c, HT_HEAD, dt, c->t + dt, &used, &res));
+    }
     return batch_prepare_diag(c, dt);
 }
 
@@ -866,9 +909,13 @@ int batch_head_end_and_heat(ht_ctx* c, double dt, ht_step_stats* st) {
     HT_TRY(launch_rhs(c, HT_TEMP, dt, c->T, c->b));
     HT_CUDA(c, cudaMemcpyAsync(c->x, c->T, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     HT_TRY(set_dirichlet_values(c, HT_TEMP, c->x));
+    st->guess_res_heat = -1.0;
+    if (c->guess_open) HT_TRY(gate_extrapolated(c, HT_TEMP, dt, c->t + dt, &st->guess_heat, &st->guess_res_heat));
     HT_TRY(solve_heat(c, dt, c->x, c->b, &st->iters_heat, &st->outer_heat, &st->res_heat));
     HT_CUDA(c, cudaMemcpyAsync(c->T, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     HT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->guess_open) guess_commit(c, c->t);   // both systems recorded their fields at t^n
+    c->guess_open = false;
     c->t += dt;
     st->t = c->t;
     return HT_OK;
@@ -942,6 +989,7 @@ int ht_default_solver(ht_solver_opts* o) {
     o->max_outer = 30;
     o->check_every = 8;
     o->use_graphs = 1;
+    o->guess = HT_GUESS_EXTRAPOLATE;
     return HT_OK;
 }
 
@@ -1068,6 +1116,7 @@ void ht_destroy(ht_ctx* c) {
     if (c->scal_host) cudaFreeHost(c->scal_host);
     for (auto& e : c->ev_pool) cudaEventDestroy(e);
     learned_free(c);
+    guess_free(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -1232,6 +1281,8 @@ int ht_set_state(ht_ctx* c, const double* h, const double* T, double t, int on_d
     if (h) HT_TRY(copy_in(c, c->h, h, n, on_device));
     if (T) HT_TRY(copy_in(c, c->T, T, n, on_device));
     c->t = t;
+    c->ghist = 0;   // the extrapolated guess starts afresh from the new state
+    c->guess_open = false;
     return HT_OK;
 }
 
@@ -1312,9 +1363,13 @@ int ht_set_solver(ht_ctx* c, const ht_solver_opts* o) {
         return fail(c, HT_EINVAL, "inner tolerances must be in [0, 1)");
     if (o->apply_variant < HT_APPLY_AUTO || o->apply_variant > HT_APPLY_SINGLE_PASS)
         return fail(c, HT_EINVAL, "unknown apply variant %d", o->apply_variant);
+    if (o->guess != HT_GUESS_PREVIOUS && o->guess != HT_GUESS_EXTRAPOLATE)
+        return fail(c, HT_EINVAL, "unknown initial guess %d", o->guess);
+    if (o->guess != HT_GUESS_EXTRAPOLATE) c->ghist = 0;   // past fields are kept only while extrapolating
     c->opts = *o;
     return HT_OK;
 }
+
 
 int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
     if (!c) return HT_EINVAL;
@@ -1336,7 +1391,12 @@ int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
     if (rc == HT_OK && cudaMemcpyAsync(c->x, c->h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
         rc = fail(c, HT_ECUDA, "copy failed");
     if (rc == HT_OK) rc = set_dirichlet_values(c, HT_HEAD, c->x);
-    if (rc == HT_OK) rc = learned_gate(c, HT_HEAD, dt, c->x, c->b, &s.guess_head, &s.guess_res_head);
+    s.guess_res_head = s.guess_res_heat = -1.0;
+    if (c->guess_open) c->ghist = 0;   // a batched step that ended early
+    c->guess_open = false;
+    const bool extrap = c->opts.guess == HT_GUESS_EXTRAPOLATE;
+    if (rc == HT_OK && extrap) rc = gate_extrapolated(c, HT_HEAD, dt, t1, &s.guess_head, &s.guess_res_head);
+    if (rc == HT_OK) rc = gate_learned(c, HT_HEAD, dt, &s.guess_head, &s.guess_res_head);
     if (rc == HT_OK) rc = solve_head(c, dt, c->x, c->b, &s.iters_head, &s.outer_head, &s.res_head);
     int rc_head = rc;
     if (rc == HT_OK || rc == HT_ENOCONV)
@@ -1350,7 +1410,8 @@ int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
         if (rc == HT_OK && cudaMemcpyAsync(c->x, c->T, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
             rc = fail(c, HT_ECUDA, "copy failed");
         if (rc == HT_OK) rc = set_dirichlet_values(c, HT_TEMP, c->x);
-        if (rc == HT_OK) rc = learned_gate(c, HT_TEMP, dt, c->x, c->b, &s.guess_heat, &s.guess_res_heat);
+        if (rc == HT_OK && extrap) rc = gate_extrapolated(c, HT_TEMP, dt, t1, &s.guess_heat, &s.guess_res_heat);
+        if (rc == HT_OK) rc = gate_learned(c, HT_TEMP, dt, &s.guess_heat, &s.guess_res_heat);
         if (rc == HT_OK) rc = solve_heat(c, dt, c->x, c->b, &s.iters_heat, &s.outer_heat, &s.res_heat);
         if (rc == HT_OK || rc == HT_ENOCONV)
             if (cudaMemcpyAsync(c->T, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
@@ -1370,6 +1431,12 @@ int ht_step(ht_ctx* c, double dt, ht_step_stats* st) {
     cudaEventElapsedTime(&ms, ev[2], ev[3]); s.ms_heat = ms;
     cudaEventElapsedTime(&ms, ev[0], ev[3]); s.ms_total = ms;
     for (auto& e : ev) cudaEventDestroy(e);
+    // the past fields of the extrapolated guess: both systems recorded their
+    // state at t^n; a step that failed anywhere forgets them
+    if (extrap) {
+        if (rc == HT_OK) guess_commit(c, c->t);
+        else c->ghist = 0;
+    }
     if (rc == HT_OK || rc == HT_ENOCONV) c->t = t1;
     s.t = c->t;
     s.status = rc;

@@ -209,6 +209,15 @@ struct ht_ctx {
     ht_solver_opts opts{};
     std::string err;
 
+    // initial guesses extrapolated in time (HT_GUESS_EXTRAPOLATE): the fields
+    // of the last completed steps, gpast[field][k] at time gtime[k] (k = 0 the
+    // step before the current state), ghist of them valid (0..2)
+    double* gpast[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    double gtime[2] = {0.0, 0.0};
+    int ghist = 0;
+    bool guess_open = false;            // a batched step has rotated the head's past fields
+    double guess_fast[2] = {-1.0, -1.0};   // FP32-operator residual of the guess in x (-1: unknown)
+
     // learned warm start
     ht_unet* net = nullptr;
     int learn_record = 0;
@@ -392,5 +401,13 @@ int true_residual(ht_ctx* c, int field, double dt, const double* x, const double
 // exact Dirichlet rows): a cheap ranking of initial guesses
 int fast_residual(ht_ctx* c, int field, double dt, const double* x, const double* b, double* rel);
 int set_dirichlet_values(ht_ctx* c, int field, double* x);
+// the extrapolated initial guess of a step to t1 (HT_GUESS_EXTRAPOLATE): when
+// past fields are kept, forms their Lagrange extrapolation with the current
+// field into z (Dirichlet values set) and reports its degree in *deg (0: none
+// formed); in any case records the current field as the newest past one.
+// The caller commits the new history with guess_commit after the step.
+int guess_extrapolate(ht_ctx* c, int field, double t1, double* z, int* deg);
+void guess_commit(ht_ctx* c, double t_prev);
+void guess_free(ht_ctx* c);
 
 }  // namespace ht

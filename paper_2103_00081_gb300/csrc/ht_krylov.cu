@@ -1271,6 +1271,11 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
     const double tol = c->opts.tol;
     const int max_iter = c->opts.max_iter;
     const char* what = field == HT_HEAD ? "head solve" : "heat solve";
+    // the FP32-operator residual of the initial guess, when a guess gate has
+    // formed it already (consumed here; it only lets the mixed form skip
+    // forming that residual again)
+    const double known_fast = c->guess_fast[field];
+    c->guess_fast[field] = -1.0;
     HT_TRY(prepare_diag(c, field, dt));
     *iters = 0;
     *outer = 0;
@@ -1318,10 +1323,14 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
     const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 30;
     Vecs32 w{c->d32, c->r32, c->p32, c->q32, c->D32, c->rh32, c->v32, c->s32, c->t32, c->ph32, c->sh32};
     int total = 0;
-    // The first outer residual only seeds the first correction, which the
-    // inner tolerance limits to about 1e-4 relative anyway, so it is formed
-    // with the FP32 operator; every later residual, and any residual that
-    // ends the loop, is formed with the accurate (float-float or FP64) one.
+    // The first outer residual only seeds the first correction, so it is
+    // formed with the FP32 operator while that is accurate enough: its
+    // rounding noise is about 1e-7 of ||b||, and the correction it seeds must
+    // not solve for noise above the inner tolerance.  A guess whose residual
+    // is below 1e-6 / inner_tol of ||b|| (a good previous or extrapolated
+    // field) has its first residual formed again with the accurate operator.
+    // Every later residual, and any residual that ends the loop, is formed
+    // with the accurate (float-float or FP64) one.
     auto outer_residual = [&](bool fast, int* np) -> int {
         *np = G;
         if (fast) {
@@ -1342,12 +1351,16 @@ int solve_field(ht_ctx* c, int field, double dt, double* x, const double* b, int
         HT_CUDA(c, cudaGetLastError());
         return sync_scal(c, 2);
     };
+    const double floor_rel = 1e-6 / inner_tol;
     for (int k = 0; k <= max_outer; ++k) {
         int np = G;
-        const bool fast = k == 0;
+        const bool fast = k == 0 && !(known_fast >= 0 && known_fast < floor_rel);
         HT_TRY(outer_residual(fast, &np));
-        if (fast && c->scal_host[2].rr <= tol * tol * c->scal_host[2].bb)
-            HT_TRY(outer_residual(false, &np));   // confirm convergence accurately
+        if (fast) {
+            const Scal f = c->scal_host[2];
+            if (f.rr <= tol * tol * f.bb || f.rr < floor_rel * floor_rel * f.bb)
+                HT_TRY(outer_residual(false, &np));   // confirm convergence, or seed accurately
+        }
         const Scal s = c->scal_host[2];
         if (!isfinite(s.rr)) return fail(c, HT_EINVAL, "%s: non-finite residual", what);
         *res = s.bb > 0 ? sqrt(s.rr / s.bb) : 0.0;
@@ -1447,6 +1460,70 @@ int set_dirichlet_values(ht_ctx* c, int field, double* x) {
     dirichlet_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>(g, c->g[field], x); ++c->n_launch;
     HT_CUDA(c, cudaGetLastError());
     return HT_OK;
+}
+
+// z = w0 y0 + w1 y1 + w2 y2 over the first `deg` + 1 terms, then y2 = y0
+// (the buffer of the oldest past field takes the current one)
+static __global__ void extrap_kernel(long long n, const double* __restrict__ y0, const double* __restrict__ y1,
+                                     double* __restrict__ y2, int deg, double w0, double w1, double w2,
+                                     double* __restrict__ z) {
+    GRID_LOOP(i, n) {
+        const double a = y0[i];
+        double v = w0 * a;
+        if (deg >= 1) v += w1 * y1[i];
+        if (deg >= 2) v += w2 * y2[i];
+        if (z) z[i] = v;
+        y2[i] = a;
+    }
+}
+
+int guess_extrapolate(ht_ctx* c, int field, double t1, double* z, int* deg) {
+    *deg = 0;
+    const size_t n = (size_t)c->grid.nn;
+    for (double*& p : c->gpast[field])
+        if (!p && cudaMalloc(&p, n * sizeof(double)) != cudaSuccess) {
+            c->ghist = 0;
+            return fail(c, HT_ENOMEM, "extrapolated guess: allocation failed");
+        }
+    // Lagrange weights at t1 through (t^n, y0), (gtime[0], y1), (gtime[1], y2);
+    // the times must be distinct and decreasing, else fewer points are used
+    const double tn = c->t, ta = c->gtime[0], tb = c->gtime[1];
+    int d = c->ghist;
+    if (d >= 2 && !(ta > tb)) d = 1;
+    if (d >= 1 && !(tn > ta)) d = 0;
+    double w[3] = {1.0, 0.0, 0.0};
+    if (d == 1) {
+        w[0] = (t1 - ta) / (tn - ta);
+        w[1] = (t1 - tn) / (ta - tn);
+    } else if (d == 2) {
+        w[0] = (t1 - ta) * (t1 - tb) / ((tn - ta) * (tn - tb));
+        w[1] = (t1 - tn) * (t1 - tb) / ((ta - tn) * (ta - tb));
+        w[2] = (t1 - tn) * (t1 - ta) / ((tb - tn) * (tb - ta));
+    }
+    double* y0 = field == HT_HEAD ? c->h : c->T;
+    extrap_kernel<<<vec_grid(c), kVecThreads, 0, c->stream>>>((long long)n, y0, c->gpast[field][0], c->gpast[field][1],
+                                                              d, w[0], w[1], w[2], d > 0 ? z : nullptr);
+    ++c->n_launch;
+    HT_CUDA(c, cudaGetLastError());
+    std::swap(c->gpast[field][0], c->gpast[field][1]);   // the newest past field is y0
+    if (d > 0) HT_TRY(set_dirichlet_values(c, field, z));
+    *deg = d;
+    return HT_OK;
+}
+
+void guess_commit(ht_ctx* c, double t_prev) {
+    c->gtime[1] = c->gtime[0];
+    c->gtime[0] = t_prev;
+    c->ghist = std::min(c->ghist + 1, 2);
+}
+
+void guess_free(ht_ctx* c) {
+    for (auto& f : c->gpast)
+        for (double*& p : f) {
+            if (p) cudaFree(p);
+            p = nullptr;
+        }
+    c->ghist = 0;
 }
 
 int solve_head(ht_ctx* c, double dt, double* x, const double* b, int* iters, int* outer, double* res) {

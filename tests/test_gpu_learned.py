@@ -19,7 +19,8 @@ def test_learned_guess_trains_and_cuts_iterations(built_lib, mixed):
     pytest.importorskip("torch")
     from paper_2103_00081_gb300 import _lib as L
     from paper_2103_00081_gb300 import hydro, learned
-    opts = dict(tol=1e-10, precision=L.HT_MIXED if mixed else L.HT_FP64)
+    # against the previous-step guess, the fallback the learned guess replaces
+    opts = dict(tol=1e-10, precision=L.HT_MIXED if mixed else L.HT_FP64, guess=L.HT_GUESS_PREVIOUS)
     train_sc = _scenario(11)
     sim = hydro.Simulator.from_scenario(train_sc, **opts)
     samples = learned.collect_samples(sim, train_sc.dt, 40)
@@ -39,7 +40,7 @@ def test_learned_guess_trains_and_cuts_iterations(built_lib, mixed):
             st = s.step(test_sc.dt)
             if k >= 3:
                 its += st["iters_head"] + st["iters_heat"]
-                wins += st["guess_head"] + st["guess_heat"]
+                wins += (st["guess_head"] == 1) + (st["guess_heat"] == 1)
         runs[use] = (its, wins, s.get_field(S.HEAD), s.get_field(S.TEMP))
         s.close()
     its0, _, h0, T0 = runs[False]
