@@ -18,6 +18,8 @@ def test_algorithmic_bytes_per_node():
     # Q2 fused CG: the apply (x, y, K per cell) plus 24 B per node of CG vectors;
     # 32.5 B per node when a cell holds eight nodes
     assert bench.cg_bytes(2, 8000, 1000) / 8000 == 32.5
+    # a graded mesh runs the fused two-pass iteration and reads 16 B of geometry per cell
+    assert bench.cg_bytes(1, nn, nc, graded=True) == 4.0 * (2 * nn + nc) + 24.0 * nn + 16.0 * nc
     # operator apply: x read, y written, K once per cell
     assert bench.apply_bytes_per_node(2, False) == 17.0
     assert bench.apply_bytes_per_node(1, True) == 12.0
@@ -86,3 +88,16 @@ def test_cpu_baseline_reports_rate_fit_and_spmv_bandwidth():
     n = cb["nodes_samples"]
     assert cb["s_per_step_full_extrapolated"] == pytest.approx(
         cb["s_per_step_samples"][1] * (sc_full.n_nodes / n[1]) ** cb["exponent"])
+
+
+def test_ates_workload_and_its_oracle_samples():
+    """The ATES benchmark workload is the generator's default mesh, and the
+    oracle arm times coarser meshes of the same problem (graded in the same
+    way, ascending in size)."""
+    sc = bench.workload("ates_table1")
+    assert (sc.nx, sc.ny, sc.nz, sc.n_nodes) == (266, 266, 90, 6487299)
+    samples = bench.oracle_samples("ates_table1", sc)
+    assert len(samples) == 2 and samples[0].n_nodes < samples[1].n_nodes < sc.n_nodes
+    for s in samples:
+        assert s.spacing is not None and s.name == sc.name
+        assert s.pile_temps.shape == (1, 9) and s.wells.shape == (1, 7)
