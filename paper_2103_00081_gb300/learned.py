@@ -3,7 +3,8 @@
 The network (include/ht.h, ht_unet_*) predicts the next step's increments of
 temperature and head from the last two increments of both fields, the Darcy
 flux and the heat sources; the solver gates the prediction against the
-previous-step initial guess (ht_set_learned_guess).
+initial guess it would take without it: the field at t^n, or its
+extrapolation in time (ht_set_learned_guess, HT_GUESS_EXTRAPOLATE).
 Samples come from trajectories the simulator itself generates
 (ht_learned_sample); all arithmetic runs in the library's kernels and torch
 only provides device buffers.
