@@ -20,6 +20,9 @@ def test_algorithmic_bytes_per_node():
     assert bench.cg_bytes(2, 8000, 1000) / 8000 == 32.5
     # a graded mesh runs the fused two-pass iteration and reads 16 B of geometry per cell
     assert bench.cg_bytes(1, nn, nc, graded=True) == 4.0 * (2 * nn + nc) + 24.0 * nn + 16.0 * nc
+    # FP64 heat apply: x read, y written, three velocity components at each Gauss point
+    assert bench.heat_apply_bytes(1, nn, nc) == 16.0 * nn + 24.0 * 8 * nc
+    assert bench.heat_apply_bytes(2, 8000, 1000) == 16.0 * 8000 + 24.0 * 27 * 1000
     # operator apply: x read, y written, K once per cell
     assert bench.apply_bytes_per_node(2, False) == 17.0
     assert bench.apply_bytes_per_node(1, True) == 12.0
