@@ -606,6 +606,46 @@ def time_oracle_sample(sc, steps):
     return (time.perf_counter() - t0) / steps, o
 
 
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _oracle_replica(payload):
+    """One oracle replica (a child process): seconds of its second step on
+    the sample scenario."""
+    sc, solver = payload
+    from oracle import fem
+    o = fem.OracleSim(sc, solver=solver, tol=1e-10)
+    o.step(sc.dt)
+    t0 = time.perf_counter()
+    o.step(sc.dt)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(sc, n_procs=None, timeout_s=240.0):
+    """The oracle on every host core at once: one independent single-threaded
+    replica of the sample per core (spawned processes), each timing one step
+    while all run.  Returns (cores, slowest replica's seconds per step);
+    raises on a failure or after timeout_s (the pool is then terminated)."""
+    import multiprocessing as mp
+    n = n_procs or os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in THREAD_VARS}
+    for k in THREAD_VARS:
+        os.environ[k] = "1"
+    # by module name, so that the children find it also when this file runs as __main__
+    import importlib
+    fn = importlib.import_module("bench")._oracle_replica
+    try:
+        with mp.get_context("spawn").Pool(n) as pool:
+            times = pool.map_async(fn, [(sc, oracle_solver(sc))] * n).get(timeout_s)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return n, max(times)
+
+
 def cpu_baseline(sc_full, wl, steps=1):
     """The oracle timed on two coarser samples of the workload; the cost per
     step is extrapolated to the full mesh with the power law in node count
@@ -629,7 +669,22 @@ def cpu_baseline(sc_full, wl, steps=1):
                        + " on assembled CSR (scipy, one thread); "
                        f"extrapolated to {sc_full.n_nodes} nodes by the fitted law s/step ~ nodes^{k:.2f}"),
             "s_per_step_samples": t, "nodes_samples": n, "exponent": k, "s_per_step_full_extrapolated": s_full,
-            "host": cpu_info(), "spmv": oracle_spmv_rate(o, samples[-1])}
+            "host": cpu_info(), "spmv": oracle_spmv_rate(o, samples[-1]),
+            "all_cores": all_cores_figure(sc_full, samples[-1], k)}
+
+
+def all_cores_figure(sc_full, sample, k):
+    """Aggregate oracle throughput with every host core busy: independent
+    replicas (the oracle does not parallelise one run), each extrapolated to
+    the full mesh by the single-core law; a failure is recorded, not raised."""
+    try:
+        cores, s_rep = oracle_all_cores(sample)
+    except Exception as e:   # noqa: BLE001 -- the baseline must not stop the benchmark
+        return {"error": f"{type(e).__name__}: {str(e)[:160]}"}
+    s_full = s_rep * (sc_full.n_nodes / sample.n_nodes) ** k
+    return {"value": cores * (sc_full.dt / YEAR) / (s_full / 3600.0), "unit": UNIT, "cores": cores,
+            "kind": "oracle replicas, one per core (aggregate throughput; one run is no faster)",
+            "s_per_step_sample_under_load": s_rep}
 
 
 def oracle_spmv_rate(o, sc, reps=5):

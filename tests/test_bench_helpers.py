@@ -104,3 +104,11 @@ def test_ates_workload_and_its_oracle_samples():
     for s in samples:
         assert s.spacing is not None and s.name == sc.name
         assert s.pile_temps.shape == (1, 9) and s.wells.shape == (1, 7)
+
+
+def test_oracle_replicas_on_several_cores():
+    """The all-core figure of the CPU baseline: spawned single-threaded
+    oracle replicas each time one step of the sample."""
+    import scenarios as S
+    cores, s = bench.oracle_all_cores(S.config5(nx=16, ny=16, nz=3), n_procs=2, timeout_s=120.0)
+    assert cores == 2 and 0.0 < s < 60.0
