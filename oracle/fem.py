@@ -32,14 +32,17 @@ Parity pins (tests/test_oracle_pins.py) tie this code to closed forms: the 1D
 Q1/Q2 mass and stiffness matrices, exact symbolic integrals on one cell,
 discrete eigenmode decay, exactness for linear heads, energy balance, the
 erfc and Ogata-Banks 1D solutions, manufactured-solution convergence
-orders, and the moments of the box-source and per-node face loads.
+orders, and the moments of the box-source and per-node face loads.  On the
+ATES benchmark of Section 2 (tests/test_ates_benchmark.py) the head follows
+Thiem's steady logarithm and Theis' transient well function.
 
 Meshes are uniform along each axis, or graded with tensor-product cell
 widths (the fine-near-the-piles meshes of Section 3.3, Fig. 10b); a graded
 mesh takes every geometric quantity per cell.
 
 RowOracle evaluates the same definitions row by row (cell by cell over the
-cells holding a node) for meshes too large to assemble; it is pinned to the
+cells holding a node) for meshes too large to assemble, forming a graded
+cell's element matrices when a row first needs them; it is pinned to the
 assembled form at every row of small meshes.
 """
 from __future__ import annotations
